@@ -1,0 +1,467 @@
+/*
+ * lbhpde_oracle.c -- plain FP64 CPU oracle of the LBGK model for
+ *     phi_t + sum_{k=1..m} alpha_k d_x^k Pi_k(phi) = 0,   m <= 6
+ * (Shi, He, Guo, "Lattice Boltzmann Model for High-Order Nonlinear Partial
+ * Differential Equations", arXiv:0907.1720).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness yardstick for the
+ * CUDA library.  Only tests/, __graft_entry__.smoke() and bench.py (its CPU
+ * baseline leg and its reference arm) may load it.  It shares no code, header,
+ * table or helper with the GPU path, and the GPU path never calls it.
+ *
+ * Everything is IEEE double precision, evaluated in the order the paper writes
+ * it.  Build with -ffp-contract=off so that no multiply-add is fused.
+ *
+ * Steps, in the paper's order:
+ *   (1) tau_2..tau_6 from the relaxation time tau                Eq. (taus)
+ *   (2) beta_k = alpha_k / (dt^{k-1} tau_k)                       Eqs. (NPDE3)-(NPDE6)
+ *   (3) A_40, A_50, A_60                                          Eqs. (Pi4), (Pi5), (Pi6), (A40)-(A60)
+ *   (4) auxiliary moments Pi_20..Pi_60 as integrals over phi      Sec. II C-F, Eqs. (Pi4)-(Pi6)
+ *   (5) scaled moments Pibar_0..Pibar_{b-1}                       Sec. III A/B
+ *   (6) EDF written out component by component                   Eqs. (EDF5), (EDF7)
+ *   (7) LBGK collide, then stream                                 Eq. (LBE)
+ *   (8) global relative error E                                   Sec. IV
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   - integration constants of the auxiliary-moment integrals are zero, i.e.
+ *     Pi_k0(phi) = integral from 0 to phi;
+ *   - alpha_1 != 1 is folded into Pi_1 (the paper fixes alpha_1 = 1);
+ *   - beta_k = 0 when alpha_k = 0 or Pi_k = 0 (Remark 2), and for m < k < b;
+ *   - A_40, A_50, A_60 are applied as printed, whatever Pi_2..Pi_4 are; the
+ *     model flags "inexact recovery" when the remarks' preconditions fail;
+ *   - scheme 2 sets the highest moment Pibar_{b-1} to zero (Sec. IV, before
+ *     Examples 4.5 and 4.8);
+ *   - f is initialised to f^eq(phi_0);
+ *   - the grid is periodic with N nodes.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_NC 64 /* capacity of a polynomial: degree < OR_NC */
+
+/* A polynomial in phi: p(phi) = sum_{i<n} c[i] phi^i. */
+typedef struct {
+    int n;
+    double c[OR_NC];
+} opoly;
+
+typedef struct {
+    int b;        /* number of lattice velocities: 5 or 7                  */
+    int m;        /* order of the NPDE                                      */
+    int scheme;   /* 1: all b moments; 2: Pibar_{b-1} = 0                   */
+    int inexact;  /* 1 if a remark's precondition for exact recovery fails */
+    double dx, dt, c, tau;
+    double tk[7];    /* tk[k] = tau_k, k = 2..6                             */
+    double alpha[7]; /* alpha[k], k = 1..6                                  */
+    double beta[7];  /* beta[k],  k = 2..6                                  */
+    double A40, A50, A60;
+    opoly Pi[7];     /* Pi[k] = Pi_k(phi), k = 1..6 (alpha_1 folded in)    */
+    opoly Pi0[7];    /* Pi0[k] = Pi_k0(phi), k = 2..6                       */
+} oracle_model;
+
+/* ---------------------------------------------------------------- polys */
+
+static void op_zero(opoly *p) { memset(p, 0, sizeof(*p)); }
+
+static int op_is_zero(const opoly *p)
+{
+    for (int i = 0; i < p->n; i++)
+        if (p->c[i] != 0.0) return 0;
+    return 1;
+}
+
+/* dst += s * src */
+static int op_axpy(opoly *dst, double s, const opoly *src)
+{
+    if (src->n > OR_NC) return -1;
+    for (int i = 0; i < src->n; i++) dst->c[i] += s * src->c[i];
+    if (src->n > dst->n) dst->n = src->n;
+    return 0;
+}
+
+/* r = a * b */
+static int op_mul(opoly *r, const opoly *a, const opoly *b)
+{
+    opoly t;
+    op_zero(&t);
+    if (a->n == 0 || b->n == 0) { *r = t; return 0; }
+    if (a->n + b->n - 1 > OR_NC) return -1;
+    t.n = a->n + b->n - 1;
+    for (int i = 0; i < a->n; i++)
+        for (int j = 0; j < b->n; j++) t.c[i + j] += a->c[i] * b->c[j];
+    *r = t;
+    return 0;
+}
+
+/* r = a^k, k >= 0 */
+static int op_pow(opoly *r, const opoly *a, int k)
+{
+    opoly t;
+    op_zero(&t);
+    t.n = 1;
+    t.c[0] = 1.0;
+    for (int i = 0; i < k; i++)
+        if (op_mul(&t, &t, a)) return -1;
+    *r = t;
+    return 0;
+}
+
+/* r = d/dphi a */
+static void op_deriv(opoly *r, const opoly *a)
+{
+    opoly t;
+    op_zero(&t);
+    for (int i = 1; i < a->n; i++) t.c[i - 1] = (double)i * a->c[i];
+    t.n = a->n > 1 ? a->n - 1 : 0;
+    *r = t;
+}
+
+/* r = integral_0^phi a(s) ds  (zero integration constant) */
+static int op_integ(opoly *r, const opoly *a)
+{
+    opoly t;
+    op_zero(&t);
+    if (a->n + 1 > OR_NC) return -1;
+    for (int i = 0; i < a->n; i++) t.c[i + 1] = a->c[i] / (double)(i + 1);
+    t.n = a->n + 1;
+    *r = t;
+    return 0;
+}
+
+/* Plain power-sum evaluation: sum_i c[i] * phi^i, phi^i by repeated products. */
+static double op_eval(const opoly *p, double phi)
+{
+    double s = 0.0, pw = 1.0;
+    for (int i = 0; i < p->n; i++) {
+        s += p->c[i] * pw;
+        pw *= phi;
+    }
+    return s;
+}
+
+/* --------------------------------------------------------------- setup */
+
+/* Step (1): Eq. (taus), the coefficients that the Taylor expansion of the
+ * LBGK equation attaches to D^k f (Sec. II B). */
+static void oracle_taus(double tau, double tk[7])
+{
+    double t2 = tau * tau, t3 = t2 * tau, t4 = t3 * tau, t5 = t4 * tau;
+    tk[0] = 0.0;
+    tk[1] = 1.0;
+    tk[2] = -tau + 0.5;
+    tk[3] = t2 - tau + 1.0 / 6.0;
+    tk[4] = -t3 + 1.5 * t2 - 7.0 / 12.0 * tau + 1.0 / 24.0;
+    tk[5] = t4 - 2.0 * t3 + 1.25 * t2 - 0.25 * tau + 1.0 / 120.0;
+    tk[6] = -t5 + 2.5 * t4 - 13.0 / 6.0 * t3 + 0.75 * t2 - 31.0 / 360.0 * tau + 1.0 / 720.0;
+}
+
+/* Return codes shared with the Python wrapper. */
+enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_TAU_SINGULAR = 2, OR_ERR_DEGREE = 3 };
+
+static int singular(double x) { return fabs(x) < 1e-13; }
+
+/*
+ * Build the model.  pi_coef is [m][ncoef] row-major: Pi_k(phi) =
+ * sum_p pi_coef[(k-1)*ncoef + p] phi^p.  lattice: 0 = auto (5 for m <= 4, else 7).
+ */
+int oracle_model_init(oracle_model *M, int m, const double *alpha, const double *pi_coef,
+                      int ncoef, double dx, double dt, double tau, int lattice, int scheme)
+{
+    memset(M, 0, sizeof(*M));
+    if (m < 1 || m > 6 || ncoef < 1 || ncoef > 16) return OR_ERR_ARG;
+    if (!(dx > 0.0) || !(dt > 0.0) || !(tau > 0.0) || !isfinite(dx) || !isfinite(dt) ||
+        !isfinite(tau))
+        return OR_ERR_ARG;
+    if (lattice == 0) lattice = (m <= 4) ? 5 : 7;
+    if (lattice != 5 && lattice != 7) return OR_ERR_ARG;
+    if (m > lattice - 1) return OR_ERR_ARG;          /* Sec. III: b >= m + 1 */
+    if (scheme != 1 && scheme != 2) return OR_ERR_ARG;
+    if (scheme == 2 && m >= lattice - 1) return OR_ERR_ARG; /* top moment needed */
+    M->b = lattice;
+    M->m = m;
+    M->scheme = scheme;
+    M->dx = dx;
+    M->dt = dt;
+    M->c = dx / dt;
+    M->tau = tau;
+
+    for (int k = 1; k <= m; k++) {
+        M->alpha[k] = alpha[k - 1];
+        op_zero(&M->Pi[k]);
+        M->Pi[k].n = ncoef;
+        for (int p = 0; p < ncoef; p++) M->Pi[k].c[p] = pi_coef[(k - 1) * ncoef + p];
+    }
+    /* alpha_1 is 1 in Eq. (NPDE); any other value is folded into Pi_1. */
+    for (int p = 0; p < ncoef; p++) M->Pi[1].c[p] *= M->alpha[1];
+    M->alpha[1] = 1.0;
+    for (int k = m + 1; k <= 6; k++) op_zero(&M->Pi[k]);
+
+    /* (1) */
+    oracle_taus(tau, M->tk);
+
+    /* (2) alpha_k = dt^{k-1} tau_k beta_k, Eqs. (NPDE3)-(NPDE6); beta_k = 0 when
+     * the term is absent (Remark 2). */
+    for (int k = 2; k <= 6; k++) {
+        M->beta[k] = 0.0;
+        if (k > m) continue;
+        if (M->alpha[k] == 0.0 || op_is_zero(&M->Pi[k])) continue;
+        if (singular(M->tk[k])) return OR_ERR_TAU_SINGULAR;
+        M->beta[k] = M->alpha[k] / (pow(dt, (double)(k - 1)) * M->tk[k]);
+    }
+    double t2 = M->tk[2], t3 = M->tk[3], t4 = M->tk[4], t5 = M->tk[5], t6 = M->tk[6];
+    double b2 = M->beta[2], b3 = M->beta[3], b4 = M->beta[4];
+
+    /* (3) The A_k0 corrections, Eqs. (Pi4), (Pi5), (Pi6) and (A40)-(A60).  A moment
+     * that the lattice does not carry needs no correction. */
+    M->A40 = M->A50 = M->A60 = 0.0;
+    if (M->b - 1 >= 4 && b2 != 0.0) {
+        if (singular(t4)) return OR_ERR_TAU_SINGULAR;
+        M->A40 = t2 * (3.0 * t3 - t2 * t2) * b2 * b2 / t4;
+    }
+    if (M->b - 1 >= 5 && b2 != 0.0 && b3 != 0.0) {
+        if (singular(t5)) return OR_ERR_TAU_SINGULAR;
+        M->A50 = (4.0 * t2 * t4 + 3.0 * t3 * t3 - 2.0 * t2 * t2 * t3) * b2 * b3 / t5;
+    }
+    if (M->b - 1 >= 6 && (b2 != 0.0 || b3 != 0.0)) {
+        if (singular(t6)) return OR_ERR_TAU_SINGULAR;
+        M->A60 = ((5.0 * t2 * t5 + 3.0 * t3 * t4 - 2.0 * t2 * t2 * t4) * b2 * b4 +
+                  (4.0 * t4 - t2 * t3) * t3 * b3 * b3 + (t2 * t3 - 6.0 * t4) * t2 * t2 * b2 * b2 * b2) /
+                 t6;
+    }
+
+    /* Preconditions of exact recovery, for the terms that are present: Pi_2 = phi for
+     * A_40 (Sec. II D), Pi_2 = Pi_3 = phi for A_50 (Sec. II E), Pi_2 = Pi_3 = Pi_4 = phi
+     * for A_60 (Sec. II F), and alpha_2 = 0 on D1Q7 (Remark 5). */
+    {
+        opoly phi1;
+        op_zero(&phi1);
+        phi1.n = 2;
+        phi1.c[1] = 1.0;
+        int is_phi[7] = {0};
+        for (int k = 2; k <= 6; k++) {
+            opoly d = M->Pi[k];
+            op_axpy(&d, -1.0, &phi1);
+            is_phi[k] = op_is_zero(&d);
+        }
+        if (M->b - 1 >= 4 && b2 != 0.0 && !is_phi[2]) M->inexact = 1;
+        if (M->b - 1 >= 5 && b2 != 0.0 && b3 != 0.0 && !(is_phi[2] && is_phi[3])) M->inexact = 1;
+        if (M->b - 1 >= 6) {
+            if (b3 != 0.0 && !is_phi[3]) M->inexact = 1;
+            if (b2 != 0.0 && b4 != 0.0 && !(is_phi[2] && is_phi[4])) M->inexact = 1;
+        }
+        if (M->b == 7 && b2 != 0.0) M->inexact = 1; /* Remark 5 */
+    }
+
+    /* (4) Auxiliary moments, each written as the paper prints its integrand. */
+    opoly d1, d2, d3, d4, d5; /* Pi_k' */
+    op_deriv(&d1, &M->Pi[1]);
+    op_deriv(&d2, &M->Pi[2]);
+    op_deriv(&d3, &M->Pi[3]);
+    op_deriv(&d4, &M->Pi[4]);
+    op_deriv(&d5, &M->Pi[5]);
+    opoly p1[7]; /* (Pi_1')^k */
+    for (int k = 0; k <= 6; k++)
+        if (op_pow(&p1[k], &d1, k)) return OR_ERR_DEGREE;
+    opoly one;
+    op_zero(&one);
+    one.n = 1;
+    one.c[0] = 1.0;
+    opoly g, t;
+    for (int k = 2; k <= 6; k++) op_zero(&M->Pi0[k]);
+
+    /* Pi_20 = int (Pi_1')^2 dphi                                      Sec. II C */
+    g = p1[2];
+    if (op_integ(&M->Pi0[2], &g)) return OR_ERR_DEGREE;
+
+    /* Pi_30 = int [ (Pi_1')^3 + 3 beta_2 Pi_2' Pi_1' ] dphi              Sec. II C */
+    g = p1[3];
+    if (op_mul(&t, &d2, &p1[1]) || op_axpy(&g, 3.0 * b2, &t)) return OR_ERR_DEGREE;
+    if (op_integ(&M->Pi0[3], &g)) return OR_ERR_DEGREE;
+
+    /* Pi_40 = int [ (Pi_1')^4 + 6 beta_2 Pi_2' (Pi_1')^2
+     *             + 4 beta_3 Pi_3' Pi_1' + A_40 ] dphi                   Eq. (Pi4) */
+    g = p1[4];
+    if (op_mul(&t, &d2, &p1[2]) || op_axpy(&g, 6.0 * b2, &t)) return OR_ERR_DEGREE;
+    if (op_mul(&t, &d3, &p1[1]) || op_axpy(&g, 4.0 * b3, &t)) return OR_ERR_DEGREE;
+    op_axpy(&g, M->A40, &one);
+    if (op_integ(&M->Pi0[4], &g)) return OR_ERR_DEGREE;
+
+    /* Pi_50 = int [ (Pi_1')^5 + 10 beta_2 Pi_2' (Pi_1')^3 + 10 beta_3 Pi_3' (Pi_1')^2
+     *             + 5 beta_4 Pi_4' Pi_1' + A_50 ] dphi                   Eq. (Pi5) */
+    g = p1[5];
+    if (op_mul(&t, &d2, &p1[3]) || op_axpy(&g, 10.0 * b2, &t)) return OR_ERR_DEGREE;
+    if (op_mul(&t, &d3, &p1[2]) || op_axpy(&g, 10.0 * b3, &t)) return OR_ERR_DEGREE;
+    if (op_mul(&t, &d4, &p1[1]) || op_axpy(&g, 5.0 * b4, &t)) return OR_ERR_DEGREE;
+    op_axpy(&g, M->A50, &one);
+    if (op_integ(&M->Pi0[5], &g)) return OR_ERR_DEGREE;
+
+    /* Pi_60 = int [ (Pi_1')^6 + 15 beta_2 Pi_2' (Pi_1')^4 + 20 beta_3 Pi_3' (Pi_1')^3
+     *             + 15 beta_4 Pi_4' (Pi_1')^2 + 6 beta_5 Pi_5' Pi_1' + A_60 ] dphi
+     *                                                                    Eq. (Pi6) */
+    g = p1[6];
+    if (op_mul(&t, &d2, &p1[4]) || op_axpy(&g, 15.0 * b2, &t)) return OR_ERR_DEGREE;
+    if (op_mul(&t, &d3, &p1[3]) || op_axpy(&g, 20.0 * b3, &t)) return OR_ERR_DEGREE;
+    if (op_mul(&t, &d4, &p1[2]) || op_axpy(&g, 15.0 * b4, &t)) return OR_ERR_DEGREE;
+    if (op_mul(&t, &d5, &p1[1]) || op_axpy(&g, 6.0 * M->beta[5], &t)) return OR_ERR_DEGREE;
+    op_axpy(&g, M->A60, &one);
+    if (op_integ(&M->Pi0[6], &g)) return OR_ERR_DEGREE;
+
+    return OR_OK;
+}
+
+/* (5) The scaled moments of Sec. III A (D1Q5) and III B (D1Q7):
+ *   Pibar_0 = phi, Pibar_1 = Pi_1 / c, Pibar_k = (Pi_k0 + beta_k Pi_k) / c^k. */
+void oracle_moments(const oracle_model *M, double phi, double *pibar)
+{
+    pibar[0] = phi;
+    pibar[1] = op_eval(&M->Pi[1], phi) / M->c;
+    for (int k = 2; k < M->b; k++) {
+        double ck = pow(M->c, (double)k);
+        pibar[k] = (op_eval(&M->Pi0[k], phi) + M->beta[k] * op_eval(&M->Pi[k], phi)) / ck;
+    }
+    if (M->scheme == 2) pibar[M->b - 1] = 0.0;
+}
+
+/* (6) The EDFs, Eq. (EDF5) with e = {0, 1, -1, 2, -2} and Eq. (EDF7) with
+ * e = {0, 1, -1, 2, -2, 3, -3}, from the scaled moments. */
+void oracle_edf(int b, const double *P, double *feq)
+{
+    if (b == 5) {
+        feq[0] = (4.0 * P[0] - 5.0 * P[2] + P[4]) / 4.0;
+        feq[1] = (4.0 * (P[1] + P[2]) - P[3] - P[4]) / 6.0;
+        feq[2] = (4.0 * (-P[1] + P[2]) + P[3] - P[4]) / 6.0;
+        feq[3] = (-2.0 * (P[1] - P[3]) - P[2] + P[4]) / 24.0;
+        feq[4] = (2.0 * (P[1] - P[3]) - P[2] + P[4]) / 24.0;
+    } else {
+        feq[0] = (36.0 * P[0] - 49.0 * P[2] + 14.0 * P[4] - P[6]) / 36.0;
+        feq[1] = (36.0 * (P[1] + P[2]) - 13.0 * (P[3] + P[4]) + P[5] + P[6]) / 48.0;
+        feq[2] = (36.0 * (-P[1] + P[2]) + 13.0 * (P[3] - P[4]) - P[5] + P[6]) / 48.0;
+        feq[3] = (-18.0 * P[1] - 9.0 * P[2] + 20.0 * P[3] + 10.0 * P[4] - 2.0 * P[5] - P[6]) / 120.0;
+        feq[4] = (18.0 * P[1] - 9.0 * P[2] - 20.0 * P[3] + 10.0 * P[4] + 2.0 * P[5] - P[6]) / 120.0;
+        feq[5] = (12.0 * P[1] + 4.0 * P[2] - 15.0 * P[3] - 5.0 * P[4] + 3.0 * P[5] + P[6]) / 720.0;
+        feq[6] = (-12.0 * P[1] + 4.0 * P[2] + 15.0 * P[3] - 5.0 * P[4] - 3.0 * P[5] + P[6]) / 720.0;
+    }
+}
+
+void oracle_feq(const oracle_model *M, double phi, double *feq)
+{
+    double P[7];
+    oracle_moments(M, phi, P);
+    oracle_edf(M->b, P, feq);
+}
+
+/* d f^eq_j / d phi, from the exact derivatives of the moment polynomials; used by
+ * the linear (Fourier) analysis in the tests. */
+void oracle_dfeq(const oracle_model *M, double phi, double *dfeq)
+{
+    double P[7];
+    opoly d;
+    P[0] = 1.0;
+    op_deriv(&d, &M->Pi[1]);
+    P[1] = op_eval(&d, phi) / M->c;
+    for (int k = 2; k < M->b; k++) {
+        opoly s = M->Pi0[k];
+        op_axpy(&s, M->beta[k], &M->Pi[k]);
+        op_deriv(&d, &s);
+        P[k] = op_eval(&d, phi) / pow(M->c, (double)k);
+    }
+    if (M->scheme == 2) P[M->b - 1] = 0.0;
+    oracle_edf(M->b, P, dfeq);
+}
+
+/* The lattice velocities in units of c (Sec. III A, III B). */
+static const int E7[7] = {0, 1, -1, 2, -2, 3, -3};
+
+/* (7) initial state: f_j(x, 0) = f^eq_j(phi_0(x)).  f is [b][N] row-major. */
+void oracle_init(const oracle_model *M, long N, const double *phi0, double *f)
+{
+    double feq[7];
+    for (long i = 0; i < N; i++) {
+        oracle_feq(M, phi0[i], feq);
+        for (int j = 0; j < M->b; j++) f[(long)j * N + i] = feq[j];
+    }
+}
+
+/* (7) nsteps of Eq. (LBE) on a periodic grid: collide at every node, then move
+ * each post-collision f_j to node i + e_j (mod N).  tmp has the size of f. */
+void oracle_step(const oracle_model *M, long N, double *f, double *tmp, long nsteps)
+{
+    const int b = M->b;
+    const double tau = M->tau;
+    double feq[7];
+    for (long n = 0; n < nsteps; n++) {
+        for (long i = 0; i < N; i++) {
+            double phi = 0.0;
+            for (int j = 0; j < b; j++) phi += f[(long)j * N + i];
+            oracle_feq(M, phi, feq);
+            for (int j = 0; j < b; j++) {
+                double fj = f[(long)j * N + i];
+                double fstar = fj - (fj - feq[j]) / tau;
+                long dst = ((i + E7[j]) % N + N) % N;
+                tmp[(long)j * N + dst] = fstar;
+            }
+        }
+        memcpy(f, tmp, sizeof(double) * (size_t)b * (size_t)N);
+    }
+}
+
+/* phi(x) = sum_j f_j(x)  (first constraint of Eq. (moments)) */
+void oracle_phi(const oracle_model *M, long N, const double *f, double *phi)
+{
+    for (long i = 0; i < N; i++) {
+        double s = 0.0;
+        for (int j = 0; j < M->b; j++) s += f[(long)j * N + i];
+        phi[i] = s;
+    }
+}
+
+/* (8) E = sum |phi - phi*| / sum |phi*|  (Sec. IV) */
+double oracle_error_E(long N, const double *phi, const double *phistar)
+{
+    double num = 0.0, den = 0.0;
+    for (long i = 0; i < N; i++) {
+        num += fabs(phi[i] - phistar[i]);
+        den += fabs(phistar[i]);
+    }
+    return num / den;
+}
+
+/* One-call driver: phi0 -> phi after nsteps.  Returns an oracle_model_init code. */
+int oracle_run(int m, const double *alpha, const double *pi_coef, int ncoef, double dx, double dt,
+               double tau, int lattice, int scheme, long N, const double *phi0, long nsteps,
+               double *phi_out)
+{
+    oracle_model *M = (oracle_model *)malloc(sizeof(oracle_model));
+    if (!M) return OR_ERR_ARG;
+    int rc = oracle_model_init(M, m, alpha, pi_coef, ncoef, dx, dt, tau, lattice, scheme);
+    if (rc != OR_OK) { free(M); return rc; }
+    double *f = (double *)malloc(sizeof(double) * (size_t)M->b * (size_t)N);
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)M->b * (size_t)N);
+    if (!f || !tmp) { free(f); free(tmp); free(M); return OR_ERR_ARG; }
+    oracle_init(M, N, phi0, f);
+    oracle_step(M, N, f, tmp, nsteps);
+    oracle_phi(M, N, f, phi_out);
+    free(f);
+    free(tmp);
+    free(M);
+    return OR_OK;
+}
+
+/* Accessors for the Python wrapper (the struct layout stays private to C). */
+size_t oracle_model_size(void) { return sizeof(oracle_model); }
+int oracle_model_b(const oracle_model *M) { return M->b; }
+int oracle_model_inexact(const oracle_model *M) { return M->inexact; }
+void oracle_model_params(const oracle_model *M, double *tk, double *beta, double *A)
+{
+    for (int k = 0; k < 7; k++) { tk[k] = M->tk[k]; beta[k] = M->beta[k]; }
+    A[0] = M->A40;
+    A[1] = M->A50;
+    A[2] = M->A60;
+}
+/* Value of Pi_k0(phi), k = 2..6 (0 for other k). */
+double oracle_aux_moment(const oracle_model *M, int k, double phi)
+{
+    if (k < 2 || k > 6) return 0.0;
+    return op_eval(&M->Pi0[k], phi);
+}
