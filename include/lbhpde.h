@@ -1,0 +1,203 @@
+/*
+ * lbhpde.h -- C ABI of a GB300 (sm_103a) lattice Boltzmann solver for
+ *
+ *     phi_t + sum_{k=1..m} alpha_k d_x^k Pi_k(phi) = 0,     1 <= m <= 6,
+ *
+ * the general LBGK model of B. Shi, N. He, Z. Guo, "Lattice Boltzmann Model for
+ * High-Order Nonlinear Partial Differential Equations", arXiv:0907.1720
+ * (Eq. (NPDE), Sec. II A).
+ *
+ * Conventions for every function below:
+ *   - Return value: an LBHPDE_* status code (0 = success).  No function aborts or
+ *     prints; lbhpde_strerror() turns a code into text.
+ *   - Host pointers are owned by the caller and are only read or written during
+ *     the call (inputs are copied).  Device memory that a handle needs is
+ *     allocated by the library through the allocator given at creation (or
+ *     cudaMalloc when none is given) and released by the matching destroy call.
+ *   - Distribution arrays live in HBM as structure-of-arrays rows of length ld
+ *     (ld >= N, a multiple of 32 elements): row 0 holds phi, rows 1..b-1 hold
+ *     the post-collision populations f*_j, j = 1..b-1, of the velocities
+ *     e = {1,-1,2,-2[,3,-3]} (Sec. III A/B).  The rest population is implied by
+ *     sum_j f*_j = phi, which collision preserves (first relation of Eq. (moments)).
+ *   - Work is enqueued on the handle's CUDA stream; calls that return data to the
+ *     host synchronise that stream.  A handle may be used by one host thread at
+ *     a time; the server (lbhpde_server_*) is internally synchronised.
+ *   - Grids are periodic (LBHPDE_PERIODIC); the paper's non-equilibrium
+ *     extrapolation boundary (Sec. IV) is not provided.
+ */
+#ifndef LBHPDE_H
+#define LBHPDE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define LBHPDE_OK 0
+#define LBHPDE_ERR_ARG 1          /* invalid argument (sizes, orders, lattice, pointers) */
+#define LBHPDE_ERR_TAU_SINGULAR 2 /* tau_k = 0 for a needed k: beta_k or A_k0 undefined  */
+#define LBHPDE_ERR_OOM 3          /* device allocation failed / over the memory budget   */
+#define LBHPDE_ERR_DIVERGED 4     /* a non-finite phi was found                          */
+#define LBHPDE_PENDING 5          /* request accepted but not finished (lbhpde_poll)     */
+#define LBHPDE_ERR_TIMEOUT 6      /* a bounded wait ran out                              */
+#define LBHPDE_ERR_CUDA 7         /* a CUDA runtime call failed                          */
+#define LBHPDE_ERR_NOT_FOUND 8    /* unknown request id                                  */
+#define LBHPDE_ERR_UNSUPPORTED 9  /* valid request this build does not handle            */
+
+/* -------------------------------------------------------------- enumerations */
+#define LBHPDE_FP64 0      /* populations and arithmetic in IEEE double                   */
+#define LBHPDE_FP32_DEV 1  /* float populations stored as deviations from the rest         */
+                           /* equilibrium (phi kept apart), float arithmetic               */
+#define LBHPDE_PERIODIC 0
+
+#define LBHPDE_PI_ZERO 0   /* Pi_k = 0                         */
+#define LBHPDE_PI_PHI 1    /* Pi_k = phi                       */
+#define LBHPDE_PI_POWER 2  /* Pi_k = phi^power, 1 <= power <= 7 */
+#define LBHPDE_PI_POLY 3   /* Pi_k = sum_p coef[p] phi^p        */
+#define LBHPDE_PI_NCOEF 8
+#define LBHPDE_MAX_DEG 31  /* highest degree of f^eq_j(phi) the kernels accept */
+
+#define LBHPDE_KERNEL_AUTO 0    /* choose per instance                                     */
+#define LBHPDE_KERNEL_STREAM 1  /* one fused collide+stream launch per step through HBM    */
+#define LBHPDE_KERNEL_ONCHIP 2  /* whole instance resident on one SM for many steps        */
+
+/* One flux function Pi_k of Eq. (NPDE): the paper requires "known differential
+ * functions of phi"; this library takes polynomials in phi (every worked class of
+ * Sec. III C is of that form). */
+typedef struct {
+    int kind;                        /* LBHPDE_PI_*                       */
+    int power;                       /* for LBHPDE_PI_POWER               */
+    double coef[LBHPDE_PI_NCOEF];    /* for LBHPDE_PI_POLY: coef[p] phi^p */
+} lbhpde_pi;
+
+/* The model the library derives from an equation (Secs. II and III): step a0 of the
+ * hot path.  P_j(phi) = sum_p coef[j][p] phi^p equals omega * f^eq_j(phi) with
+ * omega = 1/tau; feq[j][p] are the unscaled coefficients of f^eq_j.  Row j follows
+ * the velocity order e = {0,1,-1,2,-2,3,-3}. */
+typedef struct {
+    int b;                 /* lattice velocities: 5 (D1Q5) or 7 (D1Q7)                    */
+    int m;                 /* order of the equation                                        */
+    int scheme;            /* 1 = all b moments, 2 = highest moment set to zero (Sec. IV) */
+    int D;                 /* degree of the f^eq_j polynomials                             */
+    int inexact;           /* 1 if a precondition of exact recovery fails (Remarks 2, 4, 5)*/
+    double c;              /* lattice speed dx/dt                                          */
+    double omega;          /* 1/tau                                                         */
+    double tk[7];          /* tau_k, k = 2..6, Eq. (taus)                                   */
+    double beta[7];        /* beta_k, k = 2..6: alpha_k = dt^{k-1} tau_k beta_k             */
+    double A[3];           /* A_40, A_50, A_60, Eqs. (Pi4)-(Pi6)                            */
+    double feq[7][LBHPDE_MAX_DEG + 1];
+    double coef[7][LBHPDE_MAX_DEG + 1];
+} lbhpde_model_info;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a
+ * device pointer with at least 256-byte alignment or NULL; release frees it. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*release)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} lbhpde_allocator;
+
+/* ------------------------------------------------------------------ step a0 */
+
+/* Build the model of Secs. II-III on the host (no GPU is touched):
+ * tau_k (Eq. (taus)), beta_k (Eqs. (NPDE3)-(NPDE6)), A_40/A_50/A_60 (Eqs. (Pi4)-(Pi6)),
+ * the auxiliary moments Pi_k0 = int_0^phi [...] dphi (Sec. II C-F, integration constant
+ * zero), the scaled moments Pibar_k = (Pi_k0 + beta_k Pi_k)/c^k (Sec. III A/B) and
+ * f^eq = M^-1 Pibar (Eqs. (EDF5), (EDF7)), folded into polynomial coefficients.
+ *   m          order, 1..6; m <= b-1
+ *   alpha      [m], alpha[k-1] = alpha_k; alpha[0] scales Pi_1 (the paper fixes alpha_1 = 1)
+ *   pi         [m], Pi_1..Pi_m
+ *   dx, dt     lattice spacing and time step (> 0, finite); c = dx/dt
+ *   tau        dimensionless relaxation time (> 0)
+ *   lattice    0 = auto (5 for m <= 4, else 7), 5 or 7
+ *   scheme     1 or 2 (scheme 2 needs m < b-1)
+ * Errors: LBHPDE_ERR_ARG, LBHPDE_ERR_TAU_SINGULAR (tau_k = 0 where beta_k or A_k0 needs it). */
+int lbhpde_model(int m, const double *alpha, const lbhpde_pi *pi, double dx, double dt, double tau,
+                 int lattice, int scheme, lbhpde_model_info *out);
+
+/* --------------------------------------------------------- single instance */
+
+typedef struct lbhpde_ctx *lbhpde_t;
+
+/* Create one periodic instance of N nodes (N >= 2 * max|e_j|, i.e. 4 on D1Q5 and 6 on
+ * D1Q7).  precision is LBHPDE_FP64 or LBHPDE_FP32_DEV; boundary must be LBHPDE_PERIODIC.
+ * cuda_stream is a cudaStream_t (NULL = the legacy default stream); alloc may be NULL.
+ * The state is undefined until lbhpde_set_phi. */
+int lbhpde_create(lbhpde_t *out, int m, const double *alpha, const lbhpde_pi *pi, long N, double dx,
+                  double dt, double tau, int lattice, int scheme, int precision, int boundary,
+                  void *cuda_stream, const lbhpde_allocator *alloc);
+
+/* Step a1: f_j(x, 0) = f^eq_j(phi0(x)) (the paper sets initial conditions from the
+ * analytic solution, Sec. IV; equilibrium initial populations are this library's reading).
+ * phi0 is [N] doubles in host memory (phi0_on_device = 0) or device memory (= 1). */
+int lbhpde_set_phi(lbhpde_t h, const double *phi0, int phi0_on_device);
+
+/* Steps a2-a6, nsteps times: stream (pull form), phi = sum_j f_j, f^eq_j(phi), BGK relaxation
+ * f*_j = f_j - (f_j - f^eq_j)/tau (Eq. (LBE)).  Asynchronous on the handle's stream. */
+int lbhpde_step(lbhpde_t h, long nsteps);
+
+/* Step a7: copy phi (t = steps taken * dt) into phi_out ([N] doubles, host or device).
+ * Host output synchronises.  Returns LBHPDE_ERR_DIVERGED (after copying) if phi has a
+ * non-finite value. */
+int lbhpde_read_phi(lbhpde_t h, double *phi_out, int out_on_device);
+
+/* Diagnostics of step a7, reduced on the GPU in double precision. */
+typedef struct {
+    double sum_phi;     /* sum_x phi: invariant on periodic grids                        */
+    double max_abs_phi;
+    long nonfinite;     /* nodes whose phi is NaN or Inf                                  */
+    double err_E;       /* sum|phi - phi*| / sum|phi*| (Sec. IV), when phi* is given     */
+    double err_L2;      /* ||phi - phi*||_2 / ||phi*||_2, when phi* is given             */
+    long steps;         /* time steps taken since lbhpde_set_phi                         */
+} lbhpde_diag;
+
+/* phistar: [N] doubles in device memory, or NULL.  Synchronises the stream. */
+int lbhpde_diagnostics(lbhpde_t h, const double *phistar_device, lbhpde_diag *out);
+
+/* Which kernel lbhpde_step uses (LBHPDE_KERNEL_*), and for the on-chip kernel the nodes per
+ * thread and the steps per launch (0 = automatic).  Returns LBHPDE_ERR_UNSUPPORTED when the
+ * instance does not fit the requested kernel. */
+int lbhpde_set_kernel(lbhpde_t h, int kernel, int nodes_per_thread, int steps_per_launch);
+
+int lbhpde_get_model(lbhpde_t h, lbhpde_model_info *out);
+int lbhpde_destroy(lbhpde_t h);
+const char *lbhpde_strerror(int code);
+
+/* ------------------------------------------------------------------ batches */
+
+/* One member of a batch (the same arguments as lbhpde_create). */
+typedef struct {
+    int m;
+    double alpha[6];
+    lbhpde_pi pi[6];
+    long N;
+    double dx, dt, tau;
+    int lattice, scheme;
+} lbhpde_instance;
+
+typedef struct lbhpde_batch_s *lbhpde_batch_t;
+
+/* Many independent periodic instances of one precision, stepped together: the on-chip
+ * kernel packs whole instances onto CTAs (one launch advances all of them); instances too
+ * long for one SM use the streaming kernel.  Members may mix lattices, orders and sizes. */
+int lbhpde_batch_create(lbhpde_batch_t *out, int count, const lbhpde_instance *members, int precision,
+                        void *cuda_stream, const lbhpde_allocator *alloc);
+/* phi0: the members' initial profiles concatenated ([sum N] doubles, host or device). */
+int lbhpde_batch_set_phi(lbhpde_batch_t b, const double *phi0, int phi0_on_device);
+int lbhpde_batch_step(lbhpde_batch_t b, long nsteps);
+/* phi_out: [sum N] doubles, host or device.  LBHPDE_ERR_DIVERGED if any phi is non-finite. */
+int lbhpde_batch_read_phi(lbhpde_batch_t b, double *phi_out, int out_on_device);
+/* out: [count] records.  phistar: [sum N] doubles in device memory, or NULL. */
+int lbhpde_batch_diagnostics(lbhpde_batch_t b, const double *phistar_device, lbhpde_diag *out);
+int lbhpde_batch_set_kernel(lbhpde_batch_t b, int kernel, int nodes_per_thread, int steps_per_launch);
+/* Total node count (sum N) and device bytes held. */
+int lbhpde_batch_size(lbhpde_batch_t b, long *total_nodes, size_t *device_bytes);
+int lbhpde_batch_destroy(lbhpde_batch_t b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBHPDE_H */

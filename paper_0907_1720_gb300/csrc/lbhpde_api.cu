@@ -1,0 +1,658 @@
+// C ABI of the solver: batches of periodic instances (and the single-instance handle as a
+// batch of one).  Host planning (arena layout, block maps, CTA packing), kernel launches,
+// readout and diagnostics.  See include/lbhpde.h for the contract of each entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbhpde.h"
+#include "lbhpde_kernels.cuh"
+
+using lbk::DiagPart;
+using lbk::OnchipInst;
+using lbk::Seg;
+
+namespace {
+
+constexpr int kChunk = 1024;          // nodes per block of the node-parallel kernels
+constexpr int kStreamThreads = 256;   // k_stream: 256 threads x 4 nodes = kChunk
+constexpr int kStreamNPT = kChunk / kStreamThreads;
+constexpr int kGenericThreads = 256;  // init / readout / diagnostics
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) {                              \
+            (void)cudaGetLastError();                         \
+            return LBHPDE_ERR_CUDA;                           \
+        }                                                     \
+    } while (0)
+
+#define RC(call)                    \
+    do {                            \
+        int r_ = (call);            \
+        if (r_ != LBHPDE_OK) return r_; \
+    } while (0)
+
+// One kernel group: the instances of one lattice (the kernels are compiled per b).
+struct Group {
+    int b = 0;
+    std::vector<int> members;     // batch indices
+    int maxD = 0;
+    // node-parallel block map (segment, first node), kChunk nodes per block
+    std::vector<int2> blocks_h;
+    int2 *blocks = nullptr;
+    long long *blk_off = nullptr;  // per block: offset of its member in a concatenated phi array
+    // on-chip plan
+    bool onchip_ok = false;
+    int K = 0, maxt = 0, nthreads = 0, max_inst = 0, ncta = 0;
+    size_t smem = 0;
+    OnchipInst *insts = nullptr;
+    int *cta_first = nullptr;
+};
+
+}  // namespace
+
+struct lbhpde_batch_s {
+    int precision = LBHPDE_FP64;
+    size_t esz = 8;
+    int count = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool has_alloc = false;
+    lbhpde_allocator alloc{};
+    std::vector<lbhpde_model_info> mi;
+    std::vector<long long> N;
+    std::vector<long long> phi_off;  // prefix sums of N: concatenated host/device phi arrays
+    long long total = 0;
+    std::vector<Seg> segs_h;
+    Seg *segs = nullptr;
+    void *st[2] = {nullptr, nullptr};
+    size_t st_bytes = 0;
+    int cur = 0;
+    void *coefT = nullptr;  // coefficient arena in the state type
+    double *coefD = nullptr;  // the same in double (initialisation)
+    long long *phi_off_d = nullptr;  // per block of the combined map: offset into a concatenated array
+    std::vector<int2> all_blocks_h;  // combined block map over all members (segment order)
+    std::vector<int> part_first_h;
+    int2 *all_blocks = nullptr;
+    long long *blk_off = nullptr;
+    int *part_first = nullptr;
+    DiagPart *part = nullptr;      // scratch: one record per block of the combined map
+    DiagPart *diag_out = nullptr;  // one record per member
+    double *phi_buf = nullptr;     // device staging of phi in double (host transfers)
+    Group groups[2];               // b = 5, b = 7
+    int kernel = LBHPDE_KERNEL_AUTO;
+    int K_req = 0, spl_req = 0;
+    long steps = 0;
+    bool initialised = false;
+    std::vector<std::pair<void *, size_t>> allocations;
+
+    int dev_alloc(void **p, size_t bytes) {
+        bytes = std::max<size_t>(bytes, 256);
+        void *q = nullptr;
+        if (has_alloc) {
+            q = alloc.alloc(bytes, (void *)stream, alloc.user);
+            if (!q) return LBHPDE_ERR_OOM;
+        } else {
+            cudaError_t e = cudaMalloc(&q, bytes);
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();
+                return e == cudaErrorMemoryAllocation ? LBHPDE_ERR_OOM : LBHPDE_ERR_CUDA;
+            }
+        }
+        allocations.emplace_back(q, bytes);
+        *p = q;
+        return LBHPDE_OK;
+    }
+    template <typename X>
+    int upload(X **dst, const std::vector<X> &src) {
+        RC(dev_alloc((void **)dst, sizeof(X) * std::max<size_t>(src.size(), 1)));
+        if (!src.empty())
+            CK(cudaMemcpyAsync(*dst, src.data(), sizeof(X) * src.size(), cudaMemcpyHostToDevice, stream));
+        return LBHPDE_OK;
+    }
+    void free_all() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (auto &a : allocations) {
+            if (has_alloc)
+                alloc.release(a.first, a.second, (void *)stream, alloc.user);
+            else
+                cudaFree(a.first);
+        }
+        allocations.clear();
+        if (own_stream && stream) cudaStreamDestroy(stream);
+        stream = nullptr;
+    }
+};
+
+struct lbhpde_ctx {
+    lbhpde_batch_s *b = nullptr;
+};
+
+namespace {
+
+// On-chip kernel variants: (state type, lattice, nodes per thread) -> maximum CTA threads.
+int onchip_maxt(size_t esz, int b, int K) {
+    if (esz == 4) {
+        if (b == 5) return K == 8 ? 512 : (K == 4 ? 1024 : (K == 2 ? 1024 : 0));
+        return K == 8 ? 256 : (K == 4 ? 512 : 0);
+    }
+    if (b == 5) return K == 4 ? 512 : (K == 2 ? 1024 : 0);
+    return K == 4 ? 256 : 0;
+}
+int default_K(size_t esz, int b) { return esz == 4 && b == 5 ? 8 : 4; }
+
+template <typename T, int B, int K, int MAXT>
+int launch_onchip_t(lbhpde_batch_s *bt, Group &g, int nsteps) {
+    auto fn = lbk::k_onchip<T, B, K, MAXT>;
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
+    fn<<<g.ncta, g.nthreads, g.smem, bt->stream>>>((T *)bt->st[bt->cur], g.insts, g.cta_first,
+                                                    (const T *)bt->coefT, nsteps, g.max_inst);
+    CK(cudaGetLastError());
+    return LBHPDE_OK;
+}
+
+template <typename T, int B>
+int launch_onchip_b(lbhpde_batch_s *bt, Group &g, int nsteps) {
+    if constexpr (sizeof(T) == 4) {
+        if constexpr (B == 5) {
+            if (g.K == 8) return launch_onchip_t<T, B, 8, 512>(bt, g, nsteps);
+            if (g.K == 4) return launch_onchip_t<T, B, 4, 1024>(bt, g, nsteps);
+            if (g.K == 2) return launch_onchip_t<T, B, 2, 1024>(bt, g, nsteps);
+        } else {
+            if (g.K == 8) return launch_onchip_t<T, B, 8, 256>(bt, g, nsteps);
+            if (g.K == 4) return launch_onchip_t<T, B, 4, 512>(bt, g, nsteps);
+        }
+    } else {
+        if constexpr (B == 5) {
+            if (g.K == 4) return launch_onchip_t<T, B, 4, 512>(bt, g, nsteps);
+            if (g.K == 2) return launch_onchip_t<T, B, 2, 1024>(bt, g, nsteps);
+        } else {
+            if (g.K == 4) return launch_onchip_t<T, B, 4, 256>(bt, g, nsteps);
+        }
+    }
+    return LBHPDE_ERR_UNSUPPORTED;
+}
+
+template <typename T, int B>
+int launch_stream_b(lbhpde_batch_s *bt, Group &g) {
+    const T *in = (const T *)bt->st[bt->cur];
+    T *out = (T *)bt->st[bt->cur ^ 1];
+    const int nb = (int)g.blocks_h.size();
+    if (g.maxD <= 5)
+        lbk::k_stream<T, B, 5, kStreamNPT><<<nb, kStreamThreads, 0, bt->stream>>>(in, out, bt->segs, g.blocks,
+                                                                                (const T *)bt->coefT);
+    else if (g.maxD <= 7)
+        lbk::k_stream<T, B, 7, kStreamNPT><<<nb, kStreamThreads, 0, bt->stream>>>(in, out, bt->segs, g.blocks,
+                                                                                (const T *)bt->coefT);
+    else
+        lbk::k_stream<T, B, 0, kStreamNPT><<<nb, kStreamThreads, 0, bt->stream>>>(in, out, bt->segs, g.blocks,
+                                                                                (const T *)bt->coefT);
+    CK(cudaGetLastError());
+    return LBHPDE_OK;
+}
+
+// Pack a group's instances onto CTAs for the on-chip kernel (first fit, largest first,
+// warp-aligned thread ranges, at most 32 instances per CTA).
+int plan_onchip(lbhpde_batch_s *bt, Group &g, int K) {
+    g.onchip_ok = false;
+    const int maxt = onchip_maxt(bt->esz, g.b, K);
+    if (maxt == 0 || K < lbk::wmax(g.b)) return LBHPDE_ERR_UNSUPPORTED;
+    for (int i : g.members)
+        if (bt->N[i] > (long long)maxt * K) return LBHPDE_ERR_UNSUPPORTED;
+    std::vector<int> order = g.members;
+    auto thr = [&](int i) { return (int)((bt->N[i] + K - 1) / K); };
+    auto pad = [&](int i) { return (thr(i) + 31) & ~31; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return pad(a) > pad(c); });
+    struct Cta {
+        int used = 0;
+        std::vector<int> inst;
+    };
+    std::vector<Cta> ctas;
+    for (int i : order) {
+        bool placed = false;
+        for (auto &c : ctas) {
+            if (c.used + pad(i) <= maxt && (int)c.inst.size() < 32) {
+                c.inst.push_back(i);
+                c.used += pad(i);
+                placed = true;
+                break;
+            }
+        }
+        if (!placed) {
+            Cta c;
+            c.inst.push_back(i);
+            c.used = pad(i);
+            ctas.push_back(c);
+        }
+    }
+    std::vector<OnchipInst> insts;
+    std::vector<int> first;
+    int nthreads = 32, max_inst = 1;
+    size_t coef_max = 0;
+    for (auto &c : ctas) {
+        first.push_back((int)insts.size());
+        int tb = 0, sco = 0, il = 0;
+        for (int i : c.inst) {
+            const Seg &s = bt->segs_h[i];
+            OnchipInst I{};
+            I.off = s.off;
+            I.ld = s.ld;
+            I.N = s.N;
+            I.D = s.D;
+            I.gcoef = s.coef;
+            I.scoef = sco;
+            I.tbase = tb;
+            I.nthr = thr(i);
+            I.il = il++;
+            insts.push_back(I);
+            sco += (g.b - 1) * (s.D + 1) + 1;
+            tb += pad(i);
+        }
+        nthreads = std::max(nthreads, tb);
+        max_inst = std::max(max_inst, (int)c.inst.size());
+        coef_max = std::max(coef_max, (size_t)sco);
+    }
+    first.push_back((int)insts.size());
+    const int ne = lbk::nedge(g.b);
+    size_t smem = (size_t(4) * ne * nthreads + size_t(2) * ne * max_inst + coef_max) * bt->esz;
+    if (smem > 227 * 1024) return LBHPDE_ERR_UNSUPPORTED;
+    RC(bt->upload(&g.insts, insts));
+    RC(bt->upload(&g.cta_first, first));
+    g.K = K;
+    g.maxt = maxt;
+    g.nthreads = nthreads;
+    g.max_inst = max_inst;
+    g.ncta = (int)ctas.size();
+    g.smem = smem;
+    g.onchip_ok = true;
+    return LBHPDE_OK;
+}
+
+int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
+    bt->count = count;
+    bt->mi.resize(count);
+    bt->N.resize(count);
+    bt->phi_off.resize(count + 1);
+    long long off = 0;
+    for (int i = 0; i < count; ++i) {
+        const lbhpde_instance &I = m[i];
+        RC(lbhpde_model(I.m, I.alpha, I.pi, I.dx, I.dt, I.tau, I.lattice, I.scheme, &bt->mi[i]));
+        const int W = (bt->mi[i].b - 1) / 2;
+        if (I.N < 2 * W || I.N > (1LL << 30)) return LBHPDE_ERR_ARG;
+        bt->N[i] = I.N;
+        bt->phi_off[i] = off;
+        off += I.N;
+    }
+    bt->phi_off[count] = off;
+    bt->total = off;
+
+    // arena: per member b rows of ld elements; coefficient blocks
+    std::vector<Seg> segs(count);
+    long long st_elems = 0;
+    std::vector<double> coefd;
+    for (int i = 0; i < count; ++i) {
+        const lbhpde_model_info &M = bt->mi[i];
+        Seg s{};
+        s.off = st_elems;
+        s.ld = (bt->N[i] + 31) / 32 * 32;
+        s.N = (int)bt->N[i];
+        s.D = M.D;
+        s.coef = (int)coefd.size();
+        st_elems += s.ld * M.b;
+        for (int j = 1; j < M.b; ++j)
+            for (int p = 0; p <= M.D; ++p) coefd.push_back(M.coef[j][p]);
+        for (int j = 1; j < M.b; ++j)
+            for (int p = 0; p <= M.D; ++p) coefd.push_back(M.feq[j][p]);
+        coefd.push_back(1.0 - M.omega);
+        segs[i] = s;
+    }
+    bt->segs_h = segs;
+    bt->st_bytes = size_t(st_elems) * bt->esz;
+    RC(bt->dev_alloc(&bt->st[0], bt->st_bytes));
+    RC(bt->dev_alloc(&bt->st[1], bt->st_bytes));
+    RC(bt->upload(&bt->segs, segs));
+    RC(bt->upload(&bt->coefD, coefd));
+    if (bt->esz == 4) {
+        std::vector<float> cf(coefd.begin(), coefd.end());
+        RC(bt->upload((float **)&bt->coefT, cf));
+    } else {
+        bt->coefT = bt->coefD;
+    }
+
+    // block maps
+    std::vector<int2> all;
+    std::vector<long long> blk_off;
+    std::vector<int> part_first;
+    for (int i = 0; i < count; ++i) {
+        part_first.push_back((int)all.size());
+        for (long long x = 0; x < bt->N[i]; x += kChunk) {
+            all.push_back(make_int2(i, (int)x));
+            blk_off.push_back(bt->phi_off[i]);
+        }
+    }
+    part_first.push_back((int)all.size());
+    bt->all_blocks_h = all;
+    bt->part_first_h = part_first;
+    RC(bt->upload(&bt->all_blocks, all));
+    RC(bt->upload(&bt->blk_off, blk_off));
+    RC(bt->upload(&bt->part_first, part_first));
+    RC(bt->dev_alloc((void **)&bt->part, sizeof(DiagPart) * all.size()));
+    RC(bt->dev_alloc((void **)&bt->diag_out, sizeof(DiagPart) * count));
+    RC(bt->dev_alloc((void **)&bt->phi_buf, sizeof(double) * bt->total));
+
+    for (int gi = 0; gi < 2; ++gi) {
+        Group &g = bt->groups[gi];
+        g.b = gi == 0 ? 5 : 7;
+        for (int i = 0; i < count; ++i)
+            if (bt->mi[i].b == g.b) {
+                g.members.push_back(i);
+                g.maxD = std::max(g.maxD, bt->mi[i].D);
+                for (long long x = 0; x < bt->N[i]; x += kChunk) g.blocks_h.push_back(make_int2(i, (int)x));
+            }
+        if (!g.members.empty()) {
+            std::vector<long long> off(g.blocks_h.size());
+            for (size_t q = 0; q < off.size(); ++q) off[q] = bt->phi_off[g.blocks_h[q].x];
+            RC(bt->upload(&g.blocks, g.blocks_h));
+            RC(bt->upload(&g.blk_off, off));
+        }
+    }
+    return LBHPDE_OK;
+}
+
+int choose_kernels(lbhpde_batch_s *bt) {
+    for (auto &g : bt->groups) {
+        if (g.members.empty()) continue;
+        g.onchip_ok = false;
+        if (bt->kernel == LBHPDE_KERNEL_STREAM) continue;
+        const int K = bt->K_req > 0 ? bt->K_req : default_K(bt->esz, g.b);
+        int rc = plan_onchip(bt, g, K);
+        if (rc != LBHPDE_OK && bt->kernel == LBHPDE_KERNEL_ONCHIP) return rc;
+    }
+    return LBHPDE_OK;
+}
+
+int batch_step(lbhpde_batch_s *bt, long nsteps) {
+    if (nsteps < 0) return LBHPDE_ERR_ARG;
+    if (!bt->initialised) return LBHPDE_ERR_ARG;
+    if (nsteps == 0) return LBHPDE_OK;
+    // on-chip groups: state stays in st[cur]; streaming groups ping-pong.  When both kinds
+    // are present the on-chip group's rows are copied along with each stream step.
+    bool any_stream = false;
+    for (auto &g : bt->groups)
+        if (!g.members.empty() && !g.onchip_ok) any_stream = true;
+    for (auto &g : bt->groups) {
+        if (g.members.empty() || !g.onchip_ok) continue;
+        long left = nsteps;
+        const long spl = bt->spl_req > 0 ? bt->spl_req : (1L << 30);
+        while (left > 0) {
+            const int n = (int)std::min(left, spl);
+            int rc = bt->esz == 4 ? (g.b == 5 ? launch_onchip_b<float, 5>(bt, g, n) : launch_onchip_b<float, 7>(bt, g, n))
+                                  : (g.b == 5 ? launch_onchip_b<double, 5>(bt, g, n) : launch_onchip_b<double, 7>(bt, g, n));
+            RC(rc);
+            left -= n;
+        }
+    }
+    if (any_stream) {
+        for (long s = 0; s < nsteps; ++s) {
+            for (auto &g : bt->groups) {
+                if (g.members.empty() || g.onchip_ok) continue;
+                int rc = bt->esz == 4 ? (g.b == 5 ? launch_stream_b<float, 5>(bt, g) : launch_stream_b<float, 7>(bt, g))
+                                      : (g.b == 5 ? launch_stream_b<double, 5>(bt, g) : launch_stream_b<double, 7>(bt, g));
+                RC(rc);
+            }
+            // keep on-chip members' rows valid in the buffer that becomes current
+            for (auto &g : bt->groups) {
+                if (g.members.empty() || !g.onchip_ok) continue;
+                for (int i : g.members) {
+                    const Seg &s = bt->segs_h[i];
+                    const size_t bytes = size_t(s.ld) * bt->mi[i].b * bt->esz;
+                    const size_t o = size_t(s.off) * bt->esz;
+                    CK(cudaMemcpyAsync((char *)bt->st[bt->cur ^ 1] + o, (char *)bt->st[bt->cur] + o, bytes,
+                                       cudaMemcpyDeviceToDevice, bt->stream));
+                }
+            }
+            bt->cur ^= 1;
+        }
+    }
+    bt->steps += nsteps;
+    return LBHPDE_OK;
+}
+
+int batch_set_phi(lbhpde_batch_s *bt, const double *phi0, int on_device) {
+    if (!phi0) return LBHPDE_ERR_ARG;
+    const double *src = phi0;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(bt->phi_buf, phi0, sizeof(double) * bt->total, cudaMemcpyHostToDevice, bt->stream));
+        src = bt->phi_buf;
+    }
+    bt->cur = 0;
+    for (auto &g : bt->groups) {
+        if (g.members.empty()) continue;
+        const int nb = (int)g.blocks_h.size();
+        const long long *off_d = g.blk_off;
+        if (bt->esz == 4) {
+            if (g.b == 5)
+                lbk::k_init<float, 5><<<nb, kGenericThreads, 0, bt->stream>>>((float *)bt->st[0], bt->segs, g.blocks,
+                                                                               bt->coefD, src, off_d, kChunk);
+            else
+                lbk::k_init<float, 7><<<nb, kGenericThreads, 0, bt->stream>>>((float *)bt->st[0], bt->segs, g.blocks,
+                                                                               bt->coefD, src, off_d, kChunk);
+        } else {
+            if (g.b == 5)
+                lbk::k_init<double, 5><<<nb, kGenericThreads, 0, bt->stream>>>((double *)bt->st[0], bt->segs,
+                                                                                g.blocks, bt->coefD, src, off_d, kChunk);
+            else
+                lbk::k_init<double, 7><<<nb, kGenericThreads, 0, bt->stream>>>((double *)bt->st[0], bt->segs,
+                                                                                g.blocks, bt->coefD, src, off_d, kChunk);
+        }
+        CK(cudaGetLastError());
+    }
+    bt->steps = 0;
+    bt->initialised = true;
+    return LBHPDE_OK;
+}
+
+int batch_read_phi(lbhpde_batch_s *bt, double *out, int on_device) {
+    if (!out) return LBHPDE_ERR_ARG;
+    if (!bt->initialised) return LBHPDE_ERR_ARG;
+    double *dst = on_device ? out : bt->phi_buf;
+    const int nb = (int)bt->all_blocks_h.size();
+    if (bt->esz == 4)
+        lbk::k_read_phi<float><<<nb, kGenericThreads, 0, bt->stream>>>((const float *)bt->st[bt->cur], bt->segs,
+                                                                       bt->all_blocks, dst, bt->blk_off, kChunk);
+    else
+        lbk::k_read_phi<double><<<nb, kGenericThreads, 0, bt->stream>>>((const double *)bt->st[bt->cur], bt->segs,
+                                                                        bt->all_blocks, dst, bt->blk_off, kChunk);
+    CK(cudaGetLastError());
+    if (!on_device) {
+        CK(cudaMemcpyAsync(out, bt->phi_buf, sizeof(double) * bt->total, cudaMemcpyDeviceToHost, bt->stream));
+        CK(cudaStreamSynchronize(bt->stream));
+        for (long long i = 0; i < bt->total; ++i)
+            if (!std::isfinite(out[i])) return LBHPDE_ERR_DIVERGED;
+    }
+    return LBHPDE_OK;
+}
+
+int batch_diag(lbhpde_batch_s *bt, const double *phistar, lbhpde_diag *out) {
+    if (!out) return LBHPDE_ERR_ARG;
+    if (!bt->initialised) return LBHPDE_ERR_ARG;
+    const int nb = (int)bt->all_blocks_h.size();
+    if (bt->esz == 4)
+        lbk::k_diag_partial<float><<<nb, kGenericThreads, 0, bt->stream>>>(
+            (const float *)bt->st[bt->cur], bt->segs, bt->all_blocks, phistar, bt->blk_off, kChunk, bt->part);
+    else
+        lbk::k_diag_partial<double><<<nb, kGenericThreads, 0, bt->stream>>>(
+            (const double *)bt->st[bt->cur], bt->segs, bt->all_blocks, phistar, bt->blk_off, kChunk, bt->part);
+    CK(cudaGetLastError());
+    lbk::k_diag_final<<<(bt->count + 127) / 128, 128, 0, bt->stream>>>(bt->part, bt->part_first, bt->count,
+                                                                      bt->diag_out);
+    CK(cudaGetLastError());
+    std::vector<DiagPart> h(bt->count);
+    CK(cudaMemcpyAsync(h.data(), bt->diag_out, sizeof(DiagPart) * bt->count, cudaMemcpyDeviceToHost, bt->stream));
+    CK(cudaStreamSynchronize(bt->stream));
+    int rc = LBHPDE_OK;
+    for (int i = 0; i < bt->count; ++i) {
+        lbhpde_diag &d = out[i];
+        d.sum_phi = h[i].sum;
+        d.max_abs_phi = h[i].maxabs;
+        d.nonfinite = (long)h[i].nonfinite;
+        d.err_E = phistar ? h[i].l1d / h[i].l1s : 0.0;
+        d.err_L2 = phistar ? std::sqrt(h[i].l2d / h[i].l2s) : 0.0;
+        d.steps = bt->steps;
+        if (h[i].nonfinite) rc = LBHPDE_ERR_DIVERGED;
+    }
+    return rc;
+}
+
+int batch_create(lbhpde_batch_s **out, int count, const lbhpde_instance *members, int precision, void *stream,
+                 const lbhpde_allocator *alloc) {
+    if (!out || count <= 0 || !members) return LBHPDE_ERR_ARG;
+    if (precision != LBHPDE_FP64 && precision != LBHPDE_FP32_DEV) return LBHPDE_ERR_ARG;
+    if (alloc && (!alloc->alloc || !alloc->release)) return LBHPDE_ERR_ARG;
+    *out = nullptr;
+    auto *bt = new (std::nothrow) lbhpde_batch_s();
+    if (!bt) return LBHPDE_ERR_OOM;
+    bt->precision = precision;
+    bt->esz = precision == LBHPDE_FP64 ? 8 : 4;
+    if (alloc) {
+        bt->has_alloc = true;
+        bt->alloc = *alloc;
+    }
+    if (stream) {
+        bt->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            (void)cudaGetLastError();
+            delete bt;
+            return LBHPDE_ERR_CUDA;
+        }
+        bt->own_stream = true;
+    }
+    int rc = batch_build(bt, count, members);
+    if (rc == LBHPDE_OK) rc = choose_kernels(bt);
+    if (rc == LBHPDE_OK && cudaStreamSynchronize(bt->stream) != cudaSuccess) rc = LBHPDE_ERR_CUDA;
+    if (rc != LBHPDE_OK) {
+        bt->free_all();
+        delete bt;
+        return rc;
+    }
+    *out = bt;
+    return LBHPDE_OK;
+}
+
+void fill_instance(lbhpde_instance &I, int m, const double *alpha, const lbhpde_pi *pi, long N, double dx, double dt,
+                   double tau, int lattice, int scheme) {
+    std::memset(&I, 0, sizeof(I));
+    I.m = m;
+    for (int k = 0; k < m && k < 6; ++k) {
+        I.alpha[k] = alpha[k];
+        I.pi[k] = pi[k];
+    }
+    I.N = N;
+    I.dx = dx;
+    I.dt = dt;
+    I.tau = tau;
+    I.lattice = lattice;
+    I.scheme = scheme;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" int lbhpde_batch_create(lbhpde_batch_t *out, int count, const lbhpde_instance *members, int precision,
+                                   void *cuda_stream, const lbhpde_allocator *alloc) {
+    return batch_create(out, count, members, precision, cuda_stream, alloc);
+}
+extern "C" int lbhpde_batch_set_phi(lbhpde_batch_t b, const double *phi0, int on_device) {
+    return b ? batch_set_phi(b, phi0, on_device) : LBHPDE_ERR_ARG;
+}
+extern "C" int lbhpde_batch_step(lbhpde_batch_t b, long nsteps) { return b ? batch_step(b, nsteps) : LBHPDE_ERR_ARG; }
+extern "C" int lbhpde_batch_read_phi(lbhpde_batch_t b, double *out, int on_device) {
+    return b ? batch_read_phi(b, out, on_device) : LBHPDE_ERR_ARG;
+}
+extern "C" int lbhpde_batch_diagnostics(lbhpde_batch_t b, const double *phistar, lbhpde_diag *out) {
+    return b ? batch_diag(b, phistar, out) : LBHPDE_ERR_ARG;
+}
+extern "C" int lbhpde_batch_set_kernel(lbhpde_batch_t b, int kernel, int nodes_per_thread, int steps_per_launch) {
+    if (!b || kernel < LBHPDE_KERNEL_AUTO || kernel > LBHPDE_KERNEL_ONCHIP || nodes_per_thread < 0 ||
+        steps_per_launch < 0)
+        return LBHPDE_ERR_ARG;
+    const int old_k = b->kernel, old_K = b->K_req, old_s = b->spl_req;
+    b->kernel = kernel;
+    b->K_req = nodes_per_thread;
+    b->spl_req = steps_per_launch;
+    int rc = choose_kernels(b);
+    if (rc != LBHPDE_OK) {
+        b->kernel = old_k;
+        b->K_req = old_K;
+        b->spl_req = old_s;
+        choose_kernels(b);
+    }
+    return rc;
+}
+extern "C" int lbhpde_batch_size(lbhpde_batch_t b, long *total_nodes, size_t *device_bytes) {
+    if (!b) return LBHPDE_ERR_ARG;
+    if (total_nodes) *total_nodes = (long)b->total;
+    if (device_bytes) {
+        size_t s = 0;
+        for (auto &a : b->allocations) s += a.second;
+        *device_bytes = s;
+    }
+    return LBHPDE_OK;
+}
+extern "C" int lbhpde_batch_destroy(lbhpde_batch_t b) {
+    if (!b) return LBHPDE_ERR_ARG;
+    b->free_all();
+    delete b;
+    return LBHPDE_OK;
+}
+
+extern "C" int lbhpde_create(lbhpde_t *out, int m, const double *alpha, const lbhpde_pi *pi, long N, double dx,
+                             double dt, double tau, int lattice, int scheme, int precision, int boundary,
+                             void *cuda_stream, const lbhpde_allocator *alloc) {
+    if (!out || !alpha || !pi || m < 1 || m > 6) return LBHPDE_ERR_ARG;
+    if (boundary != LBHPDE_PERIODIC) return LBHPDE_ERR_UNSUPPORTED;
+    *out = nullptr;
+    lbhpde_instance I;
+    fill_instance(I, m, alpha, pi, N, dx, dt, tau, lattice, scheme);
+    auto *h = new (std::nothrow) lbhpde_ctx();
+    if (!h) return LBHPDE_ERR_OOM;
+    int rc = batch_create(&h->b, 1, &I, precision, cuda_stream, alloc);
+    if (rc != LBHPDE_OK) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return LBHPDE_OK;
+}
+extern "C" int lbhpde_set_phi(lbhpde_t h, const double *phi0, int on_device) {
+    return h ? batch_set_phi(h->b, phi0, on_device) : LBHPDE_ERR_ARG;
+}
+extern "C" int lbhpde_step(lbhpde_t h, long nsteps) { return h ? batch_step(h->b, nsteps) : LBHPDE_ERR_ARG; }
+extern "C" int lbhpde_read_phi(lbhpde_t h, double *out, int on_device) {
+    return h ? batch_read_phi(h->b, out, on_device) : LBHPDE_ERR_ARG;
+}
+extern "C" int lbhpde_diagnostics(lbhpde_t h, const double *phistar, lbhpde_diag *out) {
+    return h ? batch_diag(h->b, phistar, out) : LBHPDE_ERR_ARG;
+}
+extern "C" int lbhpde_set_kernel(lbhpde_t h, int kernel, int nodes_per_thread, int steps_per_launch) {
+    return h ? lbhpde_batch_set_kernel(h->b, kernel, nodes_per_thread, steps_per_launch) : LBHPDE_ERR_ARG;
+}
+extern "C" int lbhpde_get_model(lbhpde_t h, lbhpde_model_info *out) {
+    if (!h || !out) return LBHPDE_ERR_ARG;
+    *out = h->b->mi[0];
+    return LBHPDE_OK;
+}
+extern "C" int lbhpde_destroy(lbhpde_t h) {
+    if (!h) return LBHPDE_ERR_ARG;
+    lbhpde_batch_destroy(h->b);
+    delete h;
+    return LBHPDE_OK;
+}

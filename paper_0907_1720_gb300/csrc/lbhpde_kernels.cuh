@@ -1,0 +1,450 @@
+// CUDA kernels of the collide-and-stream hot path (Eq. (LBE)) for sm_103a.
+//
+// State of one instance in HBM (structure of arrays, rows of stride ld):
+//   row 0      phi(x)
+//   row j>=1   s_j(x) = f*_j(x), the post-collision population of velocity e_j,
+//              e = {_, 1, -1, 2, -2, 3, -3} (Sec. III A/B).
+// The rest population is not stored: collision keeps sum_j f*_j = phi (first relation of
+// Eq. (moments)), so f*_0 = phi - sum_{j>=1} s_j.  In FP32 this makes every stored
+// population a deviation from the rest equilibrium (phi, 0, ..., 0), whose magnitude is
+// O(phi / c): the "deviation storage" of the FP32 path.
+//
+// One time step at node x (pull form of Eq. (LBE)):
+//   f_j(x)   = s_j(x - e_j)                       stream                 (a2)
+//   phi'(x)  = phi(x) + sum_{j>=1} [f_j(x) - s_j(x)]                      (a3)
+//   s'_j(x)  = (1 - omega) f_j(x) + P_j(phi'(x))  relax, P_j = omega f^eq_j (a4, a5)
+// where f^eq_j is the polynomial of Eqs. (EDF5)/(EDF7) built on the host.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbk {
+
+constexpr int kMaxDeg = 31;
+
+// e_j for j = 0..6: {0, 1, -1, 2, -2, 3, -3}
+__host__ __device__ constexpr int vel(int j) { return j == 0 ? 0 : ((j & 1) ? (j + 1) / 2 : -(j / 2)); }
+// Largest |e_j| of the lattice
+__host__ __device__ constexpr int wmax(int B) { return (B - 1) / 2; }
+// Number of edge values a thread publishes for the populations moving one way:
+// 1 + 2 (+ 3) = 3 on D1Q5, 6 on D1Q7.
+__host__ __device__ constexpr int nedge(int B) { return wmax(B) * (wmax(B) + 1) / 2; }
+// First edge slot of the population with |e| = a (a = 1, 2, 3): 0, 1, 3.
+__host__ __device__ constexpr int eslot(int a) { return (a - 1) * a / 2; }
+
+// One instance's place in the state and coefficient arenas.
+struct Seg {
+    long long off;  // element offset of row 0 (phi)
+    long long ld;   // row stride in elements (multiple of 32)
+    int N;          // nodes
+    int D;          // degree of the f^eq polynomials
+    int coef;       // element offset of the coefficient block:
+                    //   [(B-1)(D+1)]  P_j = omega f^eq_j, j = 1..B-1 (row j-1)
+                    //   [(B-1)(D+1)]  f^eq_j (unscaled, for initialisation)
+                    //   [1]           1 - omega
+    int pad;
+};
+
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fma_t<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <>
+__device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// ---------------------------------------------------------------------------- a1: init
+// s_j(x) = f^eq_j(phi0(x)) (post-collision state of an equilibrium, collision leaves it
+// unchanged), phi(x) = phi0(x).  f^eq is evaluated in double and rounded once to T.
+// Grid: blocks[i] = (segment, first node); each block covers `chunk` nodes; phi0_off[i] is
+// the offset of block i's segment in the concatenated phi0 array.
+template <typename T, int B>
+__global__ void k_init(T *__restrict__ st, const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
+                       const double *__restrict__ coefd, const double *__restrict__ phi0,
+                       const long long *__restrict__ phi0_off, int chunk) {
+    const int2 bl = blocks[blockIdx.x];
+    const Seg s = segs[bl.x];
+    const double *__restrict__ fe = coefd + s.coef + (B - 1) * (s.D + 1);
+    const double *__restrict__ p0 = phi0 + phi0_off[blockIdx.x];
+    const int xend = min(bl.y + chunk, s.N);
+    for (int x = bl.y + threadIdx.x; x < xend; x += blockDim.x) {
+        const double ph = p0[x];
+        st[s.off + x] = (T)ph;
+#pragma unroll
+        for (int j = 1; j < B; ++j) {
+            const double *c = fe + (j - 1) * (s.D + 1);
+            double acc = c[s.D];
+            for (int p = s.D - 1; p >= 0; --p) acc = __fma_rn(acc, ph, c[p]);
+            st[s.off + (long long)j * s.ld + x] = (T)acc;
+        }
+    }
+}
+
+// ------------------------------------------------------------- a2-a6: streaming step
+// One fused collide+stream step through HBM.  Each thread owns NPT nodes spaced by
+// blockDim.x (coalesced rows); the shifted reads s_j(x - e_j) are served by L1/L2 from the
+// lines the neighbouring lanes fetch, so DRAM sees each row once per step.
+// DC > 0: compile-time polynomial degree (coefficients kept in registers; segments with a
+// smaller degree are zero-padded by the host).  DC == 0: degree read at run time.
+template <typename T, int B, int DC, int NPT>
+__global__ void __launch_bounds__(256) k_stream(const T *__restrict__ in, T *__restrict__ out,
+                                                const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
+                                                const T *__restrict__ coefs) {
+    constexpr int NC = (DC > 0 ? DC : kMaxDeg) + 1;
+    __shared__ T sc[(B - 1) * NC + 1];
+    const int2 bl = blocks[blockIdx.x];
+    const Seg s = segs[bl.x];
+    const int D = DC > 0 ? DC : s.D;
+    for (int i = threadIdx.x; i < (B - 1) * (s.D + 1); i += blockDim.x) {
+        const int j = i / (s.D + 1), p = i % (s.D + 1);
+        sc[j * NC + p] = coefs[s.coef + i];
+    }
+    if (DC > 0)
+        for (int i = threadIdx.x; i < (B - 1) * NC; i += blockDim.x)
+            if (i % NC > s.D) sc[i] = T(0);
+    if (threadIdx.x == 0) sc[(B - 1) * NC] = coefs[s.coef + 2 * (B - 1) * (s.D + 1)];
+    __syncthreads();
+    const T omw = sc[(B - 1) * NC];
+    T creg[DC > 0 ? (B - 1) * (DC + 1) : 1];
+    if (DC > 0) {
+#pragma unroll
+        for (int j = 0; j < B - 1; ++j)
+#pragma unroll
+            for (int p = 0; p <= (DC > 0 ? DC : 0); ++p) creg[j * (DC + 1) + p] = sc[j * NC + p];
+    }
+    const T *__restrict__ src = in + s.off;
+    T *__restrict__ dst = out + s.off;
+    const long long ld = s.ld;
+    const int N = s.N;
+    const int chunk = blockDim.x * NPT;
+    const int x0 = bl.y + threadIdx.x;
+    T phi[NPT], f[NPT][B];
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        const int x = min(x0 + u * (int)blockDim.x, N - 1);
+        T d = T(0);
+        phi[u] = src[x];
+#pragma unroll
+        for (int j = 1; j < B; ++j) {
+            int xs = x - vel(j);
+            xs += xs < 0 ? N : 0;
+            xs -= xs >= N ? N : 0;
+            const T sj = src[(long long)j * ld + xs];
+            const T cur = src[(long long)j * ld + x];
+            d += sj - cur;
+            f[u][j] = sj;
+        }
+        phi[u] += d;
+    }
+    const int xend = min(bl.y + chunk, N);
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        const int x = x0 + u * (int)blockDim.x;
+        if (x >= xend) break;
+        const T ph = phi[u];
+        dst[x] = ph;
+#pragma unroll
+        for (int j = 1; j < B; ++j) {
+            T acc;
+            if (DC > 0) {
+                acc = creg[(j - 1) * (DC + 1) + (DC > 0 ? DC : 0)];
+#pragma unroll
+                for (int p = (DC > 0 ? DC : 1) - 1; p >= 0; --p) acc = fma_t(acc, ph, creg[(j - 1) * (DC + 1) + p]);
+            } else {
+                const T *c = sc + (j - 1) * NC;
+                acc = c[D];
+                for (int p = D - 1; p >= 0; --p) acc = fma_t(acc, ph, c[p]);
+            }
+            dst[(long long)j * ld + x] = fma_t(omw, f[u][j], acc);
+        }
+    }
+}
+
+// ------------------------------------------------------ a2-a6: on-chip, many steps
+// A whole periodic instance lives in the registers of a run of threads for `nsteps` steps.
+// Thread t of an instance owns nodes tK .. tK+K-1 (the last thread may own fewer: the
+// instance's nodes are not padded).  Each step, the populations that cross a thread boundary
+// are exchanged through double-buffered shared memory (one __syncthreads per step):
+//   R: the last |e| values of every right-moving population (read by thread t+1),
+//   L: the first |e| values of every left-moving population (read by thread t-1),
+//   tail: the last |e| nodes of the instance (read by thread 0: periodic wrap),
+//   head = thread 0's L window (read by the threads at the end of the instance).
+// Instances are packed onto CTAs on warp boundaries; all CTA threads take part in the
+// barriers.
+struct OnchipInst {
+    long long off, ld;  // state placement (as Seg)
+    int N, D;
+    int gcoef;          // coefficient block in global memory (as Seg::coef)
+    int scoef;          // this instance's copy of P_j and 1 - omega in shared memory
+    int tbase;          // first CTA thread
+    int nthr;           // threads that own nodes: ceil(N / K)
+    int il;             // index among the CTA's instances (tail buffer slot)
+    int pad;
+};
+
+template <typename T, int B, int K, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1)
+    k_onchip(T *__restrict__ st, const OnchipInst *__restrict__ insts, const int *__restrict__ cta_first,
+             const T *__restrict__ coefs, int nsteps, int max_inst) {
+    static_assert(K >= wmax(B), "a thread must own at least max|e| nodes");
+    constexpr int NE = nedge(B);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *smem = reinterpret_cast<T *>(smem_raw);
+    const int nt = blockDim.x;
+    T *R = smem;                        // [2][NE][nt]
+    T *L = R + 2 * NE * nt;             // [2][NE][nt]
+    T *tail = L + 2 * NE * nt;          // [2][NE][max_inst]
+    T *scoef = tail + 2 * NE * max_inst;
+
+    const int first = cta_first[blockIdx.x], last = cta_first[blockIdx.x + 1];
+    const int tid = threadIdx.x;
+    // stage every instance's coefficients (P_j rows then 1 - omega) into shared memory
+    for (int i = first; i < last; ++i) {
+        const OnchipInst I = insts[i];
+        const int n = (B - 1) * (I.D + 1);
+        for (int q = tid; q < n; q += nt) scoef[I.scoef + q] = coefs[I.gcoef + q];
+        if (tid == 0) scoef[I.scoef + n] = coefs[I.gcoef + 2 * n];
+    }
+    // which instance does this thread serve?
+    int me = -1;
+    for (int i = first; i < last; ++i) {
+        const int tb = insts[i].tbase;
+        if (tid >= tb && tid < tb + ((insts[i].nthr + 31) & ~31)) me = i;
+    }
+    OnchipInst I{};
+    if (me >= 0) I = insts[me];
+    const int t = tid - I.tbase;
+    const bool has = me >= 0 && t < I.nthr;
+    const int N = I.N;
+    const bool near_end = has && (t + 1) * K + wmax(B) > N;
+    const int xb = t * K;
+
+    T phi[K], v[B][K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int x = xb + k;
+        const bool ok = has && x < N;
+        phi[k] = ok ? st[I.off + x] : T(0);
+#pragma unroll
+        for (int j = 1; j < B; ++j) v[j][k] = ok ? st[I.off + (long long)j * I.ld + x] : T(0);
+    }
+    __syncthreads();
+    const T *sc = scoef + I.scoef;
+    const int D = I.D;
+    const T omw = has ? sc[(B - 1) * (D + 1)] : T(0);
+
+    for (int s = 0; s < nsteps; ++s) {
+        T *Rb = R + (s & 1) * NE * nt;
+        T *Lb = L + (s & 1) * NE * nt;
+        T *Tb = tail + (s & 1) * NE * max_inst;
+        if (has) {
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const int e = vel(j);
+                if (e > 0) {
+#pragma unroll
+                    for (int i = 0; i < e; ++i) Rb[(eslot(e) + i) * nt + tid] = v[j][K - e + i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < -e; ++i) Lb[(eslot(-e) + i) * nt + tid] = v[j][i];
+                }
+            }
+            if (near_end) {
+#pragma unroll
+                for (int j = 1; j < B; ++j) {
+                    const int e = vel(j);
+                    if (e > 0) {
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            const int x = xb + k;
+                            if (x >= N - e && x < N) Tb[(eslot(e) + x - (N - e)) * max_inst + I.il] = v[j][k];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (has) {
+            T d[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) d[k] = T(0);
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const int e = vel(j);
+                if (e > 0) {
+                    // f_j(x) = s_j(x - e): descending k keeps v[j][k - e] unread-overwritten
+#pragma unroll
+                    for (int k = K - 1; k >= 0; --k) {
+                        T nv;
+                        if (k >= e) {
+                            nv = v[j][k - e];
+                        } else {
+                            const T *p = t > 0 ? &Rb[(eslot(e) + k) * nt + tid - 1]
+                                               : &Tb[(eslot(e) + k) * max_inst + I.il];
+                            nv = *p;
+                        }
+                        d[k] += nv - v[j][k];
+                        v[j][k] = nv;
+                    }
+                } else {
+                    const int a = -e;
+                    if (!near_end) {
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            const T nv = (k + a < K) ? v[j][k + a] : Lb[(eslot(a) + k + a - K) * nt + tid + 1];
+                            d[k] += nv - v[j][k];
+                            v[j][k] = nv;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {
+                            const int src = xb + k + a;
+                            T nv;
+                            if (src >= N) {
+                                const int h = min(src - N, a - 1);  // node (src - N) of thread 0
+                                nv = Lb[(eslot(a) + h) * nt + I.tbase];
+                            } else if (k + a < K) {
+                                nv = v[j][k + a];
+                            } else {
+                                nv = Lb[(eslot(a) + k + a - K) * nt + tid + 1];
+                            }
+                            d[k] += nv - v[j][k];
+                            v[j][k] = nv;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) phi[k] += d[k];
+            // relax: s'_j = (1 - omega) f_j + P_j(phi'), Horner with coefficients from shared memory
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const T *c = sc + (j - 1) * (D + 1);
+                T acc[K];
+                const T cD = c[D];
+#pragma unroll
+                for (int k = 0; k < K; ++k) acc[k] = cD;
+                for (int p = D - 1; p >= 0; --p) {
+                    const T cp = c[p];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc[k] = fma_t(acc[k], phi[k], cp);
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) v[j][k] = fma_t(omw, v[j][k], acc[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int x = xb + k;
+        if (has && x < N) {
+            st[I.off + x] = phi[k];
+#pragma unroll
+            for (int j = 1; j < B; ++j) st[I.off + (long long)j * I.ld + x] = v[j][k];
+        }
+    }
+}
+
+// ------------------------------------------------------------------- a7: readout
+// phi (row 0, type T) of every segment into a concatenated double array.
+template <typename T>
+__global__ void k_read_phi(const T *__restrict__ st, const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
+                           double *__restrict__ out, const long long *__restrict__ out_off, int chunk) {
+    const int2 bl = blocks[blockIdx.x];
+    const Seg s = segs[bl.x];
+    const int xend = min(bl.y + chunk, s.N);
+    double *o = out + out_off[blockIdx.x];
+    for (int x = bl.y + threadIdx.x; x < xend; x += blockDim.x) o[x] = (double)st[s.off + x];
+}
+
+// ------------------------------------------------------------ a7: diagnostics
+// Deterministic two-pass FP64 reduction per segment.  Pass 1 writes one record per block
+// into the scratch array `part`; pass 2 (one thread block per segment) sums its blocks'
+// records in block order.
+struct DiagPart {
+    double sum, maxabs, l1d, l1s, l2d, l2s;
+    long long nonfinite;
+    long long pad;
+};
+
+template <typename T>
+__device__ void diag_block(const T *__restrict__ st, const Seg &s, int x0, int chunk, const double *__restrict__ ps,
+                           DiagPart *__restrict__ dst) {
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    long long nf = 0;
+    const int xend = min(x0 + chunk, s.N);
+    for (int x = x0 + threadIdx.x; x < xend; x += blockDim.x) {
+        const double ph = (double)st[s.off + x];
+        if (!isfinite(ph)) {
+            ++nf;
+            continue;
+        }
+        a[0] += ph;
+        a[1] = fmax(a[1], fabs(ph));
+        if (ps) {
+            const double q = ps[x], dd = ph - q;
+            a[2] += fabs(dd);
+            a[3] += fabs(q);
+            a[4] += dd * dd;
+            a[5] += q * q;
+        }
+    }
+    __shared__ double red[6][32];
+    __shared__ long long rnf[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+        double v = a[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double u = __shfl_down_sync(0xffffffffu, v, o);
+            v = q == 1 ? fmax(v, u) : v + u;
+        }
+        if (lane == 0) red[q][w] = v;
+    }
+    for (int o = 16; o > 0; o >>= 1) nf += __shfl_down_sync(0xffffffffu, nf, o);
+    if (lane == 0) rnf[w] = nf;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DiagPart r{};
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 0; i < nw; ++i) {
+            r.sum += red[0][i];
+            r.maxabs = fmax(r.maxabs, red[1][i]);
+            r.l1d += red[2][i];
+            r.l1s += red[3][i];
+            r.l2d += red[4][i];
+            r.l2s += red[5][i];
+            r.nonfinite += rnf[i];
+        }
+        *dst = r;
+    }
+}
+
+template <typename T>
+__global__ void k_diag_partial(const T *__restrict__ st, const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
+                               const double *__restrict__ phistar, const long long *__restrict__ ps_off, int chunk,
+                               DiagPart *__restrict__ part) {
+    const int2 bl = blocks[blockIdx.x];
+    const Seg s = segs[bl.x];
+    diag_block<T>(st, s, bl.y, chunk, phistar ? phistar + ps_off[blockIdx.x] : nullptr, part + blockIdx.x);
+}
+
+// part_first[seg] .. part_first[seg + 1]: the pass-1 records of segment seg.
+__global__ void k_diag_final(const DiagPart *__restrict__ part, const int *__restrict__ part_first, int nseg,
+                             DiagPart *__restrict__ out) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nseg) return;
+    DiagPart r{};
+    for (int i = part_first[g]; i < part_first[g + 1]; ++i) {
+        const DiagPart &p = part[i];
+        r.sum += p.sum;
+        r.maxabs = fmax(r.maxabs, p.maxabs);
+        r.l1d += p.l1d;
+        r.l1s += p.l1s;
+        r.l2d += p.l2d;
+        r.l2s += p.l2s;
+        r.nonfinite += p.nonfinite;
+    }
+    out[g] = r;
+}
+
+}  // namespace lbk

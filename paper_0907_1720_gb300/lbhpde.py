@@ -1,0 +1,352 @@
+"""Python binding of the C ABI in ``include/lbhpde.h`` (ctypes; argument marshalling only).
+
+Every step of the solver runs in the CUDA library ``_build/liblbhpde.so``; this module
+only converts Python/numpy/torch arguments into the C structures and pointers.  If the
+library has not been built, :func:`lib` raises ``RuntimeError`` -- there is no fallback.
+
+Low-level functions carry the C names (``lbhpde_model``, ``lbhpde_create`` ...).  The
+classes :class:`Solver` and :class:`Batch` wrap a handle for convenience; device memory
+is obtained through torch's caching allocator and work runs on the torch stream current
+at creation time.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblbhpde.so")
+
+OK, ERR_ARG, ERR_TAU_SINGULAR, ERR_OOM, ERR_DIVERGED, PENDING, ERR_TIMEOUT, ERR_CUDA, ERR_NOT_FOUND, \
+    ERR_UNSUPPORTED = range(10)
+FP64, FP32_DEV = 0, 1
+PERIODIC = 0
+PI_ZERO, PI_PHI, PI_POWER, PI_POLY = 0, 1, 2, 3
+PI_NCOEF = 8
+MAX_DEG = 31
+KERNEL_AUTO, KERNEL_STREAM, KERNEL_ONCHIP = 0, 1, 2
+
+
+class lbhpde_pi(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("power", ctypes.c_int), ("coef", ctypes.c_double * PI_NCOEF)]
+
+
+class lbhpde_model_info(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_int), ("m", ctypes.c_int), ("scheme", ctypes.c_int), ("D", ctypes.c_int),
+                ("inexact", ctypes.c_int), ("c", ctypes.c_double), ("omega", ctypes.c_double),
+                ("tk", ctypes.c_double * 7), ("beta", ctypes.c_double * 7), ("A", ctypes.c_double * 3),
+                ("feq", (ctypes.c_double * (MAX_DEG + 1)) * 7), ("coef", (ctypes.c_double * (MAX_DEG + 1)) * 7)]
+
+
+class lbhpde_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)),
+                ("release", ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                             ctypes.c_void_p)),
+                ("user", ctypes.c_void_p)]
+
+
+class lbhpde_diag(ctypes.Structure):
+    _fields_ = [("sum_phi", ctypes.c_double), ("max_abs_phi", ctypes.c_double), ("nonfinite", ctypes.c_long),
+                ("err_E", ctypes.c_double), ("err_L2", ctypes.c_double), ("steps", ctypes.c_long)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class lbhpde_instance(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("alpha", ctypes.c_double * 6), ("pi", lbhpde_pi * 6), ("N", ctypes.c_long),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
+                ("lattice", ctypes.c_int), ("scheme", ctypes.c_int)]
+
+
+class LbhpdeError(RuntimeError):
+    def __init__(self, code, where=""):
+        msg = lib().lbhpde_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} (code {code})")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes)
+_V, _I, _L, _D, _S = ctypes.c_void_p, ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_size_t
+_P = ctypes.POINTER
+_SIGS = {
+    "lbhpde_model": (_I, [_I, _P(_D), _P(lbhpde_pi), _D, _D, _D, _I, _I, _P(lbhpde_model_info)]),
+    "lbhpde_create": (_I, [_P(_V), _I, _P(_D), _P(lbhpde_pi), _L, _D, _D, _D, _I, _I, _I, _I, _V,
+                           _P(lbhpde_allocator)]),
+    "lbhpde_set_phi": (_I, [_V, _V, _I]),
+    "lbhpde_step": (_I, [_V, _L]),
+    "lbhpde_read_phi": (_I, [_V, _V, _I]),
+    "lbhpde_diagnostics": (_I, [_V, _V, _P(lbhpde_diag)]),
+    "lbhpde_set_kernel": (_I, [_V, _I, _I, _I]),
+    "lbhpde_get_model": (_I, [_V, _P(lbhpde_model_info)]),
+    "lbhpde_destroy": (_I, [_V]),
+    "lbhpde_strerror": (ctypes.c_char_p, [_I]),
+    "lbhpde_batch_create": (_I, [_P(_V), _I, _P(lbhpde_instance), _I, _V, _P(lbhpde_allocator)]),
+    "lbhpde_batch_set_phi": (_I, [_V, _V, _I]),
+    "lbhpde_batch_step": (_I, [_V, _L]),
+    "lbhpde_batch_read_phi": (_I, [_V, _V, _I]),
+    "lbhpde_batch_diagnostics": (_I, [_V, _V, _P(lbhpde_diag)]),
+    "lbhpde_batch_set_kernel": (_I, [_V, _I, _I, _I]),
+    "lbhpde_batch_size": (_I, [_V, _P(_L), _P(_S)]),
+    "lbhpde_batch_destroy": (_I, [_V]),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def lib():
+    """The loaded CUDA library; raises RuntimeError when it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                                   "(run __graft_entry__.build() or python -m paper_0907_1720_gb300.build)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.restype, fn.argtypes = res, args
+            _lib = L
+        return _lib
+
+
+def _check(code, where):
+    if code != OK:
+        raise LbhpdeError(code, where)
+
+
+# ------------------------------------------------------------------ marshalling
+
+def make_pi(coefs) -> lbhpde_pi:
+    """A Pi_k from polynomial coefficients (coef[p] of phi**p); uses the menu's closed forms."""
+    c = [float(v) for v in coefs]
+    while c and c[-1] == 0.0:
+        c.pop()
+    p = lbhpde_pi()
+    if not c:
+        p.kind = PI_ZERO
+    elif c == [0.0, 1.0]:
+        p.kind = PI_PHI
+    elif len(c) > 1 and all(v == 0.0 for v in c[:-1]) and c[-1] == 1.0:
+        p.kind, p.power = PI_POWER, len(c) - 1
+    else:
+        if len(c) > PI_NCOEF:
+            raise ValueError("Pi_k degree above 7")
+        p.kind = PI_POLY
+        for i, v in enumerate(c):
+            p.coef[i] = v
+    return p
+
+
+def _eq_args(alpha, pi):
+    m = len(alpha)
+    a = (ctypes.c_double * m)(*[float(v) for v in alpha])
+    P = (lbhpde_pi * m)(*[make_pi(r) for r in pi])
+    return m, a, P
+
+
+def lbhpde_model(alpha, pi, dx, dt, tau, lattice=0, scheme=1) -> lbhpde_model_info:
+    """Step a0 on the host: the model the library builds for one equation."""
+    m, a, P = _eq_args(alpha, pi)
+    out = lbhpde_model_info()
+    _check(lib().lbhpde_model(m, a, P, dx, dt, tau, lattice, scheme, ctypes.byref(out)), "lbhpde_model")
+    return out
+
+
+def model_coeffs(info: lbhpde_model_info):
+    """(feq[b][D+1], coef[b][D+1]) as numpy arrays."""
+    b, D = info.b, info.D
+    feq = np.array([[info.feq[j][p] for p in range(D + 1)] for j in range(b)])
+    coef = np.array([[info.coef[j][p] for p in range(D + 1)] for j in range(b)])
+    return feq, coef
+
+
+def make_instance(eq, N, dx, dt, tau, scheme=1) -> lbhpde_instance:
+    I = lbhpde_instance()
+    I.m = eq.m
+    for k in range(eq.m):
+        I.alpha[k] = float(eq.alpha[k])
+        I.pi[k] = make_pi(eq.pi[k])
+    I.N, I.dx, I.dt, I.tau, I.lattice, I.scheme = int(N), float(dx), float(dt), float(tau), int(eq.lattice), int(scheme)
+    return I
+
+
+# ------------------------------------------------------------ torch plumbing
+
+_torch_alloc_keep = []
+
+
+def torch_allocator():
+    """An lbhpde_allocator that draws device memory from torch's caching allocator."""
+    import torch
+
+    dev = torch.cuda.current_device()
+
+    @ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream if stream else None)
+        except Exception:
+            return None
+
+    @ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+    def _release(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = lbhpde_allocator(_alloc, _release, None)
+    _torch_alloc_keep.append((a, _alloc, _release))
+    return a
+
+
+def _current_stream():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ----------------------------------------------------------------- handles
+
+class Solver:
+    """One periodic instance (lbhpde_create ... lbhpde_destroy)."""
+
+    def __init__(self, eq, N, dx, dt, tau, scheme=1, precision=FP64, stream=None, use_torch=True):
+        m, a, P = _eq_args(eq.alpha, eq.pi)
+        self._alloc = torch_allocator() if use_torch else None
+        st = stream if stream is not None else (_current_stream() if use_torch else None)
+        h = ctypes.c_void_p()
+        _check(lib().lbhpde_create(ctypes.byref(h), m, a, P, int(N), float(dx), float(dt), float(tau),
+                                   int(eq.lattice), int(scheme), int(precision), PERIODIC, st,
+                                   ctypes.byref(self._alloc) if self._alloc else None), "lbhpde_create")
+        self.h, self.N = h, int(N)
+
+    @classmethod
+    def for_problem(cls, p, precision=FP64, **kw):
+        return cls(p.eq, p.N, p.dx, p.dt, p.tau, scheme=p.scheme, precision=precision, **kw)
+
+    def set_kernel(self, kernel=KERNEL_AUTO, nodes_per_thread=0, steps_per_launch=0):
+        _check(lib().lbhpde_set_kernel(self.h, kernel, nodes_per_thread, steps_per_launch), "lbhpde_set_kernel")
+        return self
+
+    def set_phi(self, phi0):
+        if hasattr(phi0, "data_ptr"):
+            _check(lib().lbhpde_set_phi(self.h, ctypes.c_void_p(phi0.data_ptr()), 1), "lbhpde_set_phi")
+        else:
+            a = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64))
+            assert a.size == self.N
+            _check(lib().lbhpde_set_phi(self.h, a.ctypes.data_as(ctypes.c_void_p), 0), "lbhpde_set_phi")
+        return self
+
+    def step(self, nsteps):
+        _check(lib().lbhpde_step(self.h, int(nsteps)), "lbhpde_step")
+        return self
+
+    def read_phi(self, out=None, check=True):
+        if out is not None and hasattr(out, "data_ptr"):
+            rc = lib().lbhpde_read_phi(self.h, ctypes.c_void_p(out.data_ptr()), 1)
+        else:
+            out = np.empty(self.N)
+            rc = lib().lbhpde_read_phi(self.h, out.ctypes.data_as(ctypes.c_void_p), 0)
+        if check or rc != ERR_DIVERGED:
+            _check(rc, "lbhpde_read_phi")
+        return out
+
+    def diagnostics(self, phistar_device=None) -> dict:
+        d = lbhpde_diag()
+        ptr = ctypes.c_void_p(phistar_device.data_ptr()) if phistar_device is not None else None
+        rc = lib().lbhpde_diagnostics(self.h, ptr, ctypes.byref(d))
+        if rc not in (OK, ERR_DIVERGED):
+            _check(rc, "lbhpde_diagnostics")
+        return d.as_dict()
+
+    def model(self) -> lbhpde_model_info:
+        out = lbhpde_model_info()
+        _check(lib().lbhpde_get_model(self.h, ctypes.byref(out)), "lbhpde_get_model")
+        return out
+
+    def close(self):
+        if self.h:
+            lib().lbhpde_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many periodic instances stepped together (lbhpde_batch_*)."""
+
+    def __init__(self, problems, precision=FP32_DEV, stream=None, use_torch=True):
+        members = (lbhpde_instance * len(problems))(
+            *[make_instance(p.eq, p.N, p.dx, p.dt, p.tau, p.scheme) for p in problems])
+        self._alloc = torch_allocator() if use_torch else None
+        st = stream if stream is not None else (_current_stream() if use_torch else None)
+        h = ctypes.c_void_p()
+        _check(lib().lbhpde_batch_create(ctypes.byref(h), len(problems), members, int(precision), st,
+                                         ctypes.byref(self._alloc) if self._alloc else None), "lbhpde_batch_create")
+        self.h = h
+        self.sizes = [int(p.N) for p in problems]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.total = int(self.offsets[-1])
+
+    def set_kernel(self, kernel=KERNEL_AUTO, nodes_per_thread=0, steps_per_launch=0):
+        _check(lib().lbhpde_batch_set_kernel(self.h, kernel, nodes_per_thread, steps_per_launch),
+               "lbhpde_batch_set_kernel")
+        return self
+
+    def set_phi(self, phi0):
+        if hasattr(phi0, "data_ptr"):
+            _check(lib().lbhpde_batch_set_phi(self.h, ctypes.c_void_p(phi0.data_ptr()), 1), "lbhpde_batch_set_phi")
+        else:
+            a = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64))
+            assert a.size == self.total
+            _check(lib().lbhpde_batch_set_phi(self.h, a.ctypes.data_as(ctypes.c_void_p), 0), "lbhpde_batch_set_phi")
+        return self
+
+    def step(self, nsteps):
+        _check(lib().lbhpde_batch_step(self.h, int(nsteps)), "lbhpde_batch_step")
+        return self
+
+    def read_phi(self, out=None, check=True):
+        if out is not None and hasattr(out, "data_ptr"):
+            rc = lib().lbhpde_batch_read_phi(self.h, ctypes.c_void_p(out.data_ptr()), 1)
+        else:
+            out = np.empty(self.total)
+            rc = lib().lbhpde_batch_read_phi(self.h, out.ctypes.data_as(ctypes.c_void_p), 0)
+        if check or rc != ERR_DIVERGED:
+            _check(rc, "lbhpde_batch_read_phi")
+        return out
+
+    def split(self, flat):
+        return [flat[self.offsets[i]:self.offsets[i + 1]] for i in range(len(self.sizes))]
+
+    def diagnostics(self, phistar_device=None):
+        out = (lbhpde_diag * len(self.sizes))()
+        ptr = ctypes.c_void_p(phistar_device.data_ptr()) if phistar_device is not None else None
+        rc = lib().lbhpde_batch_diagnostics(self.h, ptr, out)
+        if rc not in (OK, ERR_DIVERGED):
+            _check(rc, "lbhpde_batch_diagnostics")
+        return [d.as_dict() for d in out]
+
+    def size(self):
+        n, b = ctypes.c_long(), ctypes.c_size_t()
+        _check(lib().lbhpde_batch_size(self.h, ctypes.byref(n), ctypes.byref(b)), "lbhpde_batch_size")
+        return n.value, b.value
+
+    def close(self):
+        if self.h:
+            lib().lbhpde_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

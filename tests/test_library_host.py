@@ -1,0 +1,154 @@
+"""Host-side checks of the CUDA library that need no GPU.
+
+* the shared library builds here (nvcc cross-compiles for sm_103a) and exports every entry
+  point that include/lbhpde.h declares, with the binding naming the same set;
+* step a0 (lbhpde_model, pure host code) agrees with the oracle: tau_k, beta_k, A_k0,
+  the inexact-recovery flag and f^eq_j(phi) at random phi;
+* the library's set-up, on its own, satisfies the dispersion pin of the oracle tests;
+* argument validation returns the documented status codes.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_0907_1720_gb300 import build as B
+from paper_0907_1720_gb300 import lbhpde as L
+from paper_0907_1720_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lbhpde.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbhpde_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 18
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(L.EXPORTED) == names
+
+
+EQUATIONS = [
+    ("kdv", W.kdv(), 1e-4, 1.3, 1),
+    ("kdv_s2", W.kdv(), 1e-4, 1.3, 2),
+    ("mkdv", W.mkdv(), 1e-4, 1.2, 1),
+    ("kdv_burgers", W.kdv_burgers(3.0, 0.07, 0.8), 1e-4, 1.15, 1),
+    ("k22", W.k22(), 1e-3, 1.6, 1),
+    ("ks", W.ks(), 1e-4, 1.3, 1),
+    ("gks_cubic_q7", W.gks_cubic(lattice=7), 1e-3, 1.4, 1),
+    ("kawahara", W.kawahara(), 1e-4, 2.02, 1),
+    ("kawahara_s2", W.kawahara(), 1e-3, 2.55, 2),
+    ("modified_kawahara", W.modified_kawahara(), 1e-2, 4.54, 1),
+    ("kdv_kawahara", W.kdv_kawahara(), 1e-3, 3.31, 1),
+    ("sixth", W.Equation("sixth", (1.0, 0.0, 0.5, 0.3, -1.0, 0.2),
+                         ((0, 0, 0.5), (), (0, 1), (0, 1), (0, 1), (0, 1))), 1e-3, 2.2, 1),
+]
+
+
+@pytest.mark.parametrize("name,eq,dt,tau,scheme", EQUATIONS, ids=[e[0] for e in EQUATIONS])
+def test_model_matches_oracle(lib, name, eq, dt, tau, scheme):
+    info = L.lbhpde_model(eq.alpha, eq.pi, 0.1, dt, tau, lattice=eq.lattice, scheme=scheme)
+    M = oracle.Model(eq.alpha, eq.pi, 0.1, dt, tau, lattice=eq.lattice, scheme=scheme)
+    assert info.b == M.b
+    assert bool(info.inexact) == M.inexact
+    assert np.allclose(list(info.tk)[2:], M.taus[2:], rtol=1e-14, atol=0)
+    assert np.allclose(list(info.beta), M.beta, rtol=1e-13, atol=0)
+    assert np.allclose(list(info.A), M.A, rtol=1e-12, atol=0)
+    feq, coef = L.model_coeffs(info)
+    rng = np.random.default_rng(3)
+    for phi in np.concatenate([rng.uniform(-1.5, 1.5, 20), [0.0, 1.0, -1.0]]):
+        want = M.feq(phi)
+        got = np.polynomial.polynomial.polyval(phi, feq.T)
+        scale = np.abs(want).max() + 1e-300
+        assert np.abs(got - want).max() <= 1e-13 * scale + 1e-300, phi
+        assert np.allclose(coef, feq / tau, rtol=1e-15, atol=0)
+
+
+@pytest.mark.parametrize("case", [c for c in __import__("test_oracle_pins").DISPERSION_CASES],
+                         ids=[c[0] for c in __import__("test_oracle_pins").DISPERSION_CASES])
+def test_model_dispersion_pin(lib, case):
+    """The library's own a0 set-up passes the recovered-equation pin (Eqs. (NPDE3)-(NPDE6))."""
+    from test_oracle_pins import E7, expected_dispersion
+    name, eq, dx, dt, tau, scheme, phibar, n_exact = case
+    info = L.lbhpde_model(eq.alpha, eq.pi, dx, dt, tau, lattice=eq.lattice, scheme=scheme)
+    feq, _ = L.model_coeffs(info)
+    b = info.b
+    dfeq = np.array([np.polynomial.polynomial.polyval(phibar, np.polynomial.polynomial.polyder(feq[j]))
+                     for j in range(b)])
+    w = 1.0 / tau
+    C = (1 - w) * np.eye(b) + w * np.outer(dfeq, np.ones(b))
+    r, Q = 1.0, 128
+    th = 2 * np.pi * np.arange(Q) / Q
+    g = []
+    for q in range(Q):
+        kap = r * np.exp(1j * th[q])
+        ev = np.linalg.eigvals(np.diag(np.exp(-1j * kap * E7[:b] * dx)) @ C)
+        g.append(np.log(ev[np.argmin(np.abs(ev - 1))]) / dt)
+    g = np.array(g)
+    a = np.array([np.mean(g * np.exp(-1j * n * th)) / r ** n for n in range(n_exact + 1)])
+    want = expected_dispersion(eq.alpha, eq.pi, phibar, n_exact)
+    assert np.all(np.abs(a - want) <= 1e-7 * (1 + np.abs(want)))
+
+
+def _pis(pi):
+    return (L.lbhpde_pi * len(pi))(*[L.make_pi(r) for r in pi])
+
+
+def test_model_argument_errors(lib):
+    eq = W.kdv_burgers(1.0, 0.05, 1.0)
+    info = L.lbhpde_model_info()
+    a = (ctypes.c_double * 3)(*eq.alpha)
+    P = _pis(eq.pi)
+    f = lib.lbhpde_model
+    assert f(3, a, P, 0.1, 1e-3, 1.3, 0, 1, ctypes.byref(info)) == L.OK
+    assert f(0, a, P, 0.1, 1e-3, 1.3, 0, 1, ctypes.byref(info)) == L.ERR_ARG
+    assert f(7, a, P, 0.1, 1e-3, 1.3, 0, 1, ctypes.byref(info)) == L.ERR_ARG
+    assert f(3, a, P, -0.1, 1e-3, 1.3, 0, 1, ctypes.byref(info)) == L.ERR_ARG
+    assert f(3, a, P, 0.1, float("nan"), 1.3, 0, 1, ctypes.byref(info)) == L.ERR_ARG
+    assert f(3, a, P, 0.1, 1e-3, 1.3, 6, 1, ctypes.byref(info)) == L.ERR_ARG
+    assert f(3, a, P, 0.1, 1e-3, 1.3, 0, 3, ctypes.byref(info)) == L.ERR_ARG
+    assert f(3, a, P, 0.1, 1e-3, 0.5, 0, 1, ctypes.byref(info)) == L.ERR_TAU_SINGULAR
+    assert f(3, a, P, 0.1, 1e-3, 0.5 + 3 ** 0.5 / 6, 0, 1, ctypes.byref(info)) == L.ERR_TAU_SINGULAR
+    ks = W.ks()
+    a4 = (ctypes.c_double * 4)(*ks.alpha)
+    assert f(4, a4, _pis(ks.pi), 0.1, 1e-3, 1.3, 0, 2, ctypes.byref(info)) == L.ERR_ARG  # scheme 2 needs m < b-1
+    assert f(3, a, P, 0.1, 1e-3, 1.3, 0, 1, None) == L.ERR_ARG
+    bad = L.lbhpde_pi()
+    bad.kind = 9
+    P2 = (L.lbhpde_pi * 3)(P[0], bad, P[2])
+    assert f(3, a, P2, 0.1, 1e-3, 1.3, 0, 1, ctypes.byref(info)) == L.ERR_ARG
+
+
+def test_degree_limit(lib):
+    """f^eq degree above 31 is rejected: Pi_1 = phi^7 on D1Q7 gives degree 6*6+1 = 37."""
+    eq = W.Equation("deg", (1.0, 0.0, 1.0, 0.0, 1.0), ((0,) * 7 + (1.0,), (), (0, 1), (), (0, 1)), lattice=7)
+    with pytest.raises(L.LbhpdeError) as ei:
+        L.lbhpde_model(eq.alpha, eq.pi, 0.1, 1e-3, 2.0, lattice=7)
+    assert ei.value.code == L.ERR_ARG
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
+    eq = W.kdv()
+    a = (ctypes.c_double * 3)(*eq.alpha)
+    P = _pis(eq.pi)
+    h = ctypes.c_void_p()
+    assert lib.lbhpde_create(None, 3, a, P, 100, 0.1, 1e-3, 1.3, 0, 1, L.FP64, 0, None, None) == L.ERR_ARG
+    assert lib.lbhpde_create(ctypes.byref(h), 3, a, P, 100, 0.1, 1e-3, 1.3, 0, 1, L.FP64, 1, None, None) == \
+        L.ERR_UNSUPPORTED
+    assert lib.lbhpde_step(None, 1) == L.ERR_ARG
+    assert lib.lbhpde_destroy(None) == L.ERR_ARG
+    assert lib.lbhpde_strerror(L.ERR_DIVERGED).decode().startswith("non-finite")
