@@ -1,0 +1,412 @@
+"""Benchmark of the LBGK hot path on GB300 (one JSON line on stdout).
+
+Default workload: the batched ensemble of 4096 independent KdV-Burgers problems
+u_t + a u u_x - b u_xx + d u_xxx = 0 (N ~ U{256..8192}, a ~ U[1,6], b ~ U[0,0.1],
+d ~ U[0.5,1], single-soliton initial profiles with c ~ U[1,4], seed-fixed), D1Q5 scheme 1,
+dx = 0.1, dt = 1e-4, tau = 1.15, 1000 time steps, FP32 deviation storage, one launch.
+
+One benchmark step = one pass of the whole hot path over the batch: initialisation from
+the device-resident initial profiles (a1), 1000 collide+stream steps (a2-a6) and the FP64
+diagnostics reduction (a7).  The model set-up (a0) happens once, at batch creation.
+``value`` is lattice node-updates per second over all ranks.
+
+--workload long_grid: the 2^24-node Kawahara grid (D1Q7, 1000 steps) on the streaming kernel.
+--impl reference: the CPU oracle timed on the host cores on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_0907_1720_gb300 import workloads as W  # noqa: E402
+
+METRIC = "lattice-node updates/s (FP32 batched vs FP64 plain) at stated L2 error; p99 solve latency"
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# FP32 lanes per SM and SM count of GB300: the ALU roof of the on-chip kernel.
+SMS, FP32_LANES = 152, 128
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples (200 ms) while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def ensemble_problems(rank=0):
+    return W.kdv_burgers_ensemble(seed=W.SEED + rank)
+
+
+def flops_per_node_update(b, D):
+    """Algorithmic FP operations of one node-update in the kernels' formulation: per moving
+    population one Horner polynomial of degree D plus the relaxation (D + 1 multiply-adds,
+    2 flops each) and the flux-difference update of phi (one subtract, one add)."""
+    return (b - 1) * (2 * (D + 1) + 2)
+
+
+def bytes_per_node_update(b, esz):
+    """One read and one write of the b stored rows (phi and b-1 populations)."""
+    return 2 * b * esz
+
+
+# ----------------------------------------------------------------------- ours
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_0907_1720_gb300 import lbhpde as L
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    peaks, peak_src = load_peaks()
+
+    with torch.cuda.stream(stream):
+        if args.workload == "ensemble":
+            probs = ensemble_problems(rank)
+            nsteps = W.ENSEMBLE_STEPS
+            prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
+            solver = L.Batch(probs, precision=prec)
+            workload = (f"kdv_burgers_ensemble_4096: 4096 x N~U{{256..8192}} (sum N = {sum(p.N for p in probs)}), "
+                        f"D1Q5 scheme 1, dx={W.ENSEMBLE_DX}, dt={W.ENSEMBLE_DT}, tau={W.ENSEMBLE_TAU}, "
+                        f"{nsteps} steps per benchmark step")
+        else:
+            p = W.long_grid_config(nsteps=1000)
+            probs = [p]
+            nsteps = p.nsteps
+            prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
+            solver = L.Batch(probs, precision=prec)
+            workload = (f"kawahara_long_grid: N=2^24, D1Q7 scheme 1, dx=0.1, dt=1e-4, tau=2.02, "
+                        f"{nsteps} steps per benchmark step (streaming kernel)")
+        total = sum(p.N for p in probs)
+        b = 5 if args.workload == "ensemble" else 7
+        esz = 4 if prec == L.FP32_DEV else 8
+        D = solver_model_degree(L, probs)
+        phi0_h = np.concatenate([p.phi0 for p in probs])
+        phi0_d = torch.tensor(phi0_h, device="cuda", dtype=torch.float64)
+        pinned_in = torch.empty(total, dtype=torch.float64, pin_memory=True)
+        pinned_in.numpy()[:] = phi0_h
+        pinned_out = torch.empty(total, dtype=torch.float64, pin_memory=True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+        def one_step(record=None):
+            solver.set_phi(phi0_d)
+            if record is not None:
+                record[0].record(stream)
+            solver.step(nsteps)
+            if record is not None:
+                record[1].record(stream)
+            return solver.diagnostics()
+
+        for _ in range(args.warmup):
+            one_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        kernel_ms = []
+        with ClockSampler(dev) as clk:
+            torch.cuda.synchronize()
+            ev[2].record(stream)
+            for _ in range(args.steps):
+                rec = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+                diag = one_step(rec)
+                kernel_ms.append(rec)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+        total_ms = ev[2].elapsed_time(ev[3])
+        kern = [a.elapsed_time(c) for a, c in kernel_ms]
+        t_local = total_ms / 1e3
+        if world > 1:
+            t = torch.tensor([t_local], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_max = float(t.item())
+        else:
+            t_max = t_local
+        upd_step = total * nsteps
+        value = world * upd_step * args.steps / t_max
+
+        # accuracy beside the number: members against the FP64 path (ensemble) or the exact
+        # solution (long grid)
+        accuracy = accuracy_report(L, args, probs, solver, prec, torch)
+
+        # end to end through the public API, host buffers
+        e2e_steps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            solver.set_phi(pinned_in)  # host pointer (pinned): copied inside the call
+            solver.step(nsteps)
+            solver.read_phi(pinned_out.numpy())
+        t_e2e = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world * upd_step / t_e2e, "unit": "node-updates/s",
+               "h2d_bytes_per_step": total * 8, "d2h_bytes_per_step": total * 8}
+
+        # FP64 plain path on the same workload (fewer steps: it is ALU bound on GB300)
+        fp64 = None
+        if args.workload == "ensemble" and prec == L.FP32_DEV and not args.no_fp64:
+            fp64 = fp64_plain(L, probs, phi0_d, nsteps, stream, torch, steps=max(1, min(args.steps, 2)))
+
+        kern_ms = float(np.mean(kern))
+        clocks = clk.summary()
+        if args.workload == "ensemble":
+            fl = flops_per_node_update(b, D)
+            sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+            peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+            achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tf, "traffic": None, "kernel": "k_onchip<float,5,K>",
+                    "flops_per_node_update": fl,
+                    "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock under load"}
+        else:
+            by = bytes_per_node_update(b, esz)
+            achieved = by * upd_step / (kern_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_stream",
+                    "bytes_per_node_update": by, "peak_source": peak_src}
+        launches_per_step = 1 + 1 + 2  # init, on-chip (or 1000 stream launches), diagnostics x2
+        if args.workload != "ensemble":
+            launches_per_step = 1 + nsteps + 2
+        line = {
+            "metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == L.FP32_DEV else "f64", "data": "synthetic (seeded, shaped like the paper's test problems)",
+            "config": {"workload": workload, "node_updates_per_step": upd_step, "precision": args.precision,
+                       "l2": f"inputs larger than L2: state {2 * total * b * esz / 2**20:.0f} MiB (two buffers)",
+                       "parallelism": f"replicas x{world} (independent ensembles)"},
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "kernel_ms_per_step": kern_ms, "accuracy": accuracy,
+        }
+        if fp64 is not None:
+            line["fp64_plain"] = fp64
+        solver.close()
+    return line
+
+
+def solver_model_degree(L, probs):
+    D = 0
+    for p in probs[:64]:
+        info = L.lbhpde_model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, lattice=p.eq.lattice, scheme=p.scheme)
+        D = max(D, info.D)
+    return D
+
+
+def fp64_plain(L, probs, phi0_d, nsteps, stream, torch, steps=2):
+    s = L.Batch(probs, precision=L.FP64).set_kernel(L.KERNEL_STREAM)
+    s.set_phi(phi0_d)
+    s.step(5)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        s.set_phi(phi0_d)
+        s.step(nsteps)
+        s.diagnostics()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    total = sum(p.N for p in probs)
+    s.close()
+    return {"value": total * nsteps / (ms / 1e3), "unit": "node-updates/s", "ms_per_step": ms,
+            "kernel": "k_stream<double,5,5> (one fused collide+stream launch per time step, HBM)"}
+
+
+def accuracy_report(L, args, probs, solver, prec, torch):
+    import oracle as _  # noqa: F401  (not used here; accuracy vs the oracle lives in the tests)
+    out = {}
+    if args.workload == "ensemble":
+        # FP32 members against the FP64 path on the same inputs (normwise, max over 8 members)
+        idx = list(range(0, len(probs), max(1, len(probs) // 8)))[:8]
+        sub = [probs[i] for i in idx]
+        phi0 = np.concatenate([p.phi0 for p in sub])
+        res = {}
+        for pr in (L.FP64, prec):
+            bt = L.Batch(sub, precision=pr)
+            bt.set_phi(phi0).step(W.ENSEMBLE_STEPS)
+            res[pr] = bt.split(bt.read_phi())
+            bt.close()
+        errs = [float(np.abs(a - c).max() / np.abs(c).max()) for a, c in zip(res[prec], res[L.FP64])]
+        out["fp32_vs_fp64_normwise_max"] = max(errs)
+        out["members_checked"] = len(sub)
+    else:
+        p = probs[0]
+        ex = torch.tensor(p.exact(p.nsteps * p.dt), device="cuda", dtype=torch.float64)
+        solver.set_phi(torch.tensor(p.phi0, device="cuda", dtype=torch.float64)).step(p.nsteps)
+        d = solver.diagnostics(ex)[0]
+        out["E_vs_exact"] = d["err_E"]
+        out["L2_vs_exact"] = d["err_L2"]
+    return out
+
+
+# ------------------------------------------------------------ oracle on the CPU
+
+def cpu_oracle_rate(args, budget_s=15.0):
+    """Oracle node-updates/s on the host cores: one member per thread (ctypes releases the
+    GIL), on a bounded sample of the same workload."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+
+    cores = os.cpu_count() or 1
+    if args.workload == "ensemble":
+        probs = ensemble_problems(0)[: 2 * cores]
+        per_member = 20
+        # calibrate the step count so the sample takes about budget_s
+        t0 = time.perf_counter()
+        oracle.run_problem(probs[0], nsteps=per_member)
+        dt1 = time.perf_counter() - t0
+        steps = max(per_member, int(budget_s * cores / (len(probs) * dt1 / per_member) / 1.0))
+        steps = min(steps, W.ENSEMBLE_STEPS)
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(cores) as ex:
+            list(ex.map(lambda p: oracle.run_problem(p, nsteps=steps), probs))
+        el = time.perf_counter() - t0
+        upd = sum(p.N for p in probs) * steps
+        sample = f"{len(probs)} ensemble members x {steps} steps, one member per thread"
+    else:
+        p = W.long_grid_config(nsteps=1)
+        steps = 1
+        t0 = time.perf_counter()
+        oracle.run_problem(p, nsteps=steps)
+        el = time.perf_counter() - t0
+        upd = p.N * steps
+        cores = 1
+        sample = "2^24-node Kawahara grid x 1 step, single thread"
+    return {"value": upd / el, "unit": "node-updates/s", "cores": cores, "kind": "oracle", "sample": sample,
+            "seconds": el}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle as it stands, on the host cores, bounded sample."""
+    cores = os.cpu_count() or 1
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_rate(args, budget_s=2.0)
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_rate(args, budget_s=8.0))
+    v = float(np.median([r["value"] for r in vals]))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "node-updates/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean([r["seconds"] for r in vals])) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": vals[-1]["sample"]},
+            "cpu_baseline": {"value": v, "unit": "node-updates/s", "cores": vals[-1]["cores"], "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": "node-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "long_grid"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.warmup < 3:
+        args.warmup = 3
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args)), flush=True)
+        return
+
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    # the CPU baseline runs before any GPU work so no thread pool is forked after CUDA starts
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_oracle_rate(args)
+    from paper_0907_1720_gb300 import build as B
+
+    B.build()
+    line = run_ours(args, rank, world)
+    if cpu is not None:
+        line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

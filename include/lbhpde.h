@@ -60,9 +60,14 @@ extern "C" {
 #define LBHPDE_PI_NCOEF 8
 #define LBHPDE_MAX_DEG 31  /* highest degree of f^eq_j(phi) the kernels accept */
 
-#define LBHPDE_KERNEL_AUTO 0    /* choose per instance                                     */
-#define LBHPDE_KERNEL_STREAM 1  /* one fused collide+stream launch per step through HBM    */
-#define LBHPDE_KERNEL_ONCHIP 2  /* whole instance resident on one SM for many steps        */
+#define LBHPDE_KERNEL_AUTO 0    /* the on-chip kernel (ONCHIP)                                 */
+#define LBHPDE_KERNEL_STREAM 1  /* one fused collide+stream launch per step through HBM        */
+#define LBHPDE_KERNEL_ONCHIP 2  /* instances that fit one CTA stay resident in registers for   */
+                                /* all steps; longer ones advance in temporally blocked        */
+                                /* windows (HALO)                                              */
+#define LBHPDE_KERNEL_HALO 3    /* every instance in temporally blocked windows: a CTA loads a */
+                                /* window plus a halo from HBM, advances it several steps in   */
+                                /* registers and writes back the exact middle                  */
 
 /* One flux function Pi_k of Eq. (NPDE): the paper requires "known differential
  * functions of phi"; this library takes polynomials in phi (every worked class of
@@ -157,9 +162,11 @@ typedef struct {
 /* phistar: [N] doubles in device memory, or NULL.  Synchronises the stream. */
 int lbhpde_diagnostics(lbhpde_t h, const double *phistar_device, lbhpde_diag *out);
 
-/* Which kernel lbhpde_step uses (LBHPDE_KERNEL_*), and for the on-chip kernel the nodes per
- * thread and the steps per launch (0 = automatic).  Returns LBHPDE_ERR_UNSUPPORTED when the
- * instance does not fit the requested kernel. */
+/* Which kernel lbhpde_step uses (LBHPDE_KERNEL_*).  For the on-chip kernels: the nodes each
+ * thread holds (FP32: 2, 4 or 8 on D1Q5, 4 or 8 on D1Q7; FP64: 2 or 4 on D1Q5, 4 on D1Q7) and
+ * the steps per launch (resident instances: launch chunk; windows: steps per window, which
+ * sets the halo to steps * max|e| nodes); 0 = automatic.  Returns LBHPDE_ERR_UNSUPPORTED for a
+ * combination the library was not built with, leaving the previous choice in place. */
 int lbhpde_set_kernel(lbhpde_t h, int kernel, int nodes_per_thread, int steps_per_launch);
 
 int lbhpde_get_model(lbhpde_t h, lbhpde_model_info *out);

@@ -47,12 +47,16 @@ struct Group {
     std::vector<int2> blocks_h;
     int2 *blocks = nullptr;
     long long *blk_off = nullptr;  // per block: offset of its member in a concatenated phi array
-    // on-chip plan
-    bool onchip_ok = false;
-    int K = 0, maxt = 0, nthreads = 0, max_inst = 0, ncta = 0;
-    size_t smem = 0;
-    OnchipInst *insts = nullptr;
-    int *cta_first = nullptr;
+    // on-chip plans: whole instances resident for all steps (ring) and temporally blocked
+    // windows for instances longer than one CTA holds (halo)
+    bool onchip_ok = false;  // false: every member uses the streaming kernel
+    struct Plan {
+        int ncta = 0, nthreads = 0, max_inst = 0;
+        size_t smem = 0;
+        OnchipInst *insts = nullptr;
+        int *cta_first = nullptr;
+    } ring, halo;
+    int K = 0, maxt = 0, tblk = 0;
 };
 
 }  // namespace
@@ -62,7 +66,6 @@ struct lbhpde_batch_s {
     size_t esz = 8;
     int count = 0;
     cudaStream_t stream = nullptr;
-    bool own_stream = false;
     bool has_alloc = false;
     lbhpde_allocator alloc{};
     std::vector<lbhpde_model_info> mi;
@@ -117,7 +120,7 @@ struct lbhpde_batch_s {
         return LBHPDE_OK;
     }
     void free_all() {
-        if (stream) cudaStreamSynchronize(stream);
+        cudaStreamSynchronize(stream);
         for (auto &a : allocations) {
             if (has_alloc)
                 alloc.release(a.first, a.second, (void *)stream, alloc.user);
@@ -125,7 +128,6 @@ struct lbhpde_batch_s {
                 cudaFree(a.first);
         }
         allocations.clear();
-        if (own_stream && stream) cudaStreamDestroy(stream);
         stream = nullptr;
     }
 };
@@ -147,36 +149,53 @@ int onchip_maxt(size_t esz, int b, int K) {
 }
 int default_K(size_t esz, int b) { return esz == 4 && b == 5 ? 8 : 4; }
 
-template <typename T, int B, int K, int MAXT>
-int launch_onchip_t(lbhpde_batch_s *bt, Group &g, int nsteps) {
-    auto fn = lbk::k_onchip<T, B, K, MAXT>;
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem));
-    fn<<<g.ncta, g.nthreads, g.smem, bt->stream>>>((T *)bt->st[bt->cur], g.insts, g.cta_first,
-                                                    (const T *)bt->coefT, nsteps, g.max_inst);
+template <typename T, int B, int K, int MAXT, bool HALO>
+int launch_onchip_t(lbhpde_batch_s *bt, Group::Plan &pl, const void *in, void *out, int nsteps) {
+    auto fn = lbk::k_onchip<T, B, K, MAXT, HALO>;
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+    fn<<<pl.ncta, pl.nthreads, pl.smem, bt->stream>>>((const T *)in, (T *)out, pl.insts, pl.cta_first,
+                                                       (const T *)bt->coefT, nsteps, pl.max_inst);
     CK(cudaGetLastError());
     return LBHPDE_OK;
 }
 
-template <typename T, int B>
-int launch_onchip_b(lbhpde_batch_s *bt, Group &g, int nsteps) {
+template <typename T, int B, bool HALO>
+int launch_onchip_b(lbhpde_batch_s *bt, Group &g, Group::Plan &pl, const void *in, void *out, int nsteps) {
     if constexpr (sizeof(T) == 4) {
         if constexpr (B == 5) {
-            if (g.K == 8) return launch_onchip_t<T, B, 8, 512>(bt, g, nsteps);
-            if (g.K == 4) return launch_onchip_t<T, B, 4, 1024>(bt, g, nsteps);
-            if (g.K == 2) return launch_onchip_t<T, B, 2, 1024>(bt, g, nsteps);
+            if (g.K == 8) return launch_onchip_t<T, B, 8, 512, HALO>(bt, pl, in, out, nsteps);
+            if (g.K == 4) return launch_onchip_t<T, B, 4, 1024, HALO>(bt, pl, in, out, nsteps);
+            if (g.K == 2) return launch_onchip_t<T, B, 2, 1024, HALO>(bt, pl, in, out, nsteps);
         } else {
-            if (g.K == 8) return launch_onchip_t<T, B, 8, 256>(bt, g, nsteps);
-            if (g.K == 4) return launch_onchip_t<T, B, 4, 512>(bt, g, nsteps);
+            if (g.K == 8) return launch_onchip_t<T, B, 8, 256, HALO>(bt, pl, in, out, nsteps);
+            if (g.K == 4) return launch_onchip_t<T, B, 4, 512, HALO>(bt, pl, in, out, nsteps);
         }
     } else {
         if constexpr (B == 5) {
-            if (g.K == 4) return launch_onchip_t<T, B, 4, 512>(bt, g, nsteps);
-            if (g.K == 2) return launch_onchip_t<T, B, 2, 1024>(bt, g, nsteps);
+            if (g.K == 4) return launch_onchip_t<T, B, 4, 512, HALO>(bt, pl, in, out, nsteps);
+            if (g.K == 2) return launch_onchip_t<T, B, 2, 1024, HALO>(bt, pl, in, out, nsteps);
         } else {
-            if (g.K == 4) return launch_onchip_t<T, B, 4, 256>(bt, g, nsteps);
+            if (g.K == 4) return launch_onchip_t<T, B, 4, 256, HALO>(bt, pl, in, out, nsteps);
         }
     }
     return LBHPDE_ERR_UNSUPPORTED;
+}
+
+int launch_onchip(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *out, int nsteps) {
+    Group::Plan &pl = halo ? g.halo : g.ring;
+    if (pl.ncta == 0) return LBHPDE_OK;
+    if (bt->esz == 4) {
+        if (g.b == 5)
+            return halo ? launch_onchip_b<float, 5, true>(bt, g, pl, in, out, nsteps)
+                        : launch_onchip_b<float, 5, false>(bt, g, pl, in, out, nsteps);
+        return halo ? launch_onchip_b<float, 7, true>(bt, g, pl, in, out, nsteps)
+                    : launch_onchip_b<float, 7, false>(bt, g, pl, in, out, nsteps);
+    }
+    if (g.b == 5)
+        return halo ? launch_onchip_b<double, 5, true>(bt, g, pl, in, out, nsteps)
+                    : launch_onchip_b<double, 5, false>(bt, g, pl, in, out, nsteps);
+    return halo ? launch_onchip_b<double, 7, true>(bt, g, pl, in, out, nsteps)
+                : launch_onchip_b<double, 7, false>(bt, g, pl, in, out, nsteps);
 }
 
 template <typename T, int B>
@@ -197,29 +216,44 @@ int launch_stream_b(lbhpde_batch_s *bt, Group &g) {
     return LBHPDE_OK;
 }
 
-// Pack a group's instances onto CTAs for the on-chip kernel (first fit, largest first,
-// warp-aligned thread ranges, at most 32 instances per CTA).
-int plan_onchip(lbhpde_batch_s *bt, Group &g, int K) {
+// Steps per halo launch: the halo H = tblk * max|e| must leave most of a window valid.
+int default_tblk(int capacity, int W) {
+    int t = 64;
+    while (t > 1 && capacity - 2 * t * W < capacity * 3 / 4) t /= 2;
+    return t;
+}
+
+// Pack a group's instances for the on-chip kernel: members that fit one CTA become ring
+// instances (first fit, largest first, warp-aligned thread runs, at most 32 per CTA); longer
+// members are cut into halo windows, one per CTA.
+int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) {
     g.onchip_ok = false;
     const int maxt = onchip_maxt(bt->esz, g.b, K);
     if (maxt == 0 || K < lbk::wmax(g.b)) return LBHPDE_ERR_UNSUPPORTED;
-    for (int i : g.members)
-        if (bt->N[i] > (long long)maxt * K) return LBHPDE_ERR_UNSUPPORTED;
-    std::vector<int> order = g.members;
-    auto thr = [&](int i) { return (int)((bt->N[i] + K - 1) / K); };
-    auto pad = [&](int i) { return (thr(i) + 31) & ~31; };
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return pad(a) > pad(c); });
+    const int W = lbk::wmax(g.b);
+    const int cap = maxt * K;
+    if (tblk <= 0) tblk = default_tblk(cap, W);
+    const int H = tblk * W;
+    if (cap - 2 * H < 32) return LBHPDE_ERR_UNSUPPORTED;
+    const int ne = lbk::nedge(g.b);
+    auto thr = [&](long long n) { return (int)((n + K - 1) / K); };
+    auto pad = [&](long long n) { return (thr(n) + 31) & ~31; };
+
+    // ---- ring instances
+    std::vector<int> ring, halo;
+    for (int i : g.members) (bt->N[i] <= cap && !force_halo ? ring : halo).push_back(i);
+    std::stable_sort(ring.begin(), ring.end(), [&](int a, int c) { return pad(bt->N[a]) > pad(bt->N[c]); });
     struct Cta {
         int used = 0;
         std::vector<int> inst;
     };
     std::vector<Cta> ctas;
-    for (int i : order) {
+    for (int i : ring) {
         bool placed = false;
         for (auto &c : ctas) {
-            if (c.used + pad(i) <= maxt && (int)c.inst.size() < 32) {
+            if (c.used + pad(bt->N[i]) <= maxt && (int)c.inst.size() < 32) {
                 c.inst.push_back(i);
-                c.used += pad(i);
+                c.used += pad(bt->N[i]);
                 placed = true;
                 break;
             }
@@ -227,49 +261,100 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K) {
         if (!placed) {
             Cta c;
             c.inst.push_back(i);
-            c.used = pad(i);
+            c.used = pad(bt->N[i]);
             ctas.push_back(c);
         }
     }
-    std::vector<OnchipInst> insts;
-    std::vector<int> first;
-    int nthreads = 32, max_inst = 1;
-    size_t coef_max = 0;
-    for (auto &c : ctas) {
-        first.push_back((int)insts.size());
-        int tb = 0, sco = 0, il = 0;
-        for (int i : c.inst) {
-            const Seg &s = bt->segs_h[i];
-            OnchipInst I{};
-            I.off = s.off;
-            I.ld = s.ld;
-            I.N = s.N;
-            I.D = s.D;
-            I.gcoef = s.coef;
-            I.scoef = sco;
-            I.tbase = tb;
-            I.nthr = thr(i);
-            I.il = il++;
-            insts.push_back(I);
-            sco += (g.b - 1) * (s.D + 1) + 1;
-            tb += pad(i);
+    {
+        std::vector<OnchipInst> insts;
+        std::vector<int> first;
+        int nthreads = 32, max_inst = 1;
+        size_t coef_max = 0;
+        for (auto &c : ctas) {
+            first.push_back((int)insts.size());
+            int tb = 0, sco = 0, il = 0;
+            for (int i : c.inst) {
+                const Seg &s = bt->segs_h[i];
+                OnchipInst I{};
+                I.off = s.off;
+                I.ld = s.ld;
+                I.N = s.N;
+                I.D = s.D;
+                I.gcoef = s.coef;
+                I.scoef = sco;
+                I.tbase = tb;
+                I.nthr = thr(s.N);
+                I.il = il++;
+                I.x0 = 0;
+                I.npos = s.N;
+                I.vlo = 0;
+                I.vhi = s.N;
+                insts.push_back(I);
+                sco += (g.b - 1) * (s.D + 1) + 1;
+                tb += pad(s.N);
+            }
+            nthreads = std::max(nthreads, tb);
+            max_inst = std::max(max_inst, (int)c.inst.size());
+            coef_max = std::max(coef_max, (size_t)sco);
         }
-        nthreads = std::max(nthreads, tb);
-        max_inst = std::max(max_inst, (int)c.inst.size());
-        coef_max = std::max(coef_max, (size_t)sco);
+        first.push_back((int)insts.size());
+        Group::Plan &pl = g.ring;
+        pl = Group::Plan{};
+        if (!ctas.empty()) {
+            pl.smem = (size_t(4) * ne * nthreads + size_t(2) * ne * max_inst + size_t(2) * (g.b - 1) * K * max_inst +
+                       coef_max) * bt->esz;
+            if (pl.smem > 227 * 1024) return LBHPDE_ERR_UNSUPPORTED;
+            RC(bt->upload(&pl.insts, insts));
+            RC(bt->upload(&pl.cta_first, first));
+            pl.ncta = (int)ctas.size();
+            pl.nthreads = nthreads;
+            pl.max_inst = max_inst;
+        }
     }
-    first.push_back((int)insts.size());
-    const int ne = lbk::nedge(g.b);
-    size_t smem = (size_t(4) * ne * nthreads + size_t(2) * ne * max_inst + coef_max) * bt->esz;
-    if (smem > 227 * 1024) return LBHPDE_ERR_UNSUPPORTED;
-    RC(bt->upload(&g.insts, insts));
-    RC(bt->upload(&g.cta_first, first));
+    // ---- halo windows (valid width cap - 2H)
+    {
+        const int valid = cap - 2 * H;
+        std::vector<OnchipInst> insts;
+        std::vector<int> first;
+        size_t coef_max = 0;
+        for (int i : halo) {
+            const Seg &s = bt->segs_h[i];
+            for (long long x = 0; x < s.N; x += valid) {
+                const int v = (int)std::min<long long>(valid, s.N - x);
+                OnchipInst I{};
+                I.off = s.off;
+                I.ld = s.ld;
+                I.N = s.N;
+                I.D = s.D;
+                I.gcoef = s.coef;
+                I.scoef = 0;
+                I.tbase = 0;
+                I.npos = v + 2 * H;
+                I.nthr = thr(I.npos);
+                I.il = 0;
+                I.x0 = (int)(x - H);
+                I.vlo = H;
+                I.vhi = H + v;
+                first.push_back((int)insts.size());
+                insts.push_back(I);
+                coef_max = std::max(coef_max, (size_t)((g.b - 1) * (s.D + 1) + 1));
+            }
+        }
+        first.push_back((int)insts.size());
+        Group::Plan &pl = g.halo;
+        pl = Group::Plan{};
+        if (!insts.empty()) {
+            pl.nthreads = maxt;
+            pl.max_inst = 1;
+            pl.smem = (size_t(4) * ne * maxt + coef_max) * bt->esz;
+            RC(bt->upload(&pl.insts, insts));
+            RC(bt->upload(&pl.cta_first, first));
+            pl.ncta = (int)insts.size();
+        }
+    }
     g.K = K;
     g.maxt = maxt;
-    g.nthreads = nthreads;
-    g.max_inst = max_inst;
-    g.ncta = (int)ctas.size();
-    g.smem = smem;
+    g.tblk = tblk;
     g.onchip_ok = true;
     return LBHPDE_OK;
 }
@@ -371,8 +456,8 @@ int choose_kernels(lbhpde_batch_s *bt) {
         g.onchip_ok = false;
         if (bt->kernel == LBHPDE_KERNEL_STREAM) continue;
         const int K = bt->K_req > 0 ? bt->K_req : default_K(bt->esz, g.b);
-        int rc = plan_onchip(bt, g, K);
-        if (rc != LBHPDE_OK && bt->kernel == LBHPDE_KERNEL_ONCHIP) return rc;
+        int rc = plan_onchip(bt, g, K, bt->spl_req, bt->kernel == LBHPDE_KERNEL_HALO);
+        if (rc != LBHPDE_OK) return rc;
     }
     return LBHPDE_OK;
 }
@@ -381,45 +466,54 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
     if (nsteps < 0) return LBHPDE_ERR_ARG;
     if (!bt->initialised) return LBHPDE_ERR_ARG;
     if (nsteps == 0) return LBHPDE_OK;
-    // on-chip groups: state stays in st[cur]; streaming groups ping-pong.  When both kinds
-    // are present the on-chip group's rows are copied along with each stream step.
-    bool any_stream = false;
-    for (auto &g : bt->groups)
-        if (!g.members.empty() && !g.onchip_ok) any_stream = true;
+    bool any_stream = false, any_halo = false;
     for (auto &g : bt->groups) {
-        if (g.members.empty() || !g.onchip_ok) continue;
-        long left = nsteps;
-        const long spl = bt->spl_req > 0 ? bt->spl_req : (1L << 30);
-        while (left > 0) {
-            const int n = (int)std::min(left, spl);
-            int rc = bt->esz == 4 ? (g.b == 5 ? launch_onchip_b<float, 5>(bt, g, n) : launch_onchip_b<float, 7>(bt, g, n))
-                                  : (g.b == 5 ? launch_onchip_b<double, 5>(bt, g, n) : launch_onchip_b<double, 7>(bt, g, n));
-            RC(rc);
-            left -= n;
-        }
+        if (g.members.empty()) continue;
+        if (!g.onchip_ok) any_stream = true;
+        else if (g.halo.ncta) any_halo = true;
     }
     if (any_stream) {
+        // one fused collide+stream launch per step, ping-pong buffers
         for (long s = 0; s < nsteps; ++s) {
             for (auto &g : bt->groups) {
-                if (g.members.empty() || g.onchip_ok) continue;
+                if (g.members.empty()) continue;
                 int rc = bt->esz == 4 ? (g.b == 5 ? launch_stream_b<float, 5>(bt, g) : launch_stream_b<float, 7>(bt, g))
                                       : (g.b == 5 ? launch_stream_b<double, 5>(bt, g) : launch_stream_b<double, 7>(bt, g));
                 RC(rc);
             }
-            // keep on-chip members' rows valid in the buffer that becomes current
-            for (auto &g : bt->groups) {
-                if (g.members.empty() || !g.onchip_ok) continue;
-                for (int i : g.members) {
-                    const Seg &s = bt->segs_h[i];
-                    const size_t bytes = size_t(s.ld) * bt->mi[i].b * bt->esz;
-                    const size_t o = size_t(s.off) * bt->esz;
-                    CK(cudaMemcpyAsync((char *)bt->st[bt->cur ^ 1] + o, (char *)bt->st[bt->cur] + o, bytes,
-                                       cudaMemcpyDeviceToDevice, bt->stream));
-                }
-            }
             bt->cur ^= 1;
         }
+        bt->steps += nsteps;
+        return LBHPDE_OK;
     }
+    // halo windows advance tblk steps per launch through the ping-pong buffers; ring instances
+    // read the current buffer once and write the buffer the halo launches end in
+    int tb = 1 << 30;
+    for (auto &g : bt->groups)
+        if (!g.members.empty() && g.halo.ncta) tb = std::min(tb, g.tblk);
+    const long nchunks = any_halo ? (nsteps + tb - 1) / tb : 0;
+    const int cur0 = bt->cur, cur1 = bt->cur ^ (int)(nchunks & 1);
+    for (auto &g : bt->groups) {
+        if (g.members.empty() || !g.ring.ncta) continue;
+        const long spl = bt->spl_req > 0 ? bt->spl_req : (1L << 30);
+        long left = nsteps;
+        bool firstl = true;
+        while (left > 0) {
+            const int n = (int)std::min(left, spl);
+            RC(launch_onchip(bt, g, false, bt->st[firstl ? cur0 : cur1], bt->st[cur1], n));
+            firstl = false;
+            left -= n;
+        }
+    }
+    long left = nsteps;
+    for (long c = 0; c < nchunks; ++c) {
+        const int n = (int)std::min<long>(left, tb);
+        for (auto &g : bt->groups)
+            if (!g.members.empty() && g.halo.ncta) RC(launch_onchip(bt, g, true, bt->st[bt->cur], bt->st[bt->cur ^ 1], n));
+        bt->cur ^= 1;
+        left -= n;
+    }
+    bt->cur = cur1;
     bt->steps += nsteps;
     return LBHPDE_OK;
 }
@@ -524,16 +618,7 @@ int batch_create(lbhpde_batch_s **out, int count, const lbhpde_instance *members
         bt->has_alloc = true;
         bt->alloc = *alloc;
     }
-    if (stream) {
-        bt->stream = (cudaStream_t)stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            (void)cudaGetLastError();
-            delete bt;
-            return LBHPDE_ERR_CUDA;
-        }
-        bt->own_stream = true;
-    }
+    bt->stream = (cudaStream_t)stream;  // NULL: the legacy default stream
     int rc = batch_build(bt, count, members);
     if (rc == LBHPDE_OK) rc = choose_kernels(bt);
     if (rc == LBHPDE_OK && cudaStreamSynchronize(bt->stream) != cudaSuccess) rc = LBHPDE_ERR_CUDA;
@@ -581,7 +666,7 @@ extern "C" int lbhpde_batch_diagnostics(lbhpde_batch_t b, const double *phistar,
     return b ? batch_diag(b, phistar, out) : LBHPDE_ERR_ARG;
 }
 extern "C" int lbhpde_batch_set_kernel(lbhpde_batch_t b, int kernel, int nodes_per_thread, int steps_per_launch) {
-    if (!b || kernel < LBHPDE_KERNEL_AUTO || kernel > LBHPDE_KERNEL_ONCHIP || nodes_per_thread < 0 ||
+    if (!b || kernel < LBHPDE_KERNEL_AUTO || kernel > LBHPDE_KERNEL_HALO || nodes_per_thread < 0 ||
         steps_per_launch < 0)
         return LBHPDE_ERR_ARG;
     const int old_k = b->kernel, old_K = b->K_req, old_s = b->spl_req;

@@ -160,31 +160,43 @@ __global__ void __launch_bounds__(256) k_stream(const T *__restrict__ in, T *__r
 }
 
 // ------------------------------------------------------ a2-a6: on-chip, many steps
-// A whole periodic instance lives in the registers of a run of threads for `nsteps` steps.
-// Thread t of an instance owns nodes tK .. tK+K-1 (the last thread may own fewer: the
-// instance's nodes are not padded).  Each step, the populations that cross a thread boundary
-// are exchanged through double-buffered shared memory (one __syncthreads per step):
+// A run of a CTA's threads holds a window of one instance in registers for many steps.
+// Thread t of the run owns window positions tK .. tK+K-1 (the last thread may own fewer).
+// Each step the populations that cross a thread boundary are exchanged through
+// double-buffered shared memory (one __syncthreads per step):
 //   R: the last |e| values of every right-moving population (read by thread t+1),
-//   L: the first |e| values of every left-moving population (read by thread t-1),
-//   tail: the last |e| nodes of the instance (read by thread 0: periodic wrap),
-//   head = thread 0's L window (read by the threads at the end of the instance).
-// Instances are packed onto CTAs on warp boundaries; all CTA threads take part in the
-// barriers.
+//   L: the first |e| values of every left-moving population (read by thread t-1).
+// Two modes:
+//   ring (HALO = false): the window is the whole periodic instance and stays resident for
+//     all nsteps; the wrap-around uses
+//       tail: the last |e| nodes of the instance (read by thread 0),
+//       head = thread 0's L window (read by the threads at the end of the instance),
+//       wrap: a copy of the last two threads' own values (their gather runs through shared
+//             memory, since the last thread's node count is only known at run time).
+//     Several instances may share a CTA (warp-aligned thread runs).
+//   halo (HALO = true): temporal blocking.  The window is npos = valid + 2H consecutive
+//     nodes (global index taken modulo N) with H = nsteps * max|e|; the window edges read
+//     stale values, whose influence moves inward max|e| nodes per step and stays inside the
+//     H-wide borders.  After nsteps steps the middle `valid` nodes are exact and are written
+//     to the output buffer.  One window per CTA.
 struct OnchipInst {
     long long off, ld;  // state placement (as Seg)
     int N, D;
     int gcoef;          // coefficient block in global memory (as Seg::coef)
     int scoef;          // this instance's copy of P_j and 1 - omega in shared memory
     int tbase;          // first CTA thread
-    int nthr;           // threads that own nodes: ceil(N / K)
+    int nthr;           // threads that own positions: ceil(npos / K)
     int il;             // index among the CTA's instances (tail buffer slot)
+    int x0;             // global node of window position 0 (halo: may be negative)
+    int npos;           // window positions (ring: N)
+    int vlo, vhi;       // positions written back: [vlo, vhi)
     int pad;
 };
 
-template <typename T, int B, int K, int MAXT>
+template <typename T, int B, int K, int MAXT, bool HALO>
 __global__ void __launch_bounds__(MAXT, 1)
-    k_onchip(T *__restrict__ st, const OnchipInst *__restrict__ insts, const int *__restrict__ cta_first,
-             const T *__restrict__ coefs, int nsteps, int max_inst) {
+    k_onchip(const T *__restrict__ st_in, T *__restrict__ st_out, const OnchipInst *__restrict__ insts,
+             const int *__restrict__ cta_first, const T *__restrict__ coefs, int nsteps, int max_inst) {
     static_assert(K >= wmax(B), "a thread must own at least max|e| nodes");
     constexpr int NE = nedge(B);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -192,8 +204,9 @@ __global__ void __launch_bounds__(MAXT, 1)
     const int nt = blockDim.x;
     T *R = smem;                        // [2][NE][nt]
     T *L = R + 2 * NE * nt;             // [2][NE][nt]
-    T *tail = L + 2 * NE * nt;          // [2][NE][max_inst]
-    T *scoef = tail + 2 * NE * max_inst;
+    T *tail = L + 2 * NE * nt;          // [2][NE][max_inst]                (ring)
+    T *wrap = tail + 2 * NE * max_inst; // [max_inst][2][B-1][K]            (ring)
+    T *scoef = HALO ? tail : wrap + 2 * (B - 1) * K * max_inst;
 
     const int first = cta_first[blockIdx.x], last = cta_first[blockIdx.x + 1];
     const int tid = threadIdx.x;
@@ -215,17 +228,29 @@ __global__ void __launch_bounds__(MAXT, 1)
     const int t = tid - I.tbase;
     const bool has = me >= 0 && t < I.nthr;
     const int N = I.N;
-    const bool near_end = has && (t + 1) * K + wmax(B) > N;
+    const int npos = I.npos;
+    const bool near_end = !HALO && has && (t + 1) * K + wmax(B) > N;  // ring: threads nthr-2, nthr-1
     const int xb = t * K;
+    T *Sx = wrap + ((I.il * 2 + (t == I.nthr - 1 ? 1 : 0)) * (B - 1)) * K;
+    // halo windows: the outermost threads have no neighbour; they read their own edge slot
+    // (in bounds, stale) instead
+    const int left_nb = (HALO && t == 0) ? tid : tid - 1;
+    const int right_nb = (HALO && t + 1 >= I.nthr) ? tid : tid + 1;
 
     T phi[K], v[B][K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int x = xb + k;
-        const bool ok = has && x < N;
-        phi[k] = ok ? st[I.off + x] : T(0);
+        const int p = xb + k;
+        const bool ok = has && p < npos;
+        long long x = p;
+        if (HALO) {
+            x = (long long)I.x0 + p;
+            x %= N;
+            x += x < 0 ? N : 0;
+        }
+        phi[k] = ok ? st_in[I.off + x] : T(0);
 #pragma unroll
-        for (int j = 1; j < B; ++j) v[j][k] = ok ? st[I.off + (long long)j * I.ld + x] : T(0);
+        for (int j = 1; j < B; ++j) v[j][k] = ok ? st_in[I.off + (long long)j * I.ld + x] : T(0);
     }
     __syncthreads();
     const T *sc = scoef + I.scoef;
@@ -248,7 +273,7 @@ __global__ void __launch_bounds__(MAXT, 1)
                     for (int i = 0; i < -e; ++i) Lb[(eslot(-e) + i) * nt + tid] = v[j][i];
                 }
             }
-            if (near_end) {
+            if (!HALO && near_end) {
 #pragma unroll
                 for (int j = 1; j < B; ++j) {
                     const int e = vel(j);
@@ -267,49 +292,69 @@ __global__ void __launch_bounds__(MAXT, 1)
             T d[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) d[k] = T(0);
+            if (!near_end) {
+                // f_j(x) = s_j(x - e_j) from own registers or a neighbour's published edge
+                // (ring: thread 0 takes its right-moving inflow from the tail buffer)
 #pragma unroll
-            for (int j = 1; j < B; ++j) {
-                const int e = vel(j);
-                if (e > 0) {
-                    // f_j(x) = s_j(x - e): descending k keeps v[j][k - e] unread-overwritten
+                for (int j = 1; j < B; ++j) {
+                    const int e = vel(j);
+                    if (e > 0) {
 #pragma unroll
-                    for (int k = K - 1; k >= 0; --k) {
-                        T nv;
-                        if (k >= e) {
-                            nv = v[j][k - e];
-                        } else {
-                            const T *p = t > 0 ? &Rb[(eslot(e) + k) * nt + tid - 1]
-                                               : &Tb[(eslot(e) + k) * max_inst + I.il];
-                            nv = *p;
-                        }
-                        d[k] += nv - v[j][k];
-                        v[j][k] = nv;
-                    }
-                } else {
-                    const int a = -e;
-                    if (!near_end) {
-#pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const T nv = (k + a < K) ? v[j][k + a] : Lb[(eslot(a) + k + a - K) * nt + tid + 1];
-                            d[k] += nv - v[j][k];
-                            v[j][k] = nv;
-                        }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const int src = xb + k + a;
+                        for (int k = K - 1; k >= 0; --k) {  // descending: v[j][k - e] still old
                             T nv;
-                            if (src >= N) {
-                                const int h = min(src - N, a - 1);  // node (src - N) of thread 0
-                                nv = Lb[(eslot(a) + h) * nt + I.tbase];
-                            } else if (k + a < K) {
-                                nv = v[j][k + a];
+                            if (k >= e) {
+                                nv = v[j][k - e];
+                            } else if (HALO) {
+                                nv = Rb[(eslot(e) + k) * nt + left_nb];
                             } else {
-                                nv = Lb[(eslot(a) + k + a - K) * nt + tid + 1];
+                                const T *p = t > 0 ? &Rb[(eslot(e) + k) * nt + tid - 1]
+                                                   : &Tb[(eslot(e) + k) * max_inst + I.il];
+                                nv = *p;
                             }
                             d[k] += nv - v[j][k];
                             v[j][k] = nv;
                         }
+                    } else {
+                        const int a = -e;
+#pragma unroll
+                        for (int k = 0; k < K; ++k) {  // ascending: v[j][k + a] still old
+                            const T nv = (k + a < K) ? v[j][k + a] : Lb[(eslot(a) + k + a - K) * nt + right_nb];
+                            d[k] += nv - v[j][k];
+                            v[j][k] = nv;
+                        }
+                    }
+                }
+            } else {
+                // ring, last one or two threads (the last may own fewer than K nodes): stage own
+                // values in shared memory, then take every source with one load from a computed
+                // address; sources past node N-1 wrap to thread 0's head window.
+#pragma unroll
+                for (int j = 1; j < B; ++j)
+#pragma unroll
+                    for (int k = 0; k < K; ++k) Sx[(j - 1) * K + k] = v[j][k];
+#pragma unroll
+                for (int j = 1; j < B; ++j) {
+                    const int e = vel(j);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        const T *q;
+                        if (e > 0) {
+                            if (k >= e)
+                                q = &Sx[(j - 1) * K + k - e];
+                            else
+                                q = t > 0 ? &Rb[(eslot(e) + k) * nt + tid - 1] : &Tb[(eslot(e) + k) * max_inst + I.il];
+                        } else {
+                            const int a = -e, src = xb + k + a;
+                            if (src >= N)
+                                q = &Lb[(eslot(a) + min(src - N, a - 1)) * nt + I.tbase];
+                            else if (k + a < K)
+                                q = &Sx[(j - 1) * K + k + a];
+                            else
+                                q = &Lb[(eslot(a) + k + a - K) * nt + tid + 1];
+                        }
+                        const T nv = *q;
+                        d[k] += nv - v[j][k];
+                        v[j][k] = nv;
                     }
                 }
             }
@@ -335,11 +380,17 @@ __global__ void __launch_bounds__(MAXT, 1)
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int x = xb + k;
-        if (has && x < N) {
-            st[I.off + x] = phi[k];
+        const int p = xb + k;
+        if (has && p >= I.vlo && p < I.vhi) {
+            long long x = p;
+            if (HALO) {
+                x = (long long)I.x0 + p;
+                x %= N;
+                x += x < 0 ? N : 0;
+            }
+            st_out[I.off + x] = phi[k];
 #pragma unroll
-            for (int j = 1; j < B; ++j) st[I.off + (long long)j * I.ld + x] = v[j][k];
+            for (int j = 1; j < B; ++j) st_out[I.off + (long long)j * I.ld + x] = v[j][k];
         }
     }
 }

@@ -27,7 +27,7 @@ PERIODIC = 0
 PI_ZERO, PI_PHI, PI_POWER, PI_POLY = 0, 1, 2, 3
 PI_NCOEF = 8
 MAX_DEG = 31
-KERNEL_AUTO, KERNEL_STREAM, KERNEL_ONCHIP = 0, 1, 2
+KERNEL_AUTO, KERNEL_STREAM, KERNEL_ONCHIP, KERNEL_HALO = 0, 1, 2, 3
 
 
 class lbhpde_pi(ctypes.Structure):

@@ -40,6 +40,7 @@ def L():
 
 
 def normwise(a, b):
+    assert np.all(np.isfinite(b)), "the oracle diverged: the test problem is unstable"
     return float(np.abs(a - b).max() / np.abs(b).max())
 
 
@@ -72,33 +73,40 @@ CASES = [
     ("kawahara_q7_s2_601", W.kawahara(), 601, 0.1, 1e-3, 2.55, 800, 2),
     ("mod_kawahara_q7_D13", W.modified_kawahara(), 300, 0.1, 1e-2, 4.54, 200, 1),
     ("mkdv_D9_515", W.mkdv(), 515, 0.1, 1e-4, 1.2, 800, 1),
-    ("k22_333", W.k22(), 333, 0.1, 1e-3, 1.6, 600, 1),
+    ("k22_333", W.k22(), 333, 0.1, 1e-4, 1.5, 600, 1),
     ("kdv_burgers_1025", W.kdv_burgers(3.0, 0.07, 0.8), 1025, 0.1, 1e-4, 1.15, 600, 1),
     ("kdv_s2_777", W.kdv(), 777, 0.1, 1e-4, 1.3, 600, 2),
-    ("gks_cubic_q7_250", W.gks_cubic(lattice=7), 250, 0.1, 1e-3, 1.4, 300, 1),
+    ("gks_cubic_q7_250", W.gks_cubic(lattice=7), 250, 0.1, 1e-3, 3.0, 300, 1),
     ("sixth_q7_96", W.Equation("sixth", (1.0, 0.0, 0.5, 0.3, -1.0, 0.2),
-                               ((0, 0, 0.5), (), (0, 1), (0, 1), (0, 1), (0, 1))), 96, 0.1, 1e-3, 2.2, 300, 1),
+                               ((0, 0, 0.5), (), (0, 1), (0, 1), (0, 1), (0, 1))), 96, 0.1, 1e-4, 3.0, 300, 1),
 ]
 
 
+KERNELS = ["stream", "onchip", "halo"]
+
+
+def kernel_id(L, name):
+    return {"stream": L.KERNEL_STREAM, "onchip": L.KERNEL_ONCHIP, "halo": L.KERNEL_HALO}[name]
+
+
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("kernel", ["stream", "onchip"])
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_fp64_matches_oracle(L, case, kernel):
     name, eq, N, dx, dt, tau, n, scheme = case
     p = problem(eq, N, dx, dt, tau, n, scheme, seed=zlib.crc32(name.encode()) % 1000)
     want = oracle.run_problem(p)
-    K = {"stream": L.KERNEL_STREAM, "onchip": L.KERNEL_ONCHIP}[kernel]
+    K = kernel_id(L, kernel)
     got = run_gpu(L, p, L.FP64, K)
     assert normwise(got, want) <= FP64_TOL
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-@pytest.mark.parametrize("kernel", ["stream", "onchip"])
+@pytest.mark.parametrize("kernel", KERNELS)
 def test_fp32_matches_oracle(L, case, kernel):
     name, eq, N, dx, dt, tau, n, scheme = case
     p = problem(eq, N, dx, dt, tau, n, scheme, seed=zlib.crc32(name.encode()) % 1000)
     want = oracle.run_problem(p)
-    K = {"stream": L.KERNEL_STREAM, "onchip": L.KERNEL_ONCHIP}[kernel]
+    K = kernel_id(L, kernel)
     got = run_gpu(L, p, L.FP32_DEV, K)
     assert normwise(got, want) <= FP32_TOL(n)
 
@@ -113,16 +121,17 @@ SIZES = [(5, 4), (5, 5), (5, 9), (5, 17), (5, 33), (5, 255), (5, 1023), (5, 1025
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_sizes_both_kernels(L, b, N, prec):
     eq = W.kdv_burgers(2.0, 0.05, 0.9) if b == 5 else W.kawahara()
-    p = problem(eq, N, 0.1, 1e-3, 1.3 if b == 5 else 2.3, 97, seed=N)
+    p = problem(eq, N, 0.1, 1e-4 if b == 5 else 1e-3, 1.3 if b == 5 else 2.3, 97, seed=N)
     want = oracle.run_problem(p)
     P = L.FP64 if prec == "fp64" else L.FP32_DEV
     tol = FP64_TOL if prec == "fp64" else FP32_TOL(97)
     got_s = run_gpu(L, p, P, L.KERNEL_STREAM)
     assert normwise(got_s, want) <= tol
-    for K in ((2, 4, 8) if b == 5 else (4, 8)):
+    for kern, K, spl in [(k, K, spl) for k in (L.KERNEL_ONCHIP, L.KERNEL_HALO)
+                         for K in ((2, 4, 8) if b == 5 else (4, 8)) for spl in (0, 13)]:
         s = L.Solver.for_problem(p, precision=P)
         try:
-            s.set_kernel(L.KERNEL_ONCHIP, K, 0)
+            s.set_kernel(kern, K, spl)
         except L.LbhpdeError as e:
             assert e.code == L.ERR_UNSUPPORTED
             s.close()
@@ -130,7 +139,7 @@ def test_sizes_both_kernels(L, b, N, prec):
         s.set_phi(p.phi0).step(p.nsteps)
         got = s.read_phi()
         s.close()
-        assert normwise(got, want) <= tol, K
+        assert normwise(got, want) <= tol, (kern, K, spl)
 
 
 def test_onchip_step_chunks_are_seamless(L):
@@ -194,12 +203,13 @@ def test_nan_input_reports_divergence(L):
         s.close()
 
 
-def test_onchip_rejects_too_long_grid(L):
-    p = problem(W.kdv(), 100000, 0.1, 1e-4, 1.3, 1)
+def test_unsupported_nodes_per_thread(L):
+    p = problem(W.kawahara(), 1000, 0.1, 1e-3, 2.3, 1)
     s = L.Solver.for_problem(p, precision=L.FP32_DEV)
     with pytest.raises(L.LbhpdeError) as ei:
-        s.set_kernel(L.KERNEL_ONCHIP)
+        s.set_kernel(L.KERNEL_ONCHIP, 2)  # D1Q7 needs at least 3 nodes per thread
     assert ei.value.code == L.ERR_UNSUPPORTED
+    s.set_phi(p.phi0).step(1)  # the previous (automatic) choice still works
     s.close()
 
 
@@ -207,12 +217,13 @@ def test_batch_members_match_alone_bitwise(L):
     """Each instance gives the same bits alone and packed with others (both precisions)."""
     probs = []
     rng = np.random.default_rng(11)
-    eqs = [W.kdv_burgers(2.0, 0.05, 0.9), W.kdv(), W.ks(), W.kawahara(), W.mkdv(), W.k22()]
+    # (equation, dt, tau) with perturbation growth below 10 over 120 steps (oracle scan)
+    eqs = [(W.kdv_burgers(2.0, 0.05, 0.9), 1e-4, 1.3), (W.kdv(), 1e-4, 1.3), (W.ks(), 1e-4, 1.3),
+           (W.kawahara(), 1e-3, 2.5), (W.mkdv(), 1e-4, 1.2), (W.k22(), 1e-4, 1.5)]
     for i in range(14):
-        eq = eqs[i % len(eqs)]
+        eq, dt, tau = eqs[i % len(eqs)]
         N = int(rng.integers(6, 1500))
-        tau = 2.3 if eq.m >= 5 else 1.4
-        probs.append(problem(eq, N, 0.1, 1e-3 if eq.name != "mkdv" else 1e-4, tau, 120, seed=i))
+        probs.append(problem(eq, N, 0.1, dt, tau, 120, seed=i))
     for P in (L.FP64, L.FP32_DEV):
         for kernel in (L.KERNEL_AUTO, L.KERNEL_STREAM):
             bt = L.Batch(probs, precision=P).set_kernel(kernel)
