@@ -204,6 +204,33 @@ int lbhpde_batch_set_kernel(lbhpde_batch_t b, int kernel, int nodes_per_thread, 
 int lbhpde_batch_size(lbhpde_batch_t b, long *total_nodes, size_t *device_bytes);
 int lbhpde_batch_destroy(lbhpde_batch_t b);
 
+/* ------------------------------------------------- diagnostics, no allocation */
+
+/* Largest N lbhpde_phi_diagnostics_noalloc accepts (2^24 nodes). */
+#define LBHPDE_NOALLOC_MAX_NODES 16777216L
+
+/* The diagnostics reduction of lbhpde_diagnostics for a phi array the caller owns, in a form
+ * that allocates no memory at all.  The paper has no counterpart: this entry point exists for
+ * callers that cannot let a library call cudaMalloc -- applications that reserve all device
+ * memory up front for their own pool, or latency-critical loops where the implicit
+ * device-wide synchronisation of cudaMalloc/cudaFree is not acceptable.
+ *   phi_device      [N] doubles in device memory (e.g. from lbhpde_read_phi with out_on_device)
+ *   N               1 .. LBHPDE_NOALLOC_MAX_NODES; larger N returns LBHPDE_ERR_ARG
+ *   phistar_device  [N] doubles in device memory, or NULL (then err_E = err_L2 = 0)
+ *   out             host record; steps is set to 0
+ *   cuda_stream     stream for the two kernels and the copy of the result (NULL = legacy)
+ * The per-block partial sums live in a file-scope device array of about 1 MiB that every GPU
+ * loading the library keeps until the process exits.  The first call on a device (with that
+ * device current) looks up the array's device address; make that first call before any
+ * stream capture.  Every call writes each record it reads, so nothing is carried over between
+ * calls, but all calls share the one array: calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.  The call synchronises
+ * cuda_stream.  Returns LBHPDE_ERR_DIVERGED (after filling out) if phi has a non-finite
+ * value, LBHPDE_ERR_CUDA if a CUDA call fails.  Calls no cudaMalloc, cudaFree or allocating
+ * library routine. */
+int lbhpde_phi_diagnostics_noalloc(const double *phi_device, long N, const double *phistar_device,
+                                   lbhpde_diag *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

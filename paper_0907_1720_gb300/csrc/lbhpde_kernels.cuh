@@ -480,7 +480,7 @@ __global__ void k_diag_partial(const T *__restrict__ st, const Seg *__restrict__
 }
 
 // part_first[seg] .. part_first[seg + 1]: the pass-1 records of segment seg.
-__global__ void k_diag_final(const DiagPart *__restrict__ part, const int *__restrict__ part_first, int nseg,
+static __global__ void k_diag_final(const DiagPart *__restrict__ part, const int *__restrict__ part_first, int nseg,
                              DiagPart *__restrict__ out) {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= nseg) return;

@@ -95,6 +95,7 @@ _SIGS = {
     "lbhpde_batch_set_kernel": (_I, [_V, _I, _I, _I]),
     "lbhpde_batch_size": (_I, [_V, _P(_L), _P(_S)]),
     "lbhpde_batch_destroy": (_I, [_V]),
+    "lbhpde_phi_diagnostics_noalloc": (_I, [_V, _L, _V, _P(lbhpde_diag), _V]),
 }
 EXPORTED = tuple(_SIGS)
 
