@@ -10,7 +10,8 @@ the device-resident initial profiles (a1), 1000 collide+stream steps (a2-a6) and
 diagnostics reduction (a7).  The model set-up (a0) happens once, at batch creation.
 ``value`` is lattice node-updates per second over all ranks.
 
---workload long_grid: the 2^24-node Kawahara grid (D1Q7, 1000 steps) on the streaming kernel.
+--workload long_grid: the 2^24-node Kawahara grid (D1Q7, 1000 steps) in temporally blocked
+windows; with --kernel stream, on the one-step-per-launch streaming kernel (HBM roofline).
 --impl reference: the CPU oracle timed on the host cores on a bounded sample of the workload.
 """
 from __future__ import annotations
@@ -143,8 +144,11 @@ def run_ours(args, rank, world):
             nsteps = p.nsteps
             prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
             solver = L.Batch(probs, precision=prec)
+            if args.kernel == "stream":
+                solver.set_kernel(L.KERNEL_STREAM)
             workload = (f"kawahara_long_grid: N=2^24, D1Q7 scheme 1, dx=0.1, dt=1e-4, tau=2.02, "
-                        f"{nsteps} steps per benchmark step (streaming kernel)")
+                        f"{nsteps} steps per benchmark step "
+                        f"({'streaming kernel' if args.kernel == 'stream' else 'temporally blocked windows'})")
         total = sum(p.N for p in probs)
         b = 5 if args.workload == "ensemble" else 7
         esz = 4 if prec == L.FP32_DEV else 8
@@ -215,13 +219,15 @@ def run_ours(args, rank, world):
 
         kern_ms = float(np.mean(kern))
         clocks = clk.summary()
-        if args.workload == "ensemble":
+        if args.workload == "ensemble" or args.kernel != "stream":
             fl = flops_per_node_update(b, D)
             sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
             peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
             achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": achieved / peak_tf, "traffic": None, "kernel": "k_onchip<float,5,K>",
+                    "frac": achieved / peak_tf, "traffic": None,
+                    "kernel": f"k_onchip<{'float' if esz == 4 else 'double'},{b},K> "
+                              f"({'resident instances + halo windows' if args.workload == 'ensemble' else 'halo windows'})",
                     "flops_per_node_update": fl,
                     "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock under load"}
         else:
@@ -230,9 +236,7 @@ def run_ours(args, rank, world):
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_stream",
                     "bytes_per_node_update": by, "peak_source": peak_src}
-        launches_per_step = 1 + 1 + 2  # init, on-chip (or 1000 stream launches), diagnostics x2
-        if args.workload != "ensemble":
-            launches_per_step = 1 + nsteps + 2
+        launches_per_step = 1 + 2 + solver_kernel_launches(args, nsteps)  # init, diagnostics x2, steps
         line = {
             "metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
@@ -248,6 +252,17 @@ def run_ours(args, rank, world):
             line["fp64_plain"] = fp64
         solver.close()
     return line
+
+
+def solver_kernel_launches(args, nsteps):
+    """Kernel launches of one lbhpde_batch_step(nsteps) call: the streaming kernel launches once
+    per step; the ensemble's resident instances launch once and its halo windows once per 64
+    steps; the long grid's windows launch once per 32 steps (D1Q7)."""
+    if args.workload == "ensemble":
+        return 1 + (nsteps + 63) // 64
+    if args.kernel == "stream":
+        return nsteps
+    return (nsteps + 31) // 32
 
 
 def solver_model_degree(L, probs):
@@ -370,6 +385,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ensemble", choices=["ensemble", "long_grid"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--kernel", default="auto", choices=["auto", "stream"],
+                    help="long_grid only: the streaming kernel instead of temporally blocked windows")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     args = ap.parse_args()

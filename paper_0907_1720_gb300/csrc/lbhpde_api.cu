@@ -19,8 +19,7 @@ using lbk::Seg;
 namespace {
 
 constexpr int kChunk = 1024;          // nodes per block of the node-parallel kernels
-constexpr int kStreamThreads = 256;   // k_stream: 256 threads x 4 nodes = kChunk
-constexpr int kStreamNPT = kChunk / kStreamThreads;
+constexpr int kStreamThreads = kChunk / 4;  // k_stream: one group of 4 nodes per thread
 constexpr int kGenericThreads = 256;  // init / readout / diagnostics
 
 #define CK(call)                                              \
@@ -57,6 +56,8 @@ struct Group {
         int *cta_first = nullptr;
     } ring, halo;
     int K = 0, maxt = 0, tblk = 0;
+    int dc = 0;  // compile-time degree of the on-chip kernel variant (0 = run time)
+    bool uniform = false;  // every member has the same model (coefficients and omega)
 };
 
 }  // namespace
@@ -149,9 +150,9 @@ int onchip_maxt(size_t esz, int b, int K) {
 }
 int default_K(size_t esz, int b) { return esz == 4 && b == 5 ? 8 : 4; }
 
-template <typename T, int B, int K, int MAXT, bool HALO>
+template <typename T, int B, int K, int MAXT, bool HALO, int DC>
 int launch_onchip_t(lbhpde_batch_s *bt, Group::Plan &pl, const void *in, void *out, int nsteps) {
-    auto fn = lbk::k_onchip<T, B, K, MAXT, HALO>;
+    auto fn = lbk::k_onchip<T, B, K, MAXT, HALO, DC>;
     CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
     fn<<<pl.ncta, pl.nthreads, pl.smem, bt->stream>>>((const T *)in, (T *)out, pl.insts, pl.cta_first,
                                                        (const T *)bt->coefT, nsteps, pl.max_inst);
@@ -159,23 +160,32 @@ int launch_onchip_t(lbhpde_batch_s *bt, Group::Plan &pl, const void *in, void *o
     return LBHPDE_OK;
 }
 
+// compile-time polynomial degree: D = 5 on D1Q5 and D = 7 on D1Q7 (the KdV/KS/KdV-Burgers and
+// Kawahara families), run-time degree otherwise
+template <typename T, int B, int K, int MAXT, bool HALO>
+int launch_onchip_d(lbhpde_batch_s *bt, Group &g, Group::Plan &pl, const void *in, void *out, int nsteps) {
+    constexpr int DC = B == 5 ? 5 : 7;
+    if (g.dc == DC) return launch_onchip_t<T, B, K, MAXT, HALO, DC>(bt, pl, in, out, nsteps);
+    return launch_onchip_t<T, B, K, MAXT, HALO, 0>(bt, pl, in, out, nsteps);
+}
+
 template <typename T, int B, bool HALO>
 int launch_onchip_b(lbhpde_batch_s *bt, Group &g, Group::Plan &pl, const void *in, void *out, int nsteps) {
     if constexpr (sizeof(T) == 4) {
         if constexpr (B == 5) {
-            if (g.K == 8) return launch_onchip_t<T, B, 8, 512, HALO>(bt, pl, in, out, nsteps);
-            if (g.K == 4) return launch_onchip_t<T, B, 4, 1024, HALO>(bt, pl, in, out, nsteps);
-            if (g.K == 2) return launch_onchip_t<T, B, 2, 1024, HALO>(bt, pl, in, out, nsteps);
+            if (g.K == 8) return launch_onchip_d<T, B, 8, 512, HALO>(bt, g, pl, in, out, nsteps);
+            if (g.K == 4) return launch_onchip_d<T, B, 4, 1024, HALO>(bt, g, pl, in, out, nsteps);
+            if (g.K == 2) return launch_onchip_d<T, B, 2, 1024, HALO>(bt, g, pl, in, out, nsteps);
         } else {
-            if (g.K == 8) return launch_onchip_t<T, B, 8, 256, HALO>(bt, pl, in, out, nsteps);
-            if (g.K == 4) return launch_onchip_t<T, B, 4, 512, HALO>(bt, pl, in, out, nsteps);
+            if (g.K == 8) return launch_onchip_d<T, B, 8, 256, HALO>(bt, g, pl, in, out, nsteps);
+            if (g.K == 4) return launch_onchip_d<T, B, 4, 512, HALO>(bt, g, pl, in, out, nsteps);
         }
     } else {
         if constexpr (B == 5) {
-            if (g.K == 4) return launch_onchip_t<T, B, 4, 512, HALO>(bt, pl, in, out, nsteps);
-            if (g.K == 2) return launch_onchip_t<T, B, 2, 1024, HALO>(bt, pl, in, out, nsteps);
+            if (g.K == 4) return launch_onchip_d<T, B, 4, 512, HALO>(bt, g, pl, in, out, nsteps);
+            if (g.K == 2) return launch_onchip_d<T, B, 2, 1024, HALO>(bt, g, pl, in, out, nsteps);
         } else {
-            if (g.K == 4) return launch_onchip_t<T, B, 4, 256, HALO>(bt, pl, in, out, nsteps);
+            if (g.K == 4) return launch_onchip_d<T, B, 4, 256, HALO>(bt, g, pl, in, out, nsteps);
         }
     }
     return LBHPDE_ERR_UNSUPPORTED;
@@ -198,22 +208,31 @@ int launch_onchip(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void 
                 : launch_onchip_b<double, 7, false>(bt, g, pl, in, out, nsteps);
 }
 
-template <typename T, int B>
-int launch_stream_b(lbhpde_batch_s *bt, Group &g) {
+template <typename T, int B, int DC, bool PARAMC>
+int launch_stream_t(lbhpde_batch_s *bt, Group &g) {
     const T *in = (const T *)bt->st[bt->cur];
     T *out = (T *)bt->st[bt->cur ^ 1];
     const int nb = (int)g.blocks_h.size();
-    if (g.maxD <= 5)
-        lbk::k_stream<T, B, 5, kStreamNPT><<<nb, kStreamThreads, 0, bt->stream>>>(in, out, bt->segs, g.blocks,
-                                                                                (const T *)bt->coefT);
-    else if (g.maxD <= 7)
-        lbk::k_stream<T, B, 7, kStreamNPT><<<nb, kStreamThreads, 0, bt->stream>>>(in, out, bt->segs, g.blocks,
-                                                                                (const T *)bt->coefT);
-    else
-        lbk::k_stream<T, B, 0, kStreamNPT><<<nb, kStreamThreads, 0, bt->stream>>>(in, out, bt->segs, g.blocks,
-                                                                                (const T *)bt->coefT);
+    lbk::StreamCoef<T, B, (DC > 0 ? DC : 1)> pc{};
+    if constexpr (PARAMC) {
+        // one model for the whole launch: its coefficients (zero-padded to degree DC)
+        const lbhpde_model_info &M = bt->mi[g.members[0]];
+        for (int j = 1; j < B; ++j)
+            for (int p = 0; p <= DC; ++p) pc.c[(j - 1) * (DC + 1) + p] = p <= M.D ? (T)M.coef[j][p] : T(0);
+        pc.omw = (T)(1.0 - M.omega);
+    }
+    lbk::k_stream<T, B, DC, kStreamThreads, PARAMC><<<nb, kStreamThreads, 0, bt->stream>>>(
+        in, out, bt->segs, g.blocks, (const T *)bt->coefT, pc);
     CK(cudaGetLastError());
     return LBHPDE_OK;
+}
+
+template <typename T, int B>
+int launch_stream_b(lbhpde_batch_s *bt, Group &g) {
+    constexpr int DC = B == 5 ? 5 : 7;
+    if (g.maxD <= DC && g.uniform) return launch_stream_t<T, B, DC, true>(bt, g);
+    if (g.maxD <= DC) return launch_stream_t<T, B, DC, false>(bt, g);
+    return launch_stream_t<T, B, 0, false>(bt, g);
 }
 
 // Steps per halo launch: the halo H = tblk * max|e| must leave most of a window valid.
@@ -232,6 +251,7 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
     if (maxt == 0 || K < lbk::wmax(g.b)) return LBHPDE_ERR_UNSUPPORTED;
     const int W = lbk::wmax(g.b);
     const int cap = maxt * K;
+    g.dc = (g.maxD == (g.b == 5 ? 5 : 7)) ? g.maxD : 0;
     if (tblk <= 0) tblk = default_tblk(cap, W);
     const int H = tblk * W;
     if (cap - 2 * H < 32) return LBHPDE_ERR_UNSUPPORTED;
@@ -290,7 +310,7 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
                 I.vlo = 0;
                 I.vhi = s.N;
                 insts.push_back(I);
-                sco += (g.b - 1) * (s.D + 1) + 1;
+                sco += lbk::cblock(g.b, g.dc > 0 ? g.dc : s.D);
                 tb += pad(s.N);
             }
             nthreads = std::max(nthreads, tb);
@@ -298,6 +318,7 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
             coef_max = std::max(coef_max, (size_t)sco);
         }
         first.push_back((int)insts.size());
+        max_inst = (max_inst + 3) & ~3;  // keeps the shared-memory coefficient rows 16-byte aligned
         Group::Plan &pl = g.ring;
         pl = Group::Plan{};
         if (!ctas.empty()) {
@@ -337,7 +358,7 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
                 I.vhi = H + v;
                 first.push_back((int)insts.size());
                 insts.push_back(I);
-                coef_max = std::max(coef_max, (size_t)((g.b - 1) * (s.D + 1) + 1));
+                coef_max = std::max(coef_max, (size_t)lbk::cblock(g.b, g.dc > 0 ? g.dc : s.D));
             }
         }
         first.push_back((int)insts.size());
@@ -440,6 +461,13 @@ int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
                 g.maxD = std::max(g.maxD, bt->mi[i].D);
                 for (long long x = 0; x < bt->N[i]; x += kChunk) g.blocks_h.push_back(make_int2(i, (int)x));
             }
+        g.uniform = !g.members.empty();
+        for (int i : g.members) {
+            const lbhpde_model_info &A = bt->mi[g.members[0]], &Bm = bt->mi[i];
+            if (A.D != Bm.D || A.omega != Bm.omega ||
+                std::memcmp(A.coef, Bm.coef, sizeof(A.coef)) != 0)
+                g.uniform = false;
+        }
         if (!g.members.empty()) {
             std::vector<long long> off(g.blocks_h.size());
             for (size_t q = 0; q < off.size(); ++q) off[q] = bt->phi_off[g.blocks_h[q].x];

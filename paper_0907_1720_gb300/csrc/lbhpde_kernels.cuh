@@ -32,6 +32,11 @@ __host__ __device__ constexpr int nedge(int B) { return wmax(B) * (wmax(B) + 1) 
 // First edge slot of the population with |e| = a (a = 1, 2, 3): 0, 1, 3.
 __host__ __device__ constexpr int eslot(int a) { return (a - 1) * a / 2; }
 
+// Shared-memory coefficient rows of the on-chip kernel: P_j for j = 1..B-1 at stride
+// crow(D) (a multiple of 4, so rows start on 16-byte boundaries), then 1 - omega.
+__host__ __device__ constexpr int crow(int D) { return (D + 1 + 3) & ~3; }
+__host__ __device__ constexpr int cblock(int B, int D) { return (B - 1) * crow(D) + 4; }
+
 // One instance's place in the state and coefficient arenas.
 struct Seg {
     long long off;  // element offset of row 0 (phi)
@@ -44,6 +49,30 @@ struct Seg {
                     //   [1]           1 - omega
     int pad;
 };
+
+// Load NCR consecutive coefficients from a 16-byte aligned shared-memory row.
+template <typename T, int NCR>
+__device__ __forceinline__ void load_row(const T *c, T (&cr)[NCR]) {
+    if constexpr (sizeof(T) == 4) {
+        static_assert(NCR % 4 == 0, "row length");
+#pragma unroll
+        for (int q = 0; q < NCR / 4; ++q) {
+            const float4 w = reinterpret_cast<const float4 *>(c)[q];
+            cr[4 * q] = w.x;
+            cr[4 * q + 1] = w.y;
+            cr[4 * q + 2] = w.z;
+            cr[4 * q + 3] = w.w;
+        }
+    } else {
+        static_assert(NCR % 2 == 0, "row length");
+#pragma unroll
+        for (int q = 0; q < NCR / 2; ++q) {
+            const double2 w = reinterpret_cast<const double2 *>(c)[q];
+            cr[2 * q] = w.x;
+            cr[2 * q + 1] = w.y;
+        }
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ T fma_t(T a, T b, T c);
@@ -80,81 +109,162 @@ __global__ void k_init(T *__restrict__ st, const Seg *__restrict__ segs, const i
 }
 
 // ------------------------------------------------------------- a2-a6: streaming step
-// One fused collide+stream step through HBM.  Each thread owns NPT nodes spaced by
-// blockDim.x (coalesced rows); the shifted reads s_j(x - e_j) are served by L1/L2 from the
-// lines the neighbouring lanes fetch, so DRAM sees each row once per step.
-// DC > 0: compile-time polynomial degree (coefficients kept in registers; segments with a
-// smaller degree are zero-padded by the host).  DC == 0: degree read at run time.
-template <typename T, int B, int DC, int NPT>
-__global__ void __launch_bounds__(256) k_stream(const T *__restrict__ in, T *__restrict__ out,
-                                                const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
-                                                const T *__restrict__ coefs) {
+// One fused collide+stream step through HBM.  A thread owns one group of 4 consecutive nodes
+// (16 bytes per row in FP32, 32 in FP64), consecutive lanes own consecutive groups, so every
+// row is read and written with coalesced vector accesses.  The shifted sources s_j(x - e_j)
+// at a group's edges come from the neighbouring lane by warp shuffle (the lanes at a warp
+// edge load the neighbouring group themselves; it is in L1/L2).  Groups within max|e| of
+// either end of the grid take a scalar path with periodic indices.
+// DC > 0: compile-time polynomial degree (lower-degree segments are zero-padded); the
+// coefficients are kernel parameters when the whole launch shares one model (PARAMC), else
+// registers loaded per block.  DC == 0: degree read at run time from shared memory.
+template <typename T>
+__device__ __forceinline__ void load4(const T *p, T (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 w = *reinterpret_cast<const float4 *>(p);
+        v[0] = w.x, v[1] = w.y, v[2] = w.z, v[3] = w.w;
+    } else {
+        const double2 w0 = reinterpret_cast<const double2 *>(p)[0], w1 = reinterpret_cast<const double2 *>(p)[1];
+        v[0] = w0.x, v[1] = w0.y, v[2] = w1.x, v[3] = w1.y;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void store4(T *p, const T (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(v[0], v[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(v[2], v[3]);
+    }
+}
+
+// Coefficients of one model passed by value: every thread of the launch reads them as
+// uniform constant-bank operands (no registers, no loads).  Used when all segments of a launch
+// share one model.
+template <typename T, int B, int DC>
+struct StreamCoef {
+    T c[(B - 1) * (DC + 1)];  // P_j(phi) = omega f^eq_j(phi), row j - 1, degree DC
+    T omw;                    // 1 - omega
+};
+
+template <typename T, int B, int DC, int NT, bool PARAMC>
+__global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__restrict__ out,
+                                               const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
+                                               const T *__restrict__ coefs,
+                                               const __grid_constant__ StreamCoef<T, B, (DC > 0 ? DC : 1)> pc) {
+    static_assert(!PARAMC || DC > 0, "parameter coefficients need a compile-time degree");
+    constexpr int W = wmax(B);
     constexpr int NC = (DC > 0 ? DC : kMaxDeg) + 1;
-    __shared__ T sc[(B - 1) * NC + 1];
+    __shared__ T sc[PARAMC ? 1 : (B - 1) * NC + 1];
     const int2 bl = blocks[blockIdx.x];
     const Seg s = segs[bl.x];
-    const int D = DC > 0 ? DC : s.D;
-    for (int i = threadIdx.x; i < (B - 1) * (s.D + 1); i += blockDim.x) {
-        const int j = i / (s.D + 1), p = i % (s.D + 1);
-        sc[j * NC + p] = coefs[s.coef + i];
+    if constexpr (!PARAMC) {
+        for (int i = threadIdx.x; i < (B - 1) * NC; i += blockDim.x) {
+            const int j = i / NC, p = i % NC;
+            sc[i] = p <= s.D ? coefs[s.coef + j * (s.D + 1) + p] : T(0);
+        }
+        if (threadIdx.x == 0) sc[(B - 1) * NC] = coefs[s.coef + 2 * (B - 1) * (s.D + 1)];
+        __syncthreads();
     }
-    if (DC > 0)
-        for (int i = threadIdx.x; i < (B - 1) * NC; i += blockDim.x)
-            if (i % NC > s.D) sc[i] = T(0);
-    if (threadIdx.x == 0) sc[(B - 1) * NC] = coefs[s.coef + 2 * (B - 1) * (s.D + 1)];
-    __syncthreads();
-    const T omw = sc[(B - 1) * NC];
-    T creg[DC > 0 ? (B - 1) * (DC + 1) : 1];
-    if (DC > 0) {
+    const int D = DC > 0 ? DC : s.D;
+    const T omw = PARAMC ? pc.omw : sc[PARAMC ? 0 : (B - 1) * NC];
+    T creg[(DC > 0 && !PARAMC) ? (B - 1) * (DC + 1) : 1];
+    if constexpr (DC > 0 && !PARAMC) {
 #pragma unroll
         for (int j = 0; j < B - 1; ++j)
 #pragma unroll
-            for (int p = 0; p <= (DC > 0 ? DC : 0); ++p) creg[j * (DC + 1) + p] = sc[j * NC + p];
+            for (int p = 0; p <= DC; ++p) creg[j * (DC + 1) + p] = sc[j * NC + p];
     }
+    auto coef = [&](int j, int p) -> T {  // coefficient p of P_j, compile-time indices
+        if constexpr (PARAMC)
+            return pc.c[(j - 1) * (DC + 1) + p];
+        else
+            return creg[(j - 1) * ((DC > 0 ? DC : 0) + 1) + p];
+    };
+    auto poly = [&](int j, T ph) -> T {  // P_j(phi), Horner
+        T acc;
+        if constexpr (DC > 0) {
+            acc = coef(j, DC);
+#pragma unroll
+            for (int p = DC - 1; p >= 0; --p) acc = fma_t(acc, ph, coef(j, p));
+        } else {
+            const T *c = sc + (j - 1) * NC;
+            acc = c[D];
+            for (int p = D - 1; p >= 0; --p) acc = fma_t(acc, ph, c[p]);
+        }
+        return acc;
+    };
     const T *__restrict__ src = in + s.off;
     T *__restrict__ dst = out + s.off;
     const long long ld = s.ld;
     const int N = s.N;
-    const int chunk = blockDim.x * NPT;
-    const int x0 = bl.y + threadIdx.x;
-    T phi[NPT], f[NPT][B];
+    const int lane = threadIdx.x & 31;
+    const int x = bl.y + (int)threadIdx.x * 4;  // first node of this thread's group
+    const bool active = x < N;
+    const int xa = active ? x : 0;  // an in-bounds address for lanes past the end
+    T a[B][4];
+    T ed[B][W];  // edge sources: the last e nodes of the previous group (e > 0) or the first
+                 // |e| nodes of the next group (e < 0)
 #pragma unroll
-    for (int u = 0; u < NPT; ++u) {
-        const int x = min(x0 + u * (int)blockDim.x, N - 1);
-        T d = T(0);
-        phi[u] = src[x];
+    for (int j = 0; j < B; ++j) load4(src + j * ld + xa, a[j]);
 #pragma unroll
-        for (int j = 1; j < B; ++j) {
-            int xs = x - vel(j);
-            xs += xs < 0 ? N : 0;
-            xs -= xs >= N ? N : 0;
-            const T sj = src[(long long)j * ld + xs];
-            const T cur = src[(long long)j * ld + x];
-            d += sj - cur;
-            f[u][j] = sj;
+    for (int j = 1; j < B; ++j) {
+        const int e = vel(j);
+        if (e > 0) {
+#pragma unroll
+            for (int i = 0; i < e; ++i) ed[j][i] = __shfl_up_sync(0xffffffffu, a[j][4 - e + i], 1);
+            if (lane == 0 && xa >= 4)
+#pragma unroll
+                for (int i = 0; i < e; ++i) ed[j][i] = src[j * ld + xa - e + i];
+        } else {
+#pragma unroll
+            for (int i = 0; i < -e; ++i) ed[j][i] = __shfl_down_sync(0xffffffffu, a[j][i], 1);
+            if (lane == 31 && xa + 4 - e <= N)
+#pragma unroll
+                for (int i = 0; i < -e; ++i) ed[j][i] = src[j * ld + xa + 4 + i];
         }
-        phi[u] += d;
     }
-    const int xend = min(bl.y + chunk, N);
+    if (!active) return;
+    if (x >= W && x + 4 + W <= N) {
+        T o[B][4];
 #pragma unroll
-    for (int u = 0; u < NPT; ++u) {
-        const int x = x0 + u * (int)blockDim.x;
-        if (x >= xend) break;
-        const T ph = phi[u];
-        dst[x] = ph;
+        for (int i = 0; i < 4; ++i) {
+            T f[B];
+            T d = T(0);
 #pragma unroll
-        for (int j = 1; j < B; ++j) {
-            T acc;
-            if (DC > 0) {
-                acc = creg[(j - 1) * (DC + 1) + (DC > 0 ? DC : 0)];
-#pragma unroll
-                for (int p = (DC > 0 ? DC : 1) - 1; p >= 0; --p) acc = fma_t(acc, ph, creg[(j - 1) * (DC + 1) + p]);
-            } else {
-                const T *c = sc + (j - 1) * NC;
-                acc = c[D];
-                for (int p = D - 1; p >= 0; --p) acc = fma_t(acc, ph, c[p]);
+            for (int j = 1; j < B; ++j) {
+                const int e = vel(j);
+                const int q = i - e;  // source index within the group
+                const T sj = q < 0 ? ed[j][e + q] : (q >= 4 ? ed[j][q - 4] : a[j][q]);
+                d += sj - a[j][i];
+                f[j] = sj;
             }
-            dst[(long long)j * ld + x] = fma_t(omw, f[u][j], acc);
+            const T ph = a[0][i] + d;
+            o[0][i] = ph;
+#pragma unroll
+            for (int j = 1; j < B; ++j) o[j][i] = fma_t(omw, f[j], poly(j, ph));
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) store4(dst + j * ld + x, o[j]);
+    } else {
+        // within max|e| of a grid end: periodic indices, scalar accesses
+        for (int i = 0; i < 4 && x + i < N; ++i) {
+            const int xi = x + i;
+            T f[B];
+            T d = T(0);
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                int xs = xi - vel(j);
+                xs += xs < 0 ? N : 0;
+                xs -= xs >= N ? N : 0;
+                const T sj = src[j * ld + xs];
+                d += sj - src[j * ld + xi];
+                f[j] = sj;
+            }
+            const T ph = src[xi] + d;
+            dst[xi] = ph;
+#pragma unroll
+            for (int j = 1; j < B; ++j) dst[j * ld + xi] = fma_t(omw, f[j], poly(j, ph));
         }
     }
 }
@@ -193,7 +303,7 @@ struct OnchipInst {
     int pad;
 };
 
-template <typename T, int B, int K, int MAXT, bool HALO>
+template <typename T, int B, int K, int MAXT, bool HALO, int DC>
 __global__ void __launch_bounds__(MAXT, 1)
     k_onchip(const T *__restrict__ st_in, T *__restrict__ st_out, const OnchipInst *__restrict__ insts,
              const int *__restrict__ cta_first, const T *__restrict__ coefs, int nsteps, int max_inst) {
@@ -204,18 +314,23 @@ __global__ void __launch_bounds__(MAXT, 1)
     const int nt = blockDim.x;
     T *R = smem;                        // [2][NE][nt]
     T *L = R + 2 * NE * nt;             // [2][NE][nt]
-    T *tail = L + 2 * NE * nt;          // [2][NE][max_inst]                (ring)
+    T *tail = L + 2 * NE * nt;          // [2][NE][max_inst]                (ring; max_inst % 4 == 0)
     T *wrap = tail + 2 * NE * max_inst; // [max_inst][2][B-1][K]            (ring)
     T *scoef = HALO ? tail : wrap + 2 * (B - 1) * K * max_inst;
 
     const int first = cta_first[blockIdx.x], last = cta_first[blockIdx.x + 1];
     const int tid = threadIdx.x;
-    // stage every instance's coefficients (P_j rows then 1 - omega) into shared memory
+    // stage every instance's coefficients into shared memory: P_j rows at stride crow(Dk)
+    // (zero-padded up to the compile-time degree DC when DC > 0), then 1 - omega
     for (int i = first; i < last; ++i) {
         const OnchipInst I = insts[i];
-        const int n = (B - 1) * (I.D + 1);
-        for (int q = tid; q < n; q += nt) scoef[I.scoef + q] = coefs[I.gcoef + q];
-        if (tid == 0) scoef[I.scoef + n] = coefs[I.gcoef + 2 * n];
+        const int Dk = DC > 0 ? DC : I.D;
+        const int cs = crow(Dk), n = (B - 1) * (I.D + 1);
+        for (int q = tid; q < (B - 1) * cs; q += nt) {
+            const int j = q / cs, pp = q % cs;
+            scoef[I.scoef + q] = pp <= I.D ? coefs[I.gcoef + j * (I.D + 1) + pp] : T(0);
+        }
+        if (tid == 0) scoef[I.scoef + (B - 1) * cs] = coefs[I.gcoef + 2 * n];
     }
     // which instance does this thread serve?
     int me = -1;
@@ -254,8 +369,9 @@ __global__ void __launch_bounds__(MAXT, 1)
     }
     __syncthreads();
     const T *sc = scoef + I.scoef;
-    const int D = I.D;
-    const T omw = has ? sc[(B - 1) * (D + 1)] : T(0);
+    const int D = DC > 0 ? DC : I.D;
+    const int cs = crow(D);
+    const T omw = has ? sc[(B - 1) * cs] : T(0);
 
     for (int s = 0; s < nsteps; ++s) {
         T *Rb = R + (s & 1) * NE * nt;
@@ -363,15 +479,26 @@ __global__ void __launch_bounds__(MAXT, 1)
             // relax: s'_j = (1 - omega) f_j + P_j(phi'), Horner with coefficients from shared memory
 #pragma unroll
             for (int j = 1; j < B; ++j) {
-                const T *c = sc + (j - 1) * (D + 1);
+                const T *c = sc + (j - 1) * cs;
                 T acc[K];
-                const T cD = c[D];
+                if constexpr (DC > 0) {
+                    T cr[crow(DC)];
+                    load_row<T, crow(DC)>(c, cr);
 #pragma unroll
-                for (int k = 0; k < K; ++k) acc[k] = cD;
-                for (int p = D - 1; p >= 0; --p) {
-                    const T cp = c[p];
+                    for (int k = 0; k < K; ++k) acc[k] = cr[DC];
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc[k] = fma_t(acc[k], phi[k], cp);
+                    for (int p = DC - 1; p >= 0; --p)
+#pragma unroll
+                        for (int k = 0; k < K; ++k) acc[k] = fma_t(acc[k], phi[k], cr[p]);
+                } else {
+                    const T cD = c[D];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc[k] = cD;
+                    for (int p = D - 1; p >= 0; --p) {
+                        const T cp = c[p];
+#pragma unroll
+                        for (int k = 0; k < K; ++k) acc[k] = fma_t(acc[k], phi[k], cp);
+                    }
                 }
 #pragma unroll
                 for (int k = 0; k < K; ++k) v[j][k] = fma_t(omw, v[j][k], acc[k]);
