@@ -101,8 +101,8 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def ensemble_problems(rank=0):
-    return W.kdv_burgers_ensemble(seed=W.SEED + rank)
+def ensemble_problems(rank=0, members=4096):
+    return W.kdv_burgers_ensemble(count=members, seed=W.SEED + rank)
 
 
 def flops_per_node_update(b, D):
@@ -131,22 +131,23 @@ def run_ours(args, rank, world):
 
     with torch.cuda.stream(stream):
         if args.workload == "ensemble":
-            probs = ensemble_problems(rank)
+            probs = ensemble_problems(rank, args.members)
             nsteps = W.ENSEMBLE_STEPS
             prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
             solver = L.Batch(probs, precision=prec)
-            workload = (f"kdv_burgers_ensemble_4096: 4096 x N~U{{256..8192}} (sum N = {sum(p.N for p in probs)}), "
+            workload = (f"kdv_burgers_ensemble_{args.members}: {args.members} x N~U{{256..8192}} "
+                        f"(sum N = {sum(p.N for p in probs)}), "
                         f"D1Q5 scheme 1, dx={W.ENSEMBLE_DX}, dt={W.ENSEMBLE_DT}, tau={W.ENSEMBLE_TAU}, "
                         f"{nsteps} steps per benchmark step")
         else:
-            p = W.long_grid_config(nsteps=1000)
+            p = W.long_grid_config(N=args.nodes, nsteps=1000)
             probs = [p]
             nsteps = p.nsteps
             prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
             solver = L.Batch(probs, precision=prec)
             if args.kernel == "stream":
                 solver.set_kernel(L.KERNEL_STREAM)
-            workload = (f"kawahara_long_grid: N=2^24, D1Q7 scheme 1, dx=0.1, dt=1e-4, tau=2.02, "
+            workload = (f"kawahara_long_grid: N={args.nodes}, D1Q7 scheme 1, dx=0.1, dt=1e-4, tau=2.02, "
                         f"{nsteps} steps per benchmark step "
                         f"({'streaming kernel' if args.kernel == 'stream' else 'temporally blocked windows'})")
         total = sum(p.N for p in probs)
@@ -198,23 +199,23 @@ def run_ours(args, rank, world):
 
         # accuracy beside the number: members against the FP64 path (ensemble) or the exact
         # solution (long grid)
-        accuracy = accuracy_report(L, args, probs, solver, prec, torch)
+        accuracy = None if args.quick else accuracy_report(L, args, probs, solver, prec, torch)
 
         # end to end through the public API, host buffers
-        e2e_steps = max(1, min(args.steps, 5))
+        e2e_steps = 0 if args.quick else max(1, min(args.steps, 5))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             solver.set_phi(pinned_in)  # host pointer (pinned): copied inside the call
             solver.step(nsteps)
             solver.read_phi(pinned_out.numpy())
-        t_e2e = (time.perf_counter() - t0) / e2e_steps
-        e2e = {"value": world * upd_step / t_e2e, "unit": "node-updates/s",
-               "h2d_bytes_per_step": total * 8, "d2h_bytes_per_step": total * 8}
+        t_e2e = (time.perf_counter() - t0) / max(e2e_steps, 1)
+        e2e = None if args.quick else {"value": world * upd_step / t_e2e, "unit": "node-updates/s",
+                                       "h2d_bytes_per_step": total * 8, "d2h_bytes_per_step": total * 8}
 
         # FP64 plain path on the same workload (fewer steps: it is ALU bound on GB300)
         fp64 = None
-        if args.workload == "ensemble" and prec == L.FP32_DEV and not args.no_fp64:
+        if args.workload == "ensemble" and prec == L.FP32_DEV and not args.no_fp64 and not args.quick:
             fp64 = fp64_plain(L, probs, phi0_d, nsteps, stream, torch, steps=max(1, min(args.steps, 2)))
 
         kern_ms = float(np.mean(kern))
@@ -389,6 +390,10 @@ def main():
                     help="long_grid only: the streaming kernel instead of temporally blocked windows")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--members", type=int, default=4096, help="ensemble members (profiling: smaller)")
+    ap.add_argument("--nodes", type=int, default=1 << 24, help="long-grid nodes (profiling: smaller)")
+    ap.add_argument("--quick", action="store_true",
+                    help="only the timed region: no accuracy check, e2e, FP64 or CPU legs (profiling)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -408,7 +413,7 @@ def main():
         dist.init_process_group("nccl")
     # the CPU baseline runs before any GPU work so no thread pool is forked after CUDA starts
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and not args.quick:
         cpu = cpu_oracle_rate(args)
     from paper_0907_1720_gb300 import build as B
 
