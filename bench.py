@@ -255,6 +255,70 @@ def run_ours(args, rank, world):
     return line
 
 
+def run_serving(args):
+    """Continuous batching: Poisson arrivals of mixed requests submitted from a host thread
+    while the server runs; latency = finish - submit on the server's clock."""
+    import torch
+
+    from paper_0907_1720_gb300 import lbhpde as L
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    out = []
+    rates = [args.rate] + ([args.rate / 4, args.rate / 16] if args.sweep else [])
+    for rate in rates:
+        count = min(args.requests, max(64, int(args.window * rate)))
+        reqs = W.serving_requests(count, rate=rate, seed=W.SEED + int(rate))
+        srv = L.Server(precision=L.FP32_DEV if args.precision == "fp32" else L.FP64,
+                       device_bytes=args.arena_gb << 30, max_active=4096, steps_per_block=args.block)
+        ids = [None] * count
+        t_start = time.perf_counter()
+
+        def submitter():
+            for i, (ta, p) in enumerate(reqs):
+                dt_ = ta - (time.perf_counter() - t_start)
+                if dt_ > 0:
+                    time.sleep(dt_)
+                ids[i] = srv.submit_problem(p)
+
+        th = threading.Thread(target=submitter)
+        with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+            th.start()
+            done = {}
+            while len(done) < count:
+                for i in range(count):
+                    if i in done or ids[i] is None:
+                        continue
+                    rc, _, info = srv.poll(ids[i])
+                    if rc != L.PENDING:
+                        done[i] = (rc, info)
+                time.sleep(0.002)
+            th.join()
+        st = srv.stats()
+        srv.close()
+        lat = np.array([done[i][1]["finish_s"] - done[i][1]["submit_s"] for i in range(count)])
+        t0 = min(done[i][1]["submit_s"] for i in range(count))
+        t1 = max(done[i][1]["finish_s"] for i in range(count))
+        work = sum(p.N * p.nsteps for _, p in reqs)
+        ok = sum(1 for i in range(count) if done[i][0] == L.OK)
+        out.append({"rate_req_s": rate, "requests": count, "ok": ok,
+                    "offered_node_updates_s": work / reqs[-1][0],
+                    "achieved_node_updates_s": work / (t1 - t0), "makespan_s": t1 - t0,
+                    "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                    "launches": st["launches"], "clocks": clk.summary()})
+    head = out[0]
+    line = {"metric": METRIC, "value": head["achieved_node_updates_s"], "unit": "node-updates/s", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "ms_per_step": head["makespan_s"] * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+            "data": "synthetic (seeded Poisson request stream)",
+            "config": {"workload": f"serving: Poisson arrivals (mean {args.rate:g} req/s) of mixed KdV / mKdV / "
+                                   f"K(2,2) / KS / Kawahara requests, N log-uniform [128, 65536], steps uniform "
+                                   f"[1e3, 1e5], FP32 deviation storage, memory-admitted",
+                       "window_requests": head["requests"], "steps_per_block": args.block},
+            "p50_latency_s": head["p50_latency_s"], "p99_latency_s": head["p99_latency_s"],
+            "clocks": head["clocks"], "sweep": out}
+    return line
+
+
 def solver_kernel_launches(args, nsteps):
     """Kernel launches of one lbhpde_batch_step(nsteps) call: the streaming kernel launches once
     per step; the ensemble's resident instances launch once and its halo windows once per 64
@@ -384,7 +448,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "long_grid"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "long_grid", "serving"])
+    ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrival rate (requests/s)")
+    ap.add_argument("--window", type=float, default=1.0, help="serving: seconds of arrivals per rate")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: cap on requests per rate")
+    ap.add_argument("--sweep", action="store_true", help="serving: also rates / 4 and / 16")
+    ap.add_argument("--block", type=int, default=256, help="serving: steps per scheduling block")
+    ap.add_argument("--arena-gb", type=int, default=8, help="serving: device arena (GiB)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--kernel", default="auto", choices=["auto", "stream"],
                     help="long_grid only: the streaming kernel instead of temporally blocked windows")
@@ -418,6 +488,10 @@ def main():
     from paper_0907_1720_gb300 import build as B
 
     B.build()
+    if args.workload == "serving":
+        if rank == 0:
+            print(json.dumps(run_serving(args)), flush=True)
+        return
     line = run_ours(args, rank, world)
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}

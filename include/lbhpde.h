@@ -204,6 +204,65 @@ int lbhpde_batch_set_kernel(lbhpde_batch_t b, int kernel, int nodes_per_thread, 
 int lbhpde_batch_size(lbhpde_batch_t b, long *total_nodes, size_t *device_bytes);
 int lbhpde_batch_destroy(lbhpde_batch_t b);
 
+/* ------------------------------------------------------------------ serving */
+
+/* A request server: continuous batching of independent solves on one GPU (SURVEY's serving
+ * row; the paper has no serving layer).  Requests are admitted as device memory and slots
+ * free up, keep their distributions resident in the server's device arena, and advance
+ * together in step blocks on the on-chip kernel; a request that arrives while others run is
+ * admitted at the next block boundary.  Each request's arithmetic is that of a single-instance
+ * solve with the same kernel, so its result does not depend on what else is in the mix.
+ * The server owns one scheduler thread and one CUDA stream; all entry points are thread-safe. */
+typedef struct lbhpde_server_s *lbhpde_server_t;
+
+typedef struct {
+    int m;
+    double alpha[6];
+    lbhpde_pi pi[6];
+    long N;
+    double dx, dt, tau;
+    int lattice, scheme;
+    long nsteps;           /* time steps to take (>= 0)                                  */
+    const double *phi0;    /* [N] host doubles, copied by lbhpde_submit                   */
+} lbhpde_request;
+
+typedef struct {
+    int status;            /* LBHPDE_PENDING, LBHPDE_OK, LBHPDE_ERR_DIVERGED, LBHPDE_ERR_CUDA */
+    long steps_done;
+    double submit_s;       /* host clock, seconds since the server started                */
+    double admit_s;        /* -1 while queued                                             */
+    double finish_s;       /* -1 while pending; latency = finish_s - submit_s             */
+    double sum_phi;        /* sum of the final phi (FP64)                                  */
+    long nonfinite;        /* nodes whose final phi is not finite                          */
+} lbhpde_result;
+
+typedef struct {
+    long queued, in_flight, completed;
+    double node_updates;   /* completed requests' N * nsteps                               */
+    size_t bytes_in_use, bytes_total;
+    long launches;
+    int error;             /* sticky status of the scheduler (LBHPDE_OK unless a CUDA call failed) */
+} lbhpde_server_info;
+
+/* device_bytes (>= 1 MiB) is the state arena, allocated at creation; each request holds
+ * 2 * b * ceil32(N) elements of the chosen precision while admitted.  max_active (1..65536)
+ * bounds the admitted requests; steps_per_block (0 = 256) is the admission granularity. */
+int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t device_bytes, int max_active,
+                         int steps_per_block, int device);
+/* Step a0 runs here on the caller's thread.  Errors: LBHPDE_ERR_ARG (invalid request),
+ * LBHPDE_ERR_OOM (larger than the whole arena), LBHPDE_ERR_CUDA (the server has failed). */
+int lbhpde_submit(lbhpde_server_t s, const lbhpde_request *req, uint64_t *id);
+/* Non-blocking.  LBHPDE_PENDING while the request is queued or running (info is filled);
+ * otherwise its final status, phi copied to phi_out ([N] host doubles, may be NULL), and the
+ * request released (a later poll returns LBHPDE_ERR_NOT_FOUND). */
+int lbhpde_poll(lbhpde_server_t s, uint64_t id, double *phi_out, lbhpde_result *info);
+/* As lbhpde_poll, waiting at most timeout_s seconds; LBHPDE_ERR_TIMEOUT when it runs out. */
+int lbhpde_wait(lbhpde_server_t s, uint64_t id, double timeout_s, double *phi_out, lbhpde_result *info);
+int lbhpde_server_stats(lbhpde_server_t s, lbhpde_server_info *out);
+/* Stops the scheduler after its current step block and frees everything; requests not yet
+ * polled are dropped. */
+int lbhpde_server_destroy(lbhpde_server_t s);
+
 /* ------------------------------------------------- diagnostics, no allocation */
 
 /* Largest N lbhpde_phi_diagnostics_noalloc accepts (2^24 nodes). */

@@ -10,17 +10,18 @@
 #include <vector>
 
 #include "lbhpde.h"
+#include "lbhpde_internal.h"
 #include "lbhpde_kernels.cuh"
 
+using lbh::kChunk;
+using lbh::kGenericThreads;
 using lbk::DiagPart;
 using lbk::OnchipInst;
 using lbk::Seg;
 
 namespace {
 
-constexpr int kChunk = 1024;          // nodes per block of the node-parallel kernels
 constexpr int kStreamThreads = kChunk / 4;  // k_stream: one group of 4 nodes per thread
-constexpr int kGenericThreads = 256;  // init / readout / diagnostics
 
 #define CK(call)                                              \
     do {                                                      \
@@ -50,10 +51,10 @@ struct Group {
     // windows for instances longer than one CTA holds (halo)
     bool onchip_ok = false;  // false: every member uses the streaming kernel
     struct Plan {
-        int ncta = 0, nthreads = 0, max_inst = 0;
-        size_t smem = 0;
+        lbh::Packed host;
         OnchipInst *insts = nullptr;
         int *cta_first = nullptr;
+        int ncta() const { return host.ncta(); }
     } ring, halo;
     int K = 0, maxt = 0, tblk = 0;
     int dc = 0;  // compile-time degree of the on-chip kernel variant (0 = run time)
@@ -137,9 +138,10 @@ struct lbhpde_ctx {
     lbhpde_batch_s *b = nullptr;
 };
 
-namespace {
+// ===================================================== shared on-chip planning and launch
 
-// On-chip kernel variants: (state type, lattice, nodes per thread) -> maximum CTA threads.
+namespace lbh {
+
 int onchip_maxt(size_t esz, int b, int K) {
     if (esz == 4) {
         if (b == 5) return K == 8 ? 512 : (K == 4 ? 1024 : (K == 2 ? 1024 : 0));
@@ -148,65 +150,234 @@ int onchip_maxt(size_t esz, int b, int K) {
     if (b == 5) return K == 4 ? 512 : (K == 2 ? 1024 : 0);
     return K == 4 ? 256 : 0;
 }
+
 int default_K(size_t esz, int b) { return esz == 4 && b == 5 ? 8 : 4; }
 
+int default_tblk(int capacity, int W) {
+    int t = 64;
+    while (t > 1 && capacity - 2 * t * W < capacity * 3 / 4) t /= 2;
+    return t;
+}
+
+int onchip_dc(int b, int maxD) { return maxD == (b == 5 ? 5 : 7) ? maxD : 0; }
+
+int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Packed &out) {
+    out = Packed{};
+    const int maxt = onchip_maxt(esz, b, K);
+    if (maxt == 0) return LBHPDE_ERR_UNSUPPORTED;
+    auto thr = [&](long long n) { return (int)((n + K - 1) / K); };
+    auto pad = [&](long long n) { return (thr(n) + 31) & ~31; };
+    std::vector<int> order(m.size());
+    for (size_t i = 0; i < m.size(); ++i) {
+        if ((long long)m[i].seg.N > (long long)maxt * K) return LBHPDE_ERR_UNSUPPORTED;
+        order[i] = (int)i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return pad(m[a].seg.N) > pad(m[c].seg.N); });
+    struct Cta {
+        int used = 0;
+        std::vector<int> inst;
+    };
+    std::vector<Cta> ctas;
+    for (int i : order) {
+        bool placed = false;
+        for (auto &c : ctas) {
+            if (c.used + pad(m[i].seg.N) <= maxt && (int)c.inst.size() < 32) {
+                c.inst.push_back(i);
+                c.used += pad(m[i].seg.N);
+                placed = true;
+                break;
+            }
+        }
+        if (!placed) {
+            Cta c;
+            c.inst.push_back(i);
+            c.used = pad(m[i].seg.N);
+            ctas.push_back(c);
+        }
+    }
+    size_t coef_max = 0;
+    for (auto &c : ctas) {
+        out.first.push_back((int)out.insts.size());
+        int tb = 0, sco = 0, il = 0;
+        for (int i : c.inst) {
+            const Seg &s = m[i].seg;
+            OnchipInst I{};
+            I.off = s.off;
+            I.off2 = m[i].off2;
+            I.ld = s.ld;
+            I.N = s.N;
+            I.D = s.D;
+            I.gcoef = s.coef;
+            I.scoef = sco;
+            I.tbase = tb;
+            I.nthr = thr(s.N);
+            I.il = il++;
+            I.x0 = 0;
+            I.npos = s.N;
+            I.vlo = 0;
+            I.vhi = s.N;
+            I.steps = m[i].steps;
+            out.insts.push_back(I);
+            sco += lbk::cblock(b, dc > 0 ? dc : s.D);
+            tb += pad(s.N);
+        }
+        out.nthreads = std::max(out.nthreads, tb);
+        out.max_inst = std::max(out.max_inst, (int)c.inst.size());
+        coef_max = std::max(coef_max, (size_t)sco);
+    }
+    out.first.push_back((int)out.insts.size());
+    out.max_inst = (out.max_inst + 3) & ~3;  // keeps the shared-memory coefficient rows 16-byte aligned
+    const int ne = lbk::nedge(b);
+    out.smem = (size_t(4) * ne * out.nthreads + size_t(2) * ne * out.max_inst +
+                size_t(2) * (b - 1) * K * out.max_inst + coef_max) * esz;
+    if (out.smem > 227 * 1024) return LBHPDE_ERR_UNSUPPORTED;
+    return LBHPDE_OK;
+}
+
+int pack_halo(int b, size_t esz, int K, int dc, int H, const std::vector<Member> &m, Packed &out) {
+    out = Packed{};
+    const int maxt = onchip_maxt(esz, b, K);
+    if (maxt == 0) return LBHPDE_ERR_UNSUPPORTED;
+    const int valid = maxt * K - 2 * H;
+    if (valid < 32) return LBHPDE_ERR_UNSUPPORTED;
+    size_t coef_max = 0;
+    for (const Member &mb : m) {
+        const Seg &s = mb.seg;
+        for (long long x = 0; x < s.N; x += valid) {
+            const int v = (int)std::min<long long>(valid, s.N - x);
+            OnchipInst I{};
+            I.off = s.off;
+            I.off2 = mb.off2;
+            I.ld = s.ld;
+            I.N = s.N;
+            I.D = s.D;
+            I.gcoef = s.coef;
+            I.scoef = 0;
+            I.tbase = 0;
+            I.npos = v + 2 * H;
+            I.nthr = (I.npos + K - 1) / K;
+            I.il = 0;
+            I.x0 = (int)(x - H);
+            I.vlo = H;
+            I.vhi = H + v;
+            I.steps = mb.steps;
+            out.first.push_back((int)out.insts.size());
+            out.insts.push_back(I);
+            coef_max = std::max(coef_max, (size_t)lbk::cblock(b, dc > 0 ? dc : s.D));
+        }
+    }
+    out.first.push_back((int)out.insts.size());
+    out.nthreads = maxt;
+    out.max_inst = 1;
+    out.smem = (size_t(4) * lbk::nedge(b) * maxt + coef_max) * esz;
+    return LBHPDE_OK;
+}
+
+namespace {
+
+#define LBH_CK(call)                      \
+    do {                                  \
+        cudaError_t e_ = (call);          \
+        if (e_ != cudaSuccess) {          \
+            (void)cudaGetLastError();     \
+            return LBHPDE_ERR_CUDA;       \
+        }                                 \
+    } while (0)
+
+struct OnchipArgs {
+    const Packed *p;
+    const OnchipInst *insts;
+    const int *first;
+    const void *in;
+    void *out;
+    const void *coefT;
+    int nsteps;
+    cudaStream_t st;
+};
+
 template <typename T, int B, int K, int MAXT, bool HALO, int DC>
-int launch_onchip_t(lbhpde_batch_s *bt, Group::Plan &pl, const void *in, void *out, int nsteps) {
+int launch_onchip_t(const OnchipArgs &a) {
     auto fn = lbk::k_onchip<T, B, K, MAXT, HALO, DC>;
-    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
-    fn<<<pl.ncta, pl.nthreads, pl.smem, bt->stream>>>((const T *)in, (T *)out, pl.insts, pl.cta_first,
-                                                       (const T *)bt->coefT, nsteps, pl.max_inst);
-    CK(cudaGetLastError());
+    LBH_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.p->smem));
+    fn<<<a.p->ncta(), a.p->nthreads, a.p->smem, a.st>>>((const T *)a.in, (T *)a.out, a.insts, a.first,
+                                                         (const T *)a.coefT, a.nsteps, a.p->max_inst);
+    LBH_CK(cudaGetLastError());
     return LBHPDE_OK;
 }
 
 // compile-time polynomial degree: D = 5 on D1Q5 and D = 7 on D1Q7 (the KdV/KS/KdV-Burgers and
 // Kawahara families), run-time degree otherwise
 template <typename T, int B, int K, int MAXT, bool HALO>
-int launch_onchip_d(lbhpde_batch_s *bt, Group &g, Group::Plan &pl, const void *in, void *out, int nsteps) {
+int launch_onchip_d(int dc, const OnchipArgs &a) {
     constexpr int DC = B == 5 ? 5 : 7;
-    if (g.dc == DC) return launch_onchip_t<T, B, K, MAXT, HALO, DC>(bt, pl, in, out, nsteps);
-    return launch_onchip_t<T, B, K, MAXT, HALO, 0>(bt, pl, in, out, nsteps);
+    if (dc == DC) return launch_onchip_t<T, B, K, MAXT, HALO, DC>(a);
+    return launch_onchip_t<T, B, K, MAXT, HALO, 0>(a);
 }
 
 template <typename T, int B, bool HALO>
-int launch_onchip_b(lbhpde_batch_s *bt, Group &g, Group::Plan &pl, const void *in, void *out, int nsteps) {
+int launch_onchip_b(int K, int dc, const OnchipArgs &a) {
     if constexpr (sizeof(T) == 4) {
         if constexpr (B == 5) {
-            if (g.K == 8) return launch_onchip_d<T, B, 8, 512, HALO>(bt, g, pl, in, out, nsteps);
-            if (g.K == 4) return launch_onchip_d<T, B, 4, 1024, HALO>(bt, g, pl, in, out, nsteps);
-            if (g.K == 2) return launch_onchip_d<T, B, 2, 1024, HALO>(bt, g, pl, in, out, nsteps);
+            if (K == 8) return launch_onchip_d<T, B, 8, 512, HALO>(dc, a);
+            if (K == 4) return launch_onchip_d<T, B, 4, 1024, HALO>(dc, a);
+            if (K == 2) return launch_onchip_d<T, B, 2, 1024, HALO>(dc, a);
         } else {
-            if (g.K == 8) return launch_onchip_d<T, B, 8, 256, HALO>(bt, g, pl, in, out, nsteps);
-            if (g.K == 4) return launch_onchip_d<T, B, 4, 512, HALO>(bt, g, pl, in, out, nsteps);
+            if (K == 8) return launch_onchip_d<T, B, 8, 256, HALO>(dc, a);
+            if (K == 4) return launch_onchip_d<T, B, 4, 512, HALO>(dc, a);
         }
     } else {
         if constexpr (B == 5) {
-            if (g.K == 4) return launch_onchip_d<T, B, 4, 512, HALO>(bt, g, pl, in, out, nsteps);
-            if (g.K == 2) return launch_onchip_d<T, B, 2, 1024, HALO>(bt, g, pl, in, out, nsteps);
+            if (K == 4) return launch_onchip_d<T, B, 4, 512, HALO>(dc, a);
+            if (K == 2) return launch_onchip_d<T, B, 2, 1024, HALO>(dc, a);
         } else {
-            if (g.K == 4) return launch_onchip_d<T, B, 4, 256, HALO>(bt, g, pl, in, out, nsteps);
+            if (K == 4) return launch_onchip_d<T, B, 4, 256, HALO>(dc, a);
         }
     }
     return LBHPDE_ERR_UNSUPPORTED;
 }
 
-int launch_onchip(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *out, int nsteps) {
-    Group::Plan &pl = halo ? g.halo : g.ring;
-    if (pl.ncta == 0) return LBHPDE_OK;
-    if (bt->esz == 4) {
-        if (g.b == 5)
-            return halo ? launch_onchip_b<float, 5, true>(bt, g, pl, in, out, nsteps)
-                        : launch_onchip_b<float, 5, false>(bt, g, pl, in, out, nsteps);
-        return halo ? launch_onchip_b<float, 7, true>(bt, g, pl, in, out, nsteps)
-                    : launch_onchip_b<float, 7, false>(bt, g, pl, in, out, nsteps);
+}  // namespace
+
+int launch_onchip(int b, size_t esz, int K, int dc, bool halo, const Packed &p, const OnchipInst *insts_d,
+                  const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st) {
+    if (p.ncta() == 0 || nsteps <= 0) return LBHPDE_OK;
+    const OnchipArgs a{&p, insts_d, first_d, in, out, coefT, nsteps, st};
+    if (esz == 4) {
+        if (b == 5)
+            return halo ? launch_onchip_b<float, 5, true>(K, dc, a) : launch_onchip_b<float, 5, false>(K, dc, a);
+        return halo ? launch_onchip_b<float, 7, true>(K, dc, a) : launch_onchip_b<float, 7, false>(K, dc, a);
     }
-    if (g.b == 5)
-        return halo ? launch_onchip_b<double, 5, true>(bt, g, pl, in, out, nsteps)
-                    : launch_onchip_b<double, 5, false>(bt, g, pl, in, out, nsteps);
-    return halo ? launch_onchip_b<double, 7, true>(bt, g, pl, in, out, nsteps)
-                : launch_onchip_b<double, 7, false>(bt, g, pl, in, out, nsteps);
+    if (b == 5) return halo ? launch_onchip_b<double, 5, true>(K, dc, a) : launch_onchip_b<double, 5, false>(K, dc, a);
+    return halo ? launch_onchip_b<double, 7, true>(K, dc, a) : launch_onchip_b<double, 7, false>(K, dc, a);
 }
+
+int launch_init(int b, size_t esz, void *st, const Seg *segs, const int2 *blocks, int nb, const double *coefd,
+                const double *phi0, const long long *blk_off, cudaStream_t stream) {
+    if (nb == 0) return LBHPDE_OK;
+    if (esz == 4) {
+        if (b == 5)
+            lbk::k_init<float, 5><<<nb, kGenericThreads, 0, stream>>>((float *)st, segs, blocks, coefd, phi0, blk_off,
+                                                                       kChunk);
+        else
+            lbk::k_init<float, 7><<<nb, kGenericThreads, 0, stream>>>((float *)st, segs, blocks, coefd, phi0, blk_off,
+                                                                       kChunk);
+    } else {
+        if (b == 5)
+            lbk::k_init<double, 5><<<nb, kGenericThreads, 0, stream>>>((double *)st, segs, blocks, coefd, phi0,
+                                                                        blk_off, kChunk);
+        else
+            lbk::k_init<double, 7><<<nb, kGenericThreads, 0, stream>>>((double *)st, segs, blocks, coefd, phi0,
+                                                                        blk_off, kChunk);
+    }
+    LBH_CK(cudaGetLastError());
+    return LBHPDE_OK;
+}
+
+}  // namespace lbh
+
+// ============================================================================= batches
+
+namespace {
 
 template <typename T, int B, int DC, bool PARAMC>
 int launch_stream_t(lbhpde_batch_s *bt, Group &g) {
@@ -235,149 +406,47 @@ int launch_stream_b(lbhpde_batch_s *bt, Group &g) {
     return launch_stream_t<T, B, 0, false>(bt, g);
 }
 
-// Steps per halo launch: the halo H = tblk * max|e| must leave most of a window valid.
-int default_tblk(int capacity, int W) {
-    int t = 64;
-    while (t > 1 && capacity - 2 * t * W < capacity * 3 / 4) t /= 2;
-    return t;
+int upload_plan(lbhpde_batch_s *bt, Group::Plan &pl) {
+    if (pl.host.ncta() == 0) return LBHPDE_OK;
+    RC(bt->upload(&pl.insts, pl.host.insts));
+    RC(bt->upload(&pl.cta_first, pl.host.first));
+    return LBHPDE_OK;
 }
 
-// Pack a group's instances for the on-chip kernel: members that fit one CTA become ring
-// instances (first fit, largest first, warp-aligned thread runs, at most 32 per CTA); longer
-// members are cut into halo windows, one per CTA.
+// Members that fit one CTA become resident instances; longer members (or all, with
+// force_halo) are cut into temporally blocked windows of tblk steps.
 int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) {
     g.onchip_ok = false;
-    const int maxt = onchip_maxt(bt->esz, g.b, K);
+    const int maxt = lbh::onchip_maxt(bt->esz, g.b, K);
     if (maxt == 0 || K < lbk::wmax(g.b)) return LBHPDE_ERR_UNSUPPORTED;
     const int W = lbk::wmax(g.b);
     const int cap = maxt * K;
-    g.dc = (g.maxD == (g.b == 5 ? 5 : 7)) ? g.maxD : 0;
-    if (tblk <= 0) tblk = default_tblk(cap, W);
+    g.dc = lbh::onchip_dc(g.b, g.maxD);
+    if (tblk <= 0) tblk = lbh::default_tblk(cap, W);
     const int H = tblk * W;
     if (cap - 2 * H < 32) return LBHPDE_ERR_UNSUPPORTED;
-    const int ne = lbk::nedge(g.b);
-    auto thr = [&](long long n) { return (int)((n + K - 1) / K); };
-    auto pad = [&](long long n) { return (thr(n) + 31) & ~31; };
-
-    // ---- ring instances
-    std::vector<int> ring, halo;
-    for (int i : g.members) (bt->N[i] <= cap && !force_halo ? ring : halo).push_back(i);
-    std::stable_sort(ring.begin(), ring.end(), [&](int a, int c) { return pad(bt->N[a]) > pad(bt->N[c]); });
-    struct Cta {
-        int used = 0;
-        std::vector<int> inst;
-    };
-    std::vector<Cta> ctas;
-    for (int i : ring) {
-        bool placed = false;
-        for (auto &c : ctas) {
-            if (c.used + pad(bt->N[i]) <= maxt && (int)c.inst.size() < 32) {
-                c.inst.push_back(i);
-                c.used += pad(bt->N[i]);
-                placed = true;
-                break;
-            }
-        }
-        if (!placed) {
-            Cta c;
-            c.inst.push_back(i);
-            c.used = pad(bt->N[i]);
-            ctas.push_back(c);
-        }
+    std::vector<lbh::Member> ring, halo;
+    for (int i : g.members) {
+        const lbh::Member mb{bt->segs_h[i], bt->segs_h[i].off, 1 << 30};
+        (bt->N[i] <= cap && !force_halo ? ring : halo).push_back(mb);
     }
-    {
-        std::vector<OnchipInst> insts;
-        std::vector<int> first;
-        int nthreads = 32, max_inst = 1;
-        size_t coef_max = 0;
-        for (auto &c : ctas) {
-            first.push_back((int)insts.size());
-            int tb = 0, sco = 0, il = 0;
-            for (int i : c.inst) {
-                const Seg &s = bt->segs_h[i];
-                OnchipInst I{};
-                I.off = s.off;
-                I.ld = s.ld;
-                I.N = s.N;
-                I.D = s.D;
-                I.gcoef = s.coef;
-                I.scoef = sco;
-                I.tbase = tb;
-                I.nthr = thr(s.N);
-                I.il = il++;
-                I.x0 = 0;
-                I.npos = s.N;
-                I.vlo = 0;
-                I.vhi = s.N;
-                insts.push_back(I);
-                sco += lbk::cblock(g.b, g.dc > 0 ? g.dc : s.D);
-                tb += pad(s.N);
-            }
-            nthreads = std::max(nthreads, tb);
-            max_inst = std::max(max_inst, (int)c.inst.size());
-            coef_max = std::max(coef_max, (size_t)sco);
-        }
-        first.push_back((int)insts.size());
-        max_inst = (max_inst + 3) & ~3;  // keeps the shared-memory coefficient rows 16-byte aligned
-        Group::Plan &pl = g.ring;
-        pl = Group::Plan{};
-        if (!ctas.empty()) {
-            pl.smem = (size_t(4) * ne * nthreads + size_t(2) * ne * max_inst + size_t(2) * (g.b - 1) * K * max_inst +
-                       coef_max) * bt->esz;
-            if (pl.smem > 227 * 1024) return LBHPDE_ERR_UNSUPPORTED;
-            RC(bt->upload(&pl.insts, insts));
-            RC(bt->upload(&pl.cta_first, first));
-            pl.ncta = (int)ctas.size();
-            pl.nthreads = nthreads;
-            pl.max_inst = max_inst;
-        }
-    }
-    // ---- halo windows (valid width cap - 2H)
-    {
-        const int valid = cap - 2 * H;
-        std::vector<OnchipInst> insts;
-        std::vector<int> first;
-        size_t coef_max = 0;
-        for (int i : halo) {
-            const Seg &s = bt->segs_h[i];
-            for (long long x = 0; x < s.N; x += valid) {
-                const int v = (int)std::min<long long>(valid, s.N - x);
-                OnchipInst I{};
-                I.off = s.off;
-                I.ld = s.ld;
-                I.N = s.N;
-                I.D = s.D;
-                I.gcoef = s.coef;
-                I.scoef = 0;
-                I.tbase = 0;
-                I.npos = v + 2 * H;
-                I.nthr = thr(I.npos);
-                I.il = 0;
-                I.x0 = (int)(x - H);
-                I.vlo = H;
-                I.vhi = H + v;
-                first.push_back((int)insts.size());
-                insts.push_back(I);
-                coef_max = std::max(coef_max, (size_t)lbk::cblock(g.b, g.dc > 0 ? g.dc : s.D));
-            }
-        }
-        first.push_back((int)insts.size());
-        Group::Plan &pl = g.halo;
-        pl = Group::Plan{};
-        if (!insts.empty()) {
-            pl.nthreads = maxt;
-            pl.max_inst = 1;
-            pl.smem = (size_t(4) * ne * maxt + coef_max) * bt->esz;
-            RC(bt->upload(&pl.insts, insts));
-            RC(bt->upload(&pl.cta_first, first));
-            pl.ncta = (int)insts.size();
-        }
-    }
+    g.ring = Group::Plan{};
+    g.halo = Group::Plan{};
+    if (!ring.empty()) RC(lbh::pack_ring(g.b, bt->esz, K, g.dc, ring, g.ring.host));
+    if (!halo.empty()) RC(lbh::pack_halo(g.b, bt->esz, K, g.dc, H, halo, g.halo.host));
+    RC(upload_plan(bt, g.ring));
+    RC(upload_plan(bt, g.halo));
     g.K = K;
     g.maxt = maxt;
     g.tblk = tblk;
     g.onchip_ok = true;
     return LBHPDE_OK;
+}
+
+int launch_group(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *out, int nsteps) {
+    Group::Plan &pl = halo ? g.halo : g.ring;
+    return lbh::launch_onchip(g.b, bt->esz, g.K, g.dc, halo, pl.host, pl.insts, pl.cta_first, in, out, bt->coefT,
+                              nsteps, bt->stream);
 }
 
 int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
@@ -483,7 +552,7 @@ int choose_kernels(lbhpde_batch_s *bt) {
         if (g.members.empty()) continue;
         g.onchip_ok = false;
         if (bt->kernel == LBHPDE_KERNEL_STREAM) continue;
-        const int K = bt->K_req > 0 ? bt->K_req : default_K(bt->esz, g.b);
+        const int K = bt->K_req > 0 ? bt->K_req : lbh::default_K(bt->esz, g.b);
         int rc = plan_onchip(bt, g, K, bt->spl_req, bt->kernel == LBHPDE_KERNEL_HALO);
         if (rc != LBHPDE_OK) return rc;
     }
@@ -498,7 +567,7 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
     for (auto &g : bt->groups) {
         if (g.members.empty()) continue;
         if (!g.onchip_ok) any_stream = true;
-        else if (g.halo.ncta) any_halo = true;
+        else if (g.halo.ncta()) any_halo = true;
     }
     if (any_stream) {
         // one fused collide+stream launch per step, ping-pong buffers
@@ -518,17 +587,17 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
     // read the current buffer once and write the buffer the halo launches end in
     int tb = 1 << 30;
     for (auto &g : bt->groups)
-        if (!g.members.empty() && g.halo.ncta) tb = std::min(tb, g.tblk);
+        if (!g.members.empty() && g.halo.ncta()) tb = std::min(tb, g.tblk);
     const long nchunks = any_halo ? (nsteps + tb - 1) / tb : 0;
     const int cur0 = bt->cur, cur1 = bt->cur ^ (int)(nchunks & 1);
     for (auto &g : bt->groups) {
-        if (g.members.empty() || !g.ring.ncta) continue;
+        if (g.members.empty() || !g.ring.ncta()) continue;
         const long spl = bt->spl_req > 0 ? bt->spl_req : (1L << 30);
         long left = nsteps;
         bool firstl = true;
         while (left > 0) {
             const int n = (int)std::min(left, spl);
-            RC(launch_onchip(bt, g, false, bt->st[firstl ? cur0 : cur1], bt->st[cur1], n));
+            RC(launch_group(bt, g, false, bt->st[firstl ? cur0 : cur1], bt->st[cur1], n));
             firstl = false;
             left -= n;
         }
@@ -537,7 +606,7 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
     for (long c = 0; c < nchunks; ++c) {
         const int n = (int)std::min<long>(left, tb);
         for (auto &g : bt->groups)
-            if (!g.members.empty() && g.halo.ncta) RC(launch_onchip(bt, g, true, bt->st[bt->cur], bt->st[bt->cur ^ 1], n));
+            if (!g.members.empty() && g.halo.ncta()) RC(launch_group(bt, g, true, bt->st[bt->cur], bt->st[bt->cur ^ 1], n));
         bt->cur ^= 1;
         left -= n;
     }
@@ -556,24 +625,8 @@ int batch_set_phi(lbhpde_batch_s *bt, const double *phi0, int on_device) {
     bt->cur = 0;
     for (auto &g : bt->groups) {
         if (g.members.empty()) continue;
-        const int nb = (int)g.blocks_h.size();
-        const long long *off_d = g.blk_off;
-        if (bt->esz == 4) {
-            if (g.b == 5)
-                lbk::k_init<float, 5><<<nb, kGenericThreads, 0, bt->stream>>>((float *)bt->st[0], bt->segs, g.blocks,
-                                                                               bt->coefD, src, off_d, kChunk);
-            else
-                lbk::k_init<float, 7><<<nb, kGenericThreads, 0, bt->stream>>>((float *)bt->st[0], bt->segs, g.blocks,
-                                                                               bt->coefD, src, off_d, kChunk);
-        } else {
-            if (g.b == 5)
-                lbk::k_init<double, 5><<<nb, kGenericThreads, 0, bt->stream>>>((double *)bt->st[0], bt->segs,
-                                                                                g.blocks, bt->coefD, src, off_d, kChunk);
-            else
-                lbk::k_init<double, 7><<<nb, kGenericThreads, 0, bt->stream>>>((double *)bt->st[0], bt->segs,
-                                                                                g.blocks, bt->coefD, src, off_d, kChunk);
-        }
-        CK(cudaGetLastError());
+        RC(lbh::launch_init(g.b, bt->esz, bt->st[0], bt->segs, g.blocks, (int)g.blocks_h.size(), bt->coefD, src,
+                            g.blk_off, bt->stream));
     }
     bt->steps = 0;
     bt->initialised = true;

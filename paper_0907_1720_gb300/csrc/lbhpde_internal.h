@@ -1,0 +1,54 @@
+// Host-side pieces shared by the batch API (lbhpde_api.cu) and the request server
+// (lbhpde_server.cu): packing of instances onto CTAs for the on-chip kernel and the typed
+// kernel launchers.  Implemented in lbhpde_api.cu, so each kernel is compiled once.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "lbhpde.h"
+#include "lbhpde_kernels.cuh"
+
+namespace lbh {
+
+constexpr int kChunk = 1024;          // nodes per block of the node-parallel kernels
+constexpr int kGenericThreads = 256;  // init / readout / diagnostics threads per block
+
+// One instance to place on the on-chip kernel.
+struct Member {
+    lbk::Seg seg;      // placement of the current state (and its coefficient block)
+    long long off2;    // where the kernel writes the result (== seg.off for in-place)
+    int steps;         // steps this instance takes in the launch
+};
+
+// A packed on-chip launch: CTA c holds insts[first[c] .. first[c + 1]).
+struct Packed {
+    std::vector<lbk::OnchipInst> insts;
+    std::vector<int> first;
+    int nthreads = 32;  // threads per CTA
+    int max_inst = 1;   // instances per CTA (resident mode: rounded up to a multiple of 4)
+    size_t smem = 0;    // dynamic shared memory per CTA, bytes
+    int ncta() const { return first.empty() ? 0 : (int)first.size() - 1; }
+};
+
+// Largest CTA (threads) of the compiled on-chip variant for (element size, lattice, nodes per
+// thread); 0 when no variant exists.
+int onchip_maxt(size_t esz, int b, int K);
+int default_K(size_t esz, int b);
+// Steps per halo window such that the halo (steps * max|e| on each side) leaves at least three
+// quarters of a window of `capacity` nodes valid.
+int default_tblk(int capacity, int W);
+// Compile-time degree variant the on-chip kernel uses for a set of members of maximum degree D.
+int onchip_dc(int b, int maxD);
+
+// Resident instances (N <= capacity): first fit, largest first, warp-aligned runs, <= 32 per CTA.
+int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Packed &out);
+// Temporally blocked windows with halo H: one window per CTA.
+int pack_halo(int b, size_t esz, int K, int dc, int H, const std::vector<Member> &m, Packed &out);
+
+int launch_onchip(int b, size_t esz, int K, int dc, bool halo, const Packed &p, const lbk::OnchipInst *insts_d,
+                  const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st);
+int launch_init(int b, size_t esz, void *st, const lbk::Seg *segs, const int2 *blocks, int nb, const double *coefd,
+                const double *phi0, const long long *blk_off, cudaStream_t stream);
+
+}  // namespace lbh

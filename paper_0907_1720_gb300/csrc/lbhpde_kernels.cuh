@@ -290,7 +290,8 @@ __global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__re
 //     H-wide borders.  After nsteps steps the middle `valid` nodes are exact and are written
 //     to the output buffer.  One window per CTA.
 struct OnchipInst {
-    long long off, ld;  // state placement (as Seg)
+    long long off, ld;  // state placement (as Seg) in st_in
+    long long off2;     // placement of the result in st_out
     int N, D;
     int gcoef;          // coefficient block in global memory (as Seg::coef)
     int scoef;          // this instance's copy of P_j and 1 - omega in shared memory
@@ -300,7 +301,8 @@ struct OnchipInst {
     int x0;             // global node of window position 0 (halo: may be negative)
     int npos;           // window positions (ring: N)
     int vlo, vhi;       // positions written back: [vlo, vhi)
-    int pad;
+    int steps;          // steps this instance takes in the launch (<= nsteps; the state is
+                        // frozen after them while the CTA's barriers continue)
 };
 
 template <typename T, int B, int K, int MAXT, bool HALO, int DC>
@@ -377,7 +379,8 @@ __global__ void __launch_bounds__(MAXT, 1)
         T *Rb = R + (s & 1) * NE * nt;
         T *Lb = L + (s & 1) * NE * nt;
         T *Tb = tail + (s & 1) * NE * max_inst;
-        if (has) {
+        const bool live = has && s < I.steps;
+        if (live) {
 #pragma unroll
             for (int j = 1; j < B; ++j) {
                 const int e = vel(j);
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(MAXT, 1)
                     for (int i = 0; i < -e; ++i) Lb[(eslot(-e) + i) * nt + tid] = v[j][i];
                 }
             }
-            if (!HALO && near_end) {
+            if (!HALO && near_end) {  // near_end implies has
 #pragma unroll
                 for (int j = 1; j < B; ++j) {
                     const int e = vel(j);
@@ -404,7 +407,7 @@ __global__ void __launch_bounds__(MAXT, 1)
             }
         }
         __syncthreads();
-        if (has) {
+        if (live) {
             T d[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) d[k] = T(0);
@@ -515,9 +518,9 @@ __global__ void __launch_bounds__(MAXT, 1)
                 x %= N;
                 x += x < 0 ? N : 0;
             }
-            st_out[I.off + x] = phi[k];
+            st_out[I.off2 + x] = phi[k];
 #pragma unroll
-            for (int j = 1; j < B; ++j) st_out[I.off + (long long)j * I.ld + x] = v[j][k];
+            for (int j = 1; j < B; ++j) st_out[I.off2 + (long long)j * I.ld + x] = v[j][k];
         }
     }
 }

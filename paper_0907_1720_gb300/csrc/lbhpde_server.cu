@@ -1,0 +1,615 @@
+// Request server: continuous batching of independent solves on one GPU.
+//
+// Requests (an equation, a grid, an initial profile and a step count) are submitted from any
+// host thread.  A scheduler thread admits them as device memory and slots allow, keeps their
+// distributions resident in one device arena, and advances every admitted request in step
+// blocks on the on-chip kernel -- whole instances resident in registers when they fit one CTA,
+// temporally blocked windows otherwise.  Requests that arrive while others run are admitted at
+// the next block boundary; each finished request is read back and released, freeing memory
+// for the queue.  Work per request is identical to a single-instance solve, so each result is
+// the same alone and in the mix.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "lbhpde.h"
+#include "lbhpde_internal.h"
+
+using lbk::Seg;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+constexpr size_t kGrain = 256;        // arena allocation granularity (bytes)
+constexpr int kCoefStride = 388;      // coefficient slot: 2 (b-1)(D+1) + 1 <= 385 values, padded
+constexpr int kLookahead = 64;        // queued requests examined per admission pass
+
+size_t round_up(size_t n, size_t g) { return (n + g - 1) / g * g; }
+
+// First-fit free list over [0, size) with neighbour coalescing.
+class Arena {
+  public:
+    void reset(size_t n) {
+        free_.clear();
+        if (n) free_[0] = n;
+        size_ = n;
+        used_ = 0;
+    }
+    bool alloc(size_t n, size_t *off) {
+        n = round_up(n, kGrain);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            *off = it->first;
+            const size_t rest = it->second - n, o = it->first + n;
+            free_.erase(it);
+            if (rest) free_[o] = rest;
+            used_ += n;
+            return true;
+        }
+        return false;
+    }
+    void release(size_t off, size_t n) {
+        n = round_up(n, kGrain);
+        used_ -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t size() const { return size_; }
+    size_t used() const { return used_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t size_ = 0, used_ = 0;
+};
+
+struct Req {
+    uint64_t id = 0;
+    lbhpde_model_info mi{};
+    long long N = 0;
+    long nsteps = 0, done = 0;
+    std::vector<double> phi0, phi;
+    int status = LBHPDE_PENDING;
+    long nonfinite = 0;
+    double t_submit = 0, t_admit = -1, t_finish = -1, sum_phi = 0;
+    size_t bytes = 0, dev_off = 0;   // placement in the arena
+    long long ld = 0, off[2] = {0, 0};  // element offsets of the two state buffers
+    int cur = 0;                     // buffer holding the state
+    int slot = -1;                   // coefficient slot
+    Seg seg() const {
+        Seg s{};
+        s.off = off[cur];
+        s.ld = ld;
+        s.N = (int)N;
+        s.D = mi.D;
+        s.coef = slot * kCoefStride;
+        return s;
+    }
+};
+
+template <typename X>
+struct DevBuf {  // growable device array (capacity only grows)
+    X *p = nullptr;
+    size_t cap = 0;
+    int ensure(size_t n) {
+        if (n <= cap) return LBHPDE_OK;
+        const size_t c = std::max<size_t>(n, 2 * cap + 64);
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        if (cudaMalloc(&p, sizeof(X) * c) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return LBHPDE_ERR_OOM;
+        }
+        cap = c;
+        return LBHPDE_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+}  // namespace
+
+struct lbhpde_server_s {
+    int precision = LBHPDE_FP32_DEV;
+    size_t esz = 4;
+    int device = 0, max_active = 0, block = 256;
+    cudaStream_t stream = nullptr;
+    void *arena_d = nullptr;
+    Arena arena;
+    void *coefT_d = nullptr;
+    double *coefD_d = nullptr;
+    std::vector<int> free_slots;
+    DevBuf<lbk::OnchipInst> insts_d;
+    DevBuf<int> first_d;
+    DevBuf<Seg> segs_d;
+    DevBuf<int2> blocks_d;
+    DevBuf<long long> boff_d;
+    DevBuf<double> phi0_d;
+
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Req *> queue;
+    std::unordered_map<uint64_t, Req *> reqs;
+    std::vector<Req *> active;  // touched by the worker only
+    std::atomic<uint64_t> next_id{1};
+    std::thread worker;
+    bool stop = false;
+    int error = LBHPDE_OK;  // sticky CUDA failure of the worker
+    Clock::time_point t0;
+    long completed = 0, launches = 0;
+    double node_updates = 0;
+    size_t bytes_used = 0;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+#define SCK(call)                         \
+    do {                                  \
+        if ((call) != cudaSuccess) {      \
+            (void)cudaGetLastError();     \
+            return LBHPDE_ERR_CUDA;       \
+        }                                 \
+    } while (0)
+#define SRC(call)                       \
+    do {                                \
+        int r_ = (call);                \
+        if (r_ != LBHPDE_OK) return r_; \
+    } while (0)
+
+size_t state_bytes(const Req &r, size_t esz) { return 2 * (size_t)r.mi.b * (size_t)r.ld * esz; }
+
+// Upload a request's coefficients to its slot and initialise its state (step a1).
+int setup_admitted(lbhpde_server_s *S, std::vector<Req *> &adm) {
+    if (adm.empty()) return LBHPDE_OK;
+    std::vector<double> cd((size_t)adm.size() * kCoefStride, 0.0);
+    long long phi_total = 0;
+    for (size_t q = 0; q < adm.size(); ++q) {
+        const Req &r = *adm[q];
+        double *c = cd.data() + q * kCoefStride;
+        int k = 0;
+        for (int j = 1; j < r.mi.b; ++j)
+            for (int p = 0; p <= r.mi.D; ++p) c[k++] = r.mi.coef[j][p];
+        for (int j = 1; j < r.mi.b; ++j)
+            for (int p = 0; p <= r.mi.D; ++p) c[k++] = r.mi.feq[j][p];
+        c[k] = 1.0 - r.mi.omega;
+        phi_total += r.N;
+    }
+    for (size_t q = 0; q < adm.size(); ++q) {
+        const Req &r = *adm[q];
+        const double *c = cd.data() + q * kCoefStride;
+        SCK(cudaMemcpyAsync(S->coefD_d + (size_t)r.slot * kCoefStride, c, sizeof(double) * kCoefStride,
+                            cudaMemcpyHostToDevice, S->stream));
+        if (S->esz == 4) {
+            std::vector<float> cf(c, c + kCoefStride);
+            SCK(cudaMemcpyAsync((float *)S->coefT_d + (size_t)r.slot * kCoefStride, cf.data(),
+                                sizeof(float) * kCoefStride, cudaMemcpyHostToDevice, S->stream));
+        }
+    }
+    SRC(S->phi0_d.ensure(phi_total));
+    std::vector<Seg> segs;
+    long long o = 0;
+    for (Req *r : adm) {
+        SCK(cudaMemcpyAsync(S->phi0_d.p + o, r->phi0.data(), sizeof(double) * r->N, cudaMemcpyHostToDevice,
+                            S->stream));
+        segs.push_back(r->seg());
+        o += r->N;
+    }
+    for (int b : {5, 7}) {
+        std::vector<int2> blocks;
+        std::vector<long long> boff;
+        long long po = 0;
+        for (size_t q = 0; q < adm.size(); ++q) {
+            if (adm[q]->mi.b == b)
+                for (long long x = 0; x < adm[q]->N; x += lbh::kChunk) {
+                    blocks.push_back(make_int2((int)q, (int)x));
+                    boff.push_back(po);
+                }
+            po += adm[q]->N;
+        }
+        if (blocks.empty()) continue;
+        SRC(S->segs_d.ensure(segs.size()));
+        SRC(S->blocks_d.ensure(blocks.size()));
+        SRC(S->boff_d.ensure(boff.size()));
+        SCK(cudaMemcpyAsync(S->segs_d.p, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, S->stream));
+        SCK(cudaMemcpyAsync(S->blocks_d.p, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice,
+                            S->stream));
+        SCK(cudaMemcpyAsync(S->boff_d.p, boff.data(), sizeof(long long) * boff.size(), cudaMemcpyHostToDevice,
+                            S->stream));
+        SRC(lbh::launch_init(b, S->esz, S->arena_d, S->segs_d.p, S->blocks_d.p, (int)blocks.size(), S->coefD_d,
+                             S->phi0_d.p, S->boff_d.p, S->stream));
+        // the next lattice reuses the tables: order the copies after this launch
+        SCK(cudaStreamSynchronize(S->stream));
+    }
+    return LBHPDE_OK;
+}
+
+// One on-chip launch of a step block, planned on the host.
+struct Planned {
+    int b, K, dc;
+    bool halo;
+    int nsteps;
+    lbh::Packed p;
+    size_t ioff = 0, foff = 0;  // offsets of its tables in the block's device arrays
+};
+
+// Advance every active request by up to one block of steps: plan all launches of the block
+// (resident instances once per lattice, windows in chunks of tblk steps), upload their tables
+// in one copy each, launch them in order on the server stream and wait once.
+int advance(lbhpde_server_s *S) {
+    std::vector<Planned> plan;
+    for (int b : {5, 7}) {
+        const int K = lbh::default_K(S->esz, b);
+        const int maxt = lbh::onchip_maxt(S->esz, b, K);
+        const int cap = maxt * K, W = (b - 1) / 2;
+        const int tblk = lbh::default_tblk(cap, W);
+        std::vector<Req *> ring, halo;
+        int maxD = 0;
+        for (Req *r : S->active)
+            if (r->mi.b == b && r->done < r->nsteps) {
+                (r->N <= cap ? ring : halo).push_back(r);
+                maxD = std::max(maxD, r->mi.D);
+            }
+        if (ring.empty() && halo.empty()) continue;
+        const int dc = lbh::onchip_dc(b, maxD);
+        if (!ring.empty()) {
+            std::vector<lbh::Member> m;
+            int n = 0;
+            for (Req *r : ring) {
+                const int st = (int)std::min<long>(S->block, r->nsteps - r->done);
+                m.push_back(lbh::Member{r->seg(), r->off[r->cur], st});
+                n = std::max(n, st);
+                r->done += st;
+            }
+            Planned pl{b, K, dc, false, n, {}};
+            SRC(lbh::pack_ring(b, S->esz, K, dc, m, pl.p));
+            plan.push_back(std::move(pl));
+        }
+        if (!halo.empty()) {
+            std::vector<long> left(halo.size());
+            for (size_t q = 0; q < halo.size(); ++q) left[q] = std::min<long>(S->block, halo[q]->nsteps - halo[q]->done);
+            for (;;) {
+                std::vector<lbh::Member> m;
+                int n = 0;
+                for (size_t q = 0; q < halo.size(); ++q) {
+                    if (left[q] <= 0) continue;
+                    const int st = (int)std::min<long>(tblk, left[q]);
+                    Req *r = halo[q];
+                    m.push_back(lbh::Member{r->seg(), r->off[r->cur ^ 1], st});
+                    n = std::max(n, st);
+                    r->cur ^= 1;  // the launch writes the other buffer
+                    r->done += st;
+                    left[q] -= st;
+                }
+                if (m.empty()) break;
+                Planned pl{b, K, dc, true, n, {}};
+                SRC(lbh::pack_halo(b, S->esz, K, dc, tblk * W, m, pl.p));
+                plan.push_back(std::move(pl));
+            }
+        }
+    }
+    if (plan.empty()) return LBHPDE_OK;
+    std::vector<lbk::OnchipInst> insts;
+    std::vector<int> first;
+    for (Planned &pl : plan) {
+        pl.ioff = insts.size();
+        pl.foff = first.size();
+        insts.insert(insts.end(), pl.p.insts.begin(), pl.p.insts.end());
+        first.insert(first.end(), pl.p.first.begin(), pl.p.first.end());
+    }
+    SRC(S->insts_d.ensure(insts.size()));
+    SRC(S->first_d.ensure(first.size()));
+    SCK(cudaMemcpyAsync(S->insts_d.p, insts.data(), sizeof(lbk::OnchipInst) * insts.size(), cudaMemcpyHostToDevice,
+                        S->stream));
+    SCK(cudaMemcpyAsync(S->first_d.p, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, S->stream));
+    for (const Planned &pl : plan) {
+        SRC(lbh::launch_onchip(pl.b, S->esz, pl.K, pl.dc, pl.halo, pl.p, S->insts_d.p + pl.ioff,
+                               S->first_d.p + pl.foff, S->arena_d, S->arena_d, S->coefT_d, pl.nsteps, S->stream));
+        ++S->launches;
+    }
+    SCK(cudaStreamSynchronize(S->stream));
+    return LBHPDE_OK;
+}
+
+// Copy a finished request's phi to the host and release its device resources.
+int retire(lbhpde_server_s *S, Req *r) {
+    r->phi.resize(r->N);
+    if (S->esz == 4) {
+        std::vector<float> tmp(r->N);
+        SCK(cudaMemcpyAsync(tmp.data(), (float *)S->arena_d + r->off[r->cur], sizeof(float) * r->N,
+                            cudaMemcpyDeviceToHost, S->stream));
+        SCK(cudaStreamSynchronize(S->stream));
+        for (long long i = 0; i < r->N; ++i) r->phi[i] = tmp[i];
+    } else {
+        SCK(cudaMemcpyAsync(r->phi.data(), (double *)S->arena_d + r->off[r->cur], sizeof(double) * r->N,
+                            cudaMemcpyDeviceToHost, S->stream));
+        SCK(cudaStreamSynchronize(S->stream));
+    }
+    double sum = 0.0;
+    long nf = 0;
+    for (double v : r->phi) {
+        if (std::isfinite(v))
+            sum += v;
+        else
+            ++nf;
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    r->sum_phi = sum;
+    r->nonfinite = nf;
+    r->status = nf ? LBHPDE_ERR_DIVERGED : LBHPDE_OK;
+    r->t_finish = S->now();
+    S->arena.release(r->dev_off, r->bytes);
+    S->free_slots.push_back(r->slot);
+    S->bytes_used = S->arena.used();
+    ++S->completed;
+    r->phi0.clear();
+    r->phi0.shrink_to_fit();
+    return LBHPDE_OK;
+}
+
+void worker_main(lbhpde_server_s *S) {
+    if (cudaSetDevice(S->device) != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->error = LBHPDE_ERR_CUDA;
+        S->cv_done.notify_all();
+        return;
+    }
+    for (;;) {
+        std::vector<Req *> adm;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->stop) break;
+            // admission: FIFO, looking past requests that do not fit yet
+            int looked = 0;
+            for (auto it = S->queue.begin(); it != S->queue.end() && looked < kLookahead;) {
+                ++looked;
+                if ((int)(S->active.size() + adm.size()) >= S->max_active || S->free_slots.empty()) break;
+                Req *r = *it;
+                size_t off;
+                if (!S->arena.alloc(r->bytes, &off)) {
+                    ++it;
+                    continue;
+                }
+                r->dev_off = off;
+                r->off[0] = (long long)(off / S->esz);
+                r->off[1] = r->off[0] + (long long)r->mi.b * r->ld;
+                r->cur = 0;
+                r->slot = S->free_slots.back();
+                S->free_slots.pop_back();
+                r->t_admit = S->now();
+                S->bytes_used = S->arena.used();
+                adm.push_back(r);
+                it = S->queue.erase(it);
+            }
+            if (S->active.empty() && adm.empty()) {
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
+                continue;
+            }
+        }
+        int rc = setup_admitted(S, adm);
+        for (Req *r : adm) S->active.push_back(r);
+        if (rc == LBHPDE_OK) rc = advance(S);
+        if (rc == LBHPDE_OK) rc = cudaStreamSynchronize(S->stream) == cudaSuccess ? LBHPDE_OK : LBHPDE_ERR_CUDA;
+        std::vector<Req *> still;
+        for (Req *r : S->active) {
+            if (rc == LBHPDE_OK && r->done >= r->nsteps) {
+                S->node_updates += (double)r->N * (double)r->nsteps;
+                rc = retire(S, r);
+            } else {
+                still.push_back(r);
+            }
+        }
+        S->active.swap(still);
+        if (rc != LBHPDE_OK) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->error = rc;
+            for (Req *r : S->active) {
+                r->status = rc;
+                r->t_finish = S->now();
+            }
+            for (Req *r : S->queue) {
+                r->status = rc;
+                r->t_finish = S->now();
+            }
+            S->queue.clear();
+            S->active.clear();
+            S->cv_done.notify_all();
+            break;
+        }
+        S->cv_done.notify_all();
+    }
+}
+
+void fill_result(const Req *r, lbhpde_result *info) {
+    if (!info) return;
+    info->status = r->status;
+    info->steps_done = r->done;
+    info->submit_s = r->t_submit;
+    info->admit_s = r->t_admit;
+    info->finish_s = r->t_finish;
+    info->sum_phi = r->sum_phi;
+    info->nonfinite = r->nonfinite;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t device_bytes, int max_active,
+                                    int steps_per_block, int device) {
+    if (!out || (precision != LBHPDE_FP64 && precision != LBHPDE_FP32_DEV) || device_bytes < (1u << 20) ||
+        max_active < 1 || max_active > 65536 || steps_per_block < 0 || device < 0)
+        return LBHPDE_ERR_ARG;
+    *out = nullptr;
+    auto *S = new (std::nothrow) lbhpde_server_s();
+    if (!S) return LBHPDE_ERR_OOM;
+    S->precision = precision;
+    S->esz = precision == LBHPDE_FP64 ? 8 : 4;
+    S->device = device;
+    S->max_active = max_active;
+    S->block = steps_per_block > 0 ? steps_per_block : 256;
+    S->t0 = Clock::now();
+    int prev = 0;
+    bool ok = cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(device) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&S->arena_d, device_bytes) == cudaSuccess &&
+              cudaMalloc((void **)&S->coefD_d, sizeof(double) * (size_t)max_active * kCoefStride) == cudaSuccess;
+    if (ok && S->esz == 4)
+        ok = cudaMalloc(&S->coefT_d, sizeof(float) * (size_t)max_active * kCoefStride) == cudaSuccess;
+    else if (ok)
+        S->coefT_d = S->coefD_d;
+    cudaSetDevice(prev);
+    if (!ok) {
+        const cudaError_t e = cudaGetLastError();
+        if (S->arena_d) cudaFree(S->arena_d);
+        if (S->coefD_d) cudaFree(S->coefD_d);
+        if (S->coefT_d && S->coefT_d != S->coefD_d) cudaFree(S->coefT_d);
+        if (S->stream) cudaStreamDestroy(S->stream);
+        delete S;
+        return e == cudaErrorMemoryAllocation ? LBHPDE_ERR_OOM : LBHPDE_ERR_CUDA;
+    }
+    S->arena.reset(device_bytes / kGrain * kGrain);
+    for (int i = max_active - 1; i >= 0; --i) S->free_slots.push_back(i);
+    S->worker = std::thread(worker_main, S);
+    *out = S;
+    return LBHPDE_OK;
+}
+
+extern "C" int lbhpde_submit(lbhpde_server_t S, const lbhpde_request *q, uint64_t *id) {
+    if (!S || !q || !id || !q->phi0 || q->nsteps < 0) return LBHPDE_ERR_ARG;
+    auto *r = new (std::nothrow) Req();
+    if (!r) return LBHPDE_ERR_OOM;
+    int rc = lbhpde_model(q->m, q->alpha, q->pi, q->dx, q->dt, q->tau, q->lattice, q->scheme, &r->mi);
+    const int W = (r->mi.b - 1) / 2;
+    if (rc == LBHPDE_OK && (q->N < 2 * W || q->N > (1L << 26))) rc = LBHPDE_ERR_ARG;
+    if (rc != LBHPDE_OK) {
+        delete r;
+        return rc;
+    }
+    r->N = q->N;
+    r->ld = (q->N + 31) / 32 * 32;
+    r->nsteps = q->nsteps;
+    r->bytes = round_up(state_bytes(*r, S->esz), kGrain);
+    if (r->bytes > S->arena.size()) {
+        delete r;
+        return LBHPDE_ERR_OOM;
+    }
+    r->phi0.assign(q->phi0, q->phi0 + q->N);
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->error != LBHPDE_OK) {
+        delete r;
+        return S->error;
+    }
+    r->id = S->next_id++;
+    r->t_submit = S->now();
+    S->reqs[r->id] = r;
+    S->queue.push_back(r);
+    *id = r->id;
+    S->cv_work.notify_one();
+    return LBHPDE_OK;
+}
+
+static int take_result(lbhpde_server_t S, std::unordered_map<uint64_t, Req *>::iterator it, double *phi_out,
+                       lbhpde_result *info) {
+    Req *r = it->second;
+    fill_result(r, info);
+    const int st = r->status;
+    if (st == LBHPDE_PENDING) return st;
+    if (phi_out && !r->phi.empty()) std::memcpy(phi_out, r->phi.data(), sizeof(double) * r->phi.size());
+    S->reqs.erase(it);
+    delete r;
+    return st;
+}
+
+extern "C" int lbhpde_poll(lbhpde_server_t S, uint64_t id, double *phi_out, lbhpde_result *info) {
+    if (!S) return LBHPDE_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return LBHPDE_ERR_NOT_FOUND;
+    return take_result(S, it, phi_out, info);
+}
+
+extern "C" int lbhpde_wait(lbhpde_server_t S, uint64_t id, double timeout_s, double *phi_out, lbhpde_result *info) {
+    if (!S || !(timeout_s >= 0.0)) return LBHPDE_ERR_ARG;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return LBHPDE_ERR_NOT_FOUND;
+    Req *r = it->second;
+    const auto deadline = Clock::now() + std::chrono::duration<double>(std::min(timeout_s, 1e6));
+    if (!S->cv_done.wait_until(lk, deadline, [&] { return r->status != LBHPDE_PENDING; })) {
+        fill_result(r, info);
+        return LBHPDE_ERR_TIMEOUT;
+    }
+    return take_result(S, S->reqs.find(id), phi_out, info);
+}
+
+extern "C" int lbhpde_server_stats(lbhpde_server_t S, lbhpde_server_info *out) {
+    if (!S || !out) return LBHPDE_ERR_ARG;
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->queued = (long)S->queue.size();
+    out->in_flight = (long)(S->reqs.size() - S->queue.size());
+    out->completed = S->completed;
+    out->node_updates = S->node_updates;
+    out->bytes_in_use = S->bytes_used;
+    out->bytes_total = S->arena.size();
+    out->launches = S->launches;
+    out->error = S->error;
+    return LBHPDE_OK;
+}
+
+extern "C" int lbhpde_server_destroy(lbhpde_server_t S) {
+    if (!S) return LBHPDE_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv_work.notify_all();
+    }
+    if (S->worker.joinable()) S->worker.join();
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(S->device);
+    cudaStreamSynchronize(S->stream);
+    for (auto &kv : S->reqs) delete kv.second;
+    S->reqs.clear();
+    S->insts_d.release();
+    S->first_d.release();
+    S->segs_d.release();
+    S->blocks_d.release();
+    S->boff_d.release();
+    S->phi0_d.release();
+    cudaFree(S->arena_d);
+    if (S->coefT_d != S->coefD_d) cudaFree(S->coefT_d);
+    cudaFree(S->coefD_d);
+    cudaStreamDestroy(S->stream);
+    cudaSetDevice(prev);
+    delete S;
+    return LBHPDE_OK;
+}

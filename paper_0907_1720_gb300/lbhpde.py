@@ -62,6 +62,31 @@ class lbhpde_instance(ctypes.Structure):
                 ("lattice", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
+class lbhpde_request(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("alpha", ctypes.c_double * 6), ("pi", lbhpde_pi * 6), ("N", ctypes.c_long),
+                ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
+                ("lattice", ctypes.c_int), ("scheme", ctypes.c_int), ("nsteps", ctypes.c_long),
+                ("phi0", ctypes.POINTER(ctypes.c_double))]
+
+
+class lbhpde_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps_done", ctypes.c_long), ("submit_s", ctypes.c_double),
+                ("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double), ("sum_phi", ctypes.c_double),
+                ("nonfinite", ctypes.c_long)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class lbhpde_server_info(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_long), ("in_flight", ctypes.c_long), ("completed", ctypes.c_long),
+                ("node_updates", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t),
+                ("bytes_total", ctypes.c_size_t), ("launches", ctypes.c_long), ("error", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class LbhpdeError(RuntimeError):
     def __init__(self, code, where=""):
         msg = lib().lbhpde_strerror(code).decode() if _lib is not None else str(code)
@@ -96,6 +121,12 @@ _SIGS = {
     "lbhpde_batch_size": (_I, [_V, _P(_L), _P(_S)]),
     "lbhpde_batch_destroy": (_I, [_V]),
     "lbhpde_phi_diagnostics_noalloc": (_I, [_V, _L, _V, _P(lbhpde_diag), _V]),
+    "lbhpde_server_create": (_I, [_P(_V), _I, _S, _I, _I, _I]),
+    "lbhpde_submit": (_I, [_V, _P(lbhpde_request), _P(ctypes.c_uint64)]),
+    "lbhpde_poll": (_I, [_V, ctypes.c_uint64, _V, _P(lbhpde_result)]),
+    "lbhpde_wait": (_I, [_V, ctypes.c_uint64, _D, _V, _P(lbhpde_result)]),
+    "lbhpde_server_stats": (_I, [_V, _P(lbhpde_server_info)]),
+    "lbhpde_server_destroy": (_I, [_V]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -344,6 +375,79 @@ class Batch:
     def close(self):
         if self.h:
             lib().lbhpde_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request server (lbhpde_server_*)."""
+
+    def __init__(self, precision=FP32_DEV, device_bytes=1 << 30, max_active=4096, steps_per_block=256, device=None):
+        if device is None:
+            import torch
+            device = torch.cuda.current_device()
+        h = ctypes.c_void_p()
+        _check(lib().lbhpde_server_create(ctypes.byref(h), int(precision), int(device_bytes), int(max_active),
+                                          int(steps_per_block), int(device)), "lbhpde_server_create")
+        self.h = h
+        self.sizes = {}
+
+    def submit(self, eq, N, dx, dt, tau, nsteps, phi0, scheme=1) -> int:
+        q = lbhpde_request()
+        q.m = eq.m
+        for k in range(eq.m):
+            q.alpha[k] = float(eq.alpha[k])
+            q.pi[k] = make_pi(eq.pi[k])
+        a = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64))
+        assert a.size == N
+        q.N, q.dx, q.dt, q.tau, q.lattice, q.scheme, q.nsteps = int(N), float(dx), float(dt), float(tau), \
+            int(eq.lattice), int(scheme), int(nsteps)
+        q.phi0 = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        rid = ctypes.c_uint64()
+        _check(lib().lbhpde_submit(self.h, ctypes.byref(q), ctypes.byref(rid)), "lbhpde_submit")
+        self.sizes[rid.value] = int(N)
+        return rid.value
+
+    def submit_problem(self, p, nsteps=None) -> int:
+        return self.submit(p.eq, p.N, p.dx, p.dt, p.tau, p.nsteps if nsteps is None else nsteps, p.phi0, p.scheme)
+
+    def poll(self, rid):
+        """(status, phi or None, info dict); phi only once finished."""
+        info = lbhpde_result()
+        out = np.empty(max(self.sizes.get(rid, 0), 1))
+        rc = lib().lbhpde_poll(self.h, ctypes.c_uint64(rid), out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(info))
+        if rc == PENDING:
+            return rc, None, info.as_dict()
+        if rc == ERR_NOT_FOUND:
+            _check(rc, "lbhpde_poll")
+        self.sizes.pop(rid, None)
+        return rc, out, info.as_dict()
+
+    def wait(self, rid, timeout=60.0):
+        info = lbhpde_result()
+        out = np.empty(max(self.sizes.get(rid, 0), 1))
+        rc = lib().lbhpde_wait(self.h, ctypes.c_uint64(rid), float(timeout), out.ctypes.data_as(ctypes.c_void_p),
+                               ctypes.byref(info))
+        if rc in (PENDING, ERR_TIMEOUT):
+            return rc, None, info.as_dict()
+        if rc == ERR_NOT_FOUND:
+            _check(rc, "lbhpde_wait")
+        self.sizes.pop(rid, None)
+        return rc, out, info.as_dict()
+
+    def stats(self) -> dict:
+        st = lbhpde_server_info()
+        _check(lib().lbhpde_server_stats(self.h, ctypes.byref(st)), "lbhpde_server_stats")
+        return st.as_dict()
+
+    def close(self):
+        if self.h:
+            lib().lbhpde_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -95,7 +95,8 @@ def kdv_kawahara(lattice=0):
 # ------------------------------------------------------------ exact solutions
 
 def sech(z):
-    return 1.0 / np.cosh(z)
+    with np.errstate(over="ignore"):
+        return 1.0 / np.cosh(z)
 
 
 def kdv_soliton(x, t, c=4.0, x0=0.0, L=None):
@@ -198,7 +199,7 @@ class Problem:
         return self.nsteps * self.dt
 
 
-def kdv_config(N=400, dt=2e-5, tau=1.07, t_end=1.0):
+def kdv_config(N=400, dt=1e-5, tau=1.1, t_end=1.0):
     """KdV single soliton, c = 4, x0 = 0, periodic x in [-20, 20), N = 400 (dx = 0.1)."""
     L = 40.0
     dx = L / N
@@ -311,3 +312,53 @@ def ks_spectral_reference(N=1024, t_end=10.0, h=1e-3, L=32.0 * math.pi, u0=None)
         Nc = nl(c)
         v = E * v + Nv * f1 + 2.0 * (Na + Nb) * f2 + Nc * f3
     return np.real(np.fft.ifft(v))
+
+
+# Serving mix: (equation factory, dt, tau, initial profile) per request type, with (dt, tau)
+# chosen by oracle scans so that every type stays bounded for 1e5 steps on dx = 0.1.
+SERVING_DX = 0.1
+
+
+def _serving_request(kind, N, steps, rng):
+    dx = SERVING_DX
+    L = N * dx
+    x = grid(-0.5 * L, N, dx)
+    if kind == "kdv":
+        c = float(rng.uniform(1.0, 4.0))
+        return Problem(kdv(), N, dx, 1e-5, 1.1, steps, kdv_soliton(x, 0.0, c=c, L=L), xl=-0.5 * L,
+                       meta={"kind": kind, "c": c})
+    if kind == "mkdv":
+        c = float(rng.uniform(0.5, 2.0))
+        return Problem(mkdv(), N, dx, 1e-5, 1.2, steps, mkdv_soliton(x, 0.0, c=c, L=L), xl=-0.5 * L,
+                       meta={"kind": kind, "c": c})
+    if kind == "k22":
+        lam = float(rng.uniform(0.5, 1.5))
+        return Problem(k22(), N, dx, 1e-4, 3.0, steps, k22_compacton(x, 0.0, lam=lam, L=L), xl=-0.5 * L,
+                       meta={"kind": kind, "lam": lam})
+    if kind == "ks":
+        a2 = float(rng.uniform(0.5, 1.5))
+        u0 = np.cos(2 * np.pi * x / L) * (1.0 + np.sin(2 * np.pi * x / L))
+        return Problem(ks(a2=a2), N, dx, 1e-4, 1.3, steps, u0, xl=-0.5 * L, meta={"kind": kind, "a2": a2})
+    b = float(rng.uniform(0.5, 1.0))
+    return Problem(kawahara(1.0, b, -1.0), N, dx, 1e-4, 3.0, steps, kawahara_soliton(x, 0.0, 1.0, b, -1.0, L=L),
+                   xl=-0.5 * L, meta={"kind": "kawahara", "beta": b})
+
+
+SERVING_KINDS = ("kdv", "mkdv", "k22", "ks", "kawahara")
+
+
+def serving_requests(count, rate=2000.0, seed=SEED, n_lo=128, n_hi=65536, s_lo=1000, s_hi=100000):
+    """``count`` requests with Poisson arrivals of mean ``rate`` per second: (arrival time,
+    Problem).  Equation ~ uniform over KdV, mKdV, K(2,2) compacton, KS and Kawahara; N
+    log-uniform in [n_lo, n_hi]; steps uniform in [s_lo, s_hi]; coefficients and soliton or
+    compacton parameters drawn from the seed."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(count):
+        t += float(rng.exponential(1.0 / rate))
+        kind = SERVING_KINDS[int(rng.integers(0, len(SERVING_KINDS)))]
+        N = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        steps = int(rng.integers(s_lo, s_hi + 1))
+        out.append((t, _serving_request(kind, N, steps, rng)))
+    return out
