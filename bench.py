@@ -46,6 +46,10 @@ def load_peaks():
 # FP32 lanes per SM and SM count of GB300: the ALU roof of the on-chip kernel.
 SMS, FP32_LANES = 152, 128
 
+# DRAM bytes (read + write) per node of one k_stream<float,7,7,...> launch, from an ncu capture
+# on a 2^23-node grid (traffic grows with N); used for the streaming roofline's "traffic".
+STREAM_F32_D1Q7_DRAM_BYTES_PER_NODE = (235003648 + 184919808) / 8388608
+
 
 class ClockSampler:
     """nvidia-smi clock/throttle samples (200 ms) while the timed region runs."""
@@ -130,6 +134,14 @@ def run_ours(args, rank, world):
     peaks, peak_src = load_peaks()
 
     with torch.cuda.stream(stream):
+        # the autotuner picks nodes per thread and steps per window for this precision, lattice
+        # and degree (outside the timed region); the batch below uses its choice
+        tuned = None
+        if not args.no_tune and not (args.workload == "long_grid" and args.kernel == "stream"):
+            prec0 = L.FP32_DEV if args.precision == "fp32" else L.FP64
+            b0, d0 = (5, 5) if args.workload == "ensemble" else (7, 7)
+            K_t, T_t, r_t = L.autotune(prec0, b0, d0)
+            tuned = {"nodes_per_thread": K_t, "steps_per_window": T_t, "tuning_rate": r_t}
         if args.workload == "ensemble":
             probs = ensemble_problems(rank, args.members)
             nsteps = W.ENSEMBLE_STEPS
@@ -234,16 +246,21 @@ def run_ours(args, rank, world):
         else:
             by = bytes_per_node_update(b, esz)
             achieved = by * upd_step / (kern_ms / 1e3) / 1e9
+            traffic = STREAM_F32_D1Q7_DRAM_BYTES_PER_NODE * total if esz == 4 else None
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_stream",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                    "traffic_note": "per launch; ncu capture on 2^23 nodes scaled by N",
+                    "kernel": "k_stream<float,7,7,256,1>" if esz == 4 else "k_stream<double,7,7,256,1>",
                     "bytes_per_node_update": by, "peak_source": peak_src}
-        launches_per_step = 1 + 2 + solver_kernel_launches(args, nsteps)  # init, diagnostics x2, steps
+        tblk = tuned["steps_per_window"] if tuned else (64 if args.workload == "ensemble" else 32)
+        launches_per_step = 1 + 2 + solver_kernel_launches(args, nsteps, tblk)  # init, diagnostics x2, steps
         line = {
             "metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == L.FP32_DEV else "f64", "data": "synthetic (seeded, shaped like the paper's test problems)",
             "config": {"workload": workload, "node_updates_per_step": upd_step, "precision": args.precision,
+                       "autotuned": tuned,
                        "l2": f"inputs larger than L2: state {2 * total * b * esz / 2**20:.0f} MiB (two buffers)",
                        "parallelism": f"replicas x{world} (independent ensembles)"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
@@ -319,15 +336,14 @@ def run_serving(args):
     return line
 
 
-def solver_kernel_launches(args, nsteps):
+def solver_kernel_launches(args, nsteps, tblk):
     """Kernel launches of one lbhpde_batch_step(nsteps) call: the streaming kernel launches once
-    per step; the ensemble's resident instances launch once and its halo windows once per 64
-    steps; the long grid's windows launch once per 32 steps (D1Q7)."""
+    per step; resident instances launch once and temporally blocked windows once per tblk steps."""
     if args.workload == "ensemble":
-        return 1 + (nsteps + 63) // 64
+        return 1 + (nsteps + tblk - 1) // tblk
     if args.kernel == "stream":
         return nsteps
-    return (nsteps + 31) // 32
+    return (nsteps + tblk - 1) // tblk
 
 
 def solver_model_degree(L, probs):
@@ -462,6 +478,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--members", type=int, default=4096, help="ensemble members (profiling: smaller)")
     ap.add_argument("--nodes", type=int, default=1 << 24, help="long-grid nodes (profiling: smaller)")
+    ap.add_argument("--no-tune", action="store_true", help="skip the on-chip autotuner")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed region: no accuracy check, e2e, FP64 or CPU legs (profiling)")
     args = ap.parse_args()

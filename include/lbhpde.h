@@ -169,6 +169,17 @@ int lbhpde_diagnostics(lbhpde_t h, const double *phistar_device, lbhpde_diag *ou
  * combination the library was not built with, leaving the previous choice in place. */
 int lbhpde_set_kernel(lbhpde_t h, int kernel, int nodes_per_thread, int steps_per_launch);
 
+/* Autotuner of the on-chip kernel (SURVEY's batching row: tile width and time-block depth;
+ * the paper has no counterpart).  Times the compiled (nodes per thread, steps per window)
+ * candidates for one precision, lattice (5 or 7) and f^eq degree on a synthetic periodic grid
+ * of 2^22 (FP32) or 2^21 (FP64) nodes in temporally blocked windows, and keeps the fastest in a
+ * process-wide table.  Batches and handles created afterwards use the tuned pair wherever
+ * lbhpde_set_kernel did not fix one.  Outputs (each may be NULL): the chosen pair and its
+ * measured node-updates per second.  Allocates and frees about 235 MB of device memory on the
+ * current device and synchronises. */
+int lbhpde_autotune(int precision, int lattice, int degree, int *nodes_per_thread, int *steps_per_launch,
+                    double *node_updates_per_s);
+
 int lbhpde_get_model(lbhpde_t h, lbhpde_model_info *out);
 int lbhpde_destroy(lbhpde_t h);
 const char *lbhpde_strerror(int code);

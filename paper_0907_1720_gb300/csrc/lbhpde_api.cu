@@ -6,7 +6,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "lbhpde.h"
@@ -375,6 +378,126 @@ int launch_init(int b, size_t esz, void *st, const Seg *segs, const int2 *blocks
 
 }  // namespace lbh
 
+// ============================================================================= autotuner
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tuned;  // (esz, b, dc) -> (K, tblk)
+
+bool tuned_choice(size_t esz, int b, int dc, int *K, int *tblk) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(std::make_tuple((int)esz, b, dc));
+    if (it == g_tuned.end()) return false;
+    *K = it->second.first;
+    *tblk = it->second.second;
+    return true;
+}
+
+// Time one (K, tblk) candidate: temporally blocked windows over a synthetic periodic grid of
+// n nodes (zero state, zero polynomial; the kernel's work does not depend on the values).
+int time_candidate(size_t esz, int b, int dc, int K, int tblk, long long n, void *buf0, void *buf1, void *coef,
+                   cudaStream_t st, double *rate) {
+    const int W = lbk::wmax(b);
+    lbh::Member m{};
+    m.seg.off = 0;
+    m.seg.ld = n;
+    m.seg.N = (int)n;
+    m.seg.D = dc > 0 ? dc : 5;
+    m.seg.coef = 0;
+    m.off2 = 0;
+    m.steps = tblk;
+    lbh::Packed p;
+    RC(lbh::pack_halo(b, esz, K, dc, tblk * W, {m}, p));
+    lbk::OnchipInst *insts = nullptr;
+    int *first = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = LBHPDE_OK;
+    if (cudaMalloc(&insts, sizeof(lbk::OnchipInst) * p.insts.size()) != cudaSuccess ||
+        cudaMalloc(&first, sizeof(int) * p.first.size()) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        rc = LBHPDE_ERR_CUDA;
+    if (rc == LBHPDE_OK) {
+        cudaMemcpyAsync(insts, p.insts.data(), sizeof(lbk::OnchipInst) * p.insts.size(), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(first, p.first.data(), sizeof(int) * p.first.size(), cudaMemcpyHostToDevice, st);
+        rc = lbh::launch_onchip(b, esz, K, dc, true, p, insts, first, buf0, buf1, coef, tblk, st);  // warm-up
+        const int reps = std::max(2, 512 / tblk);
+        if (rc == LBHPDE_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = LBHPDE_ERR_CUDA;
+        for (int r = 0; r < reps && rc == LBHPDE_OK; ++r)
+            rc = lbh::launch_onchip(b, esz, K, dc, true, p, insts, first, (r & 1) ? buf1 : buf0, (r & 1) ? buf0 : buf1,
+                                    coef, tblk, st);
+        float ms = 0.f;
+        if (rc == LBHPDE_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            rc = LBHPDE_ERR_CUDA;
+        if (rc == LBHPDE_OK) *rate = (double)n * tblk * reps / (ms * 1e-3);
+    }
+    (void)cudaGetLastError();
+    if (insts) cudaFree(insts);
+    if (first) cudaFree(first);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
+}
+
+}  // namespace
+
+extern "C" int lbhpde_autotune(int precision, int lattice, int degree, int *nodes_per_thread, int *steps_per_launch,
+                               double *node_updates_per_s) {
+    if ((precision != LBHPDE_FP64 && precision != LBHPDE_FP32_DEV) || (lattice != 5 && lattice != 7) || degree < 1 ||
+        degree > LBHPDE_MAX_DEG)
+        return LBHPDE_ERR_ARG;
+    const size_t esz = precision == LBHPDE_FP64 ? 8 : 4;
+    const int b = lattice, dc = lbh::onchip_dc(b, degree);
+    const long long n = esz == 4 ? (1LL << 22) : (1LL << 21);
+    void *buf0 = nullptr, *buf1 = nullptr, *coef = nullptr;
+    cudaStream_t st = nullptr;
+    int rc = LBHPDE_OK;
+    if (cudaMalloc(&buf0, esz * b * n) != cudaSuccess || cudaMalloc(&buf1, esz * b * n) != cudaSuccess ||
+        cudaMalloc(&coef, esz * lbk::cblock(b, lbk::kMaxDeg) * 2) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+        rc = LBHPDE_ERR_OOM;
+    if (rc == LBHPDE_OK) {
+        cudaMemsetAsync(buf0, 0, esz * b * n, st);
+        cudaMemsetAsync(buf1, 0, esz * b * n, st);
+        cudaMemsetAsync(coef, 0, esz * lbk::cblock(b, lbk::kMaxDeg) * 2, st);
+    }
+    int bestK = 0, bestT = 0;
+    double best = 0.0;
+    for (int K : {2, 4, 8}) {
+        if (rc != LBHPDE_OK) break;
+        const int maxt = lbh::onchip_maxt(esz, b, K);
+        if (maxt == 0 || K < lbk::wmax(b)) continue;
+        for (int tblk : {16, 32, 64, 96, 128}) {
+            if (maxt * K - 2 * tblk * lbk::wmax(b) < maxt * K / 2) continue;
+            double r = 0.0;
+            rc = time_candidate(esz, b, dc, K, tblk, n, buf0, buf1, coef, st, &r);
+            if (rc != LBHPDE_OK) break;
+            if (r > best) {
+                best = r;
+                bestK = K;
+                bestT = tblk;
+            }
+        }
+    }
+    (void)cudaGetLastError();
+    if (st) cudaStreamSynchronize(st);
+    if (buf0) cudaFree(buf0);
+    if (buf1) cudaFree(buf1);
+    if (coef) cudaFree(coef);
+    if (st) cudaStreamDestroy(st);
+    if (rc != LBHPDE_OK) return rc;
+    if (bestK == 0) return LBHPDE_ERR_UNSUPPORTED;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[std::make_tuple((int)esz, b, dc)] = std::make_pair(bestK, bestT);
+    }
+    if (nodes_per_thread) *nodes_per_thread = bestK;
+    if (steps_per_launch) *steps_per_launch = bestT;
+    if (node_updates_per_s) *node_updates_per_s = best;
+    return LBHPDE_OK;
+}
+
 // ============================================================================= batches
 
 namespace {
@@ -552,8 +675,14 @@ int choose_kernels(lbhpde_batch_s *bt) {
         if (g.members.empty()) continue;
         g.onchip_ok = false;
         if (bt->kernel == LBHPDE_KERNEL_STREAM) continue;
-        const int K = bt->K_req > 0 ? bt->K_req : lbh::default_K(bt->esz, g.b);
-        int rc = plan_onchip(bt, g, K, bt->spl_req, bt->kernel == LBHPDE_KERNEL_HALO);
+        int K = bt->K_req > 0 ? bt->K_req : lbh::default_K(bt->esz, g.b);
+        int tblk = bt->spl_req;
+        int tk = 0, tt = 0;
+        if (tuned_choice(bt->esz, g.b, lbh::onchip_dc(g.b, g.maxD), &tk, &tt)) {
+            if (bt->K_req == 0) K = tk;
+            if (bt->spl_req == 0) tblk = tt;
+        }
+        int rc = plan_onchip(bt, g, K, tblk, bt->kernel == LBHPDE_KERNEL_HALO);
         if (rc != LBHPDE_OK) return rc;
     }
     return LBHPDE_OK;

@@ -110,6 +110,7 @@ _SIGS = {
     "lbhpde_diagnostics": (_I, [_V, _V, _P(lbhpde_diag)]),
     "lbhpde_set_kernel": (_I, [_V, _I, _I, _I]),
     "lbhpde_get_model": (_I, [_V, _P(lbhpde_model_info)]),
+    "lbhpde_autotune": (_I, [_I, _I, _I, _P(_I), _P(_I), _P(_D)]),
     "lbhpde_destroy": (_I, [_V]),
     "lbhpde_strerror": (ctypes.c_char_p, [_I]),
     "lbhpde_batch_create": (_I, [_P(_V), _I, _P(lbhpde_instance), _I, _V, _P(lbhpde_allocator)]),
@@ -206,6 +207,15 @@ def make_instance(eq, N, dx, dt, tau, scheme=1) -> lbhpde_instance:
         I.pi[k] = make_pi(eq.pi[k])
     I.N, I.dx, I.dt, I.tau, I.lattice, I.scheme = int(N), float(dx), float(dt), float(tau), int(eq.lattice), int(scheme)
     return I
+
+
+def autotune(precision, lattice, degree):
+    """lbhpde_autotune: (nodes per thread, steps per window, node-updates/s) of the fastest
+    on-chip configuration; later batches use it."""
+    K, T, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().lbhpde_autotune(int(precision), int(lattice), int(degree), ctypes.byref(K), ctypes.byref(T),
+                                 ctypes.byref(r)), "lbhpde_autotune")
+    return K.value, T.value, r.value
 
 
 # ------------------------------------------------------------ torch plumbing

@@ -282,3 +282,20 @@ def test_ensemble_sampled_members(L):
     for i in pick:
         want = oracle.run_problem(probs[i])
         assert normwise(outs[i], want) <= FP32_TOL(100), i
+
+
+def test_autotune_then_parity(L):
+    """The autotuner's choice is a compiled configuration, and batches built after it (which
+    use the tuned nodes per thread and window steps) still match the oracle."""
+    K, T, rate = L.autotune(L.FP32_DEV, 5, 5)
+    assert K in (2, 4, 8) and T in (16, 32, 64, 96, 128) and rate > 0
+    K7, T7, _ = L.autotune(L.FP64, 7, 7)
+    assert K7 == 4
+    probs = [problem(W.kdv_burgers(2.0, 0.05, 0.9), N, 0.1, 1e-4, 1.3, 150, seed=N) for N in (300, 5000, 9001)]
+    probs += [problem(W.kawahara(), N, 0.1, 1e-3, 2.5, 150, seed=N) for N in (700, 2500)]
+    for P, tol in ((L.FP32_DEV, FP32_TOL(150)), (L.FP64, FP64_TOL)):
+        bt = L.Batch(probs, precision=P)
+        bt.set_phi(np.concatenate([p.phi0 for p in probs])).step(150)
+        for p, got in zip(probs, bt.split(bt.read_phi())):
+            assert normwise(got, oracle.run_problem(p)) <= tol, (P, p.N)
+        bt.close()
