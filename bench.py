@@ -123,6 +123,21 @@ def bytes_per_node_update(b, esz):
 
 # ----------------------------------------------------------------------- ours
 
+def aggregate(t_local, units_local, world, device="cpu"):
+    """Whole-job throughput over ranks that each process their own units (weak scaling):
+    (sum of units over ranks) / (max of the ranks' times), and that max time."""
+    if world <= 1:
+        return units_local / t_local, t_local
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item())
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -199,15 +214,8 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
         total_ms = ev[2].elapsed_time(ev[3])
         kern = [a.elapsed_time(c) for a, c in kernel_ms]
-        t_local = total_ms / 1e3
-        if world > 1:
-            t = torch.tensor([t_local], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_max = float(t.item())
-        else:
-            t_max = t_local
         upd_step = total * nsteps
-        value = world * upd_step * args.steps / t_max
+        value, t_max = aggregate(total_ms / 1e3, upd_step * args.steps, world, device="cuda")
 
         # accuracy beside the number: members against the FP64 path (ensemble) or the exact
         # solution (long grid)

@@ -25,6 +25,7 @@ using lbk::Seg;
 namespace {
 
 constexpr int kStreamThreads = kChunk / 4;  // k_stream: one group of 4 nodes per thread
+constexpr int kGraphSteps = 64;             // one-step launches per captured graph (even)
 
 #define CK(call)                                              \
     do {                                                      \
@@ -71,6 +72,12 @@ struct lbhpde_batch_s {
     size_t esz = 8;
     int count = 0;
     cudaStream_t stream = nullptr;
+    // resident instances run on `side`, forked from and joined back into `stream` with events,
+    // so that the window launches fill the SMs the resident launch leaves idle
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // streaming path: kGraphSteps one-step launches captured once per buffer parity and replayed
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool has_alloc = false;
     lbhpde_allocator alloc{};
     std::vector<lbhpde_model_info> mi;
@@ -133,6 +140,14 @@ struct lbhpde_batch_s {
                 cudaFree(a.first);
         }
         allocations.clear();
+        for (auto &gx : graph)
+            if (gx) cudaGraphExecDestroy(gx);
+        graph[0] = graph[1] = nullptr;
+        if (side) cudaStreamDestroy(side);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        side = nullptr;
+        ev_fork = ev_join = nullptr;
         stream = nullptr;
     }
 };
@@ -566,10 +581,10 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
     return LBHPDE_OK;
 }
 
-int launch_group(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *out, int nsteps) {
+int launch_group(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *out, int nsteps, cudaStream_t st) {
     Group::Plan &pl = halo ? g.halo : g.ring;
     return lbh::launch_onchip(g.b, bt->esz, g.K, g.dc, halo, pl.host, pl.insts, pl.cta_first, in, out, bt->coefT,
-                              nsteps, bt->stream);
+                              nsteps, st);
 }
 
 int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
@@ -700,7 +715,7 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
     }
     if (any_stream) {
         // one fused collide+stream launch per step, ping-pong buffers
-        for (long s = 0; s < nsteps; ++s) {
+        auto one_step = [&]() -> int {
             for (auto &g : bt->groups) {
                 if (g.members.empty()) continue;
                 int rc = bt->esz == 4 ? (g.b == 5 ? launch_stream_b<float, 5>(bt, g) : launch_stream_b<float, 7>(bt, g))
@@ -708,7 +723,44 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
                 RC(rc);
             }
             bt->cur ^= 1;
+            return LBHPDE_OK;
+        };
+        long left = nsteps;
+        // long runs replay a captured graph of kGraphSteps launches (even, so the buffer parity
+        // after a replay is the parity before it); not on the legacy stream, and not while the
+        // caller is capturing the stream itself
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        const bool graphs = bt->stream != nullptr && left >= 2 * kGraphSteps &&
+                            cudaStreamIsCapturing(bt->stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+        (void)cudaGetLastError();
+        if (graphs) {
+            const int par = bt->cur;
+            if (!bt->graph[par]) {
+                cudaGraph_t gr = nullptr;
+                CK(cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal));
+                int rc = LBHPDE_OK;
+                for (int s = 0; s < kGraphSteps && rc == LBHPDE_OK; ++s) rc = one_step();
+                const cudaError_t ec = cudaStreamEndCapture(bt->stream, &gr);
+                bt->cur = par;  // capture launched nothing
+                RC(rc);
+                if (ec != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    return LBHPDE_ERR_CUDA;
+                }
+                const cudaError_t ei = cudaGraphInstantiate(&bt->graph[par], gr, 0);
+                cudaGraphDestroy(gr);
+                if (ei != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    bt->graph[par] = nullptr;
+                    return LBHPDE_ERR_CUDA;
+                }
+            }
+            while (left >= kGraphSteps) {
+                CK(cudaGraphLaunch(bt->graph[par], bt->stream));
+                left -= kGraphSteps;
+            }
         }
+        for (; left > 0; --left) RC(one_step());
         bt->steps += nsteps;
         return LBHPDE_OK;
     }
@@ -719,6 +771,22 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
         if (!g.members.empty() && g.halo.ncta()) tb = std::min(tb, g.tblk);
     const long nchunks = any_halo ? (nsteps + tb - 1) / tb : 0;
     const int cur0 = bt->cur, cur1 = bt->cur ^ (int)(nchunks & 1);
+    bool any_ring = false;
+    for (auto &g : bt->groups)
+        if (!g.members.empty() && g.ring.ncta()) any_ring = true;
+    // resident instances and windows touch disjoint rows: run them concurrently
+    const bool fork = any_ring && any_halo;
+    cudaStream_t rs = bt->stream;
+    if (fork) {
+        if (!bt->side) {
+            CK(cudaStreamCreateWithFlags(&bt->side, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&bt->ev_join, cudaEventDisableTiming));
+        }
+        CK(cudaEventRecord(bt->ev_fork, bt->stream));
+        CK(cudaStreamWaitEvent(bt->side, bt->ev_fork, 0));
+        rs = bt->side;
+    }
     for (auto &g : bt->groups) {
         if (g.members.empty() || !g.ring.ncta()) continue;
         const long spl = bt->spl_req > 0 ? bt->spl_req : (1L << 30);
@@ -726,19 +794,22 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
         bool firstl = true;
         while (left > 0) {
             const int n = (int)std::min(left, spl);
-            RC(launch_group(bt, g, false, bt->st[firstl ? cur0 : cur1], bt->st[cur1], n));
+            RC(launch_group(bt, g, false, bt->st[firstl ? cur0 : cur1], bt->st[cur1], n, rs));
             firstl = false;
             left -= n;
         }
     }
+    if (fork) CK(cudaEventRecord(bt->ev_join, bt->side));
     long left = nsteps;
     for (long c = 0; c < nchunks; ++c) {
         const int n = (int)std::min<long>(left, tb);
         for (auto &g : bt->groups)
-            if (!g.members.empty() && g.halo.ncta()) RC(launch_group(bt, g, true, bt->st[bt->cur], bt->st[bt->cur ^ 1], n));
+            if (!g.members.empty() && g.halo.ncta())
+                RC(launch_group(bt, g, true, bt->st[bt->cur], bt->st[bt->cur ^ 1], n, bt->stream));
         bt->cur ^= 1;
         left -= n;
     }
+    if (fork) CK(cudaStreamWaitEvent(bt->stream, bt->ev_join, 0));
     bt->cur = cur1;
     bt->steps += nsteps;
     return LBHPDE_OK;

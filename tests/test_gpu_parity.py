@@ -299,3 +299,27 @@ def test_autotune_then_parity(L):
         for p, got in zip(probs, bt.split(bt.read_phi())):
             assert normwise(got, oracle.run_problem(p)) <= tol, (P, p.N)
         bt.close()
+
+
+def test_stream_graph_replay_matches_single_launches(L):
+    """On a non-default stream, long streaming runs replay a captured graph of 64 one-step
+    launches; the result equals 200 individual launches bit for bit and matches the oracle."""
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        for P in (L.FP32_DEV, L.FP64):
+            p = problem(W.kawahara(), 2049, 0.1, 1e-3, 2.5, 200, seed=21)
+            a = L.Solver.for_problem(p, precision=P).set_kernel(L.KERNEL_STREAM)
+            a.set_phi(p.phi0).step(200)  # 3 graph replays + 8 launches
+            a.step(130)                  # graph for the other buffer parity
+            ga = a.read_phi()
+            b = L.Solver.for_problem(p, precision=P).set_kernel(L.KERNEL_STREAM)
+            b.set_phi(p.phi0)
+            for _ in range(330):
+                b.step(1)
+            gb = b.read_phi()
+            a.close()
+            b.close()
+            assert np.array_equal(ga, gb)
+            p2 = problem(W.kawahara(), 2049, 0.1, 1e-3, 2.5, 330, seed=21)
+            tol = FP64_TOL if P == L.FP64 else FP32_TOL(330)
+            assert normwise(ga, oracle.run_problem(p2)) <= tol
