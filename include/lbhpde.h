@@ -53,6 +53,12 @@ extern "C" {
                            /* equilibrium (phi kept apart), float arithmetic               */
 #define LBHPDE_PERIODIC 0
 
+/* Flag or-ed into `scheme`: leave the A_40, A_50, A_60 corrections of Eqs. (Pi4)-(Pi6) out of
+ * the auxiliary moments.  The paper derives them for exact recovery, but its printed errors
+ * for the Kuramoto-Sivashinsky examples (Tables I and II) are those of a model without A_40.
+ * The model is then flagged inexact wherever a correction would be present. */
+#define LBHPDE_NO_AUX_CORRECTION 0x100
+
 #define LBHPDE_PI_ZERO 0   /* Pi_k = 0                         */
 #define LBHPDE_PI_PHI 1    /* Pi_k = phi                       */
 #define LBHPDE_PI_POWER 2  /* Pi_k = phi^power, 1 <= power <= 7 */
@@ -118,7 +124,7 @@ typedef struct {
  *   dx, dt     lattice spacing and time step (> 0, finite); c = dx/dt
  *   tau        dimensionless relaxation time (> 0)
  *   lattice    0 = auto (5 for m <= 4, else 7), 5 or 7
- *   scheme     1 or 2 (scheme 2 needs m < b-1)
+ *   scheme     1 or 2 (scheme 2 needs m < b-1), optionally | LBHPDE_NO_AUX_CORRECTION
  * Errors: LBHPDE_ERR_ARG, LBHPDE_ERR_TAU_SINGULAR (tau_k = 0 where beta_k or A_k0 needs it). */
 int lbhpde_model(int m, const double *alpha, const lbhpde_pi *pi, double dx, double dt, double tau,
                  int lattice, int scheme, lbhpde_model_info *out);

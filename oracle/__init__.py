@@ -31,6 +31,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liblbhpde_oracle.so")
 
 OK, ERR_ARG, ERR_TAU_SINGULAR, ERR_DEGREE = 0, 1, 2, 3
+NO_AUX_CORRECTION = 0x100  # scheme flag: leave A_40, A_50, A_60 out
 _ERRORS = {ERR_ARG: "invalid argument", ERR_TAU_SINGULAR: "tau_k = 0 (singular relaxation time)",
            ERR_DEGREE: "polynomial degree too high"}
 
@@ -76,6 +77,7 @@ def bind(path: str):
     lib.oracle_edf.argtypes = [i, D, D]
     lib.oracle_init.argtypes = [V, l, D, D]
     lib.oracle_step.argtypes = [V, l, D, D, l]
+    lib.oracle_step_nee.argtypes = [V, l, D, D, l, D, i]
     lib.oracle_phi.argtypes = [V, l, D, D]
     lib.oracle_error_E.argtypes = [l, D, D]
     lib.oracle_error_E.restype = d
@@ -172,6 +174,20 @@ class Model:
         self._lib.oracle_step(self._buf, f.shape[1], _dp(f), _dp(tmp), int(nsteps))
         return f
 
+    def step_nee(self, f: np.ndarray, phib, depth: int = 2) -> np.ndarray:
+        """len(phib) steps with the non-equilibrium extrapolation boundary; phib[n] holds the
+        prescribed phi at time (n + 1) dt at the W left then the W right boundary nodes, and
+        the outer nodes extrapolate from the node ``depth`` places inside them."""
+        assert f.flags.c_contiguous and f.dtype == np.float64 and f.shape[0] == self.b
+        pb = np.ascontiguousarray(np.asarray(phib, dtype=np.float64))
+        W = (self.b - 1) // 2
+        assert pb.ndim == 2 and pb.shape[1] == 2 * W
+        if depth < 1 or f.shape[1] < 2 * (W + depth):
+            raise OracleError(ERR_ARG)
+        tmp = np.empty_like(f)
+        self._lib.oracle_step_nee(self._buf, f.shape[1], _dp(f), _dp(tmp), pb.shape[0], _dp(pb), int(depth))
+        return f
+
     def phi(self, f: np.ndarray) -> np.ndarray:
         out = np.zeros(f.shape[1])
         self._lib.oracle_phi(self._buf, f.shape[1], _dp(f), _dp(out))
@@ -202,3 +218,4 @@ def error_E(phi, phistar) -> float:
     phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64))
     ps = np.ascontiguousarray(np.asarray(phistar, dtype=np.float64))
     return _load().oracle_error_E(phi.size, _dp(phi), _dp(ps))
+

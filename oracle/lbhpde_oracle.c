@@ -31,8 +31,15 @@
  *     model flags "inexact recovery" when the remarks' preconditions fail;
  *   - scheme 2 sets the highest moment Pibar_{b-1} to zero (Sec. IV, before
  *     Examples 4.5 and 4.8);
+ *   - scheme | ORACLE_NO_AUX_CORRECTION leaves A_40, A_50, A_60 out (the paper derives them,
+ *     but its Kuramoto-Sivashinsky errors of Table I are reproduced only without A_40);
  *   - f is initialised to f^eq(phi_0);
- *   - the grid is periodic with N nodes.
+ *   - the grid is periodic with N nodes (oracle_step), or bounded by the non-equilibrium
+ *     extrapolation of Guo et al. that Sec. IV cites (oracle_step_nee): after streaming, every
+ *     population of the W = max|e| outer nodes at each end is rebuilt as
+ *     f^eq(phi_b) + [f(x_f) - f^eq(phi(x_f))], phi_b the prescribed (exact) boundary value and
+ *     x_f the node `depth` places inside the outer layer (depth 1: the nearest node that
+ *     received all its populations from inside the grid).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -158,6 +165,7 @@ static void oracle_taus(double tau, double tk[7])
 
 /* Return codes shared with the Python wrapper. */
 enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_TAU_SINGULAR = 2, OR_ERR_DEGREE = 3 };
+#define ORACLE_NO_AUX_CORRECTION 0x100
 
 static int singular(double x) { return fabs(x) < 1e-13; }
 
@@ -173,6 +181,8 @@ int oracle_model_init(oracle_model *M, int m, const double *alpha, const double 
     if (!(dx > 0.0) || !(dt > 0.0) || !(tau > 0.0) || !isfinite(dx) || !isfinite(dt) ||
         !isfinite(tau))
         return OR_ERR_ARG;
+    const int no_aux = (scheme & ORACLE_NO_AUX_CORRECTION) != 0;
+    scheme &= ~ORACLE_NO_AUX_CORRECTION;
     if (lattice == 0) lattice = (m <= 4) ? 5 : 7;
     if (lattice != 5 && lattice != 7) return OR_ERR_ARG;
     if (m > lattice - 1) return OR_ERR_ARG;          /* Sec. III: b >= m + 1 */
@@ -213,22 +223,27 @@ int oracle_model_init(oracle_model *M, int m, const double *alpha, const double 
     double b2 = M->beta[2], b3 = M->beta[3], b4 = M->beta[4];
 
     /* (3) The A_k0 corrections, Eqs. (Pi4), (Pi5), (Pi6) and (A40)-(A60).  A moment
-     * that the lattice does not carry needs no correction. */
+     * that the lattice does not carry needs no correction; ORACLE_NO_AUX_CORRECTION leaves
+     * all three out (and recovery is then inexact wherever one is needed). */
+    const int need4 = M->b - 1 >= 4 && b2 != 0.0;
+    const int need5 = M->b - 1 >= 5 && b2 != 0.0 && b3 != 0.0;
+    const int need6 = M->b - 1 >= 6 && (b2 != 0.0 || b3 != 0.0);
     M->A40 = M->A50 = M->A60 = 0.0;
-    if (M->b - 1 >= 4 && b2 != 0.0) {
+    if (need4 && !no_aux) {
         if (singular(t4)) return OR_ERR_TAU_SINGULAR;
         M->A40 = t2 * (3.0 * t3 - t2 * t2) * b2 * b2 / t4;
     }
-    if (M->b - 1 >= 5 && b2 != 0.0 && b3 != 0.0) {
+    if (need5 && !no_aux) {
         if (singular(t5)) return OR_ERR_TAU_SINGULAR;
         M->A50 = (4.0 * t2 * t4 + 3.0 * t3 * t3 - 2.0 * t2 * t2 * t3) * b2 * b3 / t5;
     }
-    if (M->b - 1 >= 6 && (b2 != 0.0 || b3 != 0.0)) {
+    if (need6 && !no_aux) {
         if (singular(t6)) return OR_ERR_TAU_SINGULAR;
         M->A60 = ((5.0 * t2 * t5 + 3.0 * t3 * t4 - 2.0 * t2 * t2 * t4) * b2 * b4 +
                   (4.0 * t4 - t2 * t3) * t3 * b3 * b3 + (t2 * t3 - 6.0 * t4) * t2 * t2 * b2 * b2 * b2) /
                  t6;
     }
+    if (no_aux && (need4 || need5 || need6)) M->inexact = 1;
 
     /* Preconditions of exact recovery, for the terms that are present: Pi_2 = phi for
      * A_40 (Sec. II D), Pi_2 = Pi_3 = phi for A_50 (Sec. II E), Pi_2 = Pi_3 = Pi_4 = phi
@@ -383,26 +398,69 @@ void oracle_init(const oracle_model *M, long N, const double *phi0, double *f)
     }
 }
 
+/* Right-hand side of Eq. (LBE) at node i: fstar_j = f_j - (f_j - f^eq_j(phi)) / tau with
+ * phi = sum_j f_j (Eq. (moments)). */
+static void collide(const oracle_model *M, long N, const double *f, long i, double *fstar)
+{
+    double feq[7];
+    double phi = 0.0;
+    for (int j = 0; j < M->b; j++) phi += f[(long)j * N + i];
+    oracle_feq(M, phi, feq);
+    for (int j = 0; j < M->b; j++) {
+        double fj = f[(long)j * N + i];
+        fstar[j] = fj - (fj - feq[j]) / M->tau;
+    }
+}
+
 /* (7) nsteps of Eq. (LBE) on a periodic grid: collide at every node, then move
  * each post-collision f_j to node i + e_j (mod N).  tmp has the size of f. */
 void oracle_step(const oracle_model *M, long N, double *f, double *tmp, long nsteps)
 {
     const int b = M->b;
-    const double tau = M->tau;
-    double feq[7];
+    double fstar[7];
     for (long n = 0; n < nsteps; n++) {
         for (long i = 0; i < N; i++) {
-            double phi = 0.0;
-            for (int j = 0; j < b; j++) phi += f[(long)j * N + i];
-            oracle_feq(M, phi, feq);
+            collide(M, N, f, i, fstar);
             for (int j = 0; j < b; j++) {
-                double fj = f[(long)j * N + i];
-                double fstar = fj - (fj - feq[j]) / tau;
                 long dst = ((i + E7[j]) % N + N) % N;
-                tmp[(long)j * N + dst] = fstar;
+                tmp[(long)j * N + dst] = fstar[j];
             }
         }
         memcpy(f, tmp, sizeof(double) * (size_t)b * (size_t)N);
+    }
+}
+
+/* nsteps of Eq. (LBE) on a bounded grid of N nodes with the non-equilibrium extrapolation
+ * boundary: collide everywhere, stream (populations leaving the grid are dropped), then rebuild
+ * the W = max|e| outer nodes at each end from x_f = W - 1 + depth (left) and N - W - depth
+ * (right).  phib holds, for step n (time (n + 1) dt), the prescribed phi at the W left nodes
+ * 0..W-1 followed by the W right nodes N-W..N-1.  Needs depth >= 1 and N >= 2 (W + depth). */
+void oracle_step_nee(const oracle_model *M, long N, double *f, double *tmp, long nsteps, const double *phib,
+                     int depth)
+{
+    const int b = M->b, W = (b - 1) / 2;
+    double fstar[7], fb[7], fk[7];
+    for (long n = 0; n < nsteps; n++) {
+        for (long q = 0; q < (long)b * N; q++) tmp[q] = 0.0;
+        for (long i = 0; i < N; i++) {
+            collide(M, N, f, i, fstar);
+            for (int j = 0; j < b; j++) {
+                long dst = i + E7[j];
+                if (dst >= 0 && dst < N) tmp[(long)j * N + dst] = fstar[j];
+            }
+        }
+        memcpy(f, tmp, sizeof(double) * (size_t)b * (size_t)N);
+        for (int side = 0; side < 2; side++) {
+            long k = side == 0 ? W - 1 + depth : N - W - depth;
+            double phik = 0.0;
+            for (int j = 0; j < b; j++) phik += f[(long)j * N + k];
+            oracle_feq(M, phik, fk);
+            for (int l = 0; l < W; l++) {
+                long i = side == 0 ? l : N - W + l;
+                oracle_feq(M, phib[n * 2 * W + side * W + l], fb);
+                for (int j = 0; j < b; j++) f[(long)j * N + i] = fb[j] + f[(long)j * N + k] - fk[j];
+            }
+        }
     }
 }
 

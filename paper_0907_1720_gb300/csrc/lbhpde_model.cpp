@@ -155,6 +155,8 @@ extern "C" int lbhpde_model(int m, const double *alpha, const lbhpde_pi *pi, dou
     const int b = lattice == 0 ? (m <= 4 ? 5 : 7) : lattice;
     if (b != 5 && b != 7) return LBHPDE_ERR_ARG;
     if (m > b - 1) return LBHPDE_ERR_ARG;  // at least m + 1 velocities (Sec. III)
+    const bool no_aux = (scheme & LBHPDE_NO_AUX_CORRECTION) != 0;
+    scheme &= ~LBHPDE_NO_AUX_CORRECTION;
     if (scheme != 1 && scheme != 2) return LBHPDE_ERR_ARG;
     if (scheme == 2 && m >= b - 1) return LBHPDE_ERR_ARG;
     for (int k = 0; k < m; ++k)
@@ -185,24 +187,31 @@ extern "C" int lbhpde_model(int m, const double *alpha, const lbhpde_pi *pi, dou
         beta[k] = alpha[k - 1] / (std::pow(dt, double(k - 1)) * tk[k]);
     }
 
-    // A_k0 of Eqs. (Pi4)-(Pi6); only moments the lattice carries need them.
+    // A_k0 of Eqs. (Pi4)-(Pi6); only moments the lattice carries need them.  With
+    // LBHPDE_NO_AUX_CORRECTION they are left out, and recovery is flagged inexact wherever
+    // one of them would be present.
     double A[7] = {0, 0, 0, 0, 0, 0, 0};
-    if (b - 1 >= 4 && beta[2] != 0.0) {
-        if (near_zero(tk[4])) return LBHPDE_ERR_TAU_SINGULAR;
-        A[4] = tk[2] * (3.0 * tk[3] - tk[2] * tk[2]) * beta[2] * beta[2] / tk[4];
-    }
-    if (b - 1 >= 5 && beta[2] != 0.0 && beta[3] != 0.0) {
-        if (near_zero(tk[5])) return LBHPDE_ERR_TAU_SINGULAR;
-        A[5] = (4.0 * tk[2] * tk[4] + 3.0 * tk[3] * tk[3] - 2.0 * tk[2] * tk[2] * tk[3]) * beta[2] *
-               beta[3] / tk[5];
-    }
-    if (b - 1 >= 6 && (beta[2] != 0.0 || beta[3] != 0.0)) {
-        if (near_zero(tk[6])) return LBHPDE_ERR_TAU_SINGULAR;
-        const double t2 = tk[2], t3 = tk[3], t4 = tk[4], t5 = tk[5];
-        A[6] = ((5.0 * t2 * t5 + 3.0 * t3 * t4 - 2.0 * t2 * t2 * t4) * beta[2] * beta[4] +
-                (4.0 * t4 - t2 * t3) * t3 * beta[3] * beta[3] +
-                (t2 * t3 - 6.0 * t4) * t2 * t2 * beta[2] * beta[2] * beta[2]) /
-               tk[6];
+    const bool need4 = b - 1 >= 4 && beta[2] != 0.0;
+    const bool need5 = b - 1 >= 5 && beta[2] != 0.0 && beta[3] != 0.0;
+    const bool need6 = b - 1 >= 6 && (beta[2] != 0.0 || beta[3] != 0.0);
+    if (!no_aux) {
+        if (need4) {
+            if (near_zero(tk[4])) return LBHPDE_ERR_TAU_SINGULAR;
+            A[4] = tk[2] * (3.0 * tk[3] - tk[2] * tk[2]) * beta[2] * beta[2] / tk[4];
+        }
+        if (need5) {
+            if (near_zero(tk[5])) return LBHPDE_ERR_TAU_SINGULAR;
+            A[5] = (4.0 * tk[2] * tk[4] + 3.0 * tk[3] * tk[3] - 2.0 * tk[2] * tk[2] * tk[3]) * beta[2] *
+                   beta[3] / tk[5];
+        }
+        if (need6) {
+            if (near_zero(tk[6])) return LBHPDE_ERR_TAU_SINGULAR;
+            const double t2 = tk[2], t3 = tk[3], t4 = tk[4], t5 = tk[5];
+            A[6] = ((5.0 * t2 * t5 + 3.0 * t3 * t4 - 2.0 * t2 * t2 * t4) * beta[2] * beta[4] +
+                    (4.0 * t4 - t2 * t3) * t3 * beta[3] * beta[3] +
+                    (t2 * t3 - 6.0 * t4) * t2 * t2 * beta[2] * beta[2] * beta[2]) /
+                   tk[6];
+        }
     }
 
     // Exact-recovery preconditions (Sec. II D-F, Remarks 2, 4, 5).
@@ -212,6 +221,7 @@ extern "C" int lbhpde_model(int m, const double *alpha, const lbhpde_pi *pi, dou
     if (b - 1 >= 6 && beta[3] != 0.0 && !is_phi(P[3])) inexact = 1;
     if (b - 1 >= 6 && beta[2] != 0.0 && beta[4] != 0.0 && !(is_phi(P[2]) && is_phi(P[4]))) inexact = 1;
     if (b == 7 && beta[2] != 0.0) inexact = 1;
+    if (no_aux && (need4 || need5 || need6)) inexact = 1;
 
     // Auxiliary moments Pi_k0, k = 2..b-1 (beta_k = 0 for k > m).
     const Poly d1 = deriv(P[1]);

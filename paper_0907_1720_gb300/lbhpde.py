@@ -24,6 +24,7 @@ OK, ERR_ARG, ERR_TAU_SINGULAR, ERR_OOM, ERR_DIVERGED, PENDING, ERR_TIMEOUT, ERR_
     ERR_UNSUPPORTED = range(10)
 FP64, FP32_DEV = 0, 1
 PERIODIC = 0
+NO_AUX_CORRECTION = 0x100  # or-ed into scheme: leave A_40, A_50, A_60 out
 PI_ZERO, PI_PHI, PI_POWER, PI_POLY = 0, 1, 2, 3
 PI_NCOEF = 8
 MAX_DEG = 31

@@ -161,6 +161,20 @@ def kdv_burgers_soliton_ic(x, a, d, c, x0=0.0):
     return (3.0 * c / a) * sech(0.5 * math.sqrt(c / d) * (x - x0)) ** 2
 
 
+def ks_shock(x, t, b=5.0, k=0.5 * math.sqrt(11.0 / 19.0), x0=-12.0):
+    """Example 4.1: b + (15/19) sqrt(11/19) (-9 z + 11 z^3), z = tanh(k (x - b t - x0)), solves
+    u_t + u u_x + u_xx + u_xxxx = 0 for k = sqrt(11/19) / 2."""
+    z = np.tanh(k * (x - b * t - x0))
+    return b + 15.0 / 19.0 * math.sqrt(11.0 / 19.0) * (-9.0 * z + 11.0 * z ** 3)
+
+
+def ks_shock2(x, t, b=5.0, k=1.0 / (2.0 * math.sqrt(19.0)), x0=-25.0):
+    """Example 4.2: b + 15/(19 sqrt 19) (-3 z + z^3), z = tanh(k (x - b t - x0)), solves
+    u_t + u u_x - u_xx + u_xxxx = 0 for k = 1 / (2 sqrt 19)."""
+    z = np.tanh(k * (x - b * t - x0))
+    return b + 15.0 / (19.0 * math.sqrt(19.0)) * (-3.0 * z + z ** 3)
+
+
 def ks_initial(x):
     """u0 = cos(x/16) (1 + sin(x/16)) on [0, 32 pi)."""
     return np.cos(x / 16.0) * (1.0 + np.sin(x / 16.0))
@@ -189,6 +203,8 @@ class Problem:
     scheme: int = 1
     exact: object = None          # callable t -> phi*(x, t) on the grid, or None
     meta: dict = field(default_factory=dict)
+    boundary: str = "periodic"    # or "nee": bounded grid, prescribed phi at both ends
+    exact_xt: object = None       # callable (x, t) -> phi*(x, t) (bounded problems)
 
     @property
     def x(self):
@@ -236,6 +252,37 @@ def modified_kawahara_config(N=600, dx=0.1, dt=1e-2, tau=4.54, t_end=1.0, scheme
     return Problem(modified_kawahara(), N, dx, dt, tau, nsteps, modified_kawahara_soliton(x, 0.0, L=L),
                    xl=-0.5 * L, scheme=scheme,
                    exact=lambda t, x=x: modified_kawahara_soliton(x, t, L=L))
+
+
+# Examples of Sec. IV solved on a bounded grid [x_L, x_R] with exact boundary data:
+# equation, x_L, x_R, exact solution phi*(x, t).
+PAPER_EXAMPLES = {
+    "4.1": (ks, -30.0, 30.0, ks_shock),
+    "4.2": (lambda: ks(a2=-1.0), -50.0, 50.0, ks_shock2),
+    "4.5": (kawahara, -30.0, 30.0, kawahara_soliton),
+    "4.6": (modified_kawahara, -30.0, 30.0, modified_kawahara_soliton),
+    "4.7": (kdv_kawahara, 0.0, 200.0, kdv_kawahara_soliton),
+}
+
+
+def bounded_config(example, dt, tau, t_end, scheme=1, dx=0.1):
+    """Example 4.x on the nodes x_L, x_L + dx, ..., x_R, phi0 = phi*(x, 0); the boundary data
+    are phi* at the outer nodes (``boundary_values``)."""
+    make, xl, xr, ex = PAPER_EXAMPLES[example]
+    N = int(round((xr - xl) / dx)) + 1
+    x = grid(xl, N, dx)
+    nsteps = int(round(t_end / dt))
+    return Problem(make(), N, dx, dt, tau, nsteps, ex(x, 0.0), xl=xl, scheme=scheme,
+                   exact=lambda t, x=x: ex(x, t), boundary="nee", exact_xt=ex,
+                   meta={"example": example})
+
+
+def boundary_values(p, W, n0, n):
+    """[n, 2W] array: phi* at the W first then the W last nodes at times (n0 + 1..n0 + n) dt."""
+    x = p.x
+    xb = np.concatenate([x[:W], x[p.N - W:]])
+    t = (n0 + 1 + np.arange(n, dtype=np.float64))[:, None] * p.dt
+    return np.ascontiguousarray(p.exact_xt(xb[None, :], t), dtype=np.float64)
 
 
 def long_grid_config(N=1 << 24, dx=0.1, dt=1e-4, tau=2.02, nsteps=1000):

@@ -56,6 +56,10 @@ EQUATIONS = [
     ("kdv_kawahara", W.kdv_kawahara(), 1e-3, 3.31, 1),
     ("sixth", W.Equation("sixth", (1.0, 0.0, 0.5, 0.3, -1.0, 0.2),
                          ((0, 0, 0.5), (), (0, 1), (0, 1), (0, 1), (0, 1))), 1e-3, 2.2, 1),
+    # A_40, A_50, A_60 left out (LBHPDE_NO_AUX_CORRECTION)
+    ("ks_noA", W.ks(), 1e-2, 5.99, 1 | 0x100),
+    ("kdv_burgers_noA", W.kdv_burgers(3.0, 0.07, 0.8), 1e-4, 1.15, 1 | 0x100),
+    ("kawahara_noA", W.kawahara(), 1e-4, 2.02, 1 | 0x100),
 ]
 
 

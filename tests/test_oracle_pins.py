@@ -440,7 +440,7 @@ MUTATIONS = [
      "feq[1] = (4.0 * (P[1] + P[2]) - P[3] - P[4]) / 8.0;"),
     ("moment scaling", "double ck = pow(M->c, (double)k);", "double ck = pow(M->c, (double)(k - 1));"),
     ("stream direction", "long dst = ((i + E7[j]) % N + N) % N;", "long dst = ((i - E7[j]) % N + N) % N;"),
-    ("relaxation", "double fstar = fj - (fj - feq[j]) / tau;", "double fstar = fj - (fj - feq[j]) * tau;"),
+    ("relaxation", "fstar[j] = fj - (fj - feq[j]) / M->tau;", "fstar[j] = fj - (fj - feq[j]) * M->tau;"),
     ("A50 coefficient", "(4.0 * t2 * t4 + 3.0 * t3 * t3", "(4.0 * t2 * t4 + 2.0 * t3 * t3"),
 ]
 
