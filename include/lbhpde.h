@@ -22,8 +22,10 @@
  *   - Work is enqueued on the handle's CUDA stream; calls that return data to the
  *     host synchronise that stream.  A handle may be used by one host thread at
  *     a time; the server (lbhpde_server_*) is internally synchronised.
- *   - Grids are periodic (LBHPDE_PERIODIC); the paper's non-equilibrium
- *     extrapolation boundary (Sec. IV) is not provided.
+ *   - Grids are periodic (LBHPDE_PERIODIC) or bounded (LBHPDE_NEE): nodes
+ *     x_0..x_{N-1} with prescribed phi at the max|e| outer nodes of each end,
+ *     applied by the non-equilibrium extrapolation that Sec. IV uses for its
+ *     test problems (see LBHPDE_NEE).
  */
 #ifndef LBHPDE_H
 #define LBHPDE_H
@@ -52,6 +54,18 @@ extern "C" {
 #define LBHPDE_FP32_DEV 1  /* float populations stored as deviations from the rest         */
                            /* equilibrium (phi kept apart), float arithmetic               */
 #define LBHPDE_PERIODIC 0
+/* Bounded grid with the non-equilibrium extrapolation boundary of Sec. IV (after Guo et al.;
+ * the paper gives no formula).  After each collide+stream step the W = max|e| outer nodes at
+ * each end (nodes 0..W-1 and N-W..N-1) are rebuilt as
+ *     f_j(x_b) = f^eq_j(phi_b) + [f_j(x_f) - f^eq_j(phi(x_f))],
+ * phi_b the prescribed value and x_f = W - 1 + depth (left), N - W - depth (right).  The plain
+ * code LBHPDE_NEE means depth 2, which reproduces the paper's printed errors for its D1Q5 and
+ * c = 10 D1Q7 examples; LBHPDE_NEE_DEPTH(d) chooses another depth (d >= 1; d = 1 is the
+ * nearest node whose populations all come from inside the grid).  Needs N >= 2 (W + depth).
+ * Bounded instances are stepped with lbhpde_step_nee / lbhpde_batch_step_nee, which take the
+ * boundary values of every step. */
+#define LBHPDE_NEE 1
+#define LBHPDE_NEE_DEPTH(d) (LBHPDE_NEE | ((d) << 8))
 
 /* Flag or-ed into `scheme`: leave the A_40, A_50, A_60 corrections of Eqs. (Pi4)-(Pi6) out of
  * the auxiliary moments.  The paper derives them for exact recovery, but its printed errors
@@ -133,8 +147,9 @@ int lbhpde_model(int m, const double *alpha, const lbhpde_pi *pi, double dx, dou
 
 typedef struct lbhpde_ctx *lbhpde_t;
 
-/* Create one periodic instance of N nodes (N >= 2 * max|e_j|, i.e. 4 on D1Q5 and 6 on
- * D1Q7).  precision is LBHPDE_FP64 or LBHPDE_FP32_DEV; boundary must be LBHPDE_PERIODIC.
+/* Create one instance of N nodes: periodic (N >= 2 * max|e_j|, i.e. 4 on D1Q5 and 6 on D1Q7)
+ * or bounded (boundary = LBHPDE_NEE or LBHPDE_NEE_DEPTH(d); N >= 2 (max|e_j| + depth)).
+ * precision is LBHPDE_FP64 or LBHPDE_FP32_DEV.  Other boundary codes: LBHPDE_ERR_UNSUPPORTED.
  * cuda_stream is a cudaStream_t (NULL = the legacy default stream); alloc may be NULL.
  * The state is undefined until lbhpde_set_phi. */
 int lbhpde_create(lbhpde_t *out, int m, const double *alpha, const lbhpde_pi *pi, long N, double dx,
@@ -147,8 +162,18 @@ int lbhpde_create(lbhpde_t *out, int m, const double *alpha, const lbhpde_pi *pi
 int lbhpde_set_phi(lbhpde_t h, const double *phi0, int phi0_on_device);
 
 /* Steps a2-a6, nsteps times: stream (pull form), phi = sum_j f_j, f^eq_j(phi), BGK relaxation
- * f*_j = f_j - (f_j - f^eq_j)/tau (Eq. (LBE)).  Asynchronous on the handle's stream. */
+ * f*_j = f_j - (f_j - f^eq_j)/tau (Eq. (LBE)).  Asynchronous on the handle's stream.
+ * LBHPDE_ERR_ARG on a bounded instance (it needs boundary values: lbhpde_step_nee). */
 int lbhpde_step(lbhpde_t h, long nsteps);
+
+/* nsteps steps of a bounded instance (LBHPDE_NEE): each step as lbhpde_step, then the outer
+ * nodes are rebuilt from the prescribed values.  phib: [nsteps][2W] doubles, W = max|e_j|;
+ * row n holds phi_b at time (steps taken + n + 1) dt at nodes 0..W-1 followed by nodes
+ * N-W..N-1.  phib is host memory (phib_on_device = 0: copied before the call returns, unless it
+ * is page-locked, in which case it must stay unchanged until the stream reaches the step) or
+ * device memory (= 1: read by the kernels, so it must stay valid until they have run).  On a
+ * periodic instance phib is ignored (may be NULL). */
+int lbhpde_step_nee(lbhpde_t h, long nsteps, const double *phib, int phib_on_device);
 
 /* Step a7: copy phi (t = steps taken * dt) into phi_out ([N] doubles, host or device).
  * Host output synchronises.  Returns LBHPDE_ERR_DIVERGED (after copying) if phi has a
@@ -175,8 +200,8 @@ int lbhpde_diagnostics(lbhpde_t h, const double *phistar_device, lbhpde_diag *ou
  * combination the library was not built with, leaving the previous choice in place. */
 int lbhpde_set_kernel(lbhpde_t h, int kernel, int nodes_per_thread, int steps_per_launch);
 
-/* Autotuner of the on-chip kernel (SURVEY's batching row: tile width and time-block depth;
- * the paper has no counterpart).  Times the compiled (nodes per thread, steps per window)
+/* Autotuner of the on-chip kernel (tile width and time-block depth; the paper has no
+ * counterpart).  Times the compiled (nodes per thread, steps per window)
  * candidates for one precision, lattice (5 or 7) and f^eq degree on a synthetic periodic grid
  * of 2^22 (FP32) or 2^21 (FP64) nodes in temporally blocked windows, and keeps the fastest in a
  * process-wide table.  Batches and handles created afterwards use the tuned pair wherever
@@ -200,18 +225,27 @@ typedef struct {
     long N;
     double dx, dt, tau;
     int lattice, scheme;
+    int boundary;          /* LBHPDE_PERIODIC (0), LBHPDE_NEE or LBHPDE_NEE_DEPTH(d) */
 } lbhpde_instance;
 
 typedef struct lbhpde_batch_s *lbhpde_batch_t;
 
-/* Many independent periodic instances of one precision, stepped together: the on-chip
- * kernel packs whole instances onto CTAs (one launch advances all of them); instances too
- * long for one SM use the streaming kernel.  Members may mix lattices, orders and sizes. */
+/* Many independent instances of one precision, stepped together: the on-chip kernel packs
+ * whole periodic instances onto CTAs (one launch advances all of them) and keeps each bounded
+ * instance of up to 2048 nodes resident in one CTA; longer instances use the streaming kernel.
+ * Members may mix lattices, orders, sizes and boundaries. */
 int lbhpde_batch_create(lbhpde_batch_t *out, int count, const lbhpde_instance *members, int precision,
                         void *cuda_stream, const lbhpde_allocator *alloc);
 /* phi0: the members' initial profiles concatenated ([sum N] doubles, host or device). */
 int lbhpde_batch_set_phi(lbhpde_batch_t b, const double *phi0, int phi0_on_device);
+/* LBHPDE_ERR_ARG if the batch has a bounded member (use lbhpde_batch_step_nee). */
 int lbhpde_batch_step(lbhpde_batch_t b, long nsteps);
+/* As lbhpde_step_nee for every member: the boundary values of member i are the [nsteps][2W_i]
+ * doubles at phib + i * member_stride.  member_stride = 0 lets all bounded members share one
+ * array (they must then have the same W); otherwise member_stride >= nsteps * 2W_i for every
+ * bounded member.  Periodic members ignore phib. */
+int lbhpde_batch_step_nee(lbhpde_batch_t b, long nsteps, const double *phib, long member_stride,
+                          int phib_on_device);
 /* phi_out: [sum N] doubles, host or device.  LBHPDE_ERR_DIVERGED if any phi is non-finite. */
 int lbhpde_batch_read_phi(lbhpde_batch_t b, double *phi_out, int out_on_device);
 /* out: [count] records.  phistar: [sum N] doubles in device memory, or NULL. */
@@ -223,8 +257,8 @@ int lbhpde_batch_destroy(lbhpde_batch_t b);
 
 /* ------------------------------------------------------------------ serving */
 
-/* A request server: continuous batching of independent solves on one GPU (SURVEY's serving
- * row; the paper has no serving layer).  Requests are admitted as device memory and slots
+/* A request server: continuous batching of independent solves on one GPU (the paper has no
+ * serving layer).  Requests are admitted as device memory and slots
  * free up, keep their distributions resident in the server's device arena, and advance
  * together in step blocks on the on-chip kernel; a request that arrives while others run is
  * admitted at the next block boundary.  Each request's arithmetic is that of a single-instance

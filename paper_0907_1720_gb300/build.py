@@ -17,8 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "liblbhpde.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lbhpde_model.cpp", "lbhpde_api.cu", "lbhpde_noalloc.cu", "lbhpde_server.cu"]
-HEADERS = ["lbhpde_kernels.cuh", "lbhpde_internal.h"]
+SOURCES = ["lbhpde_model.cpp", "lbhpde_api.cu", "lbhpde_bounded.cu", "lbhpde_noalloc.cu", "lbhpde_server.cu"]
+HEADERS = ["lbhpde_kernels.cuh", "lbhpde_bounded.cuh", "lbhpde_internal.h"]
 
 
 def _nvcc():

@@ -63,6 +63,14 @@ struct Group {
     int K = 0, maxt = 0, tblk = 0;
     int dc = 0;  // compile-time degree of the on-chip kernel variant (0 = run time)
     bool uniform = false;  // every member has the same model (coefficients and omega)
+    // bounded groups (LBHPDE_NEE): resident members, one CTA each, and streaming members
+    std::vector<lbk::BoundedInst> bnd_h;
+    lbk::BoundedInst *bnd = nullptr;
+    int bnd_threads = 0, bnd_dc = 0, bnd_D = 0;
+    std::vector<int> smembers_h;       // streaming members
+    int *smembers = nullptr;
+    std::vector<int2> sblocks_h;       // their node blocks (kChunk nodes each)
+    int2 *sblocks = nullptr;
 };
 
 }  // namespace
@@ -82,6 +90,7 @@ struct lbhpde_batch_s {
     lbhpde_allocator alloc{};
     std::vector<lbhpde_model_info> mi;
     std::vector<long long> N;
+    std::vector<int> depth;          // per member: NEE extrapolation depth, 0 = periodic
     std::vector<long long> phi_off;  // prefix sums of N: concatenated host/device phi arrays
     long long total = 0;
     std::vector<Seg> segs_h;
@@ -100,7 +109,11 @@ struct lbhpde_batch_s {
     DiagPart *part = nullptr;      // scratch: one record per block of the combined map
     DiagPart *diag_out = nullptr;  // one record per member
     double *phi_buf = nullptr;     // device staging of phi in double (host transfers)
-    Group groups[2];               // b = 5, b = 7
+    Group groups[2];               // periodic members: b = 5, b = 7
+    Group bgroups[2];              // bounded members: b = 5, b = 7
+    int nbounded = 0;
+    double *phib_buf = nullptr;    // device copy of host boundary values
+    size_t phib_cap = 0;           // its capacity in doubles
     int kernel = LBHPDE_KERNEL_AUTO;
     int K_req = 0, spl_req = 0;
     long steps = 0;
@@ -123,6 +136,18 @@ struct lbhpde_batch_s {
         allocations.emplace_back(q, bytes);
         *p = q;
         return LBHPDE_OK;
+    }
+    void dev_free(void *p) {
+        for (size_t i = 0; i < allocations.size(); ++i)
+            if (allocations[i].first == p) {
+                cudaStreamSynchronize(stream);
+                if (has_alloc)
+                    alloc.release(p, allocations[i].second, (void *)stream, alloc.user);
+                else
+                    cudaFree(p);
+                allocations.erase(allocations.begin() + i);
+                return;
+            }
     }
     template <typename X>
     int upload(X **dst, const std::vector<X> &src) {
@@ -518,10 +543,10 @@ extern "C" int lbhpde_autotune(int precision, int lattice, int degree, int *node
 namespace {
 
 template <typename T, int B, int DC, bool PARAMC>
-int launch_stream_t(lbhpde_batch_s *bt, Group &g) {
-    const T *in = (const T *)bt->st[bt->cur];
-    T *out = (T *)bt->st[bt->cur ^ 1];
-    const int nb = (int)g.blocks_h.size();
+int launch_stream_t(lbhpde_batch_s *bt, Group &g, const int2 *blocks, int nb, const void *in_, void *out_) {
+    if (nb == 0) return LBHPDE_OK;
+    const T *in = (const T *)in_;
+    T *out = (T *)out_;
     lbk::StreamCoef<T, B, (DC > 0 ? DC : 1)> pc{};
     if constexpr (PARAMC) {
         // one model for the whole launch: its coefficients (zero-padded to degree DC)
@@ -531,17 +556,26 @@ int launch_stream_t(lbhpde_batch_s *bt, Group &g) {
         pc.omw = (T)(1.0 - M.omega);
     }
     lbk::k_stream<T, B, DC, kStreamThreads, PARAMC><<<nb, kStreamThreads, 0, bt->stream>>>(
-        in, out, bt->segs, g.blocks, (const T *)bt->coefT, pc);
+        in, out, bt->segs, blocks, (const T *)bt->coefT, pc);
     CK(cudaGetLastError());
     return LBHPDE_OK;
 }
 
 template <typename T, int B>
-int launch_stream_b(lbhpde_batch_s *bt, Group &g) {
+int launch_stream_b(lbhpde_batch_s *bt, Group &g, const int2 *blocks, int nb, const void *in, void *out) {
     constexpr int DC = B == 5 ? 5 : 7;
-    if (g.maxD <= DC && g.uniform) return launch_stream_t<T, B, DC, true>(bt, g);
-    if (g.maxD <= DC) return launch_stream_t<T, B, DC, false>(bt, g);
-    return launch_stream_t<T, B, 0, false>(bt, g);
+    if (g.maxD <= DC && g.uniform) return launch_stream_t<T, B, DC, true>(bt, g, blocks, nb, in, out);
+    if (g.maxD <= DC) return launch_stream_t<T, B, DC, false>(bt, g, blocks, nb, in, out);
+    return launch_stream_t<T, B, 0, false>(bt, g, blocks, nb, in, out);
+}
+
+// One streaming step of the node blocks `blocks` of group g from buffer `in` to `out`.
+int launch_stream(lbhpde_batch_s *bt, Group &g, const int2 *blocks, int nb, const void *in, void *out) {
+    if (bt->esz == 4)
+        return g.b == 5 ? launch_stream_b<float, 5>(bt, g, blocks, nb, in, out)
+                        : launch_stream_b<float, 7>(bt, g, blocks, nb, in, out);
+    return g.b == 5 ? launch_stream_b<double, 5>(bt, g, blocks, nb, in, out)
+                    : launch_stream_b<double, 7>(bt, g, blocks, nb, in, out);
 }
 
 int upload_plan(lbhpde_batch_s *bt, Group::Plan &pl) {
@@ -589,6 +623,7 @@ int launch_group(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *
 
 int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
     bt->count = count;
+    bt->depth.assign(count, 0);
     bt->mi.resize(count);
     bt->N.resize(count);
     bt->phi_off.resize(count + 1);
@@ -598,6 +633,19 @@ int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
         RC(lbhpde_model(I.m, I.alpha, I.pi, I.dx, I.dt, I.tau, I.lattice, I.scheme, &bt->mi[i]));
         const int W = (bt->mi[i].b - 1) / 2;
         if (I.N < 2 * W || I.N > (1LL << 30)) return LBHPDE_ERR_ARG;
+        // boundary: LBHPDE_PERIODIC, or LBHPDE_NEE with the depth in the bits above the kind
+        if (I.boundary < 0) return LBHPDE_ERR_ARG;
+        const int kind = I.boundary & 0xff, dcode = I.boundary >> 8;
+        if (kind != LBHPDE_PERIODIC && kind != LBHPDE_NEE) return LBHPDE_ERR_UNSUPPORTED;
+        int depth = 0;
+        if (kind == LBHPDE_PERIODIC) {
+            if (dcode != 0) return LBHPDE_ERR_ARG;
+        } else {
+            depth = dcode == 0 ? 2 : dcode;
+            if (depth > 4096 || I.N < 2LL * (W + depth)) return LBHPDE_ERR_ARG;
+            ++bt->nbounded;
+        }
+        bt->depth[i] = depth;
         bt->N[i] = I.N;
         bt->phi_off[i] = off;
         off += I.N;
@@ -616,6 +664,7 @@ int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
         s.ld = (bt->N[i] + 31) / 32 * 32;
         s.N = (int)bt->N[i];
         s.D = M.D;
+        s.pad = bt->depth[i];  // extrapolation depth of a bounded member, 0 when periodic
         s.coef = (int)coefd.size();
         st_elems += s.ld * M.b;
         for (int j = 1; j < M.b; ++j)
@@ -659,11 +708,12 @@ int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
     RC(bt->dev_alloc((void **)&bt->diag_out, sizeof(DiagPart) * count));
     RC(bt->dev_alloc((void **)&bt->phi_buf, sizeof(double) * bt->total));
 
-    for (int gi = 0; gi < 2; ++gi) {
-        Group &g = bt->groups[gi];
-        g.b = gi == 0 ? 5 : 7;
+    for (int gi = 0; gi < 4; ++gi) {
+        const bool bounded = gi >= 2;
+        Group &g = bounded ? bt->bgroups[gi - 2] : bt->groups[gi];
+        g.b = gi % 2 == 0 ? 5 : 7;
         for (int i = 0; i < count; ++i)
-            if (bt->mi[i].b == g.b) {
+            if (bt->mi[i].b == g.b && (bt->depth[i] > 0) == bounded) {
                 g.members.push_back(i);
                 g.maxD = std::max(g.maxD, bt->mi[i].D);
                 for (long long x = 0; x < bt->N[i]; x += kChunk) g.blocks_h.push_back(make_int2(i, (int)x));
@@ -685,6 +735,45 @@ int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
     return LBHPDE_OK;
 }
 
+// Bounded members of up to kBoundedK * kBoundedMaxT nodes stay resident in one CTA each
+// (unless the streaming kernel was requested); longer ones stream and are rebuilt each step.
+int plan_bounded(lbhpde_batch_s *bt, Group &g) {
+    g.bnd_h.clear();
+    g.smembers_h.clear();
+    g.sblocks_h.clear();
+    const int K = lbh::kBoundedK;
+    int maxthr = 0, maxD = 0;
+    for (int i : g.members) {
+        const Seg &sg = bt->segs_h[i];
+        if (bt->kernel != LBHPDE_KERNEL_STREAM && bt->N[i] <= (long long)K * lbh::kBoundedMaxT) {
+            lbk::BoundedInst I{};
+            I.off = sg.off;
+            I.ld = sg.ld;
+            I.mi = i;
+            I.N = sg.N;
+            I.D = sg.D;
+            I.gcoef = sg.coef;
+            I.depth = sg.pad;
+            I.nthr = (sg.N + K - 1) / K;
+            g.bnd_h.push_back(I);
+            maxthr = std::max(maxthr, I.nthr);
+            maxD = std::max(maxD, sg.D);
+        } else {
+            g.smembers_h.push_back(i);
+            for (long long x = 0; x < bt->N[i]; x += kChunk) g.sblocks_h.push_back(make_int2(i, (int)x));
+        }
+    }
+    g.bnd_threads = (maxthr + 31) / 32 * 32;
+    g.bnd_dc = lbh::onchip_dc(g.b, maxD);
+    g.bnd_D = g.bnd_dc > 0 ? g.bnd_dc : maxD;
+    if (!g.bnd_h.empty()) RC(bt->upload(&g.bnd, g.bnd_h));
+    if (!g.smembers_h.empty()) {
+        RC(bt->upload(&g.smembers, g.smembers_h));
+        RC(bt->upload(&g.sblocks, g.sblocks_h));
+    }
+    return LBHPDE_OK;
+}
+
 int choose_kernels(lbhpde_batch_s *bt) {
     for (auto &g : bt->groups) {
         if (g.members.empty()) continue;
@@ -700,13 +789,13 @@ int choose_kernels(lbhpde_batch_s *bt) {
         int rc = plan_onchip(bt, g, K, tblk, bt->kernel == LBHPDE_KERNEL_HALO);
         if (rc != LBHPDE_OK) return rc;
     }
+    for (auto &g : bt->bgroups)
+        if (!g.members.empty()) RC(plan_bounded(bt, g));
     return LBHPDE_OK;
 }
 
-int batch_step(lbhpde_batch_s *bt, long nsteps) {
-    if (nsteps < 0) return LBHPDE_ERR_ARG;
-    if (!bt->initialised) return LBHPDE_ERR_ARG;
-    if (nsteps == 0) return LBHPDE_OK;
+// nsteps steps of the periodic members (groups); bt->cur ends on the buffer that holds them.
+int step_periodic(lbhpde_batch_s *bt, long nsteps) {
     bool any_stream = false, any_halo = false;
     for (auto &g : bt->groups) {
         if (g.members.empty()) continue;
@@ -718,9 +807,7 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
         auto one_step = [&]() -> int {
             for (auto &g : bt->groups) {
                 if (g.members.empty()) continue;
-                int rc = bt->esz == 4 ? (g.b == 5 ? launch_stream_b<float, 5>(bt, g) : launch_stream_b<float, 7>(bt, g))
-                                      : (g.b == 5 ? launch_stream_b<double, 5>(bt, g) : launch_stream_b<double, 7>(bt, g));
-                RC(rc);
+                RC(launch_stream(bt, g, g.blocks, (int)g.blocks_h.size(), bt->st[bt->cur], bt->st[bt->cur ^ 1]));
             }
             bt->cur ^= 1;
             return LBHPDE_OK;
@@ -761,7 +848,6 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
             }
         }
         for (; left > 0; --left) RC(one_step());
-        bt->steps += nsteps;
         return LBHPDE_OK;
     }
     // halo windows advance tblk steps per launch through the ping-pong buffers; ring instances
@@ -811,6 +897,104 @@ int batch_step(lbhpde_batch_s *bt, long nsteps) {
     }
     if (fork) CK(cudaStreamWaitEvent(bt->stream, bt->ev_join, 0));
     bt->cur = cur1;
+    return LBHPDE_OK;
+}
+
+// Device pointer to the boundary values of this call (copied from the host when needed),
+// after checking the layout: member i's [nsteps][2W_i] block at phib + i * stride.
+int stage_boundary(lbhpde_batch_s *bt, long nsteps, const double *phib, long long stride, int on_device,
+                   const double **out) {
+    if (stride < 0) return LBHPDE_ERR_ARG;
+    long long need = 0, w2_shared = -1;
+    for (int i = 0; i < bt->count; ++i) {
+        if (bt->depth[i] == 0) continue;
+        const long long w2 = 2LL * lbk::wmax(bt->mi[i].b);
+        if (stride == 0) {
+            if (w2_shared >= 0 && w2_shared != w2) return LBHPDE_ERR_ARG;
+            w2_shared = w2;
+        } else if (stride < nsteps * w2) {
+            return LBHPDE_ERR_ARG;
+        }
+        need = std::max(need, (long long)i * stride + nsteps * w2);
+    }
+    if (on_device) {
+        *out = phib;
+        return LBHPDE_OK;
+    }
+    if ((size_t)need > bt->phib_cap) {
+        if (bt->phib_buf) bt->dev_free(bt->phib_buf);
+        bt->phib_buf = nullptr;
+        bt->phib_cap = 0;
+        RC(bt->dev_alloc((void **)&bt->phib_buf, sizeof(double) * (size_t)need));
+        bt->phib_cap = (size_t)need;
+    }
+    CK(cudaMemcpyAsync(bt->phib_buf, phib, sizeof(double) * (size_t)need, cudaMemcpyHostToDevice, bt->stream));
+    *out = bt->phib_buf;
+    return LBHPDE_OK;
+}
+
+// nsteps steps of the bounded members.  Resident members read buffer cur0 once and write the
+// buffer the periodic members end in (fixed), else the one the streaming members end in;
+// streaming members ping-pong from cur0 and are copied over if they end in the other buffer.
+int step_bounded(lbhpde_batch_s *bt, long nsteps, const double *pbd, long long stride, int cur0, bool fixed) {
+    bool any_stream = false, any_res = false;
+    for (auto &g : bt->bgroups) {
+        if (!g.smembers_h.empty()) any_stream = true;
+        if (!g.bnd_h.empty()) any_res = true;
+    }
+    int a = cur0;
+    if (any_stream) {
+        for (long s = 0; s < nsteps; ++s) {
+            for (auto &g : bt->bgroups) {
+                if (g.smembers_h.empty()) continue;
+                RC(launch_stream(bt, g, g.sblocks, (int)g.sblocks_h.size(), bt->st[a], bt->st[a ^ 1]));
+                RC(lbh::launch_nee_fix(g.b, bt->esz, bt->st[a ^ 1], bt->segs, g.smembers, (int)g.smembers_h.size(),
+                                       bt->coefT, pbd, stride, s, bt->stream));
+            }
+            a ^= 1;
+        }
+    }
+    const int target = fixed ? bt->cur : (any_stream ? a : cur0);
+    if (any_res) {
+        for (auto &g : bt->bgroups) {
+            if (g.bnd_h.empty()) continue;
+            for (long done = 0; done < nsteps;) {
+                const int n = (int)std::min<long>(nsteps - done, lbh::kBoundedMaxSteps);
+                const size_t smem = lbh::bounded_smem(g.b, bt->esz, g.bnd_threads, g.bnd_D, n);
+                RC(lbh::launch_bounded(g.b, bt->esz, g.bnd_dc, (int)g.bnd_h.size(), g.bnd_threads, smem, g.bnd,
+                                       bt->st[done == 0 ? cur0 : target], bt->st[target], bt->coefT, pbd, stride,
+                                       done, n, bt->stream));
+                done += n;
+            }
+        }
+    }
+    if (any_stream && a != target) {
+        for (auto &g : bt->bgroups)
+            for (int i : g.smembers_h) {
+                const Seg &sg = bt->segs_h[i];
+                const size_t off = size_t(sg.off) * bt->esz, bytes = size_t(sg.ld) * g.b * bt->esz;
+                CK(cudaMemcpyAsync((char *)bt->st[target] + off, (const char *)bt->st[a] + off, bytes,
+                                   cudaMemcpyDeviceToDevice, bt->stream));
+            }
+    }
+    bt->cur = target;
+    return LBHPDE_OK;
+}
+
+int batch_step(lbhpde_batch_s *bt, long nsteps, const double *phib = nullptr, long long stride = 0,
+               int on_device = 0) {
+    if (nsteps < 0) return LBHPDE_ERR_ARG;
+    if (!bt->initialised) return LBHPDE_ERR_ARG;
+    if (bt->nbounded && !phib) return LBHPDE_ERR_ARG;
+    if (nsteps == 0) return LBHPDE_OK;
+    const double *pbd = nullptr;
+    if (bt->nbounded) RC(stage_boundary(bt, nsteps, phib, stride, on_device, &pbd));
+    const int cur0 = bt->cur;
+    bool any_periodic = false;
+    for (auto &g : bt->groups)
+        if (!g.members.empty()) any_periodic = true;
+    if (any_periodic) RC(step_periodic(bt, nsteps));
+    if (bt->nbounded) RC(step_bounded(bt, nsteps, pbd, stride, cur0, any_periodic));
     bt->steps += nsteps;
     return LBHPDE_OK;
 }
@@ -823,7 +1007,8 @@ int batch_set_phi(lbhpde_batch_s *bt, const double *phi0, int on_device) {
         src = bt->phi_buf;
     }
     bt->cur = 0;
-    for (auto &g : bt->groups) {
+    for (int gi = 0; gi < 4; ++gi) {
+        Group &g = gi < 2 ? bt->groups[gi] : bt->bgroups[gi - 2];
         if (g.members.empty()) continue;
         RC(lbh::launch_init(g.b, bt->esz, bt->st[0], bt->segs, g.blocks, (int)g.blocks_h.size(), bt->coefD, src,
                             g.blk_off, bt->stream));
@@ -913,7 +1098,7 @@ int batch_create(lbhpde_batch_s **out, int count, const lbhpde_instance *members
 }
 
 void fill_instance(lbhpde_instance &I, int m, const double *alpha, const lbhpde_pi *pi, long N, double dx, double dt,
-                   double tau, int lattice, int scheme) {
+                   double tau, int lattice, int scheme, int boundary) {
     std::memset(&I, 0, sizeof(I));
     I.m = m;
     for (int k = 0; k < m && k < 6; ++k) {
@@ -926,6 +1111,7 @@ void fill_instance(lbhpde_instance &I, int m, const double *alpha, const lbhpde_
     I.tau = tau;
     I.lattice = lattice;
     I.scheme = scheme;
+    I.boundary = boundary;
 }
 
 }  // namespace
@@ -940,6 +1126,10 @@ extern "C" int lbhpde_batch_set_phi(lbhpde_batch_t b, const double *phi0, int on
     return b ? batch_set_phi(b, phi0, on_device) : LBHPDE_ERR_ARG;
 }
 extern "C" int lbhpde_batch_step(lbhpde_batch_t b, long nsteps) { return b ? batch_step(b, nsteps) : LBHPDE_ERR_ARG; }
+extern "C" int lbhpde_batch_step_nee(lbhpde_batch_t b, long nsteps, const double *phib, long member_stride,
+                                     int phib_on_device) {
+    return b ? batch_step(b, nsteps, phib, member_stride, phib_on_device) : LBHPDE_ERR_ARG;
+}
 extern "C" int lbhpde_batch_read_phi(lbhpde_batch_t b, double *out, int on_device) {
     return b ? batch_read_phi(b, out, on_device) : LBHPDE_ERR_ARG;
 }
@@ -984,10 +1174,9 @@ extern "C" int lbhpde_create(lbhpde_t *out, int m, const double *alpha, const lb
                              double dt, double tau, int lattice, int scheme, int precision, int boundary,
                              void *cuda_stream, const lbhpde_allocator *alloc) {
     if (!out || !alpha || !pi || m < 1 || m > 6) return LBHPDE_ERR_ARG;
-    if (boundary != LBHPDE_PERIODIC) return LBHPDE_ERR_UNSUPPORTED;
     *out = nullptr;
     lbhpde_instance I;
-    fill_instance(I, m, alpha, pi, N, dx, dt, tau, lattice, scheme);
+    fill_instance(I, m, alpha, pi, N, dx, dt, tau, lattice, scheme, boundary);
     auto *h = new (std::nothrow) lbhpde_ctx();
     if (!h) return LBHPDE_ERR_OOM;
     int rc = batch_create(&h->b, 1, &I, precision, cuda_stream, alloc);
@@ -1002,6 +1191,11 @@ extern "C" int lbhpde_set_phi(lbhpde_t h, const double *phi0, int on_device) {
     return h ? batch_set_phi(h->b, phi0, on_device) : LBHPDE_ERR_ARG;
 }
 extern "C" int lbhpde_step(lbhpde_t h, long nsteps) { return h ? batch_step(h->b, nsteps) : LBHPDE_ERR_ARG; }
+extern "C" int lbhpde_step_nee(lbhpde_t h, long nsteps, const double *phib, int phib_on_device) {
+    if (!h) return LBHPDE_ERR_ARG;
+    if (h->b->nbounded == 0) return batch_step(h->b, nsteps);
+    return batch_step(h->b, nsteps, phib, 0, phib_on_device);
+}
 extern "C" int lbhpde_read_phi(lbhpde_t h, double *out, int on_device) {
     return h ? batch_read_phi(h->b, out, on_device) : LBHPDE_ERR_ARG;
 }

@@ -1,0 +1,251 @@
+// Bounded grids: the non-equilibrium extrapolation boundary that Sec. IV applies to its test
+// problems (after Guo et al.; the paper gives no formula).  Each step is the collide+stream of
+// Eq. (LBE) on nodes 0..N-1 followed by a rebuild of the W = max|e| outer nodes at each end:
+//   f_j(x_b) = f^eq_j(phi_b) + [f_j(x_f) - f^eq_j(phi(x_f))],
+// phi_b the prescribed value at x_b and x_f the node `depth` places inside the outer layer
+// (x_f = W - 1 + depth on the left, N - W - depth on the right).
+//
+// In the state of this library (phi and the post-collision populations s_j, j >= 1) the rule
+// reads s_j(x_b) = f^eq_j(phi_b) + [s_j(x_f) - f^eq_j(phi(x_f))], phi(x_b) = phi_b: collision
+// scales the non-equilibrium part of every node by (1 - omega) and leaves f^eq unchanged, so
+// rebuilding after the relaxation equals rebuilding before it.  Interior nodes pull only from
+// nodes 0..N-1, so the periodic step of the other kernels is exact for them; the outer nodes'
+// pulls (which wrap) are discarded by the rebuild.
+#pragma once
+#include "lbhpde_kernels.cuh"
+
+namespace lbk {
+
+// One bounded instance resident in one CTA.
+struct BoundedInst {
+    long long off, ld;  // state placement (as Seg)
+    int mi;             // batch member index: its boundary data start at phib + mi * stride
+    int N, D;
+    int gcoef;          // coefficient block in global memory (as Seg::coef)
+    int depth;          // extrapolation depth (>= 1)
+    int nthr;           // threads that own nodes: ceil(N / K)
+};
+
+// Horner evaluation of one 16-byte aligned coefficient row of degree DC (DC > 0) or D (DC == 0).
+template <typename T, int DC>
+__device__ __forceinline__ T row_eval(const T *c, int D, T x) {
+    if constexpr (DC > 0) {
+        T cr[crow(DC)];
+        load_row<T, crow(DC)>(c, cr);
+        T acc = cr[DC];
+#pragma unroll
+        for (int p = DC - 1; p >= 0; --p) acc = fma_t(acc, x, cr[p]);
+        return acc;
+    } else {
+        T acc = c[D];
+        for (int p = D - 1; p >= 0; --p) acc = fma_t(acc, x, c[p]);
+        return acc;
+    }
+}
+
+// nsteps steps of every bounded instance, one instance per CTA, the state in registers for the
+// whole launch.  Thread t owns nodes tK .. tK+K-1.  Per step:
+//   1. publish the populations that cross a thread boundary (shared memory R/L), barrier;
+//   2. pull, phi' = phi + sum_j (f_j - s_j), relax; the owner of each extrapolation node x_f
+//      publishes s_j(x_f) - f^eq_j(phi(x_f)) (shared memory F), barrier;
+//   3. the owners of the outer nodes rebuild them from phi_b and F.
+// Two barriers per step make single exchange buffers race free: R/L are read before the second
+// barrier and rewritten after it; F is read before the next step's first barrier and rewritten
+// after it.  The launch's boundary data, phib[(step0 + s) * 2W + l] for member mi, are staged in
+// shared memory first.  Dynamic shared memory (elements of T):
+//   R, L [NE][nt] | P, Q [(B-1) cs]: omega f^eq_j and f^eq_j, rows of stride cs = crow(D) |
+//   X [16]: 1 - omega | F [16]: f^neq at the two extrapolation nodes | PB [nsteps][2W]
+template <typename T, int B, int K, int MAXT, int DC>
+__global__ void __launch_bounds__(MAXT, 1)
+    k_bounded(const T *__restrict__ st_in, T *__restrict__ st_out, const BoundedInst *__restrict__ insts,
+              const T *__restrict__ coefs, const double *__restrict__ phib, long long stride, long long step0,
+              int nsteps) {
+    static_assert(K >= wmax(B), "a thread must own at least max|e| nodes");
+    constexpr int W = wmax(B);
+    constexpr int NE = nedge(B);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nt = blockDim.x;
+    const BoundedInst I = insts[blockIdx.x];
+    const int D = DC > 0 ? DC : I.D;
+    const int cs = crow(D);
+    T *R = reinterpret_cast<T *>(smem_raw);
+    T *L = R + NE * nt;
+    T *P = L + NE * nt;
+    T *Q = P + (B - 1) * cs;
+    T *X = Q + (B - 1) * cs;
+    T *F = X + 16;
+    T *PB = F + 16;
+
+    const int tid = threadIdx.x;
+    const int n = (B - 1) * (I.D + 1);
+    for (int q = tid; q < (B - 1) * cs; q += nt) {
+        const int j = q / cs, pp = q % cs;
+        P[q] = pp <= I.D ? coefs[I.gcoef + j * (I.D + 1) + pp] : T(0);
+        Q[q] = pp <= I.D ? coefs[I.gcoef + n + j * (I.D + 1) + pp] : T(0);
+    }
+    if (tid == 0) X[0] = coefs[I.gcoef + 2 * n];
+    const double *pb = phib + (long long)I.mi * stride + step0 * (2 * W);
+    for (int q = tid; q < nsteps * 2 * W; q += nt) PB[q] = (T)pb[q];
+
+    const bool has = tid < I.nthr;
+    const int N = I.N;
+    const int xb = tid * K;
+    const int kL = W - 1 + I.depth, kR = N - W - I.depth;
+    T phi[K], v[B][K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int p = xb + k;
+        const bool ok = has && p < N;
+        phi[k] = ok ? st_in[I.off + p] : T(0);
+#pragma unroll
+        for (int j = 1; j < B; ++j) v[j][k] = ok ? st_in[I.off + (long long)j * I.ld + p] : T(0);
+    }
+    __syncthreads();
+    const T omw = X[0];
+
+    for (int s = 0; s < nsteps; ++s) {
+        if (has) {
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const int e = vel(j);
+                if (e > 0) {
+#pragma unroll
+                    for (int i = 0; i < e; ++i) R[(eslot(e) + i) * nt + tid] = v[j][K - e + i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < -e; ++i) L[(eslot(-e) + i) * nt + tid] = v[j][i];
+                }
+            }
+        }
+        __syncthreads();
+        if (has) {
+            // pull f_j(x) = s_j(x - e_j); sources outside 0..N-1 only feed outer nodes, which the
+            // rebuild overwrites: thread 0 and the last thread take their own (finite) values there
+            T d[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) d[k] = T(0);
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const int e = vel(j);
+                if (e > 0) {
+#pragma unroll
+                    for (int k = K - 1; k >= 0; --k) {  // descending: v[j][k - e] still old
+                        const T nv = k >= e ? v[j][k - e] : (tid > 0 ? R[(eslot(e) + k) * nt + tid - 1] : v[j][k]);
+                        d[k] += nv - v[j][k];
+                        v[j][k] = nv;
+                    }
+                } else {
+                    const int a = -e;
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {  // ascending: v[j][k + a] still old
+                        const T nv = k + a < K ? v[j][k + a]
+                                               : (tid + 1 < I.nthr ? L[(eslot(a) + k + a - K) * nt + tid + 1] : v[j][k]);
+                        d[k] += nv - v[j][k];
+                        v[j][k] = nv;
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) phi[k] += d[k];
+            // relax: s'_j = (1 - omega) f_j + P_j(phi')
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const T *c = P + (j - 1) * cs;
+                T acc[K];
+                if constexpr (DC > 0) {
+                    T cr[crow(DC)];
+                    load_row<T, crow(DC)>(c, cr);
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc[k] = cr[DC];
+#pragma unroll
+                    for (int p = DC - 1; p >= 0; --p)
+#pragma unroll
+                        for (int k = 0; k < K; ++k) acc[k] = fma_t(acc[k], phi[k], cr[p]);
+                } else {
+                    const T cD = c[D];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) acc[k] = cD;
+                    for (int p = D - 1; p >= 0; --p) {
+                        const T cp = c[p];
+#pragma unroll
+                        for (int k = 0; k < K; ++k) acc[k] = fma_t(acc[k], phi[k], cp);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < K; ++k) v[j][k] = fma_t(omw, v[j][k], acc[k]);
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int p = xb + k;
+                if (p >= N) {  // positions past the last node stay zero
+                    phi[k] = T(0);
+#pragma unroll
+                    for (int j = 1; j < B; ++j) v[j][k] = T(0);
+                }
+                if (p == kL || p == kR) {
+                    T *f = F + (p == kL ? 0 : 8);
+#pragma unroll
+                    for (int j = 1; j < B; ++j) f[j] = v[j][k] - row_eval<T, DC>(Q + (j - 1) * cs, D, phi[k]);
+                }
+            }
+        }
+        __syncthreads();
+        if (has && (xb < W || xb + K > N - W)) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const int p = xb + k;
+                const bool left = p < W, right = p >= N - W && p < N;
+                if (left || right) {
+                    const T pbv = PB[s * 2 * W + (left ? p : W + p - (N - W))];
+                    const T *f = F + (left ? 0 : 8);
+                    phi[k] = pbv;
+#pragma unroll
+                    for (int j = 1; j < B; ++j) v[j][k] = row_eval<T, DC>(Q + (j - 1) * cs, D, pbv) + f[j];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int p = xb + k;
+        if (has && p < N) {
+            st_out[I.off + p] = phi[k];
+#pragma unroll
+            for (int j = 1; j < B; ++j) st_out[I.off + (long long)j * I.ld + p] = v[j][k];
+        }
+    }
+}
+
+// Rebuild of the outer nodes after a streaming step (k_stream) of bounded segments, for
+// instances longer than one CTA holds.  One block per member, thread l < 2W rebuilds outer node
+// l (left nodes 0..W-1, then right nodes N-W..N-1); the extrapolation nodes are never outer
+// nodes, so reads and writes do not overlap.  Seg::pad holds the depth.
+template <typename T, int B>
+__global__ void k_nee_fix(T *__restrict__ st, const Seg *__restrict__ segs, const int *__restrict__ members,
+                          const T *__restrict__ coefs, const double *__restrict__ phib, long long stride,
+                          long long step) {
+    constexpr int W = wmax(B);
+    const int l = threadIdx.x;
+    if (l >= 2 * W) return;
+    const int mi = members[blockIdx.x];
+    const Seg s = segs[mi];
+    const int side = l / W, li = l % W;
+    const long long i = side ? s.N - W + li : li;
+    const long long k = side ? s.N - W - s.pad : W - 1 + s.pad;
+    const T phik = st[s.off + k];
+    const T pbv = (T)phib[(long long)mi * stride + step * (2 * W) + l];
+    const T *fe = coefs + s.coef + (B - 1) * (s.D + 1);
+#pragma unroll
+    for (int j = 1; j < B; ++j) {
+        const T *c = fe + (j - 1) * (s.D + 1);
+        T ak = c[s.D], ab = c[s.D];
+        for (int p = s.D - 1; p >= 0; --p) {
+            ak = fma_t(ak, phik, c[p]);
+            ab = fma_t(ab, pbv, c[p]);
+        }
+        st[s.off + (long long)j * s.ld + i] = ab + (st[s.off + (long long)j * s.ld + k] - ak);
+    }
+    st[s.off + i] = pbv;
+}
+
+}  // namespace lbk

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "lbhpde.h"
+#include "lbhpde_bounded.cuh"
 #include "lbhpde_kernels.cuh"
 
 namespace lbh {
@@ -50,5 +51,18 @@ int launch_onchip(int b, size_t esz, int K, int dc, bool halo, const Packed &p, 
                   const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st);
 int launch_init(int b, size_t esz, void *st, const lbk::Seg *segs, const int2 *blocks, int nb, const double *coefd,
                 const double *phi0, const long long *blk_off, cudaStream_t stream);
+
+// Bounded grids (lbhpde_bounded.cu): instances of up to kBoundedK * kBoundedMaxT nodes stay
+// resident in one CTA each; longer ones take the streaming step plus the outer-node rebuild.
+constexpr int kBoundedK = 4;
+constexpr int kBoundedMaxT = 512;
+constexpr int kBoundedMaxSteps = 1024;  // steps per resident launch (boundary data in shared memory)
+// Dynamic shared memory of k_bounded for a launch of nsteps steps.
+size_t bounded_smem(int b, size_t esz, int nthreads, int D, int nsteps);
+int launch_bounded(int b, size_t esz, int dc, int ninst, int nthreads, size_t smem, const lbk::BoundedInst *insts_d,
+                   const void *in, void *out, const void *coefT, const double *phib, long long stride,
+                   long long step0, int nsteps, cudaStream_t st);
+int launch_nee_fix(int b, size_t esz, void *st, const lbk::Seg *segs, const int *members, int nmem,
+                   const void *coefT, const double *phib, long long stride, long long step, cudaStream_t stream);
 
 }  // namespace lbh

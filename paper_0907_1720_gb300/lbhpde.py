@@ -24,6 +24,13 @@ OK, ERR_ARG, ERR_TAU_SINGULAR, ERR_OOM, ERR_DIVERGED, PENDING, ERR_TIMEOUT, ERR_
     ERR_UNSUPPORTED = range(10)
 FP64, FP32_DEV = 0, 1
 PERIODIC = 0
+NEE = 1  # bounded grid, non-equilibrium extrapolation boundary (depth 2)
+
+
+def nee_depth(d):
+    """Boundary code of the non-equilibrium extrapolation boundary with extrapolation depth d."""
+    return NEE | (int(d) << 8)
+
 NO_AUX_CORRECTION = 0x100  # or-ed into scheme: leave A_40, A_50, A_60 out
 PI_ZERO, PI_PHI, PI_POWER, PI_POLY = 0, 1, 2, 3
 PI_NCOEF = 8
@@ -60,7 +67,7 @@ class lbhpde_diag(ctypes.Structure):
 class lbhpde_instance(ctypes.Structure):
     _fields_ = [("m", ctypes.c_int), ("alpha", ctypes.c_double * 6), ("pi", lbhpde_pi * 6), ("N", ctypes.c_long),
                 ("dx", ctypes.c_double), ("dt", ctypes.c_double), ("tau", ctypes.c_double),
-                ("lattice", ctypes.c_int), ("scheme", ctypes.c_int)]
+                ("lattice", ctypes.c_int), ("scheme", ctypes.c_int), ("boundary", ctypes.c_int)]
 
 
 class lbhpde_request(ctypes.Structure):
@@ -107,6 +114,7 @@ _SIGS = {
                            _P(lbhpde_allocator)]),
     "lbhpde_set_phi": (_I, [_V, _V, _I]),
     "lbhpde_step": (_I, [_V, _L]),
+    "lbhpde_step_nee": (_I, [_V, _L, _V, _I]),
     "lbhpde_read_phi": (_I, [_V, _V, _I]),
     "lbhpde_diagnostics": (_I, [_V, _V, _P(lbhpde_diag)]),
     "lbhpde_set_kernel": (_I, [_V, _I, _I, _I]),
@@ -117,6 +125,7 @@ _SIGS = {
     "lbhpde_batch_create": (_I, [_P(_V), _I, _P(lbhpde_instance), _I, _V, _P(lbhpde_allocator)]),
     "lbhpde_batch_set_phi": (_I, [_V, _V, _I]),
     "lbhpde_batch_step": (_I, [_V, _L]),
+    "lbhpde_batch_step_nee": (_I, [_V, _L, _V, _L, _I]),
     "lbhpde_batch_read_phi": (_I, [_V, _V, _I]),
     "lbhpde_batch_diagnostics": (_I, [_V, _V, _P(lbhpde_diag)]),
     "lbhpde_batch_set_kernel": (_I, [_V, _I, _I, _I]),
@@ -200,14 +209,32 @@ def model_coeffs(info: lbhpde_model_info):
     return feq, coef
 
 
-def make_instance(eq, N, dx, dt, tau, scheme=1) -> lbhpde_instance:
+def make_instance(eq, N, dx, dt, tau, scheme=1, boundary=PERIODIC) -> lbhpde_instance:
     I = lbhpde_instance()
     I.m = eq.m
     for k in range(eq.m):
         I.alpha[k] = float(eq.alpha[k])
         I.pi[k] = make_pi(eq.pi[k])
     I.N, I.dx, I.dt, I.tau, I.lattice, I.scheme = int(N), float(dx), float(dt), float(tau), int(eq.lattice), int(scheme)
+    I.boundary = int(boundary)
     return I
+
+
+def _boundary_code(p):
+    """Boundary code of a workloads.Problem: periodic, or NEE with meta['depth'] (default 2)."""
+    if getattr(p, "boundary", "periodic") == "nee":
+        return nee_depth(p.meta.get("depth", 2))
+    return PERIODIC
+
+
+def _phib_arg(phib):
+    """(pointer, on_device, keep-alive) for boundary values given as a torch tensor or array."""
+    if phib is None:
+        return None, 0, None
+    if hasattr(phib, "data_ptr"):
+        return ctypes.c_void_p(phib.data_ptr()), 1, phib
+    a = np.ascontiguousarray(np.asarray(phib, dtype=np.float64))
+    return a.ctypes.data_as(ctypes.c_void_p), 0, a
 
 
 def autotune(precision, lattice, degree):
@@ -255,20 +282,22 @@ def _current_stream():
 # ----------------------------------------------------------------- handles
 
 class Solver:
-    """One periodic instance (lbhpde_create ... lbhpde_destroy)."""
+    """One instance (lbhpde_create ... lbhpde_destroy), periodic or bounded (boundary=NEE)."""
 
-    def __init__(self, eq, N, dx, dt, tau, scheme=1, precision=FP64, stream=None, use_torch=True):
+    def __init__(self, eq, N, dx, dt, tau, scheme=1, precision=FP64, stream=None, use_torch=True,
+                 boundary=PERIODIC):
         m, a, P = _eq_args(eq.alpha, eq.pi)
         self._alloc = torch_allocator() if use_torch else None
         st = stream if stream is not None else (_current_stream() if use_torch else None)
         h = ctypes.c_void_p()
         _check(lib().lbhpde_create(ctypes.byref(h), m, a, P, int(N), float(dx), float(dt), float(tau),
-                                   int(eq.lattice), int(scheme), int(precision), PERIODIC, st,
+                                   int(eq.lattice), int(scheme), int(precision), int(boundary), st,
                                    ctypes.byref(self._alloc) if self._alloc else None), "lbhpde_create")
         self.h, self.N = h, int(N)
 
     @classmethod
     def for_problem(cls, p, precision=FP64, **kw):
+        kw.setdefault("boundary", _boundary_code(p))
         return cls(p.eq, p.N, p.dx, p.dt, p.tau, scheme=p.scheme, precision=precision, **kw)
 
     def set_kernel(self, kernel=KERNEL_AUTO, nodes_per_thread=0, steps_per_launch=0):
@@ -286,6 +315,12 @@ class Solver:
 
     def step(self, nsteps):
         _check(lib().lbhpde_step(self.h, int(nsteps)), "lbhpde_step")
+        return self
+
+    def step_nee(self, nsteps, phib):
+        """nsteps bounded steps; phib: [nsteps, 2W] boundary values (array or device tensor)."""
+        ptr, dev, keep = _phib_arg(phib)
+        _check(lib().lbhpde_step_nee(self.h, int(nsteps), ptr, dev), "lbhpde_step_nee")
         return self
 
     def read_phi(self, out=None, check=True):
@@ -324,11 +359,12 @@ class Solver:
 
 
 class Batch:
-    """Many periodic instances stepped together (lbhpde_batch_*)."""
+    """Many instances stepped together (lbhpde_batch_*); bounded members come from problems
+    with boundary == "nee"."""
 
     def __init__(self, problems, precision=FP32_DEV, stream=None, use_torch=True):
         members = (lbhpde_instance * len(problems))(
-            *[make_instance(p.eq, p.N, p.dx, p.dt, p.tau, p.scheme) for p in problems])
+            *[make_instance(p.eq, p.N, p.dx, p.dt, p.tau, p.scheme, _boundary_code(p)) for p in problems])
         self._alloc = torch_allocator() if use_torch else None
         st = stream if stream is not None else (_current_stream() if use_torch else None)
         h = ctypes.c_void_p()
@@ -355,6 +391,14 @@ class Batch:
 
     def step(self, nsteps):
         _check(lib().lbhpde_batch_step(self.h, int(nsteps)), "lbhpde_batch_step")
+        return self
+
+    def step_nee(self, nsteps, phib, member_stride=0):
+        """nsteps steps; member i's boundary values are the [nsteps, 2W_i] doubles at
+        phib + i * member_stride (0: one array shared by all bounded members)."""
+        ptr, dev, keep = _phib_arg(phib)
+        _check(lib().lbhpde_batch_step_nee(self.h, int(nsteps), ptr, int(member_stride), dev),
+               "lbhpde_batch_step_nee")
         return self
 
     def read_phi(self, out=None, check=True):

@@ -151,8 +151,20 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     P = _pis(eq.pi)
     h = ctypes.c_void_p()
     assert lib.lbhpde_create(None, 3, a, P, 100, 0.1, 1e-3, 1.3, 0, 1, L.FP64, 0, None, None) == L.ERR_ARG
-    assert lib.lbhpde_create(ctypes.byref(h), 3, a, P, 100, 0.1, 1e-3, 1.3, 0, 1, L.FP64, 1, None, None) == \
+    # unknown boundary kind; bounded grid too short for the extrapolation node; periodic with a
+    # depth; negative code: all rejected before any device memory is touched
+    assert lib.lbhpde_create(ctypes.byref(h), 3, a, P, 100, 0.1, 1e-3, 1.3, 0, 1, L.FP64, 2, None, None) == \
         L.ERR_UNSUPPORTED
+    assert lib.lbhpde_create(ctypes.byref(h), 3, a, P, 7, 0.1, 1e-3, 1.3, 0, 1, L.FP64, L.NEE, None, None) == \
+        L.ERR_ARG
+    assert lib.lbhpde_create(ctypes.byref(h), 3, a, P, 100, 0.1, 1e-3, 1.3, 0, 1, L.FP64, L.nee_depth(49),
+                             None, None) == L.ERR_ARG
+    assert lib.lbhpde_create(ctypes.byref(h), 3, a, P, 100, 0.1, 1e-3, 1.3, 0, 1, L.FP64, 1 << 8, None, None) == \
+        L.ERR_ARG
+    assert lib.lbhpde_create(ctypes.byref(h), 3, a, P, 100, 0.1, 1e-3, 1.3, 0, 1, L.FP64, -1, None, None) == \
+        L.ERR_ARG
+    assert lib.lbhpde_step_nee(None, 1, None, 0) == L.ERR_ARG
+    assert lib.lbhpde_batch_step_nee(None, 1, None, 0, 0) == L.ERR_ARG
     assert lib.lbhpde_step(None, 1) == L.ERR_ARG
     assert lib.lbhpde_destroy(None) == L.ERR_ARG
     assert lib.lbhpde_strerror(L.ERR_DIVERGED).decode().startswith("non-finite")
