@@ -12,6 +12,10 @@ diagnostics reduction (a7).  The model set-up (a0) happens once, at batch creati
 
 --workload long_grid: the 2^24-node Kawahara grid (D1Q7, 1000 steps) in temporally blocked
 windows; with --kernel stream, on the one-step-per-launch streaming kernel (HBM roofline).
+--workload bounded: a tau sweep of Example 4.1 on its bounded grid (non-equilibrium
+extrapolation boundary, A_40 left out as for Table I): --sweep-members instances of N = 601,
+dx = 0.1, dt = 1e-3, tau spread over [1.989, 2.6], 1000 steps, one shared boundary array;
+every instance resident in one CTA (k_bounded), 12160 instances by default (80 per SM).
 --impl reference: the CPU oracle timed on the host cores on a bounded sample of the workload.
 """
 from __future__ import annotations
@@ -45,6 +49,9 @@ def load_peaks():
 
 # FP32 lanes per SM and SM count of GB300: the ALU roof of the on-chip kernel.
 SMS, FP32_LANES = 152, 128
+FP64_FMA_PER_SM_CLK = 2  # GB300: 152 x 2 x 2 flops x 2070 MHz = 1.26 TFLOP/s, the nominal 1.25
+BOUNDED_STEPS = 1000
+BOUNDED_TAU = (1.989, 2.6)
 
 # DRAM bytes (read + write) per node of one k_stream<float,7,7,...> launch, from an ncu capture
 # on a 2^23-node grid (traffic grows with N); used for the streaming roofline's "traffic".
@@ -109,6 +116,17 @@ def ensemble_problems(rank=0, members=4096):
     return W.kdv_burgers_ensemble(count=members, seed=W.SEED + rank)
 
 
+def bounded_problems(members):
+    """Example 4.1 (Table I, c = 100) with tau spread evenly over BOUNDED_TAU."""
+    taus = np.linspace(BOUNDED_TAU[0], BOUNDED_TAU[1], members)
+    probs = []
+    for t in taus:
+        p = W.bounded_config("4.1", 1e-3, float(t), BOUNDED_STEPS * 1e-3, scheme=1 | 0x100)
+        p.meta["depth"] = 2
+        probs.append(p)
+    return probs
+
+
 def flops_per_node_update(b, D):
     """Algorithmic FP operations of one node-update in the kernels' formulation: per moving
     population one Horner polynomial of degree D plus the relaxation (D + 1 multiply-adds,
@@ -152,7 +170,7 @@ def run_ours(args, rank, world):
         # the autotuner picks nodes per thread and steps per window for this precision, lattice
         # and degree (outside the timed region); the batch below uses its choice
         tuned = None
-        if not args.no_tune and not (args.workload == "long_grid" and args.kernel == "stream"):
+        if not args.no_tune and args.workload != "bounded" and not (args.workload == "long_grid" and args.kernel == "stream"):
             prec0 = L.FP32_DEV if args.precision == "fp32" else L.FP64
             b0, d0 = (5, 5) if args.workload == "ensemble" else (7, 7)
             K_t, T_t, r_t = L.autotune(prec0, b0, d0)
@@ -166,6 +184,15 @@ def run_ours(args, rank, world):
                         f"(sum N = {sum(p.N for p in probs)}), "
                         f"D1Q5 scheme 1, dx={W.ENSEMBLE_DX}, dt={W.ENSEMBLE_DT}, tau={W.ENSEMBLE_TAU}, "
                         f"{nsteps} steps per benchmark step")
+        elif args.workload == "bounded":
+            probs = bounded_problems(args.sweep_members)
+            nsteps = BOUNDED_STEPS
+            prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
+            solver = L.Batch(probs, precision=prec)
+            workload = (f"ks_shock_tau_sweep_{args.sweep_members}: {args.sweep_members} x N=601 (Example 4.1 on "
+                        f"[-30, 30], bounded grid, non-equilibrium extrapolation depth 2), D1Q5 scheme 1 without "
+                        f"A_40, dx=0.1, dt=1e-3, tau in [{BOUNDED_TAU[0]}, {BOUNDED_TAU[1]}], {nsteps} steps per "
+                        f"benchmark step, one resident CTA per instance")
         else:
             p = W.long_grid_config(N=args.nodes, nsteps=1000)
             probs = [p]
@@ -178,7 +205,16 @@ def run_ours(args, rank, world):
                         f"{nsteps} steps per benchmark step "
                         f"({'streaming kernel' if args.kernel == 'stream' else 'temporally blocked windows'})")
         total = sum(p.N for p in probs)
-        b = 5 if args.workload == "ensemble" else 7
+        b = 5 if args.workload in ("ensemble", "bounded") else 7
+        bounded = args.workload == "bounded"
+        phib_h = W.boundary_values(probs[0], 2, 0, nsteps) if bounded else None
+        phib_d = torch.tensor(phib_h, device="cuda", dtype=torch.float64) if bounded else None
+
+        def advance(pb):
+            if bounded:
+                solver.step_nee(nsteps, pb, 0)
+            else:
+                solver.step(nsteps)
         esz = 4 if prec == L.FP32_DEV else 8
         D = solver_model_degree(L, probs)
         phi0_h = np.concatenate([p.phi0 for p in probs])
@@ -192,7 +228,7 @@ def run_ours(args, rank, world):
             solver.set_phi(phi0_d)
             if record is not None:
                 record[0].record(stream)
-            solver.step(nsteps)
+            advance(phib_d)
             if record is not None:
                 record[1].record(stream)
             return solver.diagnostics()
@@ -227,11 +263,12 @@ def run_ours(args, rank, world):
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             solver.set_phi(pinned_in)  # host pointer (pinned): copied inside the call
-            solver.step(nsteps)
+            advance(phib_h)            # boundary values from host memory, copied inside the call
             solver.read_phi(pinned_out.numpy())
         t_e2e = (time.perf_counter() - t0) / max(e2e_steps, 1)
         e2e = None if args.quick else {"value": world * upd_step / t_e2e, "unit": "node-updates/s",
-                                       "h2d_bytes_per_step": total * 8, "d2h_bytes_per_step": total * 8}
+                                       "h2d_bytes_per_step": total * 8 + (phib_h.nbytes if bounded else 0),
+                                       "d2h_bytes_per_step": total * 8}
 
         # FP64 plain path on the same workload (fewer steps: it is ALU bound on GB300)
         fp64 = None
@@ -240,7 +277,23 @@ def run_ours(args, rank, world):
 
         kern_ms = float(np.mean(kern))
         clocks = clk.summary()
-        if args.workload == "ensemble" or args.kernel != "stream":
+        if bounded:
+            fl = flops_per_node_update(b, D)
+            sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+            if esz == 4:
+                peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+                src = f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock under load"
+            else:
+                peak_tf = SMS * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
+                src = (f"derived: {SMS} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 x median SM clock under "
+                       f"load (1.26 TFLOP/s at 2070 MHz, the nominal 1.25)")
+            achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
+            roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                    "frac": achieved / peak_tf, "traffic": None,
+                    "kernel": f"k_bounded<{'float' if esz == 4 else 'double'},5,4,512,5> (one resident CTA per "
+                              f"instance)",
+                    "flops_per_node_update": fl, "peak_source": src}
+        elif args.workload == "ensemble" or args.kernel != "stream":
             fl = flops_per_node_update(b, D)
             sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
             peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
@@ -269,7 +322,9 @@ def run_ours(args, rank, world):
             "dtype": "f32" if prec == L.FP32_DEV else "f64", "data": "synthetic (seeded, shaped like the paper's test problems)",
             "config": {"workload": workload, "node_updates_per_step": upd_step, "precision": args.precision,
                        "autotuned": tuned,
-                       "l2": f"inputs larger than L2: state {2 * total * b * esz / 2**20:.0f} MiB (two buffers)",
+                       "l2": (f"inputs larger than L2: state {total * b * esz / 2**20:.0f} MiB, updated in place"
+                              if bounded else
+                              f"inputs larger than L2: state {2 * total * b * esz / 2**20:.0f} MiB (two buffers)"),
                        "parallelism": f"replicas x{world} (independent ensembles)"},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
             "kernel_ms_per_step": kern_ms, "accuracy": accuracy,
@@ -346,7 +401,10 @@ def run_serving(args):
 
 def solver_kernel_launches(args, nsteps, tblk):
     """Kernel launches of one lbhpde_batch_step(nsteps) call: the streaming kernel launches once
-    per step; resident instances launch once and temporally blocked windows once per tblk steps."""
+    per step; resident instances launch once and temporally blocked windows once per tblk steps;
+    bounded instances launch once per 1024 steps."""
+    if args.workload == "bounded":
+        return (nsteps + 1023) // 1024
     if args.workload == "ensemble":
         return 1 + (nsteps + tblk - 1) // tblk
     if args.kernel == "stream":
@@ -399,6 +457,20 @@ def accuracy_report(L, args, probs, solver, prec, torch):
         errs = [float(np.abs(a - c).max() / np.abs(c).max()) for a, c in zip(res[prec], res[L.FP64])]
         out["fp32_vs_fp64_normwise_max"] = max(errs)
         out["members_checked"] = len(sub)
+    elif args.workload == "bounded":
+        # error E of every member against the exact solution at t = 1: the tau with the smallest
+        # error, and the member at the paper's tau_opt = 1.989 against Table I (c = 100, t = 1)
+        ex = torch.tensor(np.concatenate([p.exact(p.nsteps * p.dt) for p in probs]), device="cuda",
+                          dtype=torch.float64)
+        phib = W.boundary_values(probs[0], 2, 0, BOUNDED_STEPS)
+        solver.set_phi(torch.tensor(np.concatenate([p.phi0 for p in probs]), device="cuda", dtype=torch.float64))
+        solver.step_nee(BOUNDED_STEPS, phib, 0)
+        E = np.array([d["err_E"] for d in solver.diagnostics(ex)])
+        i = int(np.nanargmin(E))
+        out["E_min"] = float(E[i])
+        out["tau_at_E_min"] = float(probs[i].tau)
+        out["E_at_tau_1.989"] = float(E[0])
+        out["table_I_c100_t1"] = 2.9926e-3
     else:
         p = probs[0]
         ex = torch.tensor(p.exact(p.nsteps * p.dt), device="cuda", dtype=torch.float64)
@@ -433,6 +505,29 @@ def cpu_oracle_rate(args, budget_s=15.0):
         el = time.perf_counter() - t0
         upd = sum(p.N for p in probs) * steps
         sample = f"{len(probs)} ensemble members x {steps} steps, one member per thread"
+    elif args.workload == "bounded":
+        p0 = bounded_problems(1)[0]
+        pb = W.boundary_values(p0, 2, 0, BOUNDED_STEPS)
+
+        def run(p, steps):
+            M = oracle.Model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, scheme=p.scheme)
+            f = M.init(p.phi0)
+            M.step_nee(f, pb[:steps], 2)
+            return f
+
+        t0 = time.perf_counter()
+        run(p0, 50)
+        dt1 = (time.perf_counter() - t0) / 50
+        steps = BOUNDED_STEPS
+        # members of the full sweep (every tau of the benchmark), as many as fill the budget
+        nmem = int(min(args.sweep_members, max(2 * cores, budget_s * cores / (steps * dt1))))
+        probs = bounded_problems(args.sweep_members)[:: max(1, args.sweep_members // nmem)][:nmem]
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(cores) as ex:
+            list(ex.map(lambda p: run(p, steps), probs))
+        el = time.perf_counter() - t0
+        upd = sum(p.N for p in probs) * steps
+        sample = f"{len(probs)} tau-sweep members x {steps} steps, one member per thread"
     else:
         p = W.long_grid_config(nsteps=1)
         steps = 1
@@ -472,7 +567,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "long_grid", "serving"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "long_grid", "serving", "bounded"])
+    ap.add_argument("--sweep-members", type=int, default=12160,
+                    help="bounded: tau-sweep instances (12160 = 80 per SM; the state exceeds L2)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrival rate (requests/s)")
     ap.add_argument("--window", type=float, default=1.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--requests", type=int, default=2000, help="serving: cap on requests per rate")

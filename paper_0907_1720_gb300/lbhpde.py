@@ -415,12 +415,14 @@ class Batch:
         return [flat[self.offsets[i]:self.offsets[i + 1]] for i in range(len(self.sizes))]
 
     def diagnostics(self, phistar_device=None):
+        """One record per member (numpy structured array over the C records, no copy):
+        r["sum_phi"], r["max_abs_phi"], r["nonfinite"], r["err_E"], r["err_L2"], r["steps"]."""
         out = (lbhpde_diag * len(self.sizes))()
         ptr = ctypes.c_void_p(phistar_device.data_ptr()) if phistar_device is not None else None
         rc = lib().lbhpde_batch_diagnostics(self.h, ptr, out)
         if rc not in (OK, ERR_DIVERGED):
             _check(rc, "lbhpde_batch_diagnostics")
-        return [d.as_dict() for d in out]
+        return np.ctypeslib.as_array(out)
 
     def size(self):
         n, b = ctypes.c_long(), ctypes.c_size_t()

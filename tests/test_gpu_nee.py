@@ -168,7 +168,8 @@ def test_batch_mixes_bounded_and_periodic_members(L, kernel, nsteps):
 def test_tau_sweep_shares_one_boundary_array(L):
     """Bounded members that differ only in tau share their boundary data (stride 0); each
     matches its own oracle run.  This is how a batch scans tau for the smallest error."""
-    taus = [1.95, 1.97, 1.989, 2.01, 2.05, 2.1]
+    # tau >= 1.989: below it rounding grows fast (x5e6 at 1.97 over 500 steps; 1.95 diverges)
+    taus = [1.989, 2.0, 2.05, 2.1, 2.2, 2.4]
     probs = [bounded("4.1", 1e-3, t, 500, 1 | NOA) for t in taus]
     b = L.Batch(probs, precision=L.FP64)
     b.set_phi(np.concatenate([p.phi0 for p in probs]))
