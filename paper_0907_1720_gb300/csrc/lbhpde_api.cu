@@ -745,7 +745,8 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
     int maxthr = 0, maxD = 0;
     for (int i : g.members) {
         const Seg &sg = bt->segs_h[i];
-        if (bt->kernel != LBHPDE_KERNEL_STREAM && bt->N[i] <= (long long)K * lbh::kBoundedMaxT) {
+        const int shift = bt->N[i] <= (long long)K * lbh::kBoundedMaxT ? lbh::bounded_shift(g.b, sg.N, sg.pad) : -1;
+        if (bt->kernel != LBHPDE_KERNEL_STREAM && shift >= 0) {
             lbk::BoundedInst I{};
             I.off = sg.off;
             I.ld = sg.ld;
@@ -754,7 +755,8 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
             I.D = sg.D;
             I.gcoef = sg.coef;
             I.depth = sg.pad;
-            I.nthr = (sg.N + K - 1) / K;
+            I.shift = shift;
+            I.nthr = (sg.N + shift + K - 1) / K;
             g.bnd_h.push_back(I);
             maxthr = std::max(maxthr, I.nthr);
             maxD = std::max(maxD, sg.D);
@@ -959,7 +961,7 @@ int step_bounded(lbhpde_batch_s *bt, long nsteps, const double *pbd, long long s
         for (auto &g : bt->bgroups) {
             if (g.bnd_h.empty()) continue;
             for (long done = 0; done < nsteps;) {
-                const int n = (int)std::min<long>(nsteps - done, lbh::kBoundedMaxSteps);
+                const int n = (int)std::min<long>(nsteps - done, lbh::bounded_launch_steps(g.b, bt->esz));
                 const size_t smem = lbh::bounded_smem(g.b, bt->esz, g.bnd_threads, g.bnd_D, n);
                 RC(lbh::launch_bounded(g.b, bt->esz, g.bnd_dc, (int)g.bnd_h.size(), g.bnd_threads, smem, g.bnd,
                                        bt->st[done == 0 ? cur0 : target], bt->st[target], bt->coefT, pbd, stride,

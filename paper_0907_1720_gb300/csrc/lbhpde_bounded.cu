@@ -1,5 +1,7 @@
 // Launchers of the bounded-grid kernels (lbhpde_bounded.cuh): the resident kernel k_bounded,
 // one instance per CTA, and the outer-node rebuild k_nee_fix that follows a streaming step.
+#include <algorithm>
+
 #include "lbhpde_bounded.cuh"
 #include "lbhpde_internal.h"
 
@@ -50,7 +52,22 @@ int launch_bounded_d(int dc, const BoundedArgs &a) {
 
 size_t bounded_smem(int b, size_t esz, int nthreads, int D, int nsteps) {
     const int W = lbk::wmax(b), NE = lbk::nedge(b), cs = lbk::crow(D);
-    return (size_t(2) * NE * nthreads + size_t(2) * (b - 1) * cs + 32 + size_t(nsteps) * 2 * W) * esz;
+    return (size_t(4) * NE * nthreads + size_t(2) * (b - 1) * cs + 16 + size_t(nsteps) * 2 * W * b) * esz;
+}
+
+int bounded_shift(int b, int N, int depth) {
+    const int W = lbk::wmax(b), K = kBoundedK;
+    const int kL = W - 1 + depth, kR = N - W - depth;
+    for (int shift = 0; kL + shift < 32 * K; ++shift) {
+        const bool right_in_one_warp = ((kR + shift) / K) / 32 == ((N - 1 + shift) / K) / 32;
+        if (right_in_one_warp && N + shift <= K * kBoundedMaxT) return shift;
+    }
+    return -1;
+}
+
+int bounded_launch_steps(int b, size_t esz) {
+    const int per_step = 2 * lbk::wmax(b) * b * (int)esz;  // bytes of staged boundary data per step
+    return std::max(32, std::min(kBoundedMaxSteps, kBoundedStageBytes / per_step));
 }
 
 int launch_bounded(int b, size_t esz, int dc, int ninst, int nthreads, size_t smem, const lbk::BoundedInst *insts_d,

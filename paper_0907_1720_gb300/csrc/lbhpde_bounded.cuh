@@ -23,7 +23,9 @@ struct BoundedInst {
     int N, D;
     int gcoef;          // coefficient block in global memory (as Seg::coef)
     int depth;          // extrapolation depth (>= 1)
-    int nthr;           // threads that own nodes: ceil(N / K)
+    int shift;          // node x sits at position x + shift
+    int nthr;           // threads that own positions: ceil((N + shift) / K)
+    int pad;
 };
 
 // Horner evaluation of one 16-byte aligned coefficient row of degree DC (DC > 0) or D (DC == 0).
@@ -44,17 +46,20 @@ __device__ __forceinline__ T row_eval(const T *c, int D, T x) {
 }
 
 // nsteps steps of every bounded instance, one instance per CTA, the state in registers for the
-// whole launch.  Thread t owns nodes tK .. tK+K-1.  Per step:
-//   1. publish the populations that cross a thread boundary (shared memory R/L), barrier;
-//   2. pull, phi' = phi + sum_j (f_j - s_j), relax; the owner of each extrapolation node x_f
-//      publishes s_j(x_f) - f^eq_j(phi(x_f)) (shared memory F), barrier;
-//   3. the owners of the outer nodes rebuild them from phi_b and F.
-// Two barriers per step make single exchange buffers race free: R/L are read before the second
-// barrier and rewritten after it; F is read before the next step's first barrier and rewritten
-// after it.  The launch's boundary data, phib[(step0 + s) * 2W + l] for member mi, are staged in
-// shared memory first.  Dynamic shared memory (elements of T):
-//   R, L [NE][nt] | P, Q [(B-1) cs]: omega f^eq_j and f^eq_j, rows of stride cs = crow(D) |
-//   X [16]: 1 - omega | F [16]: f^neq at the two extrapolation nodes | PB [nsteps][2W]
+// whole launch.  Node x sits at position x + shift; thread t owns positions tK .. tK+K-1, and
+// positions that hold no node stay zero.  The host picks the shift so that each end's outer
+// nodes and its extrapolation node x_f fall in one warp.  Per step:
+//   1. publish the populations that cross a thread boundary (shared memory R/L, one buffer per
+//      step parity), barrier;
+//   2. pull, phi' = phi + sum_j (f_j - s_j), relax;
+//   3. in the warp of each end: the lane owning x_f computes s_j(x_f) - f^eq_j(phi(x_f)), the
+//      warp shares it by shuffle, and the lanes owning outer nodes rebuild them.
+// One barrier per step is race free: a buffer written at step s + 2 was last read at step s,
+// before every thread passed the barrier of step s + 1.  The launch's boundary data,
+// phib[(step0 + s) * 2W + l] for member mi, and their equilibria f^eq_j(phi_b) are evaluated by
+// all threads before the first step.  Dynamic shared memory (elements of T):
+//   R, L [2][NE][nt] | P, Q [(B-1) cs]: omega f^eq_j and f^eq_j, rows of stride cs = crow(D) |
+//   X [16]: 1 - omega | PB [nsteps][2W][B]: phi_b, f^eq_1(phi_b) .. f^eq_{B-1}(phi_b)
 template <typename T, int B, int K, int MAXT, int DC>
 __global__ void __launch_bounds__(MAXT, 1)
     k_bounded(const T *__restrict__ st_in, T *__restrict__ st_out, const BoundedInst *__restrict__ insts,
@@ -69,12 +74,11 @@ __global__ void __launch_bounds__(MAXT, 1)
     const int D = DC > 0 ? DC : I.D;
     const int cs = crow(D);
     T *R = reinterpret_cast<T *>(smem_raw);
-    T *L = R + NE * nt;
-    T *P = L + NE * nt;
+    T *L = R + 2 * NE * nt;
+    T *P = L + 2 * NE * nt;
     T *Q = P + (B - 1) * cs;
     T *X = Q + (B - 1) * cs;
-    T *F = X + 16;
-    T *PB = F + 16;
+    T *PB = X + 16;
 
     const int tid = threadIdx.x;
     const int n = (B - 1) * (I.D + 1);
@@ -84,36 +88,49 @@ __global__ void __launch_bounds__(MAXT, 1)
         Q[q] = pp <= I.D ? coefs[I.gcoef + n + j * (I.D + 1) + pp] : T(0);
     }
     if (tid == 0) X[0] = coefs[I.gcoef + 2 * n];
+    __syncthreads();
     const double *pb = phib + (long long)I.mi * stride + step0 * (2 * W);
-    for (int q = tid; q < nsteps * 2 * W; q += nt) PB[q] = (T)pb[q];
+    for (int q = tid; q < nsteps * 2 * W; q += nt) {
+        const T pbv = (T)pb[q];
+        PB[q * B] = pbv;
+#pragma unroll
+        for (int j = 1; j < B; ++j) PB[q * B + j] = row_eval<T, DC>(Q + (j - 1) * cs, D, pbv);
+    }
 
     const bool has = tid < I.nthr;
     const int N = I.N;
-    const int xb = tid * K;
+    const int x0 = tid * K - I.shift;  // node of this thread's first position
     const int kL = W - 1 + I.depth, kR = N - W - I.depth;
+    const int lane = tid & 31, warp = tid >> 5;
+    // the warps and lanes of the two ends (fixed for the launch)
+    const int wL = ((kL + I.shift) / K) >> 5, wR = ((N - 1 + I.shift) / K) >> 5;
+    const int srcL = ((kL + I.shift) / K) & 31, srcR = ((kR + I.shift) / K) & 31;
+    const bool dead = has && (x0 < 0 || x0 + K > N);  // owns positions without a node
     T phi[K], v[B][K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int p = xb + k;
-        const bool ok = has && p < N;
-        phi[k] = ok ? st_in[I.off + p] : T(0);
+        const int x = x0 + k;
+        const bool ok = has && x >= 0 && x < N;
+        phi[k] = ok ? st_in[I.off + x] : T(0);
 #pragma unroll
-        for (int j = 1; j < B; ++j) v[j][k] = ok ? st_in[I.off + (long long)j * I.ld + p] : T(0);
+        for (int j = 1; j < B; ++j) v[j][k] = ok ? st_in[I.off + (long long)j * I.ld + x] : T(0);
     }
     __syncthreads();
     const T omw = X[0];
 
     for (int s = 0; s < nsteps; ++s) {
+        T *Rb = R + (s & 1) * NE * nt;
+        T *Lb = L + (s & 1) * NE * nt;
         if (has) {
 #pragma unroll
             for (int j = 1; j < B; ++j) {
                 const int e = vel(j);
                 if (e > 0) {
 #pragma unroll
-                    for (int i = 0; i < e; ++i) R[(eslot(e) + i) * nt + tid] = v[j][K - e + i];
+                    for (int i = 0; i < e; ++i) Rb[(eslot(e) + i) * nt + tid] = v[j][K - e + i];
                 } else {
 #pragma unroll
-                    for (int i = 0; i < -e; ++i) L[(eslot(-e) + i) * nt + tid] = v[j][i];
+                    for (int i = 0; i < -e; ++i) Lb[(eslot(-e) + i) * nt + tid] = v[j][i];
                 }
             }
         }
@@ -130,7 +147,7 @@ __global__ void __launch_bounds__(MAXT, 1)
                 if (e > 0) {
 #pragma unroll
                     for (int k = K - 1; k >= 0; --k) {  // descending: v[j][k - e] still old
-                        const T nv = k >= e ? v[j][k - e] : (tid > 0 ? R[(eslot(e) + k) * nt + tid - 1] : v[j][k]);
+                        const T nv = k >= e ? v[j][k - e] : (tid > 0 ? Rb[(eslot(e) + k) * nt + tid - 1] : v[j][k]);
                         d[k] += nv - v[j][k];
                         v[j][k] = nv;
                     }
@@ -139,7 +156,7 @@ __global__ void __launch_bounds__(MAXT, 1)
 #pragma unroll
                     for (int k = 0; k < K; ++k) {  // ascending: v[j][k + a] still old
                         const T nv = k + a < K ? v[j][k + a]
-                                               : (tid + 1 < I.nthr ? L[(eslot(a) + k + a - K) * nt + tid + 1] : v[j][k]);
+                                               : (tid + 1 < I.nthr ? Lb[(eslot(a) + k + a - K) * nt + tid + 1] : v[j][k]);
                         d[k] += nv - v[j][k];
                         v[j][k] = nv;
                     }
@@ -174,44 +191,52 @@ __global__ void __launch_bounds__(MAXT, 1)
 #pragma unroll
                 for (int k = 0; k < K; ++k) v[j][k] = fma_t(omw, v[j][k], acc[k]);
             }
+            if (dead) {
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const int p = xb + k;
-                if (p >= N) {  // positions past the last node stay zero
-                    phi[k] = T(0);
+                for (int k = 0; k < K; ++k)
+                    if (x0 + k < 0 || x0 + k >= N) {
+                        phi[k] = T(0);
 #pragma unroll
-                    for (int j = 1; j < B; ++j) v[j][k] = T(0);
-                }
-                if (p == kL || p == kR) {
-                    T *f = F + (p == kL ? 0 : 8);
-#pragma unroll
-                    for (int j = 1; j < B; ++j) f[j] = v[j][k] - row_eval<T, DC>(Q + (j - 1) * cs, D, phi[k]);
-                }
+                        for (int j = 1; j < B; ++j) v[j][k] = T(0);
+                    }
             }
         }
-        __syncthreads();
-        if (has && (xb < W || xb + K > N - W)) {
+        // the ends: warp-uniform branches, every lane of the warp takes part in the shuffles
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            if (warp != (side == 0 ? wL : wR)) continue;
+            const int kf = side == 0 ? kL : kR;
+            T fneq[B];
+#pragma unroll
+            for (int j = 0; j < B; ++j) fneq[j] = T(0);
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (has && x0 + k == kf) {
+#pragma unroll
+                    for (int j = 1; j < B; ++j) fneq[j] = v[j][k] - row_eval<T, DC>(Q + (j - 1) * cs, D, phi[k]);
+                }
+#pragma unroll
+            for (int j = 1; j < B; ++j) fneq[j] = __shfl_sync(0xffffffffu, fneq[j], side == 0 ? srcL : srcR);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const int p = xb + k;
-                const bool left = p < W, right = p >= N - W && p < N;
-                if (left || right) {
-                    const T pbv = PB[s * 2 * W + (left ? p : W + p - (N - W))];
-                    const T *f = F + (left ? 0 : 8);
-                    phi[k] = pbv;
+                const int x = x0 + k;
+                const bool mine = has && (side == 0 ? (x >= 0 && x < W) : (x >= N - W && x < N));
+                if (mine) {
+                    const T *e = PB + (s * 2 * W + (side == 0 ? x : W + x - (N - W))) * B;
+                    phi[k] = e[0];
 #pragma unroll
-                    for (int j = 1; j < B; ++j) v[j][k] = row_eval<T, DC>(Q + (j - 1) * cs, D, pbv) + f[j];
+                    for (int j = 1; j < B; ++j) v[j][k] = e[j] + fneq[j];
                 }
             }
         }
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const int p = xb + k;
-        if (has && p < N) {
-            st_out[I.off + p] = phi[k];
+        const int x = x0 + k;
+        if (has && x >= 0 && x < N) {
+            st_out[I.off + x] = phi[k];
 #pragma unroll
-            for (int j = 1; j < B; ++j) st_out[I.off + (long long)j * I.ld + p] = v[j][k];
+            for (int j = 1; j < B; ++j) st_out[I.off + (long long)j * I.ld + x] = v[j][k];
         }
     }
 }

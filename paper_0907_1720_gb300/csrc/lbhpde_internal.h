@@ -56,9 +56,15 @@ int launch_init(int b, size_t esz, void *st, const lbk::Seg *segs, const int2 *b
 // resident in one CTA each; longer ones take the streaming step plus the outer-node rebuild.
 constexpr int kBoundedK = 4;
 constexpr int kBoundedMaxT = 512;
-constexpr int kBoundedMaxSteps = 1024;  // steps per resident launch (boundary data in shared memory)
+constexpr int kBoundedMaxSteps = 1024;     // steps per resident launch, at most
+constexpr int kBoundedStageBytes = 16384;  // shared memory for the launch's boundary data
 // Dynamic shared memory of k_bounded for a launch of nsteps steps.
 size_t bounded_smem(int b, size_t esz, int nthreads, int D, int nsteps);
+// Steps per resident launch: as many as kBoundedStageBytes of staged boundary data hold.
+int bounded_launch_steps(int b, size_t esz);
+// Smallest position shift that puts each end's outer nodes and extrapolation node in one warp of
+// the resident kernel (and keeps the instance within one CTA); -1 if there is none.
+int bounded_shift(int b, int N, int depth);
 int launch_bounded(int b, size_t esz, int dc, int ninst, int nthreads, size_t smem, const lbk::BoundedInst *insts_d,
                    const void *in, void *out, const void *coefT, const double *phib, long long stride,
                    long long step0, int nsteps, cudaStream_t st);
