@@ -71,6 +71,8 @@ def bind(path: str):
     lib.oracle_model_size.restype = ctypes.c_size_t
     lib.oracle_model_init.argtypes = [V, i, D, D, i, d, d, d, i, i]
     lib.oracle_model_init.restype = i
+    lib.oracle_model_init_nu.argtypes = [V, i, D, D, D, i, d, d, d, d, i, i]
+    lib.oracle_model_init_nu.restype = i
     lib.oracle_moments.argtypes = [V, d, D]
     lib.oracle_feq.argtypes = [V, d, D]
     lib.oracle_dfeq.argtypes = [V, d, D]
@@ -126,14 +128,27 @@ def edf(b: int, pibar, lib=None) -> np.ndarray:
 
 
 class Model:
-    """One LBGK model (lattice, moments, relaxation) built by the oracle."""
+    """One LBGK model (lattice, moments, relaxation) built by the oracle.  With ``nu`` and
+    ``pi_nu`` (``pi_nu[k-1][p]`` = coefficient of phi**(p + nu) in Pi_k, p >= 1) the Pi_k carry
+    terms with the real exponent nu as well."""
 
-    def __init__(self, alpha, pi, dx, dt, tau, lattice=0, scheme=1, lib=None):
+    def __init__(self, alpha, pi, dx, dt, tau, lattice=0, scheme=1, lib=None, nu=0.0, pi_nu=None):
         self._lib = lib = lib or _load()
         self._buf = ctypes.create_string_buffer(lib.oracle_model_size())
+        if pi_nu is not None:
+            rows = [list(r) for r in pi]
+            rows_nu = [list(r) for r in pi_nu]
+            ncoef = max(1, max(len(r) for r in rows + rows_nu))
+            pi = [r + [0.0] * (ncoef - len(r)) for r in rows]
+            pi_nu = [r + [0.0] * (ncoef - len(r)) for r in rows_nu]
         m, a, P, ncoef = _pack(alpha, pi)
-        rc = lib.oracle_model_init(self._buf, m, _dp(a), _dp(P), ncoef, float(dx), float(dt),
-                                   float(tau), int(lattice), int(scheme))
+        if pi_nu is not None:
+            _, _, Pn, _ = _pack(alpha, pi_nu)
+            rc = lib.oracle_model_init_nu(self._buf, m, _dp(a), _dp(P), _dp(Pn), ncoef, float(nu), float(dx),
+                                          float(dt), float(tau), int(lattice), int(scheme))
+        else:
+            rc = lib.oracle_model_init(self._buf, m, _dp(a), _dp(P), ncoef, float(dx), float(dt),
+                                       float(tau), int(lattice), int(scheme))
         if rc != OK:
             raise OracleError(rc)
         self.b = lib.oracle_model_b(self._buf)

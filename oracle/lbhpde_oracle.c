@@ -45,12 +45,15 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define OR_NC 64 /* capacity of a polynomial: degree < OR_NC */
+#define OR_NC 64 /* capacity in powers of phi: i < OR_NC */
+#define OR_NA 8  /* capacity in powers of phi^nu: a < OR_NA */
 
-/* A polynomial in phi: p(phi) = sum_{i<n} c[i] phi^i. */
+/* A generalised polynomial in phi with one real exponent nu > 0 (Sec. III C, class (1):
+ * beta u^n u_x with real n):  p(phi) = sum_{a<na} sum_{i<n} c[a][i] phi^(i + a nu).
+ * With na = 1 it is an ordinary polynomial, and nu plays no part. */
 typedef struct {
-    int n;
-    double c[OR_NC];
+    int n, na;
+    double c[OR_NA][OR_NC];
 } opoly;
 
 typedef struct {
@@ -59,6 +62,7 @@ typedef struct {
     int scheme;   /* 1: all b moments; 2: Pibar_{b-1} = 0                   */
     int inexact;  /* 1 if a remark's precondition for exact recovery fails */
     double dx, dt, c, tau;
+    double nu;       /* the real exponent of the phi^(i + a nu) terms (0: none) */
     double tk[7];    /* tk[k] = tau_k, k = 2..6                             */
     double alpha[7]; /* alpha[k], k = 1..6                                  */
     double beta[7];  /* beta[k],  k = 2..6                                  */
@@ -73,76 +77,102 @@ static void op_zero(opoly *p) { memset(p, 0, sizeof(*p)); }
 
 static int op_is_zero(const opoly *p)
 {
-    for (int i = 0; i < p->n; i++)
-        if (p->c[i] != 0.0) return 0;
+    for (int a = 0; a < p->na; a++)
+        for (int i = 0; i < p->n; i++)
+            if (p->c[a][i] != 0.0) return 0;
     return 1;
 }
 
 /* dst += s * src */
 static int op_axpy(opoly *dst, double s, const opoly *src)
 {
-    if (src->n > OR_NC) return -1;
-    for (int i = 0; i < src->n; i++) dst->c[i] += s * src->c[i];
+    if (src->n > OR_NC || src->na > OR_NA) return -1;
+    for (int a = 0; a < src->na; a++)
+        for (int i = 0; i < src->n; i++) dst->c[a][i] += s * src->c[a][i];
     if (src->n > dst->n) dst->n = src->n;
+    if (src->na > dst->na) dst->na = src->na;
     return 0;
 }
 
-/* r = a * b */
-static int op_mul(opoly *r, const opoly *a, const opoly *b)
+/* r = x * y:  phi^(i + a nu) phi^(j + b nu) = phi^(i + j + (a + b) nu) */
+static int op_mul(opoly *r, const opoly *x, const opoly *y)
 {
     opoly t;
     op_zero(&t);
-    if (a->n == 0 || b->n == 0) { *r = t; return 0; }
-    if (a->n + b->n - 1 > OR_NC) return -1;
-    t.n = a->n + b->n - 1;
-    for (int i = 0; i < a->n; i++)
-        for (int j = 0; j < b->n; j++) t.c[i + j] += a->c[i] * b->c[j];
+    if (x->n == 0 || y->n == 0 || x->na == 0 || y->na == 0) { *r = t; return 0; }
+    if (x->n + y->n - 1 > OR_NC || x->na + y->na - 1 > OR_NA) return -1;
+    t.n = x->n + y->n - 1;
+    t.na = x->na + y->na - 1;
+    for (int a = 0; a < x->na; a++)
+        for (int i = 0; i < x->n; i++) {
+            if (x->c[a][i] == 0.0) continue;
+            for (int b = 0; b < y->na; b++)
+                for (int j = 0; j < y->n; j++) t.c[a + b][i + j] += x->c[a][i] * y->c[b][j];
+        }
     *r = t;
     return 0;
 }
 
-/* r = a^k, k >= 0 */
-static int op_pow(opoly *r, const opoly *a, int k)
+/* r = x^k, k >= 0 */
+static int op_pow(opoly *r, const opoly *x, int k)
 {
     opoly t;
     op_zero(&t);
     t.n = 1;
-    t.c[0] = 1.0;
+    t.na = 1;
+    t.c[0][0] = 1.0;
     for (int i = 0; i < k; i++)
-        if (op_mul(&t, &t, a)) return -1;
+        if (op_mul(&t, &t, x)) return -1;
     *r = t;
     return 0;
 }
 
-/* r = d/dphi a */
-static void op_deriv(opoly *r, const opoly *a)
+/* r = d/dphi x:  d phi^(i + a nu) = (i + a nu) phi^(i - 1 + a nu).  A term phi^(a nu) with
+ * a >= 1 has no derivative of this form: -1. */
+static int op_deriv(opoly *r, const opoly *x, double nu)
 {
     opoly t;
     op_zero(&t);
-    for (int i = 1; i < a->n; i++) t.c[i - 1] = (double)i * a->c[i];
-    t.n = a->n > 1 ? a->n - 1 : 0;
-    *r = t;
-}
-
-/* r = integral_0^phi a(s) ds  (zero integration constant) */
-static int op_integ(opoly *r, const opoly *a)
-{
-    opoly t;
-    op_zero(&t);
-    if (a->n + 1 > OR_NC) return -1;
-    for (int i = 0; i < a->n; i++) t.c[i + 1] = a->c[i] / (double)(i + 1);
-    t.n = a->n + 1;
+    for (int a = 1; a < x->na; a++)
+        if (x->n > 0 && x->c[a][0] != 0.0) return -1;
+    for (int a = 0; a < x->na; a++)
+        for (int i = 1; i < x->n; i++) t.c[a][i - 1] = ((double)i + (double)a * nu) * x->c[a][i];
+    t.n = x->n > 1 ? x->n - 1 : 0;
+    t.na = x->na;
     *r = t;
     return 0;
 }
 
-/* Plain power-sum evaluation: sum_i c[i] * phi^i, phi^i by repeated products. */
-static double op_eval(const opoly *p, double phi)
+/* r = integral_0^phi x(s) ds  (zero integration constant):
+ *   phi^(i + a nu) -> phi^(i + 1 + a nu) / (i + 1 + a nu) */
+static int op_integ(opoly *r, const opoly *x, double nu)
 {
-    double s = 0.0, pw = 1.0;
-    for (int i = 0; i < p->n; i++) {
-        s += p->c[i] * pw;
-        pw *= phi;
+    opoly t;
+    op_zero(&t);
+    if (x->n + 1 > OR_NC) return -1;
+    for (int a = 0; a < x->na; a++)
+        for (int i = 0; i < x->n; i++) t.c[a][i + 1] = x->c[a][i] / ((double)(i + 1) + (double)a * nu);
+    t.n = x->n + 1;
+    t.na = x->na;
+    *r = t;
+    return 0;
+}
+
+/* Plain power-sum evaluation: sum_a (phi^nu)^a sum_i c[a][i] phi^i, powers by repeated
+ * products (phi^nu by the C library's pow).  The terms with a >= 1 are taken as zero where
+ * phi <= 0: the paper's class (1) has u > 0, and phi^nu -> 0 as phi -> 0+ makes this the
+ * continuous extension. */
+static double op_eval(const opoly *p, double phi, double nu)
+{
+    double s = 0.0, wa = 1.0;
+    const double w = p->na > 1 ? (phi > 0.0 ? pow(phi, nu) : 0.0) : 1.0;
+    for (int a = 0; a < p->na; a++) {
+        double pw = 1.0;
+        for (int i = 0; i < p->n; i++) {
+            s += p->c[a][i] * wa * pw;
+            pw *= phi;
+        }
+        wa *= w;
     }
     return s;
 }
@@ -171,13 +201,22 @@ static int singular(double x) { return fabs(x) < 1e-13; }
 
 /*
  * Build the model.  pi_coef is [m][ncoef] row-major: Pi_k(phi) =
- * sum_p pi_coef[(k-1)*ncoef + p] phi^p.  lattice: 0 = auto (5 for m <= 4, else 7).
+ * sum_p pi_coef[(k-1)*ncoef + p] phi^p + sum_p pi_coef_nu[(k-1)*ncoef + p] phi^(p + nu).
+ * pi_coef_nu may be NULL (nu unused); otherwise nu > 0 and pi_coef_nu[.. + 0] = 0, so that
+ * every Pi_k' is again of the same form.  lattice: 0 = auto (5 for m <= 4, else 7).
  */
-int oracle_model_init(oracle_model *M, int m, const double *alpha, const double *pi_coef,
-                      int ncoef, double dx, double dt, double tau, int lattice, int scheme)
+int oracle_model_init_nu(oracle_model *M, int m, const double *alpha, const double *pi_coef,
+                         const double *pi_coef_nu, int ncoef, double nu_exp, double dx, double dt, double tau,
+                         int lattice, int scheme)
 {
     memset(M, 0, sizeof(*M));
     if (m < 1 || m > 6 || ncoef < 1 || ncoef > 16) return OR_ERR_ARG;
+    if (pi_coef_nu) {
+        if (!(nu_exp > 0.0) || !isfinite(nu_exp)) return OR_ERR_ARG;
+        for (int k = 0; k < m; k++)
+            if (pi_coef_nu[k * ncoef] != 0.0) return OR_ERR_ARG;
+        M->nu = nu_exp;
+    }
     if (!(dx > 0.0) || !(dt > 0.0) || !(tau > 0.0) || !isfinite(dx) || !isfinite(dt) ||
         !isfinite(tau))
         return OR_ERR_ARG;
@@ -200,10 +239,15 @@ int oracle_model_init(oracle_model *M, int m, const double *alpha, const double 
         M->alpha[k] = alpha[k - 1];
         op_zero(&M->Pi[k]);
         M->Pi[k].n = ncoef;
-        for (int p = 0; p < ncoef; p++) M->Pi[k].c[p] = pi_coef[(k - 1) * ncoef + p];
+        M->Pi[k].na = pi_coef_nu ? 2 : 1;
+        for (int p = 0; p < ncoef; p++) {
+            M->Pi[k].c[0][p] = pi_coef[(k - 1) * ncoef + p];
+            if (pi_coef_nu) M->Pi[k].c[1][p] = pi_coef_nu[(k - 1) * ncoef + p];
+        }
     }
     /* alpha_1 is 1 in Eq. (NPDE); any other value is folded into Pi_1. */
-    for (int p = 0; p < ncoef; p++) M->Pi[1].c[p] *= M->alpha[1];
+    for (int a = 0; a < M->Pi[1].na; a++)
+        for (int p = 0; p < ncoef; p++) M->Pi[1].c[a][p] *= M->alpha[1];
     M->alpha[1] = 1.0;
     for (int k = m + 1; k <= 6; k++) op_zero(&M->Pi[k]);
 
@@ -252,7 +296,8 @@ int oracle_model_init(oracle_model *M, int m, const double *alpha, const double 
         opoly phi1;
         op_zero(&phi1);
         phi1.n = 2;
-        phi1.c[1] = 1.0;
+        phi1.na = 1;
+        phi1.c[0][1] = 1.0;
         int is_phi[7] = {0};
         for (int k = 2; k <= 6; k++) {
             opoly d = M->Pi[k];
@@ -270,29 +315,29 @@ int oracle_model_init(oracle_model *M, int m, const double *alpha, const double 
 
     /* (4) Auxiliary moments, each written as the paper prints its integrand. */
     opoly d1, d2, d3, d4, d5; /* Pi_k' */
-    op_deriv(&d1, &M->Pi[1]);
-    op_deriv(&d2, &M->Pi[2]);
-    op_deriv(&d3, &M->Pi[3]);
-    op_deriv(&d4, &M->Pi[4]);
-    op_deriv(&d5, &M->Pi[5]);
+    const double nu = M->nu;
+    if (op_deriv(&d1, &M->Pi[1], nu) || op_deriv(&d2, &M->Pi[2], nu) || op_deriv(&d3, &M->Pi[3], nu) ||
+        op_deriv(&d4, &M->Pi[4], nu) || op_deriv(&d5, &M->Pi[5], nu))
+        return OR_ERR_ARG;
     opoly p1[7]; /* (Pi_1')^k */
     for (int k = 0; k <= 6; k++)
         if (op_pow(&p1[k], &d1, k)) return OR_ERR_DEGREE;
     opoly one;
     op_zero(&one);
     one.n = 1;
-    one.c[0] = 1.0;
+    one.na = 1;
+    one.c[0][0] = 1.0;
     opoly g, t;
     for (int k = 2; k <= 6; k++) op_zero(&M->Pi0[k]);
 
     /* Pi_20 = int (Pi_1')^2 dphi                                      Sec. II C */
     g = p1[2];
-    if (op_integ(&M->Pi0[2], &g)) return OR_ERR_DEGREE;
+    if (op_integ(&M->Pi0[2], &g, nu)) return OR_ERR_DEGREE;
 
     /* Pi_30 = int [ (Pi_1')^3 + 3 beta_2 Pi_2' Pi_1' ] dphi              Sec. II C */
     g = p1[3];
     if (op_mul(&t, &d2, &p1[1]) || op_axpy(&g, 3.0 * b2, &t)) return OR_ERR_DEGREE;
-    if (op_integ(&M->Pi0[3], &g)) return OR_ERR_DEGREE;
+    if (op_integ(&M->Pi0[3], &g, nu)) return OR_ERR_DEGREE;
 
     /* Pi_40 = int [ (Pi_1')^4 + 6 beta_2 Pi_2' (Pi_1')^2
      *             + 4 beta_3 Pi_3' Pi_1' + A_40 ] dphi                   Eq. (Pi4) */
@@ -300,7 +345,7 @@ int oracle_model_init(oracle_model *M, int m, const double *alpha, const double 
     if (op_mul(&t, &d2, &p1[2]) || op_axpy(&g, 6.0 * b2, &t)) return OR_ERR_DEGREE;
     if (op_mul(&t, &d3, &p1[1]) || op_axpy(&g, 4.0 * b3, &t)) return OR_ERR_DEGREE;
     op_axpy(&g, M->A40, &one);
-    if (op_integ(&M->Pi0[4], &g)) return OR_ERR_DEGREE;
+    if (op_integ(&M->Pi0[4], &g, nu)) return OR_ERR_DEGREE;
 
     /* Pi_50 = int [ (Pi_1')^5 + 10 beta_2 Pi_2' (Pi_1')^3 + 10 beta_3 Pi_3' (Pi_1')^2
      *             + 5 beta_4 Pi_4' Pi_1' + A_50 ] dphi                   Eq. (Pi5) */
@@ -309,7 +354,7 @@ int oracle_model_init(oracle_model *M, int m, const double *alpha, const double 
     if (op_mul(&t, &d3, &p1[2]) || op_axpy(&g, 10.0 * b3, &t)) return OR_ERR_DEGREE;
     if (op_mul(&t, &d4, &p1[1]) || op_axpy(&g, 5.0 * b4, &t)) return OR_ERR_DEGREE;
     op_axpy(&g, M->A50, &one);
-    if (op_integ(&M->Pi0[5], &g)) return OR_ERR_DEGREE;
+    if (op_integ(&M->Pi0[5], &g, nu)) return OR_ERR_DEGREE;
 
     /* Pi_60 = int [ (Pi_1')^6 + 15 beta_2 Pi_2' (Pi_1')^4 + 20 beta_3 Pi_3' (Pi_1')^3
      *             + 15 beta_4 Pi_4' (Pi_1')^2 + 6 beta_5 Pi_5' Pi_1' + A_60 ] dphi
@@ -320,9 +365,16 @@ int oracle_model_init(oracle_model *M, int m, const double *alpha, const double 
     if (op_mul(&t, &d4, &p1[2]) || op_axpy(&g, 15.0 * b4, &t)) return OR_ERR_DEGREE;
     if (op_mul(&t, &d5, &p1[1]) || op_axpy(&g, 6.0 * M->beta[5], &t)) return OR_ERR_DEGREE;
     op_axpy(&g, M->A60, &one);
-    if (op_integ(&M->Pi0[6], &g)) return OR_ERR_DEGREE;
+    if (op_integ(&M->Pi0[6], &g, nu)) return OR_ERR_DEGREE;
 
     return OR_OK;
+}
+
+/* The model of an equation whose Pi_k are ordinary polynomials. */
+int oracle_model_init(oracle_model *M, int m, const double *alpha, const double *pi_coef,
+                      int ncoef, double dx, double dt, double tau, int lattice, int scheme)
+{
+    return oracle_model_init_nu(M, m, alpha, pi_coef, NULL, ncoef, 0.0, dx, dt, tau, lattice, scheme);
 }
 
 /* (5) The scaled moments of Sec. III A (D1Q5) and III B (D1Q7):
@@ -330,10 +382,10 @@ int oracle_model_init(oracle_model *M, int m, const double *alpha, const double 
 void oracle_moments(const oracle_model *M, double phi, double *pibar)
 {
     pibar[0] = phi;
-    pibar[1] = op_eval(&M->Pi[1], phi) / M->c;
+    pibar[1] = op_eval(&M->Pi[1], phi, M->nu) / M->c;
     for (int k = 2; k < M->b; k++) {
         double ck = pow(M->c, (double)k);
-        pibar[k] = (op_eval(&M->Pi0[k], phi) + M->beta[k] * op_eval(&M->Pi[k], phi)) / ck;
+        pibar[k] = (op_eval(&M->Pi0[k], phi, M->nu) + M->beta[k] * op_eval(&M->Pi[k], phi, M->nu)) / ck;
     }
     if (M->scheme == 2) pibar[M->b - 1] = 0.0;
 }
@@ -373,13 +425,13 @@ void oracle_dfeq(const oracle_model *M, double phi, double *dfeq)
     double P[7];
     opoly d;
     P[0] = 1.0;
-    op_deriv(&d, &M->Pi[1]);
-    P[1] = op_eval(&d, phi) / M->c;
+    op_deriv(&d, &M->Pi[1], M->nu);
+    P[1] = op_eval(&d, phi, M->nu) / M->c;
     for (int k = 2; k < M->b; k++) {
         opoly s = M->Pi0[k];
         op_axpy(&s, M->beta[k], &M->Pi[k]);
-        op_deriv(&d, &s);
-        P[k] = op_eval(&d, phi) / pow(M->c, (double)k);
+        op_deriv(&d, &s, M->nu);
+        P[k] = op_eval(&d, phi, M->nu) / pow(M->c, (double)k);
     }
     if (M->scheme == 2) P[M->b - 1] = 0.0;
     oracle_edf(M->b, P, dfeq);
@@ -521,5 +573,5 @@ void oracle_model_params(const oracle_model *M, double *tk, double *beta, double
 double oracle_aux_moment(const oracle_model *M, int k, double phi)
 {
     if (k < 2 || k > 6) return 0.0;
-    return op_eval(&M->Pi0[k], phi);
+    return op_eval(&M->Pi0[k], phi, M->nu);
 }

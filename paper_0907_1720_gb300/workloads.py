@@ -25,6 +25,8 @@ class Equation:
     alpha: tuple
     pi: tuple
     lattice: int = 0  # 0 = the smallest lattice that carries order m (5 for m <= 4, else 7)
+    nu: float = 0.0   # real exponent of the phi^(p + nu) terms (0: none)
+    pi_nu: tuple = None  # pi_nu[k-1][p]: coefficient of phi^(p + nu) in Pi_k (p >= 1)
 
     @property
     def m(self) -> int:
@@ -87,6 +89,22 @@ def modified_kawahara(a=1.0, b=1.0, k=1.0, lattice=0):
     return _eq("modified_kawahara", 5, {3: (b, (0, 1)), 5: (-k, (0, 1))}, (0, 0, 0, a / 3.0), lattice)
 
 
+def class1_real(a, b, n, alphas, lattice=0):
+    """Class (1) of Sec. III C with a real exponent n > 0:
+    u_t + a u u_x + b u^n u_x + sum_{k>=2} alpha_k d_x^k u = 0, i.e. Pi_1 = a u^2 / 2 +
+    b u^(n+1) / (n+1), Pi_k = u.  alphas = (alpha_2, ..., alpha_m)."""
+    m = 1 + len(alphas)
+    alpha = (1.0,) + tuple(float(x) for x in alphas)
+    pi = ((0.0, 0.0, a / 2.0),) + ((0.0, 1.0),) * (m - 1)
+    pi_nu = ((0.0, b / (n + 1.0)),) + ((),) * (m - 1)
+    return Equation(f"class1_n{n:g}", alpha, pi, lattice, float(n), pi_nu)
+
+
+def gkdv(n, b=1.0, lattice=0):
+    """Generalised KdV u_t + b u^n u_x + u_xxx = 0 with a real exponent n (class (1))."""
+    return class1_real(0.0, b, n, (0.0, 1.0), lattice)
+
+
 def kdv_kawahara(lattice=0):
     """Example 4.7: u_t + u u_x + u_x + u_xxx - u_xxxxx = 0 (Pi_1 = u^2/2 + u)."""
     return _eq("kdv_kawahara", 5, {3: (1.0, (0, 1)), 5: (-1.0, (0, 1))}, (0, 1.0, 0.5), lattice)
@@ -145,6 +163,15 @@ def modified_kawahara_soliton(x, t, a=1.0, b=1.0, k=1.0, x0=0.0, L=None):
     if L is not None:
         z = (z + 0.5 * L) % L - 0.5 * L
     return A * sech(B * z) ** 2
+
+
+def gkdv_soliton(x, t, n, b=1.0, c=1.0, x0=0.0, L=None):
+    """Solitary wave of u_t + b u^n u_x + u_xxx = 0 (real n > 0, b > 0, speed c > 0):
+    [c (n + 1)(n + 2) / (2 b) sech^2(n sqrt(c) (x - c t - x0) / 2)]^(1/n)."""
+    z = x - c * t - x0
+    if L is not None:
+        z = (z + 0.5 * L) % L - 0.5 * L
+    return (c * (n + 1.0) * (n + 2.0) / (2.0 * b) * sech(0.5 * n * math.sqrt(c) * z) ** 2) ** (1.0 / n)
 
 
 def kdv_kawahara_soliton(x, t, x0=20.0, L=None):
