@@ -16,6 +16,9 @@ windows; with --kernel stream, on the one-step-per-launch streaming kernel (HBM 
 extrapolation boundary, A_40 left out as for Table I): --sweep-members instances of N = 601,
 dx = 0.1, dt = 1e-3, tau spread over [1.989, 2.6], 1000 steps, one shared boundary array;
 every instance resident in one CTA (k_bounded), 12160 instances by default (80 per SM).
+--workload nu_grid: a 2^24-node periodic grid of u_t + u^1.5 u_x + u_xxx = 0 (class (1) with a
+real exponent), 1000 steps on the streaming kernel (its run-time path evaluates phi^nu once per
+node); HBM roofline.
 --impl reference: the CPU oracle timed on the host cores on a bounded sample of the workload.
 """
 from __future__ import annotations
@@ -170,7 +173,8 @@ def run_ours(args, rank, world):
         # the autotuner picks nodes per thread and steps per window for this precision, lattice
         # and degree (outside the timed region); the batch below uses its choice
         tuned = None
-        if not args.no_tune and args.workload != "bounded" and not (args.workload == "long_grid" and args.kernel == "stream"):
+        if (not args.no_tune and args.workload not in ("bounded", "nu_grid")
+                and not (args.workload == "long_grid" and args.kernel == "stream")):
             prec0 = L.FP32_DEV if args.precision == "fp32" else L.FP64
             b0, d0 = (5, 5) if args.workload == "ensemble" else (7, 7)
             K_t, T_t, r_t = L.autotune(prec0, b0, d0)
@@ -193,6 +197,15 @@ def run_ours(args, rank, world):
                         f"[-30, 30], bounded grid, non-equilibrium extrapolation depth 2), D1Q5 scheme 1 without "
                         f"A_40, dx=0.1, dt=1e-3, tau in [{BOUNDED_TAU[0]}, {BOUNDED_TAU[1]}], {nsteps} steps per "
                         f"benchmark step, one resident CTA per instance")
+        elif args.workload == "nu_grid":
+            p = W.gkdv_grid_config(N=args.nodes, nsteps=1000)
+            probs = [p]
+            nsteps = p.nsteps
+            prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
+            solver = L.Batch(probs, precision=prec)
+            workload = (f"gkdv_real_exponent_grid: N={args.nodes}, u_t + u^1.5 u_x + u_xxx = 0, D1Q5 scheme 1, "
+                        f"dx=0.1, dt=1e-4, tau=1.3, {nsteps} steps per benchmark step (streaming kernel, "
+                        f"run-time degree path with phi^nu)")
         else:
             p = W.long_grid_config(N=args.nodes, nsteps=1000)
             probs = [p]
@@ -205,7 +218,7 @@ def run_ours(args, rank, world):
                         f"{nsteps} steps per benchmark step "
                         f"({'streaming kernel' if args.kernel == 'stream' else 'temporally blocked windows'})")
         total = sum(p.N for p in probs)
-        b = 5 if args.workload in ("ensemble", "bounded") else 7
+        b = 5 if args.workload in ("ensemble", "bounded", "nu_grid") else 7
         bounded = args.workload == "bounded"
         phib_h = W.boundary_values(probs[0], 2, 0, nsteps) if bounded else None
         phib_d = torch.tensor(phib_h, device="cuda", dtype=torch.float64) if bounded else None
@@ -293,6 +306,13 @@ def run_ours(args, rank, world):
                     "kernel": f"k_bounded<{'float' if esz == 4 else 'double'},5,4,512,5> (one resident CTA per "
                               f"instance)",
                     "flops_per_node_update": fl, "peak_source": src}
+        elif args.workload == "nu_grid":
+            by = bytes_per_node_update(b, esz)
+            achieved = by * upd_step / (kern_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                    "kernel": f"k_stream<{'float' if esz == 4 else 'double'},5,0,256,0> (run-time degree, phi^nu)",
+                    "bytes_per_node_update": by, "peak_source": peak_src}
         elif args.workload == "ensemble" or args.kernel != "stream":
             fl = flops_per_node_update(b, D)
             sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
@@ -405,6 +425,8 @@ def solver_kernel_launches(args, nsteps, tblk):
     bounded instances launch once per 1024 steps."""
     if args.workload == "bounded":
         return (nsteps + 1023) // 1024
+    if args.workload == "nu_grid":
+        return nsteps
     if args.workload == "ensemble":
         return 1 + (nsteps + tblk - 1) // tblk
     if args.kernel == "stream":
@@ -415,7 +437,8 @@ def solver_kernel_launches(args, nsteps, tblk):
 def solver_model_degree(L, probs):
     D = 0
     for p in probs[:64]:
-        info = L.lbhpde_model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, lattice=p.eq.lattice, scheme=p.scheme)
+        info = L.lbhpde_model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, lattice=p.eq.lattice, scheme=p.scheme,
+                              nu=p.eq.nu, pi_nu=p.eq.pi_nu)
         D = max(D, info.D)
     return D
 
@@ -457,6 +480,18 @@ def accuracy_report(L, args, probs, solver, prec, torch):
         errs = [float(np.abs(a - c).max() / np.abs(c).max()) for a, c in zip(res[prec], res[L.FP64])]
         out["fp32_vs_fp64_normwise_max"] = max(errs)
         out["members_checked"] = len(sub)
+    elif args.workload == "nu_grid":
+        # FP32 against FP64 on a 2^16-node grid of the same configuration (no exact solution for
+        # the soliton train), normwise
+        q = W.gkdv_grid_config(N=1 << 16, nsteps=1000)
+        res = {}
+        for pr in (L.FP64, prec):
+            bt = L.Batch([q], precision=pr)
+            bt.set_phi(q.phi0).step(q.nsteps)
+            res[pr] = bt.read_phi()
+            bt.close()
+        out["fp32_vs_fp64_normwise_2^16_nodes"] = float(np.abs(res[prec] - res[L.FP64]).max()
+                                                       / np.abs(res[L.FP64]).max())
     elif args.workload == "bounded":
         # error E of every member against the exact solution at t = 1: the tau with the smallest
         # error, and the member at the paper's tau_opt = 1.989 against Table I (c = 100, t = 1)
@@ -528,6 +563,20 @@ def cpu_oracle_rate(args, budget_s=15.0):
         el = time.perf_counter() - t0
         upd = sum(p.N for p in probs) * steps
         sample = f"{len(probs)} tau-sweep members x {steps} steps, one member per thread"
+    elif args.workload == "nu_grid":
+        p = W.gkdv_grid_config(N=1 << 16, nsteps=1)
+        M = oracle.Model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, nu=p.eq.nu, pi_nu=p.eq.pi_nu)
+        f = M.init(p.phi0)
+        t0 = time.perf_counter()
+        M.step(f, 1)
+        dt1 = time.perf_counter() - t0
+        steps = int(max(1, min(1000, budget_s / dt1)))
+        t0 = time.perf_counter()
+        M.step(f, steps)
+        el = time.perf_counter() - t0
+        upd = p.N * steps
+        cores = 1
+        sample = f"2^16-node gKdV (n = 1.5) grid x {steps} steps, single thread"
     else:
         p = W.long_grid_config(nsteps=1)
         steps = 1
@@ -567,7 +616,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "long_grid", "serving", "bounded"])
+    ap.add_argument("--workload", default="ensemble",
+                    choices=["ensemble", "long_grid", "serving", "bounded", "nu_grid"])
     ap.add_argument("--sweep-members", type=int, default=12160,
                     help="bounded: tau-sweep instances (12160 = 80 per SM; the state exceeds L2)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrival rate (requests/s)")

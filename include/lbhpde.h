@@ -77,8 +77,11 @@ extern "C" {
 #define LBHPDE_PI_PHI 1    /* Pi_k = phi                       */
 #define LBHPDE_PI_POWER 2  /* Pi_k = phi^power, 1 <= power <= 7 */
 #define LBHPDE_PI_POLY 3   /* Pi_k = sum_p coef[p] phi^p        */
+#define LBHPDE_PI_POLY_NU 4 /* Pi_k = sum_p coef[p] phi^p + sum_{p>=1} coef_nu[p] phi^(p + nu), nu > 0 real:
+                              * the u^n u_x terms of class (1), Sec. III C, with a real n */
 #define LBHPDE_PI_NCOEF 8
 #define LBHPDE_MAX_DEG 31  /* highest degree of f^eq_j(phi) the kernels accept */
+#define LBHPDE_NU_TERMS 64 /* capacity of the generalised f^eq tables: (A + 1)(Dg + 1) <= 64 */
 
 #define LBHPDE_KERNEL_AUTO 0    /* the on-chip kernel (ONCHIP)                                 */
 #define LBHPDE_KERNEL_STREAM 1  /* one fused collide+stream launch per step through HBM        */
@@ -91,11 +94,17 @@ extern "C" {
 
 /* One flux function Pi_k of Eq. (NPDE): the paper requires "known differential
  * functions of phi"; this library takes polynomials in phi (every worked class of
- * Sec. III C is of that form). */
+ * Sec. III C is of that form), optionally with terms phi^(p + nu) of one real exponent
+ * nu > 0 (class (1) with a real n: Pi_1 = a u^2/2 + b u^(n+1)/(n+1), nu = n).  All Pi_k of
+ * kind LBHPDE_PI_POLY_NU of one equation must share nu.  The phi^(p + nu) terms are taken
+ * as zero where phi <= 0 (the paper's class has u > 0; this is the continuous extension). */
 typedef struct {
-    int kind;                        /* LBHPDE_PI_*                       */
-    int power;                       /* for LBHPDE_PI_POWER               */
-    double coef[LBHPDE_PI_NCOEF];    /* for LBHPDE_PI_POLY: coef[p] phi^p */
+    int kind;                        /* LBHPDE_PI_*                                      */
+    int power;                       /* for LBHPDE_PI_POWER                              */
+    double coef[LBHPDE_PI_NCOEF];    /* for LBHPDE_PI_POLY(_NU): coef[p] phi^p           */
+    double nu;                       /* for LBHPDE_PI_POLY_NU: the real exponent, > 0    */
+    double coef_nu[LBHPDE_PI_NCOEF]; /* for LBHPDE_PI_POLY_NU: coef_nu[p] phi^(p + nu);  */
+                                     /* coef_nu[0] must be 0                             */
 } lbhpde_pi;
 
 /* The model the library derives from an equation (Secs. II and III): step a0 of the
@@ -115,6 +124,15 @@ typedef struct {
     double A[3];           /* A_40, A_50, A_60, Eqs. (Pi4)-(Pi6)                            */
     double feq[7][LBHPDE_MAX_DEG + 1];
     double coef[7][LBHPDE_MAX_DEG + 1];
+    /* The same in generalised form, for every model:
+     *   f^eq_j(phi) = sum_{a=0}^{A} (phi^nu)^a sum_{i=0}^{Dg} gfeq[j][a (Dg + 1) + i] phi^i,
+     * A = nu_rows - 1, Dg = nu_deg; gcoef = omega gfeq.  Without real exponents nu = 0,
+     * nu_rows = 1, nu_deg = D and the rows equal feq and coef; with them, D = (A + 1)(Dg + 1) - 1
+     * (the flattened row length minus one) and feq, coef are zero. */
+    double nu;
+    int nu_rows, nu_deg;
+    double gfeq[7][LBHPDE_NU_TERMS];
+    double gcoef[7][LBHPDE_NU_TERMS];
 } lbhpde_model_info;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  alloc returns a

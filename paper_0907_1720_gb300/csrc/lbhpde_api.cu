@@ -63,6 +63,7 @@ struct Group {
     int K = 0, maxt = 0, tblk = 0;
     int dc = 0;  // compile-time degree of the on-chip kernel variant (0 = run time)
     bool uniform = false;  // every member has the same model (coefficients and omega)
+    bool has_nu = false;   // a member has real-exponent terms: streaming kernel, run-time degree
     // bounded groups (LBHPDE_NEE): resident members, one CTA each, and streaming members
     std::vector<lbk::BoundedInst> bnd_h;
     lbk::BoundedInst *bnd = nullptr;
@@ -564,8 +565,8 @@ int launch_stream_t(lbhpde_batch_s *bt, Group &g, const int2 *blocks, int nb, co
 template <typename T, int B>
 int launch_stream_b(lbhpde_batch_s *bt, Group &g, const int2 *blocks, int nb, const void *in, void *out) {
     constexpr int DC = B == 5 ? 5 : 7;
-    if (g.maxD <= DC && g.uniform) return launch_stream_t<T, B, DC, true>(bt, g, blocks, nb, in, out);
-    if (g.maxD <= DC) return launch_stream_t<T, B, DC, false>(bt, g, blocks, nb, in, out);
+    if (g.maxD <= DC && g.uniform && !g.has_nu) return launch_stream_t<T, B, DC, true>(bt, g, blocks, nb, in, out);
+    if (g.maxD <= DC && !g.has_nu) return launch_stream_t<T, B, DC, false>(bt, g, blocks, nb, in, out);
     return launch_stream_t<T, B, 0, false>(bt, g, blocks, nb, in, out);
 }
 
@@ -665,12 +666,17 @@ int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
         s.N = (int)bt->N[i];
         s.D = M.D;
         s.pad = bt->depth[i];  // extrapolation depth of a bounded member, 0 when periodic
+        s.A = M.nu_rows - 1;
+        s.Dg = M.nu_deg;
+        s.nu = M.nu;
         s.coef = (int)coefd.size();
         st_elems += s.ld * M.b;
+        // rows of the generalised tables: for an ordinary polynomial model they are the degree-D
+        // coefficients; with real exponents, the flattened (A + 1)(Dg + 1) = D + 1 entries
         for (int j = 1; j < M.b; ++j)
-            for (int p = 0; p <= M.D; ++p) coefd.push_back(M.coef[j][p]);
+            for (int p = 0; p <= M.D; ++p) coefd.push_back(M.gcoef[j][p]);
         for (int j = 1; j < M.b; ++j)
-            for (int p = 0; p <= M.D; ++p) coefd.push_back(M.feq[j][p]);
+            for (int p = 0; p <= M.D; ++p) coefd.push_back(M.gfeq[j][p]);
         coefd.push_back(1.0 - M.omega);
         segs[i] = s;
     }
@@ -716,6 +722,7 @@ int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
             if (bt->mi[i].b == g.b && (bt->depth[i] > 0) == bounded) {
                 g.members.push_back(i);
                 g.maxD = std::max(g.maxD, bt->mi[i].D);
+                if (bt->mi[i].nu_rows > 1) g.has_nu = true;
                 for (long long x = 0; x < bt->N[i]; x += kChunk) g.blocks_h.push_back(make_int2(i, (int)x));
             }
         g.uniform = !g.members.empty();
@@ -745,7 +752,9 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
     int maxthr = 0, maxD = 0;
     for (int i : g.members) {
         const Seg &sg = bt->segs_h[i];
-        const int shift = bt->N[i] <= (long long)K * lbh::kBoundedMaxT ? lbh::bounded_shift(g.b, sg.N, sg.pad) : -1;
+        const int shift = bt->N[i] <= (long long)K * lbh::kBoundedMaxT && sg.A == 0
+                              ? lbh::bounded_shift(g.b, sg.N, sg.pad)
+                              : -1;  // real-exponent members stream
         if (bt->kernel != LBHPDE_KERNEL_STREAM && shift >= 0) {
             lbk::BoundedInst I{};
             I.off = sg.off;
@@ -780,7 +789,7 @@ int choose_kernels(lbhpde_batch_s *bt) {
     for (auto &g : bt->groups) {
         if (g.members.empty()) continue;
         g.onchip_ok = false;
-        if (bt->kernel == LBHPDE_KERNEL_STREAM) continue;
+        if (bt->kernel == LBHPDE_KERNEL_STREAM || g.has_nu) continue;
         int K = bt->K_req > 0 ? bt->K_req : lbh::default_K(bt->esz, g.b);
         int tblk = bt->spl_req;
         int tk = 0, tt = 0;

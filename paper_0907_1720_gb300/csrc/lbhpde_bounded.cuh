@@ -260,13 +260,20 @@ __global__ void k_nee_fix(T *__restrict__ st, const Seg *__restrict__ segs, cons
     const T phik = st[s.off + k];
     const T pbv = (T)phib[(long long)mi * stride + step * (2 * W) + l];
     const T *fe = coefs + s.coef + (B - 1) * (s.D + 1);
+    const T wk = s.A > 0 ? nu_pow<T>(phik, s.nu) : T(0), wb = s.A > 0 ? nu_pow<T>(pbv, s.nu) : T(0);
 #pragma unroll
     for (int j = 1; j < B; ++j) {
         const T *c = fe + (j - 1) * (s.D + 1);
-        T ak = c[s.D], ab = c[s.D];
-        for (int p = s.D - 1; p >= 0; --p) {
-            ak = fma_t(ak, phik, c[p]);
-            ab = fma_t(ab, pbv, c[p]);
+        T ak, ab;
+        if (s.A > 0) {
+            ak = gen_eval<T>(c, s.A, s.Dg, phik, wk);
+            ab = gen_eval<T>(c, s.A, s.Dg, pbv, wb);
+        } else {
+            ak = c[s.D], ab = c[s.D];
+            for (int p = s.D - 1; p >= 0; --p) {
+                ak = fma_t(ak, phik, c[p]);
+                ab = fma_t(ab, pbv, c[p]);
+            }
         }
         st[s.off + (long long)j * s.ld + i] = ab + (st[s.off + (long long)j * s.ld + k] - ak);
     }

@@ -21,6 +21,7 @@
 namespace lbk {
 
 constexpr int kMaxDeg = 31;
+constexpr int kMaxRow = 64;  // longest coefficient row (real-exponent models: (A + 1)(Dg + 1))
 
 // e_j for j = 0..6: {0, 1, -1, 2, -2, 3, -3}
 __host__ __device__ constexpr int vel(int j) { return j == 0 ? 0 : ((j & 1) ? (j + 1) / 2 : -(j / 2)); }
@@ -42,12 +43,14 @@ struct Seg {
     long long off;  // element offset of row 0 (phi)
     long long ld;   // row stride in elements (multiple of 32)
     int N;          // nodes
-    int D;          // degree of the f^eq polynomials
+    int D;          // degree of the f^eq polynomials (A > 0: row length - 1, (A + 1)(Dg + 1) - 1)
     int coef;       // element offset of the coefficient block:
                     //   [(B-1)(D+1)]  P_j = omega f^eq_j, j = 1..B-1 (row j-1)
                     //   [(B-1)(D+1)]  f^eq_j (unscaled, for initialisation)
                     //   [1]           1 - omega
-    int pad;
+    int pad;        // bounded grids: extrapolation depth (0: periodic)
+    int A, Dg;      // real-exponent models: f^eq_j = sum_{a<=A} (phi^nu)^a sum_{i<=Dg} c[a(Dg+1)+i] phi^i
+    double nu;      //   (A = 0: an ordinary polynomial of degree D = Dg)
 };
 
 // Load NCR consecutive coefficients from a 16-byte aligned shared-memory row.
@@ -81,6 +84,28 @@ __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { retur
 template <>
 __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 
+// phi^nu for the real-exponent terms, zero where phi <= 0 (the continuous extension).
+template <typename T>
+__device__ __forceinline__ T nu_pow(T phi, double nu) {
+    if constexpr (sizeof(T) == 4)
+        return phi > 0.0f ? powf(phi, (float)nu) : 0.0f;
+    else
+        return phi > 0.0 ? pow(phi, nu) : 0.0;
+}
+
+// sum_{a<=A} w^a sum_{i<=Dg} c[a(Dg+1)+i] phi^i: Horner in phi within a row, in w across rows.
+template <typename T>
+__device__ __forceinline__ T gen_eval(const T *c, int A, int Dg, T phi, T w) {
+    T acc = T(0);
+    for (int a = A; a >= 0; --a) {
+        const T *r = c + a * (Dg + 1);
+        T h = r[Dg];
+        for (int p = Dg - 1; p >= 0; --p) h = fma_t(h, phi, r[p]);
+        acc = a == A ? h : fma_t(acc, w, h);
+    }
+    return acc;
+}
+
 // ---------------------------------------------------------------------------- a1: init
 // s_j(x) = f^eq_j(phi0(x)) (post-collision state of an equilibrium, collision leaves it
 // unchanged), phi(x) = phi0(x).  f^eq is evaluated in double and rounded once to T.
@@ -98,11 +123,17 @@ __global__ void k_init(T *__restrict__ st, const Seg *__restrict__ segs, const i
     for (int x = bl.y + threadIdx.x; x < xend; x += blockDim.x) {
         const double ph = p0[x];
         st[s.off + x] = (T)ph;
+        const double w = s.A > 0 ? nu_pow<double>(ph, s.nu) : 0.0;
 #pragma unroll
         for (int j = 1; j < B; ++j) {
             const double *c = fe + (j - 1) * (s.D + 1);
-            double acc = c[s.D];
-            for (int p = s.D - 1; p >= 0; --p) acc = __fma_rn(acc, ph, c[p]);
+            double acc;
+            if (s.A > 0) {
+                acc = gen_eval<double>(c, s.A, s.Dg, ph, w);
+            } else {
+                acc = c[s.D];
+                for (int p = s.D - 1; p >= 0; --p) acc = __fma_rn(acc, ph, c[p]);
+            }
             st[s.off + (long long)j * s.ld + x] = (T)acc;
         }
     }
@@ -154,7 +185,7 @@ __global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__re
                                                const __grid_constant__ StreamCoef<T, B, (DC > 0 ? DC : 1)> pc) {
     static_assert(!PARAMC || DC > 0, "parameter coefficients need a compile-time degree");
     constexpr int W = wmax(B);
-    constexpr int NC = (DC > 0 ? DC : kMaxDeg) + 1;
+    constexpr int NC = DC > 0 ? DC + 1 : kMaxRow;
     __shared__ T sc[PARAMC ? 1 : (B - 1) * NC + 1];
     const int2 bl = blocks[blockIdx.x];
     const Seg s = segs[bl.x];
@@ -181,7 +212,15 @@ __global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__re
         else
             return creg[(j - 1) * ((DC > 0 ? DC : 0) + 1) + p];
     };
-    auto poly = [&](int j, T ph) -> T {  // P_j(phi), Horner
+    // real-exponent models (run-time degree path only): w = phi^nu once per node
+    const int A = DC > 0 ? 0 : s.A;
+    auto wpow = [&](T ph) -> T {
+        if constexpr (DC > 0)
+            return T(0);
+        else
+            return A > 0 ? nu_pow<T>(ph, s.nu) : T(0);
+    };
+    auto poly = [&](int j, T ph, T w) -> T {  // P_j(phi), Horner
         T acc;
         if constexpr (DC > 0) {
             acc = coef(j, DC);
@@ -189,6 +228,7 @@ __global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__re
             for (int p = DC - 1; p >= 0; --p) acc = fma_t(acc, ph, coef(j, p));
         } else {
             const T *c = sc + (j - 1) * NC;
+            if (A > 0) return gen_eval<T>(c, A, s.Dg, ph, w);
             acc = c[D];
             for (int p = D - 1; p >= 0; --p) acc = fma_t(acc, ph, c[p]);
         }
@@ -241,8 +281,9 @@ __global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__re
             }
             const T ph = a[0][i] + d;
             o[0][i] = ph;
+            const T w = wpow(ph);
 #pragma unroll
-            for (int j = 1; j < B; ++j) o[j][i] = fma_t(omw, f[j], poly(j, ph));
+            for (int j = 1; j < B; ++j) o[j][i] = fma_t(omw, f[j], poly(j, ph, w));
         }
 #pragma unroll
         for (int j = 0; j < B; ++j) store4(dst + j * ld + x, o[j]);
@@ -263,8 +304,9 @@ __global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__re
             }
             const T ph = src[xi] + d;
             dst[xi] = ph;
+            const T w = wpow(ph);
 #pragma unroll
-            for (int j = 1; j < B; ++j) dst[j * ld + xi] = fma_t(omw, f[j], poly(j, ph));
+            for (int j = 1; j < B; ++j) dst[j * ld + xi] = fma_t(omw, f[j], poly(j, ph, w));
         }
     }
 }

@@ -7,6 +7,7 @@
 // with A_20 = A_30 = 0.  The inverse moment matrix M^-1 of Sec. III A/B is computed here
 // exactly, in rationals, from the velocity set, and f^eq = M^-1 Pibar is folded into one
 // polynomial per velocity.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -53,6 +54,64 @@ bool is_phi(const Poly &a) {
     Poly t = a;
     trim(t);
     return t.size() == 2 && t[0] == 0.0 && t[1] == 1.0;
+}
+
+// Generalised polynomial in phi with one real exponent nu: sum_a (phi^nu)^a r[a](phi).  With one
+// row it is an ordinary polynomial, and every operation below reduces to the Poly one exactly.
+struct GPoly {
+    std::vector<Poly> r;
+};
+void gtrim(GPoly &x) {
+    for (auto &p : x.r) trim(p);
+    while (!x.r.empty() && x.r.back().empty()) x.r.pop_back();
+}
+GPoly gmul(const GPoly &x, const GPoly &y) {
+    GPoly t;
+    if (x.r.empty() || y.r.empty()) return t;
+    t.r.resize(x.r.size() + y.r.size() - 1);
+    for (size_t a = 0; a < x.r.size(); ++a)
+        for (size_t c = 0; c < y.r.size(); ++c) axpy(t.r[a + c], 1.0, mul(x.r[a], y.r[c]));
+    return t;
+}
+void gaxpy(GPoly &y, double s, const GPoly &x) {
+    if (s == 0.0) return;
+    if (y.r.size() < x.r.size()) y.r.resize(x.r.size());
+    for (size_t a = 0; a < x.r.size(); ++a) axpy(y.r[a], s, x.r[a]);
+}
+// d/dphi phi^(i + a nu) = (i + a nu) phi^(i - 1 + a nu); false if a term phi^(a nu), a >= 1, has
+// no derivative of that form
+bool gderiv(const GPoly &x, double nu, GPoly &out) {
+    out.r.assign(x.r.size(), Poly{});
+    for (size_t a = 0; a < x.r.size(); ++a) {
+        const Poly &p = x.r[a];
+        if (a >= 1 && !p.empty() && p[0] != 0.0) return false;
+        if (p.size() <= 1) continue;
+        Poly d(p.size() - 1);
+        for (size_t i = 1; i < p.size(); ++i) d[i - 1] = (double(i) + double(a) * nu) * p[i];
+        out.r[a] = d;
+    }
+    return true;
+}
+// int_0^phi: phi^(i + a nu) -> phi^(i + 1 + a nu) / (i + 1 + a nu)
+GPoly ginteg0(const GPoly &x, double nu) {
+    GPoly t;
+    t.r.resize(x.r.size());
+    for (size_t a = 0; a < x.r.size(); ++a) {
+        Poly q(x.r[a].size() + 1, 0.0);
+        for (size_t i = 0; i < x.r[a].size(); ++i) q[i + 1] = x.r[a][i] / (double(i + 1) + double(a) * nu);
+        t.r[a] = q;
+    }
+    return t;
+}
+bool gis_zero(const GPoly &x) {
+    for (const auto &p : x.r)
+        if (!is_zero(p)) return false;
+    return true;
+}
+bool gis_phi(const GPoly &x) {
+    for (size_t a = 1; a < x.r.size(); ++a)
+        if (!is_zero(x.r[a])) return false;
+    return !x.r.empty() && is_phi(x.r[0]);
 }
 
 // Exact rational arithmetic for M^-1 (entries are small: denominators divide 720).
@@ -115,6 +174,34 @@ double binom(int n, int k) {
 
 bool near_zero(double x) { return std::fabs(x) < 1e-13; }
 
+int pi_to_poly(const lbhpde_pi &p, Poly &out);
+
+// Pi_k as a generalised polynomial; nu: the equation's real exponent so far (0 = none yet),
+// set or checked by a LBHPDE_PI_POLY_NU term.
+int pi_to_gpoly(const lbhpde_pi &p, double &nu, GPoly &out) {
+    out.r.clear();
+    Poly row0;
+    if (p.kind != LBHPDE_PI_POLY_NU) {
+        int rc = pi_to_poly(p, row0);
+        if (rc) return rc;
+        out.r.push_back(row0);
+        return LBHPDE_OK;
+    }
+    if (!(p.nu > 0.0) || !std::isfinite(p.nu) || p.nu > 64.0) return LBHPDE_ERR_ARG;
+    if (nu != 0.0 && nu != p.nu) return LBHPDE_ERR_ARG;  // one real exponent per equation
+    nu = p.nu;
+    if (p.coef_nu[0] != 0.0) return LBHPDE_ERR_ARG;  // phi^nu would have no derivative of the form
+    row0.assign(p.coef, p.coef + LBHPDE_PI_NCOEF);
+    Poly row1(p.coef_nu, p.coef_nu + LBHPDE_PI_NCOEF);
+    for (double v : row0)
+        if (!std::isfinite(v)) return LBHPDE_ERR_ARG;
+    for (double v : row1)
+        if (!std::isfinite(v)) return LBHPDE_ERR_ARG;
+    out.r = {row0, row1};
+    gtrim(out);
+    return LBHPDE_OK;
+}
+
 int pi_to_poly(const lbhpde_pi &p, Poly &out) {
     out.clear();
     switch (p.kind) {
@@ -164,12 +251,14 @@ extern "C" int lbhpde_model(int m, const double *alpha, const lbhpde_pi *pi, dou
 
     const double c = dx / dt;
     // Pi_1..Pi_6 (index 1..6); alpha_1 folded into Pi_1.
-    Poly P[7];
+    GPoly P[7];
+    double nu = 0.0;
     for (int k = 1; k <= m; ++k) {
-        int rc = pi_to_poly(pi[k - 1], P[k]);
+        int rc = pi_to_gpoly(pi[k - 1], nu, P[k]);
         if (rc) return rc;
     }
-    for (double &v : P[1]) v *= alpha[0];
+    for (auto &row : P[1].r)
+        for (double &v : row) v *= alpha[0];
 
     // Eq. (taus), evaluated by Horner's rule in tau.
     double tk[7] = {0.0, 1.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -182,7 +271,7 @@ extern "C" int lbhpde_model(int m, const double *alpha, const lbhpde_pi *pi, dou
     // alpha_k = dt^{k-1} tau_k beta_k; a term that is absent takes beta_k = 0 (Remark 2).
     double beta[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int k = 2; k <= m; ++k) {
-        if (alpha[k - 1] == 0.0 || is_zero(P[k])) continue;
+        if (alpha[k - 1] == 0.0 || gis_zero(P[k])) continue;
         if (near_zero(tk[k])) return LBHPDE_ERR_TAU_SINGULAR;
         beta[k] = alpha[k - 1] / (std::pow(dt, double(k - 1)) * tk[k]);
     }
@@ -216,47 +305,61 @@ extern "C" int lbhpde_model(int m, const double *alpha, const lbhpde_pi *pi, dou
 
     // Exact-recovery preconditions (Sec. II D-F, Remarks 2, 4, 5).
     int inexact = 0;
-    if (b - 1 >= 4 && beta[2] != 0.0 && !is_phi(P[2])) inexact = 1;
-    if (b - 1 >= 5 && beta[2] != 0.0 && beta[3] != 0.0 && !(is_phi(P[2]) && is_phi(P[3]))) inexact = 1;
-    if (b - 1 >= 6 && beta[3] != 0.0 && !is_phi(P[3])) inexact = 1;
-    if (b - 1 >= 6 && beta[2] != 0.0 && beta[4] != 0.0 && !(is_phi(P[2]) && is_phi(P[4]))) inexact = 1;
+    if (b - 1 >= 4 && beta[2] != 0.0 && !gis_phi(P[2])) inexact = 1;
+    if (b - 1 >= 5 && beta[2] != 0.0 && beta[3] != 0.0 && !(gis_phi(P[2]) && gis_phi(P[3]))) inexact = 1;
+    if (b - 1 >= 6 && beta[3] != 0.0 && !gis_phi(P[3])) inexact = 1;
+    if (b - 1 >= 6 && beta[2] != 0.0 && beta[4] != 0.0 && !(gis_phi(P[2]) && gis_phi(P[4]))) inexact = 1;
     if (b == 7 && beta[2] != 0.0) inexact = 1;
     if (no_aux && (need4 || need5 || need6)) inexact = 1;
 
     // Auxiliary moments Pi_k0, k = 2..b-1 (beta_k = 0 for k > m).
-    const Poly d1 = deriv(P[1]);
-    Poly d1pow[7];
-    d1pow[0] = {1.0};
-    for (int k = 1; k <= 6; ++k) d1pow[k] = mul(d1pow[k - 1], d1);
-    Poly Pibar[7];
-    Pibar[0] = {0.0, 1.0};
+    GPoly d1;
+    if (!gderiv(P[1], nu, d1)) return LBHPDE_ERR_ARG;
+    GPoly d1pow[7];
+    d1pow[0].r = {Poly{1.0}};
+    for (int k = 1; k <= 6; ++k) d1pow[k] = gmul(d1pow[k - 1], d1);
+    GPoly Pibar[7];
+    Pibar[0].r = {Poly{0.0, 1.0}};
     Pibar[1] = P[1];
-    for (double &v : Pibar[1]) v /= c;
+    for (auto &row : Pibar[1].r)
+        for (double &v : row) v /= c;
     for (int k = 2; k < b; ++k) {
-        Poly g = d1pow[k];
+        GPoly g = d1pow[k];
         for (int j = 2; j <= k - 1; ++j) {
             if (beta[j] == 0.0) continue;
-            axpy(g, binom(k, j) * beta[j], mul(deriv(P[j]), d1pow[k - j]));
+            GPoly dj;
+            if (!gderiv(P[j], nu, dj)) return LBHPDE_ERR_ARG;
+            gaxpy(g, binom(k, j) * beta[j], gmul(dj, d1pow[k - j]));
         }
-        axpy(g, A[k], Poly{1.0});
-        Poly Pk0 = integ0(g);
-        axpy(Pk0, beta[k], P[k]);
+        GPoly one;
+        one.r = {Poly{1.0}};
+        gaxpy(g, A[k], one);
+        GPoly Pk0 = ginteg0(g, nu);
+        gaxpy(Pk0, beta[k], P[k]);
         const double ck = std::pow(c, double(k));
-        for (double &v : Pk0) v /= ck;
+        for (auto &row : Pk0.r)
+            for (double &v : row) v /= ck;
         Pibar[k] = Pk0;
     }
-    if (scheme == 2) Pibar[b - 1].clear();
+    if (scheme == 2) Pibar[b - 1].r.clear();
 
     double Minv[7][7];
     moment_matrix_inverse(b, kVel, Minv);
-    int D = 0;
-    Poly feq[7];
+    int Dg = 0, rows = 1;
+    GPoly feq[7];
     for (int j = 0; j < b; ++j) {
-        for (int k = 0; k < b; ++k) axpy(feq[j], Minv[j][k], Pibar[k]);
-        trim(feq[j]);
-        if ((int)feq[j].size() - 1 > D) D = (int)feq[j].size() - 1;
+        for (int k = 0; k < b; ++k) gaxpy(feq[j], Minv[j][k], Pibar[k]);
+        gtrim(feq[j]);
+        rows = std::max(rows, (int)feq[j].r.size());
+        for (const auto &row : feq[j].r) Dg = std::max(Dg, (int)row.size() - 1);
     }
-    if (D > LBHPDE_MAX_DEG) return LBHPDE_ERR_ARG;
+    if (rows == 1) nu = 0.0;  // no real-exponent term survives: an ordinary polynomial model
+    int D = Dg;
+    if (rows == 1 && D > LBHPDE_MAX_DEG) return LBHPDE_ERR_ARG;
+    if (rows > 1) {
+        if (rows * (Dg + 1) > LBHPDE_NU_TERMS) return LBHPDE_ERR_ARG;
+        D = rows * (Dg + 1) - 1;
+    }
 
     out->b = b;
     out->m = m;
@@ -272,11 +375,20 @@ extern "C" int lbhpde_model(int m, const double *alpha, const lbhpde_pi *pi, dou
     out->A[0] = A[4];
     out->A[1] = A[5];
     out->A[2] = A[6];
+    out->nu = nu;
+    out->nu_rows = rows;
+    out->nu_deg = Dg;
     for (int j = 0; j < b; ++j)
-        for (size_t p = 0; p < feq[j].size(); ++p) {
-            out->feq[j][p] = feq[j][p];
-            out->coef[j][p] = feq[j][p] / tau;
-        }
+        for (size_t a = 0; a < feq[j].r.size(); ++a)
+            for (size_t p = 0; p < feq[j].r[a].size(); ++p) {
+                const double v = feq[j].r[a][p];
+                out->gfeq[j][a * (Dg + 1) + p] = v;
+                out->gcoef[j][a * (Dg + 1) + p] = v / tau;
+                if (rows == 1) {
+                    out->feq[j][p] = v;
+                    out->coef[j][p] = v / tau;
+                }
+            }
     return LBHPDE_OK;
 }
 

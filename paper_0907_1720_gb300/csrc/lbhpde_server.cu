@@ -510,6 +510,8 @@ extern "C" int lbhpde_submit(lbhpde_server_t S, const lbhpde_request *q, uint64_
     int rc = lbhpde_model(q->m, q->alpha, q->pi, q->dx, q->dt, q->tau, q->lattice, q->scheme, &r->mi);
     const int W = (r->mi.b - 1) / 2;
     if (rc == LBHPDE_OK && (q->N < 2 * W || q->N > (1L << 26))) rc = LBHPDE_ERR_ARG;
+    // the server's kernels are the on-chip ones, which take ordinary polynomial models only
+    if (rc == LBHPDE_OK && r->mi.nu_rows > 1) rc = LBHPDE_ERR_UNSUPPORTED;
     if (rc != LBHPDE_OK) {
         delete r;
         return rc;

@@ -32,21 +32,25 @@ def nee_depth(d):
     return NEE | (int(d) << 8)
 
 NO_AUX_CORRECTION = 0x100  # or-ed into scheme: leave A_40, A_50, A_60 out
-PI_ZERO, PI_PHI, PI_POWER, PI_POLY = 0, 1, 2, 3
+PI_ZERO, PI_PHI, PI_POWER, PI_POLY, PI_POLY_NU = 0, 1, 2, 3, 4
 PI_NCOEF = 8
 MAX_DEG = 31
+NU_TERMS = 64
 KERNEL_AUTO, KERNEL_STREAM, KERNEL_ONCHIP, KERNEL_HALO = 0, 1, 2, 3
 
 
 class lbhpde_pi(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("power", ctypes.c_int), ("coef", ctypes.c_double * PI_NCOEF)]
+    _fields_ = [("kind", ctypes.c_int), ("power", ctypes.c_int), ("coef", ctypes.c_double * PI_NCOEF),
+                ("nu", ctypes.c_double), ("coef_nu", ctypes.c_double * PI_NCOEF)]
 
 
 class lbhpde_model_info(ctypes.Structure):
     _fields_ = [("b", ctypes.c_int), ("m", ctypes.c_int), ("scheme", ctypes.c_int), ("D", ctypes.c_int),
                 ("inexact", ctypes.c_int), ("c", ctypes.c_double), ("omega", ctypes.c_double),
                 ("tk", ctypes.c_double * 7), ("beta", ctypes.c_double * 7), ("A", ctypes.c_double * 3),
-                ("feq", (ctypes.c_double * (MAX_DEG + 1)) * 7), ("coef", (ctypes.c_double * (MAX_DEG + 1)) * 7)]
+                ("feq", (ctypes.c_double * (MAX_DEG + 1)) * 7), ("coef", (ctypes.c_double * (MAX_DEG + 1)) * 7),
+                ("nu", ctypes.c_double), ("nu_rows", ctypes.c_int), ("nu_deg", ctypes.c_int),
+                ("gfeq", (ctypes.c_double * NU_TERMS) * 7), ("gcoef", (ctypes.c_double * NU_TERMS) * 7)]
 
 
 class lbhpde_allocator(ctypes.Structure):
@@ -165,8 +169,22 @@ def _check(code, where):
 
 # ------------------------------------------------------------------ marshalling
 
-def make_pi(coefs) -> lbhpde_pi:
-    """A Pi_k from polynomial coefficients (coef[p] of phi**p); uses the menu's closed forms."""
+def make_pi(coefs, nu=0.0, coefs_nu=None) -> lbhpde_pi:
+    """A Pi_k from polynomial coefficients (coef[p] of phi**p), plus coefs_nu[p] of phi**(p + nu)
+    when the equation has a real exponent nu; uses the menu's closed forms."""
+    cn = [float(v) for v in (coefs_nu or ())]
+    while cn and cn[-1] == 0.0:
+        cn.pop()
+    if cn:
+        if len(coefs) > PI_NCOEF or len(cn) > PI_NCOEF:
+            raise ValueError("Pi_k degree above 7")
+        p = lbhpde_pi()
+        p.kind, p.nu = PI_POLY_NU, float(nu)
+        for i, v in enumerate(coefs):
+            p.coef[i] = float(v)
+        for i, v in enumerate(cn):
+            p.coef_nu[i] = v
+        return p
     c = [float(v) for v in coefs]
     while c and c[-1] == 0.0:
         c.pop()
@@ -186,24 +204,36 @@ def make_pi(coefs) -> lbhpde_pi:
     return p
 
 
-def _eq_args(alpha, pi):
+def _pis(pi, nu=0.0, pi_nu=None):
+    rows_nu = pi_nu if pi_nu is not None else [()] * len(pi)
+    return [make_pi(r, nu, rn) for r, rn in zip(pi, rows_nu)]
+
+
+def _eq_args(alpha, pi, nu=0.0, pi_nu=None):
     m = len(alpha)
     a = (ctypes.c_double * m)(*[float(v) for v in alpha])
-    P = (lbhpde_pi * m)(*[make_pi(r) for r in pi])
+    P = (lbhpde_pi * m)(*_pis(pi, nu, pi_nu))
     return m, a, P
 
 
-def lbhpde_model(alpha, pi, dx, dt, tau, lattice=0, scheme=1) -> lbhpde_model_info:
-    """Step a0 on the host: the model the library builds for one equation."""
-    m, a, P = _eq_args(alpha, pi)
+def lbhpde_model(alpha, pi, dx, dt, tau, lattice=0, scheme=1, nu=0.0, pi_nu=None) -> lbhpde_model_info:
+    """Step a0 on the host: the model the library builds for one equation (with nu and pi_nu,
+    pi_nu[k-1][p] the coefficient of phi**(p + nu) in Pi_k)."""
+    m, a, P = _eq_args(alpha, pi, nu, pi_nu)
     out = lbhpde_model_info()
     _check(lib().lbhpde_model(m, a, P, dx, dt, tau, lattice, scheme, ctypes.byref(out)), "lbhpde_model")
     return out
 
 
 def model_coeffs(info: lbhpde_model_info):
-    """(feq[b][D+1], coef[b][D+1]) as numpy arrays."""
+    """(feq[b][D+1], coef[b][D+1]) as numpy arrays; for a real-exponent model (nu_rows > 1)
+    (gfeq[b][A+1][Dg+1], gcoef[b][A+1][Dg+1]) with f^eq_j = sum_a (phi**nu)**a sum_i g[j][a][i] phi**i."""
     b, D = info.b, info.D
+    if info.nu_rows > 1:
+        R, Dg = info.nu_rows, info.nu_deg
+        g = np.array([[info.gfeq[j][p] for p in range(R * (Dg + 1))] for j in range(b)]).reshape(b, R, Dg + 1)
+        gc = np.array([[info.gcoef[j][p] for p in range(R * (Dg + 1))] for j in range(b)]).reshape(b, R, Dg + 1)
+        return g, gc
     feq = np.array([[info.feq[j][p] for p in range(D + 1)] for j in range(b)])
     coef = np.array([[info.coef[j][p] for p in range(D + 1)] for j in range(b)])
     return feq, coef
@@ -212,9 +242,10 @@ def model_coeffs(info: lbhpde_model_info):
 def make_instance(eq, N, dx, dt, tau, scheme=1, boundary=PERIODIC) -> lbhpde_instance:
     I = lbhpde_instance()
     I.m = eq.m
+    pis = _pis(eq.pi, getattr(eq, "nu", 0.0), getattr(eq, "pi_nu", None))
     for k in range(eq.m):
         I.alpha[k] = float(eq.alpha[k])
-        I.pi[k] = make_pi(eq.pi[k])
+        I.pi[k] = pis[k]
     I.N, I.dx, I.dt, I.tau, I.lattice, I.scheme = int(N), float(dx), float(dt), float(tau), int(eq.lattice), int(scheme)
     I.boundary = int(boundary)
     return I
@@ -286,7 +317,7 @@ class Solver:
 
     def __init__(self, eq, N, dx, dt, tau, scheme=1, precision=FP64, stream=None, use_torch=True,
                  boundary=PERIODIC):
-        m, a, P = _eq_args(eq.alpha, eq.pi)
+        m, a, P = _eq_args(eq.alpha, eq.pi, getattr(eq, "nu", 0.0), getattr(eq, "pi_nu", None))
         self._alloc = torch_allocator() if use_torch else None
         st = stream if stream is not None else (_current_stream() if use_torch else None)
         h = ctypes.c_void_p()
@@ -457,9 +488,10 @@ class Server:
     def submit(self, eq, N, dx, dt, tau, nsteps, phi0, scheme=1) -> int:
         q = lbhpde_request()
         q.m = eq.m
+        pis = _pis(eq.pi, getattr(eq, "nu", 0.0), getattr(eq, "pi_nu", None))
         for k in range(eq.m):
             q.alpha[k] = float(eq.alpha[k])
-            q.pi[k] = make_pi(eq.pi[k])
+            q.pi[k] = pis[k]
         a = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64))
         assert a.size == N
         q.N, q.dx, q.dt, q.tau, q.lattice, q.scheme, q.nsteps = int(N), float(dx), float(dt), float(tau), \

@@ -322,6 +322,16 @@ def long_grid_config(N=1 << 24, dx=0.1, dt=1e-4, tau=2.02, nsteps=1000):
 
 # Batched KdV-Burgers ensemble: fixed dx, dt, tau for every member (chosen by an oracle
 # stability scan over the sampled coefficient ranges).
+def gkdv_grid_config(N=1 << 24, dx=0.1, dt=1e-4, tau=1.3, nsteps=1000, n=1.5):
+    """Periodic grid of N nodes for u_t + u^n u_x + u_xxx = 0 (real n): a train of solitary
+    waves (c = 1, one per 60 length units) on a background that keeps u > 0."""
+    x = grid(0.0, N, dx)
+    period = 60.0
+    z = (x % period) - 0.5 * period
+    phi0 = 0.05 + gkdv_soliton(z, 0.0, n)
+    return Problem(gkdv(n), N, dx, dt, tau, nsteps, phi0, xl=0.0, meta={"n": n})
+
+
 ENSEMBLE_DX = 0.1
 ENSEMBLE_DT = 1e-4
 ENSEMBLE_TAU = 1.15

@@ -1,0 +1,130 @@
+"""Real-exponent flux functions on the GPU (class (1) of Sec. III C with u^n u_x, real n)
+against the oracle, through the C ABI.  Such models take the streaming kernel's run-time
+degree path (w = phi^nu once per node, then a Horner evaluation in phi and w).
+
+FP64 tolerance 1e-12 normwise on problems whose rounding growth the oracle measures below 2
+(a 1e-13 perturbation of phi0). Where n < 1, phi stays away from 0: phi^n has an infinite
+slope there, and two roundings on either side of zero would differ by far more than an ulp.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0907_1720_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+FP64_TOL = 1e-12
+N, DX = 600, 0.1
+X = W.grid(-30.0, N, DX)
+LEN = N * DX
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_0907_1720_gb300 import build as B
+    B.build()
+    from paper_0907_1720_gb300 import lbhpde
+    lbhpde.lib()
+    return lbhpde
+
+
+def normwise(a, b):
+    assert np.all(np.isfinite(b)), "the oracle diverged"
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def oracle_periodic(p):
+    eq = p.eq
+    M = oracle.Model(eq.alpha, eq.pi, p.dx, p.dt, p.tau, lattice=eq.lattice, scheme=p.scheme, nu=eq.nu,
+                     pi_nu=eq.pi_nu)
+    f = M.init(p.phi0)
+    M.step(f, p.nsteps)
+    return M.phi(f)
+
+
+def problems():
+    return {
+        "gkdv_1.5_soliton": W.Problem(W.gkdv(1.5), N, DX, 1e-4, 1.3, 2000, W.gkdv_soliton(X, 0.0, 1.5, L=LEN),
+                                      xl=-30.0),
+        "gkdv_0.5_offset": W.Problem(W.gkdv(0.5), N, DX, 1e-4, 1.3, 2000, 0.8 + 0.4 * W.sech(X / 2.0) ** 2,
+                                     xl=-30.0),
+        "ks_real_d1q5": W.Problem(W.class1_real(1.0, 0.6, 2.3, (0.05, 0.8, 0.2)), N, DX, 1e-4, 1.3, 2000,
+                                  0.6 + 0.3 * np.cos(2 * np.pi * X / LEN), xl=-30.0),
+        "kawahara_real_d1q7": W.Problem(W.class1_real(1.0, -0.4, 1.7, (0.0, 1.0, 0.0, -1.0)), N, DX, 1e-4, 2.02,
+                                        1000, 0.5 + 0.3 * W.sech(X / 3.0) ** 2, xl=-30.0),
+    }
+
+
+@pytest.mark.parametrize("name", list(problems()))
+@pytest.mark.parametrize("kernel", ["auto", "stream"])
+def test_fp64_matches_oracle(L, name, kernel):
+    p = problems()[name]
+    want = oracle_periodic(p)
+    s = L.Solver.for_problem(p, precision=L.FP64)
+    s.set_kernel(L.KERNEL_STREAM if kernel == "stream" else L.KERNEL_AUTO)
+    got = s.set_phi(p.phi0).step(p.nsteps).read_phi()
+    s.close()
+    assert normwise(got, want) <= FP64_TOL
+
+
+def test_batch_with_real_exponent_and_polynomial_members(L):
+    """A real-exponent member sends its lattice group to the streaming kernel; every member,
+    ordinary ones included, still matches its own oracle run."""
+    ps = problems()
+    kdv = W.kdv_config(N=400, dt=1e-4, tau=1.3, t_end=0.1)
+    probs = [ps["gkdv_1.5_soliton"], kdv, ps["kawahara_real_d1q7"], W.kawahara_config(N=600, t_end=0.05)]
+    n = 500
+    for p in probs:
+        p.nsteps = n
+    b = L.Batch(probs, precision=L.FP64)
+    b.set_phi(np.concatenate([p.phi0 for p in probs])).step(n)
+    got = b.split(b.read_phi())
+    b.close()
+    for p, g in zip(probs, got):
+        want = oracle_periodic(p) if p.eq.pi_nu is not None else oracle.run_problem(p)
+        assert normwise(g, want) <= FP64_TOL, p.eq.name
+
+
+def test_bounded_real_exponent(L):
+    """The gKdV soliton (n = 1.5) on a bounded grid with exact boundary values: the streaming
+    step and the outer-node rebuild with the generalised f^eq."""
+    n, dt, tau, steps = 1.5, 1e-4, 1.3, 1500
+    ex = lambda x, t: W.gkdv_soliton(x, t, n, x0=-5.0)  # noqa: E731
+    x = W.grid(-30.0, 601, DX)
+    p = W.Problem(W.gkdv(n), 601, DX, dt, tau, steps, ex(x, 0.0), xl=-30.0, exact=lambda t: ex(x, t),
+                  boundary="nee", exact_xt=ex, meta={"depth": 2})
+    M = oracle.Model(p.eq.alpha, p.eq.pi, DX, dt, tau, nu=n, pi_nu=p.eq.pi_nu)
+    pb = W.boundary_values(p, 2, 0, steps)
+    f = M.init(p.phi0)
+    want = M.phi(M.step_nee(f, pb, 2))
+    s = L.Solver.for_problem(p, precision=L.FP64)
+    got = s.set_phi(p.phi0).step_nee(steps, pb).read_phi()
+    s.close()
+    assert normwise(got, want) <= FP64_TOL
+
+
+def test_fp32_accuracy(L):
+    """FP32 on the gKdV soliton: error against the exact solution within twice the FP64 path's."""
+    p = problems()["gkdv_1.5_soliton"]
+    p.nsteps = 10000
+    ex = W.gkdv_soliton(X, 1.0, 1.5, L=LEN)
+    errs = {}
+    for prec in (L.FP64, L.FP32_DEV):
+        s = L.Solver.for_problem(p, precision=prec)
+        errs[prec] = oracle.error_E(s.set_phi(p.phi0).step(p.nsteps).read_phi(), ex)
+        s.close()
+    assert errs[L.FP64] < 0.05
+    assert errs[L.FP32_DEV] <= 2.0 * errs[L.FP64]
+
+
+def test_server_rejects_real_exponent_requests(L):
+    srv = L.Server(precision=L.FP32_DEV, device_bytes=1 << 24, max_active=4, steps_per_block=64)
+    p = problems()["gkdv_1.5_soliton"]
+    with pytest.raises(L.LbhpdeError) as e:
+        srv.submit(p.eq, p.N, p.dx, p.dt, p.tau, 10, p.phi0)
+    assert e.value.code == L.ERR_UNSUPPORTED
+    srv.close()

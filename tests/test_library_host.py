@@ -168,3 +168,51 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
     assert lib.lbhpde_step(None, 1) == L.ERR_ARG
     assert lib.lbhpde_destroy(None) == L.ERR_ARG
     assert lib.lbhpde_strerror(L.ERR_DIVERGED).decode().startswith("non-finite")
+
+
+NU_EQUATIONS = [
+    # (name, equation, dt, tau): class (1) with a real exponent n on D1Q5 and D1Q7
+    ("gkdv_1.5", W.gkdv(1.5), 1e-4, 1.3),
+    ("gkdv_0.5", W.gkdv(0.5), 1e-4, 1.3),
+    ("ks_real", W.class1_real(1.0, 0.6, 2.3, (1.0, 0.0, 1.0)), 1e-4, 1.3),
+    ("kawahara_real", W.class1_real(1.0, -0.4, 1.7, (0.0, 1.0, 0.0, -1.0)), 1e-4, 2.02),
+    ("sixth_real", W.class1_real(0.5, 0.3, 0.8, (0.2, 0.5, 0.3, -1.0, 0.2)), 1e-3, 2.2),
+]
+
+
+@pytest.mark.parametrize("name,eq,dt,tau", NU_EQUATIONS, ids=[e[0] for e in NU_EQUATIONS])
+def test_real_exponent_model_matches_oracle(lib, name, eq, dt, tau):
+    """The library's generalised f^eq tables (sum_a (phi^nu)^a sum_i g[j][a][i] phi^i) against
+    the oracle's f^eq at positive phi, and zero real-exponent terms at phi <= 0."""
+    info = L.lbhpde_model(eq.alpha, eq.pi, 0.1, dt, tau, lattice=eq.lattice, nu=eq.nu, pi_nu=eq.pi_nu)
+    M = oracle.Model(eq.alpha, eq.pi, 0.1, dt, tau, lattice=eq.lattice, nu=eq.nu, pi_nu=eq.pi_nu)
+    assert info.b == M.b and info.nu_rows > 1 and info.nu == eq.nu
+    assert bool(info.inexact) == M.inexact
+    assert np.allclose(list(info.beta), M.beta, rtol=1e-13, atol=0)
+    assert np.allclose(list(info.A), M.A, rtol=1e-12, atol=0)
+    g, gc = L.model_coeffs(info)
+    assert np.allclose(gc, g / tau, rtol=1e-15, atol=0)
+    rng = np.random.default_rng(5)
+    for phi in np.concatenate([rng.uniform(0.01, 2.0, 16), [1.0, -0.3, 0.0]]):
+        w = phi ** eq.nu if phi > 0 else 0.0
+        got = np.array([sum(w ** a * np.polynomial.polynomial.polyval(phi, g[j, a]) for a in range(g.shape[1]))
+                        for j in range(info.b)])
+        want = M.feq(phi)
+        assert np.abs(got - want).max() <= 1e-12 * (np.abs(want).max() + 1e-300), phi
+
+
+def test_real_exponent_argument_errors(lib):
+    eq = W.gkdv(1.5)
+    bad_nu = [L.make_pi(eq.pi[0], -1.0, eq.pi_nu[0])] + [L.make_pi(r) for r in eq.pi[1:]]
+    a = (ctypes.c_double * 3)(*eq.alpha)
+    info = L.lbhpde_model_info()
+    P = (L.lbhpde_pi * 3)(*bad_nu)
+    assert lib.lbhpde_model(3, a, P, 0.1, 1e-4, 1.3, 0, 1, ctypes.byref(info)) == L.ERR_ARG
+    p0 = L.make_pi((0.0, 0.0, 0.5), 1.5, (0.0, 1.0))
+    p0.coef_nu[0] = 1.0  # a phi^nu term with no derivative of the form
+    P = (L.lbhpde_pi * 3)(p0, L.make_pi(eq.pi[1]), L.make_pi(eq.pi[2]))
+    assert lib.lbhpde_model(3, a, P, 0.1, 1e-4, 1.3, 0, 1, ctypes.byref(info)) == L.ERR_ARG
+    # two different real exponents in one equation
+    P = (L.lbhpde_pi * 3)(L.make_pi((0, 0, 0.5), 1.5, (0, 1.0)), L.make_pi((0, 1.0)),
+                          L.make_pi((0, 0.0), 2.5, (0, 1.0)))
+    assert lib.lbhpde_model(3, a, P, 0.1, 1e-4, 1.3, 0, 1, ctypes.byref(info)) == L.ERR_ARG
