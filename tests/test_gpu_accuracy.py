@@ -5,6 +5,8 @@
 * The FP32 deviation-storage path stays within twice the FP64 path's error against the
   exact solution (KdV soliton, Kawahara Table V case) or the spectral ETDRK4 reference (KS).
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -91,3 +93,24 @@ def test_kawahara_table_v_on_gpu(L, dt, tau, E_paper):
     e32 = err_E(run(L, p, L.FP32_DEV), ex)
     assert e64 == pytest.approx(E_paper, rel=3e-4)
     assert e32 <= 2.0 * e64
+
+
+def test_observed_order_on_the_gpu(L):
+    """The joint refinement of the oracle test (dt = 1e-2 dx^3, tau = 1.1, KdV soliton, t = 0.1)
+    one level further on the GPU (FP64, resident kernel): E at dx = 0.1 and 0.05 equals the
+    oracle's, and the order between dx = 0.05 and 0.025 (640 000 steps) is above 1.9."""
+    from test_oracle_pins import kdv_refinement_error
+    Es = {}
+    for dx in (0.1, 0.05, 0.025):
+        N = int(round(40.0 / dx))
+        dt = 1e-2 * dx ** 3
+        n = int(round(0.1 / dt))
+        x = W.grid(-20.0, N, dx)
+        p = W.Problem(W.kdv(), N, dx, dt, 1.1, n, W.kdv_soliton(x, 0.0, L=40.0), xl=-20.0)
+        s = L.Solver.for_problem(p, precision=L.FP64)
+        phi = s.set_phi(p.phi0).step(n).read_phi()
+        s.close()
+        Es[dx] = oracle.error_E(phi, W.kdv_soliton(x, n * dt, L=40.0))
+    for dx in (0.1, 0.05):
+        assert Es[dx] == pytest.approx(kdv_refinement_error(dx), rel=1e-9)
+    assert math.log2(Es[0.05] / Es[0.025]) > 1.9, Es
