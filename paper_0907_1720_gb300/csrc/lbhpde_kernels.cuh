@@ -106,6 +106,27 @@ __device__ __forceinline__ T gen_eval(const T *c, int A, int Dg, T phi, T w) {
     return acc;
 }
 
+// gen_eval for the four nodes of a k_stream group at once: each coefficient is loaded once and
+// feeds four independent accumulators.
+template <typename T>
+__device__ __forceinline__ void gen_eval4(const T *c, int A, int Dg, const T (&phi)[4], const T (&w)[4],
+                                          T (&out)[4]) {
+    for (int a = A; a >= 0; --a) {
+        const T *r = c + a * (Dg + 1);
+        T h[4];
+        const T cD = r[Dg];
+#pragma unroll
+        for (int n = 0; n < 4; ++n) h[n] = cD;
+        for (int p = Dg - 1; p >= 0; --p) {
+            const T cp = r[p];
+#pragma unroll
+            for (int n = 0; n < 4; ++n) h[n] = fma_t(h[n], phi[n], cp);
+        }
+#pragma unroll
+        for (int n = 0; n < 4; ++n) out[n] = a == A ? h[n] : fma_t(out[n], w[n], h[n]);
+    }
+}
+
 // ---------------------------------------------------------------------------- a1: init
 // s_j(x) = f^eq_j(phi0(x)) (post-collision state of an equilibrium, collision leaves it
 // unchanged), phi(x) = phi0(x).  f^eq is evaluated in double and rounded once to T.
@@ -265,7 +286,34 @@ __global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__re
         }
     }
     if (!active) return;
-    if (x >= W && x + 4 + W <= N) {
+    if (DC == 0 && A > 0 && x >= W && x + 4 + W <= N) {
+        // real-exponent model: pull and phi' for the whole group first, then every P_j for the
+        // four nodes together
+        T o[B][4], w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            T d = T(0);
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const int e = vel(j);
+                const int q = i - e;
+                const T sj = q < 0 ? ed[j][e + q] : (q >= 4 ? ed[j][q - 4] : a[j][q]);
+                d += sj - a[j][i];
+                o[j][i] = sj;
+            }
+            o[0][i] = a[0][i] + d;
+            w[i] = wpow(o[0][i]);
+        }
+#pragma unroll
+        for (int j = 1; j < B; ++j) {
+            T acc[4];
+            gen_eval4<T>(sc + (j - 1) * NC, A, s.Dg, o[0], w, acc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) o[j][i] = fma_t(omw, o[j][i], acc[i]);
+        }
+#pragma unroll
+        for (int j = 0; j < B; ++j) store4(dst + j * ld + x, o[j]);
+    } else if (x >= W && x + 4 + W <= N) {
         T o[B][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
