@@ -556,8 +556,12 @@ int launch_stream_t(lbhpde_batch_s *bt, Group &g, const int2 *blocks, int nb, co
             for (int p = 0; p <= DC; ++p) pc.c[(j - 1) * (DC + 1) + p] = p <= M.D ? (T)M.coef[j][p] : T(0);
         pc.omw = (T)(1.0 - M.omega);
     }
-    lbk::k_stream<T, B, DC, kStreamThreads, PARAMC><<<nb, kStreamThreads, 0, bt->stream>>>(
-        in, out, bt->segs, blocks, (const T *)bt->coefT, pc);
+    if constexpr (DC == 0)
+        lbk::k_stream_rt<T, B, kStreamThreads><<<nb, kStreamThreads, 0, bt->stream>>>(in, out, bt->segs, blocks,
+                                                                                    (const T *)bt->coefT);
+    else
+        lbk::k_stream<T, B, DC, kStreamThreads, PARAMC><<<nb, kStreamThreads, 0, bt->stream>>>(
+            in, out, bt->segs, blocks, (const T *)bt->coefT, pc);
     CK(cudaGetLastError());
     return LBHPDE_OK;
 }

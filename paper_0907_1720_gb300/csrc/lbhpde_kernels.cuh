@@ -84,11 +84,12 @@ __device__ __forceinline__ float fma_t<float>(float a, float b, float c) { retur
 template <>
 __device__ __forceinline__ double fma_t<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 
-// phi^nu for the real-exponent terms, zero where phi <= 0 (the continuous extension).
+// phi^nu for the real-exponent terms, zero where phi <= 0 (the continuous extension).  FP32 takes
+// the fast intrinsic (relative error ~1e-6, far below the FP32 path's discretisation error).
 template <typename T>
 __device__ __forceinline__ T nu_pow(T phi, double nu) {
     if constexpr (sizeof(T) == 4)
-        return phi > 0.0f ? powf(phi, (float)nu) : 0.0f;
+        return phi > 0.0f ? __powf(phi, (float)nu) : 0.0f;
     else
         return phi > 0.0 ? pow(phi, nu) : 0.0;
 }
@@ -107,23 +108,65 @@ __device__ __forceinline__ T gen_eval(const T *c, int A, int Dg, T phi, T w) {
 }
 
 // gen_eval for the four nodes of a k_stream group at once: each coefficient is loaded once and
-// feeds four independent accumulators.
-template <typename T>
+// feeds four independent accumulators.  DG: the row degree at compile time (the rows unroll);
+// DG < 0: run time.
+template <typename T, int DG>
 __device__ __forceinline__ void gen_eval4(const T *c, int A, int Dg, const T (&phi)[4], const T (&w)[4],
                                           T (&out)[4]) {
+    const int dg = DG >= 0 ? DG : Dg;
     for (int a = A; a >= 0; --a) {
-        const T *r = c + a * (Dg + 1);
+        const T *r = c + a * (dg + 1);
         T h[4];
-        const T cD = r[Dg];
+        if constexpr (DG >= 0) {
+            T cr[DG + 1];
 #pragma unroll
-        for (int n = 0; n < 4; ++n) h[n] = cD;
-        for (int p = Dg - 1; p >= 0; --p) {
-            const T cp = r[p];
+            for (int p = 0; p <= DG; ++p) cr[p] = r[p];
 #pragma unroll
-            for (int n = 0; n < 4; ++n) h[n] = fma_t(h[n], phi[n], cp);
+            for (int n = 0; n < 4; ++n) h[n] = cr[DG];
+#pragma unroll
+            for (int p = DG - 1; p >= 0; --p)
+#pragma unroll
+                for (int n = 0; n < 4; ++n) h[n] = fma_t(h[n], phi[n], cr[p]);
+        } else {
+            const T cD = r[dg];
+#pragma unroll
+            for (int n = 0; n < 4; ++n) h[n] = cD;
+            for (int p = dg - 1; p >= 0; --p) {
+                const T cp = r[p];
+#pragma unroll
+                for (int n = 0; n < 4; ++n) h[n] = fma_t(h[n], phi[n], cp);
+            }
         }
 #pragma unroll
         for (int n = 0; n < 4; ++n) out[n] = a == A ? h[n] : fma_t(out[n], w[n], h[n]);
+    }
+}
+
+// gen_eval4 with the row degree dispatched to a compile-time variant (0..7 in FP32, 0..3 in FP64,
+// where more would spill), else run time.
+template <typename T>
+__device__ __forceinline__ void gen_eval4_any(const T *c, int A, int Dg, const T (&phi)[4], const T (&w)[4],
+                                              T (&out)[4]) {
+    if constexpr (sizeof(T) == 8) {
+        switch (Dg) {
+        case 0: gen_eval4<T, 0>(c, A, Dg, phi, w, out); break;
+        case 1: gen_eval4<T, 1>(c, A, Dg, phi, w, out); break;
+        case 2: gen_eval4<T, 2>(c, A, Dg, phi, w, out); break;
+        case 3: gen_eval4<T, 3>(c, A, Dg, phi, w, out); break;
+        default: gen_eval4<T, -1>(c, A, Dg, phi, w, out); break;
+        }
+    } else {
+        switch (Dg) {
+        case 0: gen_eval4<T, 0>(c, A, Dg, phi, w, out); break;
+        case 1: gen_eval4<T, 1>(c, A, Dg, phi, w, out); break;
+        case 2: gen_eval4<T, 2>(c, A, Dg, phi, w, out); break;
+        case 3: gen_eval4<T, 3>(c, A, Dg, phi, w, out); break;
+        case 4: gen_eval4<T, 4>(c, A, Dg, phi, w, out); break;
+        case 5: gen_eval4<T, 5>(c, A, Dg, phi, w, out); break;
+        case 6: gen_eval4<T, 6>(c, A, Dg, phi, w, out); break;
+        case 7: gen_eval4<T, 7>(c, A, Dg, phi, w, out); break;
+        default: gen_eval4<T, -1>(c, A, Dg, phi, w, out); break;
+        }
     }
 }
 
@@ -200,10 +243,10 @@ struct StreamCoef {
 };
 
 template <typename T, int B, int DC, int NT, bool PARAMC>
-__global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__restrict__ out,
-                                               const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
-                                               const T *__restrict__ coefs,
-                                               const __grid_constant__ StreamCoef<T, B, (DC > 0 ? DC : 1)> pc) {
+__device__ __forceinline__ void stream_body(const T *__restrict__ in, T *__restrict__ out,
+                                            const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
+                                            const T *__restrict__ coefs,
+                                            const StreamCoef<T, B, (DC > 0 ? DC : 1)> &pc) {
     static_assert(!PARAMC || DC > 0, "parameter coefficients need a compile-time degree");
     constexpr int W = wmax(B);
     constexpr int NC = DC > 0 ? DC + 1 : kMaxRow;
@@ -307,7 +350,7 @@ __global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__re
 #pragma unroll
         for (int j = 1; j < B; ++j) {
             T acc[4];
-            gen_eval4<T>(sc + (j - 1) * NC, A, s.Dg, o[0], w, acc);
+            gen_eval4_any<T>(sc + (j - 1) * NC, A, s.Dg, o[0], w, acc);
 #pragma unroll
             for (int i = 0; i < 4; ++i) o[j][i] = fma_t(omw, o[j][i], acc[i]);
         }
@@ -357,6 +400,24 @@ __global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__re
             for (int j = 1; j < B; ++j) dst[j * ld + xi] = fma_t(omw, f[j], poly(j, ph, w));
         }
     }
+}
+
+template <typename T, int B, int DC, int NT, bool PARAMC>
+__global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__restrict__ out,
+                                               const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
+                                               const T *__restrict__ coefs,
+                                               const __grid_constant__ StreamCoef<T, B, (DC > 0 ? DC : 1)> pc) {
+    stream_body<T, B, DC, NT, PARAMC>(in, out, segs, blocks, coefs, pc);
+}
+
+// The run-time-degree variant (high degrees and real exponents): its general evaluation needs
+// more registers than the compile-time variants, so it may take up to 255 (no spills).
+template <typename T, int B, int NT>
+__global__ void __launch_bounds__(NT, 1) k_stream_rt(const T *__restrict__ in, T *__restrict__ out,
+                                                     const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
+                                                     const T *__restrict__ coefs) {
+    const StreamCoef<T, B, 1> unused{};
+    stream_body<T, B, 0, NT, false>(in, out, segs, blocks, coefs, unused);
 }
 
 // ------------------------------------------------------ a2-a6: on-chip, many steps
