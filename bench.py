@@ -311,7 +311,7 @@ def run_ours(args, rank, world):
             achieved = by * upd_step / (kern_ms / 1e3) / 1e9
             roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                    "kernel": f"k_stream<{'float' if esz == 4 else 'double'},5,0,256,0> (run-time degree, phi^nu)",
+                    "kernel": f"k_stream_rt<{'float' if esz == 4 else 'double'},5,256> (run-time degree, phi^nu)",
                     "bytes_per_node_update": by, "peak_source": peak_src}
         elif args.workload == "ensemble" or args.kernel != "stream":
             fl = flops_per_node_update(b, D)

@@ -411,9 +411,10 @@ __global__ void __launch_bounds__(NT) k_stream(const T *__restrict__ in, T *__re
 }
 
 // The run-time-degree variant (high degrees and real exponents): its general evaluation needs
-// more registers than the compile-time variants, so it may take up to 255 (no spills).
+// more registers than the compile-time variants, so it may take up to 255 (no spills), except
+// FP32 D1Q5, which fits 64 and so keeps four CTAs per SM for more loads in flight.
 template <typename T, int B, int NT>
-__global__ void __launch_bounds__(NT, 1) k_stream_rt(const T *__restrict__ in, T *__restrict__ out,
+__global__ void __launch_bounds__(NT, (sizeof(T) == 4 && B == 5) ? 4 : 1) k_stream_rt(const T *__restrict__ in, T *__restrict__ out,
                                                      const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
                                                      const T *__restrict__ coefs) {
     const StreamCoef<T, B, 1> unused{};
