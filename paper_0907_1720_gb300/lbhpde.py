@@ -277,6 +277,42 @@ def autotune(precision, lattice, degree):
     return K.value, T.value, r.value
 
 
+def tau_sweep(problem, taus, precision=FP64, nsteps=None, phib=None):
+    """The global relative error E (Sec. IV) of ``problem`` for every tau in ``taus``, all solved
+    in one batch: one member per tau, the same grid, initial profile and boundary data.  Sec. IV
+    picks tau_opt per lattice speed as the tau with the smallest error; this scans for it.
+    problem: a workloads.Problem with ``exact`` (phi* at t_end) and, for a bounded grid,
+    ``boundary == "nee"`` and ``exact_xt``; phib: [nsteps, 2W] boundary values (default: phi*
+    at the outer nodes).  Returns (taus, E) as numpy arrays."""
+    import copy
+
+    import torch
+
+    from . import workloads as W
+
+    n = problem.nsteps if nsteps is None else int(nsteps)
+    members = []
+    for t in taus:
+        q = copy.copy(problem)
+        q.tau, q.nsteps = float(t), n
+        members.append(q)
+    b = Batch(members, precision=precision)
+    try:
+        b.set_phi(np.tile(np.asarray(problem.phi0, dtype=np.float64), len(members)))
+        if problem.boundary == "nee":
+            if phib is None:
+                Wd = 3 if (problem.eq.lattice == 7 or problem.eq.m > 4) else 2
+                phib = W.boundary_values(problem, Wd, 0, n)
+            b.step_nee(n, phib, 0)
+        else:
+            b.step(n)
+        ex = np.tile(np.asarray(problem.exact(n * problem.dt), dtype=np.float64), len(members))
+        d = b.diagnostics(torch.tensor(ex, device="cuda", dtype=torch.float64))
+        return np.asarray(taus, dtype=np.float64), np.array(d["err_E"])
+    finally:
+        b.close()
+
+
 # ------------------------------------------------------------ torch plumbing
 
 _torch_alloc_keep = []

@@ -225,3 +225,12 @@ def test_bounded_instance_needs_boundary_values(L):
     with pytest.raises(L.LbhpdeError) as e:  # stride shorter than a member's block
         b.step_nee(10, np.zeros(200), 30)
     assert e.value.code == L.ERR_ARG
+
+
+def test_tau_sweep_helper(L):
+    """lbhpde.tau_sweep: E for every tau from one batch equals the oracle's E for that tau."""
+    p = bounded("4.1", 1e-3, 2.0, 300, 1 | NOA)
+    taus, E = L.tau_sweep(p, [1.989, 2.1, 2.3], precision=L.FP64)
+    for t, e in zip(taus, E):
+        q = bounded("4.1", 1e-3, float(t), 300, 1 | NOA)
+        assert e == pytest.approx(oracle.error_E(oracle_run(q), q.exact(q.t_end)), rel=1e-9)
