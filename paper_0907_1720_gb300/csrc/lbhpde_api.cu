@@ -138,7 +138,10 @@ struct lbhpde_batch_s {
         *p = q;
         return LBHPDE_OK;
     }
+    // Release one allocation made by dev_alloc (waits for the stream first: kernels in flight may
+    // still read it).  nullptr is ignored.
     void dev_free(void *p) {
+        if (!p) return;
         for (size_t i = 0; i < allocations.size(); ++i)
             if (allocations[i].first == p) {
                 cudaStreamSynchronize(stream);
@@ -607,6 +610,11 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
         const lbh::Member mb{bt->segs_h[i], bt->segs_h[i].off, 1 << 30};
         (bt->N[i] <= cap && !force_halo ? ring : halo).push_back(mb);
     }
+    // the previous plan's device tables (a re-plan after lbhpde_batch_set_kernel)
+    bt->dev_free(g.ring.insts);
+    bt->dev_free(g.ring.cta_first);
+    bt->dev_free(g.halo.insts);
+    bt->dev_free(g.halo.cta_first);
     g.ring = Group::Plan{};
     g.halo = Group::Plan{};
     if (!ring.empty()) RC(lbh::pack_ring(g.b, bt->esz, K, g.dc, ring, g.ring.host));
@@ -781,6 +789,12 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
     g.bnd_threads = (maxthr + 31) / 32 * 32;
     g.bnd_dc = lbh::onchip_dc(g.b, maxD);
     g.bnd_D = g.bnd_dc > 0 ? g.bnd_dc : maxD;
+    bt->dev_free(g.bnd);
+    bt->dev_free(g.smembers);
+    bt->dev_free(g.sblocks);
+    g.bnd = nullptr;
+    g.smembers = nullptr;
+    g.sblocks = nullptr;
     if (!g.bnd_h.empty()) RC(bt->upload(&g.bnd, g.bnd_h));
     if (!g.smembers_h.empty()) {
         RC(bt->upload(&g.smembers, g.smembers_h));
@@ -790,6 +804,14 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
 }
 
 int choose_kernels(lbhpde_batch_s *bt) {
+    // captured streaming graphs hold the launches of the groups that streamed when they were
+    // captured: a new plan may change that set, so they are rebuilt on the next long run
+    if (bt->graph[0] || bt->graph[1]) {
+        cudaStreamSynchronize(bt->stream);
+        for (auto &gx : bt->graph)
+            if (gx) cudaGraphExecDestroy(gx);
+        bt->graph[0] = bt->graph[1] = nullptr;
+    }
     for (auto &g : bt->groups) {
         if (g.members.empty()) continue;
         g.onchip_ok = false;

@@ -128,3 +128,23 @@ def test_server_rejects_real_exponent_requests(L):
         srv.submit(p.eq, p.N, p.dx, p.dt, p.tau, 10, p.phi0)
     assert e.value.code == L.ERR_UNSUPPORTED
     srv.close()
+
+
+def test_replan_discards_captured_graphs(L):
+    """Re-planning between long streaming runs (lbhpde_batch_set_kernel, which rebuilds the
+    captured graphs) keeps every member of a mixed batch on its oracle trajectory: a
+    real-exponent member and an ordinary D1Q7 member, 200 steps, a re-plan, 200 more."""
+    ps = problems()
+    gk = ps["gkdv_1.5_soliton"]
+    kaw = W.kawahara_config(N=600, dt=1e-4, tau=2.02, t_end=0.0)
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        b = L.Batch([gk, kaw], precision=L.FP64)
+        b.set_phi(np.concatenate([gk.phi0, kaw.phi0])).step(200)
+        b.set_kernel(L.KERNEL_STREAM)
+        b.step(200)
+        got = b.split(b.read_phi())
+        b.close()
+    gk.nsteps = kaw.nsteps = 400
+    assert normwise(got[0], oracle_periodic(gk)) <= FP64_TOL
+    assert normwise(got[1], oracle.run_problem(kaw)) <= FP64_TOL
