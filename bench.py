@@ -406,6 +406,8 @@ def run_serving(args):
                     "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                     "launches": st["launches"], "clocks": clk.summary()})
     head = out[0]
+    fp64 = None if args.quick else serving_fp64_plain(L, W.serving_requests(
+        min(args.requests, max(64, int(args.window * args.rate))), rate=args.rate, seed=W.SEED + int(args.rate)))
     line = {"metric": METRIC, "value": head["achieved_node_updates_s"], "unit": "node-updates/s", "n_gpus": 1,
             "steps": 1, "warmup": 0, "ms_per_step": head["makespan_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
@@ -416,7 +418,38 @@ def run_serving(args):
                        "window_requests": head["requests"], "steps_per_block": args.block},
             "p50_latency_s": head["p50_latency_s"], "p99_latency_s": head["p99_latency_s"],
             "clocks": head["clocks"], "sweep": out}
+    if fp64 is not None:
+        line["fp64_plain"] = fp64
     return line
+
+
+def serving_fp64_plain(L, reqs, budget_updates=2e9):
+    """The plain per-instance FP64 path on the same request stream: requests taken in arrival
+    order until about budget_updates node-updates, each solved alone (its own handle, FP64,
+    streaming kernel) back to back on one stream; CUDA-event service time per request."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    times, work = [], 0
+    with torch.cuda.stream(stream):
+        for _, p in reqs:
+            if work > budget_updates:
+                break
+            s = L.Solver.for_problem(p, precision=L.FP64).set_kernel(L.KERNEL_STREAM)
+            phi0 = torch.tensor(p.phi0, device="cuda", dtype=torch.float64)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.set_phi(phi0)
+            a.record(stream)
+            s.step(p.nsteps)
+            b.record(stream)
+            b.synchronize()
+            times.append(a.elapsed_time(b) / 1e3)
+            work += p.N * p.nsteps
+            s.close()
+    t = np.array(times)
+    return {"value": work / t.sum(), "unit": "node-updates/s", "requests": len(t),
+            "service_s_p50": float(np.percentile(t, 50)), "service_s_p99": float(np.percentile(t, 99)),
+            "path": "one handle per request, FP64, k_stream one launch per step (graph-replayed), back to back"}
 
 
 def solver_kernel_launches(args, nsteps, tblk):
