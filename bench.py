@@ -119,6 +119,17 @@ def ensemble_problems(rank=0, members=4096):
     return W.kdv_burgers_ensemble(count=members, seed=W.SEED + rank)
 
 
+def alu_peak(esz, clocks, peaks):
+    """ALU roof at the median SM clock under load: FP32 lanes, or GB300's FP64 FMA rate."""
+    sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
+    if esz == 4:
+        return (SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12,
+                f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock under load")
+    return (SMS * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12,
+            f"derived: {SMS} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 x median SM clock under load "
+            f"(1.26 TFLOP/s at 2070 MHz, the nominal 1.25)")
+
+
 def bounded_problems(members):
     """Example 4.1 (Table I, c = 100) with tau spread evenly over BOUNDED_TAU."""
     taus = np.linspace(BOUNDED_TAU[0], BOUNDED_TAU[1], members)
@@ -292,14 +303,7 @@ def run_ours(args, rank, world):
         clocks = clk.summary()
         if bounded:
             fl = flops_per_node_update(b, D)
-            sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-            if esz == 4:
-                peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-                src = f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock under load"
-            else:
-                peak_tf = SMS * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12
-                src = (f"derived: {SMS} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 x median SM clock under "
-                       f"load (1.26 TFLOP/s at 2070 MHz, the nominal 1.25)")
+            peak_tf, src = alu_peak(esz, clocks, peaks)
             achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                     "frac": achieved / peak_tf, "traffic": None,
@@ -315,15 +319,13 @@ def run_ours(args, rank, world):
                     "bytes_per_node_update": by, "peak_source": peak_src}
         elif args.workload == "ensemble" or args.kernel != "stream":
             fl = flops_per_node_update(b, D)
-            sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
-            peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+            peak_tf, src = alu_peak(esz, clocks, peaks)
             achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                     "frac": achieved / peak_tf, "traffic": None,
                     "kernel": f"k_onchip<{'float' if esz == 4 else 'double'},{b},K> "
                               f"({'resident instances + halo windows' if args.workload == 'ensemble' else 'halo windows'})",
-                    "flops_per_node_update": fl,
-                    "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock under load"}
+                    "flops_per_node_update": fl, "peak_source": src}
         else:
             by = bytes_per_node_update(b, esz)
             achieved = by * upd_step / (kern_ms / 1e3) / 1e9
@@ -333,6 +335,16 @@ def run_ours(args, rank, world):
                     "traffic_note": "per launch; ncu capture on 2^23 nodes scaled by N",
                     "kernel": "k_stream<float,7,7,256,1>" if esz == 4 else "k_stream<double,7,7,256,1>",
                     "bytes_per_node_update": by, "peak_source": peak_src}
+            if esz == 8:
+                # FP64 on GB300: the FP64 units bind long before HBM does
+                fl = flops_per_node_update(b, D)
+                peak_tf, src = alu_peak(esz, clocks, peaks)
+                alu = fl * upd_step / (kern_ms / 1e3) / 1e12
+                roof = {"bound": "alu", "achieved": alu, "peak": peak_tf, "unit": "TFLOP/s",
+                        "frac": alu / peak_tf, "traffic": None, "kernel": roof["kernel"],
+                        "flops_per_node_update": fl, "peak_source": src,
+                        "hbm": {"achieved_gbs": achieved, "frac": achieved / peaks["hbm_gbs"],
+                                "bytes_per_node_update": by}}
         tblk = tuned["steps_per_window"] if tuned else (64 if args.workload == "ensemble" else 32)
         launches_per_step = 1 + 2 + solver_kernel_launches(args, nsteps, tblk)  # init, diagnostics x2, steps
         line = {
