@@ -435,9 +435,9 @@ def run_serving(args):
     return line
 
 
-def serving_fp64_plain(L, reqs, budget_updates=2e9):
+def serving_fp64_plain(L, reqs, max_updates=2e9):
     """The plain per-instance FP64 path on the same request stream: requests taken in arrival
-    order until about budget_updates node-updates, each solved alone (its own handle, FP64,
+    order until about max_updates node-updates, each solved alone (its own handle, FP64,
     streaming kernel) back to back on one stream; CUDA-event service time per request."""
     import torch
 
@@ -445,7 +445,7 @@ def serving_fp64_plain(L, reqs, budget_updates=2e9):
     times, work = [], 0
     with torch.cuda.stream(stream):
         for _, p in reqs:
-            if work > budget_updates:
+            if work > max_updates:
                 break
             s = L.Solver.for_problem(p, precision=L.FP64).set_kernel(L.KERNEL_STREAM)
             phi0 = torch.tensor(p.phi0, device="cuda", dtype=torch.float64)
@@ -563,7 +563,7 @@ def accuracy_report(L, args, probs, solver, prec, torch):
 
 # ------------------------------------------------------------ oracle on the CPU
 
-def cpu_oracle_rate(args, budget_s=15.0):
+def cpu_oracle_rate(args, sample_s=15.0):
     """Oracle node-updates/s on the host cores: one member per thread (ctypes releases the
     GIL), on a bounded sample of the same workload."""
     import oracle
@@ -573,11 +573,11 @@ def cpu_oracle_rate(args, budget_s=15.0):
     if args.workload == "ensemble":
         probs = ensemble_problems(0)[: 2 * cores]
         per_member = 20
-        # calibrate the step count so the sample takes about budget_s
+        # calibrate the step count so the sample takes about sample_s
         t0 = time.perf_counter()
         oracle.run_problem(probs[0], nsteps=per_member)
         dt1 = time.perf_counter() - t0
-        steps = max(per_member, int(budget_s * cores / (len(probs) * dt1 / per_member) / 1.0))
+        steps = max(per_member, int(sample_s * cores / (len(probs) * dt1 / per_member) / 1.0))
         steps = min(steps, W.ENSEMBLE_STEPS)
         t0 = time.perf_counter()
         with ThreadPoolExecutor(cores) as ex:
@@ -599,8 +599,8 @@ def cpu_oracle_rate(args, budget_s=15.0):
         run(p0, 50)
         dt1 = (time.perf_counter() - t0) / 50
         steps = BOUNDED_STEPS
-        # members of the full sweep (every tau of the benchmark), as many as fill the budget
-        nmem = int(min(args.sweep_members, max(2 * cores, budget_s * cores / (steps * dt1))))
+        # members of the full sweep (every tau of the benchmark), as many as fill the sample time
+        nmem = int(min(args.sweep_members, max(2 * cores, sample_s * cores / (steps * dt1))))
         probs = bounded_problems(args.sweep_members)[:: max(1, args.sweep_members // nmem)][:nmem]
         t0 = time.perf_counter()
         with ThreadPoolExecutor(cores) as ex:
@@ -615,7 +615,7 @@ def cpu_oracle_rate(args, budget_s=15.0):
         t0 = time.perf_counter()
         M.step(f, 1)
         dt1 = time.perf_counter() - t0
-        steps = int(max(1, min(1000, budget_s / dt1)))
+        steps = int(max(1, min(1000, sample_s / dt1)))
         t0 = time.perf_counter()
         M.step(f, steps)
         el = time.perf_counter() - t0
@@ -640,9 +640,9 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     vals = []
     for _ in range(args.warmup):
-        cpu_oracle_rate(args, budget_s=2.0)
+        cpu_oracle_rate(args, sample_s=2.0)
     for _ in range(args.steps):
-        vals.append(cpu_oracle_rate(args, budget_s=8.0))
+        vals.append(cpu_oracle_rate(args, sample_s=8.0))
     v = float(np.median([r["value"] for r in vals]))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "node-updates/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
