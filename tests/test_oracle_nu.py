@@ -139,6 +139,23 @@ def test_gkdv_soliton_accuracy():
     assert E < 0.05
 
 
+def test_gkdv_solitary_wave_solves_its_equation():
+    """The solitary wave used as the yardstick of the real-exponent path solves
+    u_t + b u^n u_x + u_xxx = 0 (symbolic substitution at rational n, b, c)."""
+    sp = pytest.importorskip("sympy")
+    x, t = sp.symbols("x t", real=True)
+    for n, b, c in ((sp.Rational(3, 2), 1, 1), (sp.Rational(7, 10), 2, sp.Rational(1, 2))):
+        u = (c * (n + 1) * (n + 2) / (2 * b) * sp.sech(n * sp.sqrt(c) * (x - c * t) / 2) ** 2) ** (1 / n)
+        r = sp.diff(u, t) + b * u ** n * sp.diff(u, x) + sp.diff(u, x, 3)
+        for xv, tv in ((sp.Rational(3, 10), sp.Rational(1, 5)), (-1, 2)):
+            assert abs(float(sp.N(r.subs({x: xv, t: tv}), 30))) < 1e-20
+        # and the workloads' numeric version agrees with the closed form
+        xs = np.linspace(-5.0, 5.0, 7)
+        got = W.gkdv_soliton(xs, 0.3, float(n), b=float(b), c=float(c))
+        want = [float(u.subs({x: xv, t: sp.Rational(3, 10)})) for xv in xs]
+        assert np.allclose(got, want, rtol=1e-13)
+
+
 def test_real_exponent_argument_checks():
     eq = W.class1_real(1.0, 1.0, 1.5, (0.0, 1.0))
     with pytest.raises(oracle.OracleError):  # nu must be positive
