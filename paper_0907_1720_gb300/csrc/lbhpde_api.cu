@@ -110,6 +110,7 @@ struct lbhpde_batch_s {
     DiagPart *part = nullptr;      // scratch: one record per block of the combined map
     DiagPart *diag_out = nullptr;  // one record per member
     double *phi_buf = nullptr;     // device staging of phi in double (host transfers)
+    int *nonfinite = nullptr;      // readout flag: a non-finite phi was copied
     Group groups[2];               // periodic members: b = 5, b = 7
     Group bgroups[2];              // bounded members: b = 5, b = 7
     int nbounded = 0;
@@ -725,6 +726,7 @@ int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
     RC(bt->dev_alloc((void **)&bt->part, sizeof(DiagPart) * all.size()));
     RC(bt->dev_alloc((void **)&bt->diag_out, sizeof(DiagPart) * count));
     RC(bt->dev_alloc((void **)&bt->phi_buf, sizeof(double) * bt->total));
+    RC(bt->dev_alloc((void **)&bt->nonfinite, sizeof(int)));
 
     for (int gi = 0; gi < 4; ++gi) {
         const bool bounded = gi >= 2;
@@ -1060,18 +1062,21 @@ int batch_read_phi(lbhpde_batch_s *bt, double *out, int on_device) {
     if (!bt->initialised) return LBHPDE_ERR_ARG;
     double *dst = on_device ? out : bt->phi_buf;
     const int nb = (int)bt->all_blocks_h.size();
+    int *flag = on_device ? nullptr : bt->nonfinite;
+    if (flag) CK(cudaMemsetAsync(flag, 0, sizeof(int), bt->stream));
     if (bt->esz == 4)
         lbk::k_read_phi<float><<<nb, kGenericThreads, 0, bt->stream>>>((const float *)bt->st[bt->cur], bt->segs,
-                                                                       bt->all_blocks, dst, bt->blk_off, kChunk);
+                                                                       bt->all_blocks, dst, bt->blk_off, kChunk, flag);
     else
         lbk::k_read_phi<double><<<nb, kGenericThreads, 0, bt->stream>>>((const double *)bt->st[bt->cur], bt->segs,
-                                                                        bt->all_blocks, dst, bt->blk_off, kChunk);
+                                                                        bt->all_blocks, dst, bt->blk_off, kChunk, flag);
     CK(cudaGetLastError());
     if (!on_device) {
+        int bad = 0;
         CK(cudaMemcpyAsync(out, bt->phi_buf, sizeof(double) * bt->total, cudaMemcpyDeviceToHost, bt->stream));
+        CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, bt->stream));
         CK(cudaStreamSynchronize(bt->stream));
-        for (long long i = 0; i < bt->total; ++i)
-            if (!std::isfinite(out[i])) return LBHPDE_ERR_DIVERGED;
+        if (bad) return LBHPDE_ERR_DIVERGED;
     }
     return LBHPDE_OK;
 }

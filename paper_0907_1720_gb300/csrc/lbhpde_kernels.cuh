@@ -678,15 +678,23 @@ __global__ void __launch_bounds__(MAXT, 1)
 }
 
 // ------------------------------------------------------------------- a7: readout
-// phi (row 0, type T) of every segment into a concatenated double array.
+// phi (row 0, type T) of every segment into a concatenated double array; any non-finite value
+// sets *nonfinite (when given), so the host need not scan the copy.
 template <typename T>
 __global__ void k_read_phi(const T *__restrict__ st, const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
-                           double *__restrict__ out, const long long *__restrict__ out_off, int chunk) {
+                           double *__restrict__ out, const long long *__restrict__ out_off, int chunk,
+                           int *__restrict__ nonfinite) {
     const int2 bl = blocks[blockIdx.x];
     const Seg s = segs[bl.x];
     const int xend = min(bl.y + chunk, s.N);
     double *o = out + out_off[blockIdx.x];
-    for (int x = bl.y + threadIdx.x; x < xend; x += blockDim.x) o[x] = (double)st[s.off + x];
+    bool bad = false;
+    for (int x = bl.y + threadIdx.x; x < xend; x += blockDim.x) {
+        const double v = (double)st[s.off + x];
+        o[x] = v;
+        bad |= !isfinite(v);
+    }
+    if (bad && nonfinite) atomicOr(nonfinite, 1);
 }
 
 // ------------------------------------------------------------ a7: diagnostics
