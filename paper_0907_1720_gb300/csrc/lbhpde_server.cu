@@ -141,6 +141,12 @@ struct lbhpde_server_s {
     size_t esz = 4;
     int device = 0, max_active = 0, block = 256;
     cudaStream_t stream = nullptr;
+    // A step block's independent launch chains (per lattice and degree class: the resident launch,
+    // and the window launches, which follow each other) run on lanes of their own, after the
+    // table uploads on `stream`, and join it before the block's one synchronisation.
+    static constexpr int kLanes = 8;
+    cudaStream_t lane[kLanes] = {};
+    cudaEvent_t ev_up = nullptr, ev_done[kLanes] = {};
     void *arena_d = nullptr;
     Arena arena;
     void *coefT_d = nullptr;
@@ -256,6 +262,7 @@ int setup_admitted(lbhpde_server_s *S, std::vector<Req *> &adm) {
 struct Planned {
     int b, K, dc;
     bool halo;
+    int lane;    // stream lane: 2 * (lattice, degree class) + (windows ? 1 : 0)
     int nsteps;
     lbh::Packed p;
     size_t ioff = 0, foff = 0;  // offsets of its tables in the block's device arrays
@@ -266,7 +273,13 @@ struct Planned {
 // in one copy each, launch them in order on the server stream and wait once.
 int advance(lbhpde_server_s *S) {
     std::vector<Planned> plan;
-    for (int b : {5, 7}) {
+    // per lattice, two degree classes: requests whose f^eq degree the compiled variant covers
+    // (D <= 5 on D1Q5, <= 7 on D1Q7) and the rest, each with its own launches, so that one
+    // high-degree request does not send the whole lattice to the run-time-degree variant
+    for (int cls = 0; cls < 4; ++cls) {
+        const int b = cls < 2 ? 5 : 7;
+        const bool high = (cls & 1) != 0;
+        const int dcmax = b == 5 ? 5 : 7;
         const int K = lbh::default_K(S->esz, b);
         const int maxt = lbh::onchip_maxt(S->esz, b, K);
         const int cap = maxt * K, W = (b - 1) / 2;
@@ -274,7 +287,7 @@ int advance(lbhpde_server_s *S) {
         std::vector<Req *> ring, halo;
         int maxD = 0;
         for (Req *r : S->active)
-            if (r->mi.b == b && r->done < r->nsteps) {
+            if (r->mi.b == b && r->done < r->nsteps && (r->mi.D > dcmax) == high) {
                 (r->N <= cap ? ring : halo).push_back(r);
                 maxD = std::max(maxD, r->mi.D);
             }
@@ -289,7 +302,7 @@ int advance(lbhpde_server_s *S) {
                 n = std::max(n, st);
                 r->done += st;
             }
-            Planned pl{b, K, dc, false, n, {}};
+            Planned pl{b, K, dc, false, 2 * cls, n, {}};
             SRC(lbh::pack_ring(b, S->esz, K, dc, m, pl.p));
             plan.push_back(std::move(pl));
         }
@@ -310,7 +323,7 @@ int advance(lbhpde_server_s *S) {
                     left[q] -= st;
                 }
                 if (m.empty()) break;
-                Planned pl{b, K, dc, true, n, {}};
+                Planned pl{b, K, dc, true, 2 * cls + 1, n, {}};
                 SRC(lbh::pack_halo(b, S->esz, K, dc, tblk * W, m, pl.p));
                 plan.push_back(std::move(pl));
             }
@@ -330,11 +343,22 @@ int advance(lbhpde_server_s *S) {
     SCK(cudaMemcpyAsync(S->insts_d.p, insts.data(), sizeof(lbk::OnchipInst) * insts.size(), cudaMemcpyHostToDevice,
                         S->stream));
     SCK(cudaMemcpyAsync(S->first_d.p, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, S->stream));
+    // the lanes start after the uploads; different lanes touch disjoint requests
+    SCK(cudaEventRecord(S->ev_up, S->stream));
+    bool used[lbhpde_server_s::kLanes] = {};
     for (const Planned &pl : plan) {
+        if (!used[pl.lane]) SCK(cudaStreamWaitEvent(S->lane[pl.lane], S->ev_up, 0));
+        used[pl.lane] = true;
         SRC(lbh::launch_onchip(pl.b, S->esz, pl.K, pl.dc, pl.halo, pl.p, S->insts_d.p + pl.ioff,
-                               S->first_d.p + pl.foff, S->arena_d, S->arena_d, S->coefT_d, pl.nsteps, S->stream));
+                               S->first_d.p + pl.foff, S->arena_d, S->arena_d, S->coefT_d, pl.nsteps,
+                               S->lane[pl.lane]));
         ++S->launches;
     }
+    for (int i = 0; i < lbhpde_server_s::kLanes; ++i)
+        if (used[i]) {
+            SCK(cudaEventRecord(S->ev_done[i], S->lane[i]));
+            SCK(cudaStreamWaitEvent(S->stream, S->ev_done[i], 0));
+        }
     SCK(cudaStreamSynchronize(S->stream));
     return LBHPDE_OK;
 }
@@ -480,8 +504,12 @@ extern "C" int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t 
     int prev = 0;
     bool ok = cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(device) == cudaSuccess &&
               cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&S->ev_up, cudaEventDisableTiming) == cudaSuccess &&
               cudaMalloc(&S->arena_d, device_bytes) == cudaSuccess &&
               cudaMalloc((void **)&S->coefD_d, sizeof(double) * (size_t)max_active * kCoefStride) == cudaSuccess;
+    for (int i = 0; ok && i < lbhpde_server_s::kLanes; ++i)
+        ok = cudaStreamCreateWithFlags(&S->lane[i], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&S->ev_done[i], cudaEventDisableTiming) == cudaSuccess;
     if (ok && S->esz == 4)
         ok = cudaMalloc(&S->coefT_d, sizeof(float) * (size_t)max_active * kCoefStride) == cudaSuccess;
     else if (ok)
@@ -493,6 +521,11 @@ extern "C" int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t 
         if (S->coefD_d) cudaFree(S->coefD_d);
         if (S->coefT_d && S->coefT_d != S->coefD_d) cudaFree(S->coefT_d);
         if (S->stream) cudaStreamDestroy(S->stream);
+        for (int i = 0; i < lbhpde_server_s::kLanes; ++i) {
+            if (S->lane[i]) cudaStreamDestroy(S->lane[i]);
+            if (S->ev_done[i]) cudaEventDestroy(S->ev_done[i]);
+        }
+        if (S->ev_up) cudaEventDestroy(S->ev_up);
         delete S;
         return e == cudaErrorMemoryAllocation ? LBHPDE_ERR_OOM : LBHPDE_ERR_CUDA;
     }
@@ -611,6 +644,11 @@ extern "C" int lbhpde_server_destroy(lbhpde_server_t S) {
     if (S->coefT_d != S->coefD_d) cudaFree(S->coefT_d);
     cudaFree(S->coefD_d);
     cudaStreamDestroy(S->stream);
+    for (int i = 0; i < lbhpde_server_s::kLanes; ++i) {
+        cudaStreamDestroy(S->lane[i]);
+        cudaEventDestroy(S->ev_done[i]);
+    }
+    cudaEventDestroy(S->ev_up);
     cudaSetDevice(prev);
     delete S;
     return LBHPDE_OK;
