@@ -416,7 +416,8 @@ def run_serving(args):
                     "offered_node_updates_s": work / reqs[-1][0],
                     "achieved_node_updates_s": work / (t1 - t0), "makespan_s": t1 - t0,
                     "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                    "launches": st["launches"], "clocks": clk.summary()})
+                    "launches": st["launches"], "gpu_busy_s": st["gpu_busy_s"],
+                    "gpu_busy_frac": st["gpu_busy_s"] / (t1 - t0), "clocks": clk.summary()})
     head = out[0]
     fp64 = None if args.quick else serving_fp64_plain(L, W.serving_requests(
         min(args.requests, max(64, int(args.window * args.rate))), rate=args.rate, seed=W.SEED + int(args.rate)))

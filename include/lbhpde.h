@@ -311,6 +311,8 @@ typedef struct {
     size_t bytes_in_use, bytes_total;
     long launches;
     int error;             /* sticky status of the scheduler (LBHPDE_OK unless a CUDA call failed) */
+    double gpu_busy_s;     /* summed GPU time of the step blocks, from their uploads to their last
+                            * launch (CUDA events): busy / wall time is the device's share of work */
 } lbhpde_server_info;
 
 /* device_bytes (>= 1 MiB) is the state arena, allocated at creation; each request holds

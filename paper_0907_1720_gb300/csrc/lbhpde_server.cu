@@ -147,6 +147,8 @@ struct lbhpde_server_s {
     static constexpr int kLanes = 8;
     cudaStream_t lane[kLanes] = {};
     cudaEvent_t ev_up = nullptr, ev_done[kLanes] = {};
+    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // timing of one step block
+    double gpu_busy = 0.0;
     void *arena_d = nullptr;
     Arena arena;
     void *coefT_d = nullptr;
@@ -340,6 +342,7 @@ int advance(lbhpde_server_s *S) {
     }
     SRC(S->insts_d.ensure(insts.size()));
     SRC(S->first_d.ensure(first.size()));
+    SCK(cudaEventRecord(S->ev_t0, S->stream));
     SCK(cudaMemcpyAsync(S->insts_d.p, insts.data(), sizeof(lbk::OnchipInst) * insts.size(), cudaMemcpyHostToDevice,
                         S->stream));
     SCK(cudaMemcpyAsync(S->first_d.p, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, S->stream));
@@ -359,7 +362,12 @@ int advance(lbhpde_server_s *S) {
             SCK(cudaEventRecord(S->ev_done[i], S->lane[i]));
             SCK(cudaStreamWaitEvent(S->stream, S->ev_done[i], 0));
         }
+    SCK(cudaEventRecord(S->ev_t1, S->stream));
     SCK(cudaStreamSynchronize(S->stream));
+    float ms = 0.0f;
+    SCK(cudaEventElapsedTime(&ms, S->ev_t0, S->ev_t1));
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->gpu_busy += ms * 1e-3;
     return LBHPDE_OK;
 }
 
@@ -505,6 +513,7 @@ extern "C" int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t 
     bool ok = cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(device) == cudaSuccess &&
               cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&S->ev_up, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreate(&S->ev_t0) == cudaSuccess && cudaEventCreate(&S->ev_t1) == cudaSuccess &&
               cudaMalloc(&S->arena_d, device_bytes) == cudaSuccess &&
               cudaMalloc((void **)&S->coefD_d, sizeof(double) * (size_t)max_active * kCoefStride) == cudaSuccess;
     for (int i = 0; ok && i < lbhpde_server_s::kLanes; ++i)
@@ -526,6 +535,8 @@ extern "C" int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t 
             if (S->ev_done[i]) cudaEventDestroy(S->ev_done[i]);
         }
         if (S->ev_up) cudaEventDestroy(S->ev_up);
+        if (S->ev_t0) cudaEventDestroy(S->ev_t0);
+        if (S->ev_t1) cudaEventDestroy(S->ev_t1);
         delete S;
         return e == cudaErrorMemoryAllocation ? LBHPDE_ERR_OOM : LBHPDE_ERR_CUDA;
     }
@@ -617,6 +628,7 @@ extern "C" int lbhpde_server_stats(lbhpde_server_t S, lbhpde_server_info *out) {
     out->bytes_total = S->arena.size();
     out->launches = S->launches;
     out->error = S->error;
+    out->gpu_busy_s = S->gpu_busy;
     return LBHPDE_OK;
 }
 
@@ -649,6 +661,8 @@ extern "C" int lbhpde_server_destroy(lbhpde_server_t S) {
         cudaEventDestroy(S->ev_done[i]);
     }
     cudaEventDestroy(S->ev_up);
+    cudaEventDestroy(S->ev_t0);
+    cudaEventDestroy(S->ev_t1);
     cudaSetDevice(prev);
     delete S;
     return LBHPDE_OK;

@@ -93,7 +93,8 @@ class lbhpde_result(ctypes.Structure):
 class lbhpde_server_info(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_long), ("in_flight", ctypes.c_long), ("completed", ctypes.c_long),
                 ("node_updates", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t),
-                ("bytes_total", ctypes.c_size_t), ("launches", ctypes.c_long), ("error", ctypes.c_int)]
+                ("bytes_total", ctypes.c_size_t), ("launches", ctypes.c_long), ("error", ctypes.c_int),
+                ("gpu_busy_s", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
