@@ -276,8 +276,7 @@ int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Pa
     out.first.push_back((int)out.insts.size());
     out.max_inst = (out.max_inst + 3) & ~3;  // keeps the shared-memory coefficient rows 16-byte aligned
     const int ne = lbk::nedge(b);
-    out.smem = (size_t(4) * ne * out.nthreads + size_t(2) * ne * out.max_inst +
-                size_t(2) * (b - 1) * K * out.max_inst + coef_max) * esz;
+    out.smem = (size_t(4) * ne * out.nthreads + size_t(2) * ne * out.max_inst + coef_max) * esz;
     if (out.smem > 227 * 1024) return LBHPDE_ERR_UNSUPPORTED;
     return LBHPDE_OK;
 }

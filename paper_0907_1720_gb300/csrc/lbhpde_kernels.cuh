@@ -23,6 +23,9 @@ namespace lbk {
 constexpr int kMaxDeg = 31;
 constexpr int kMaxRow = 64;  // longest coefficient row (real-exponent models: (A + 1)(Dg + 1))
 
+// compile-time flag passed to generic lambdas
+template <bool V> struct BoolC { static constexpr bool value = V; };
+
 // e_j for j = 0..6: {0, 1, -1, 2, -2, 3, -3}
 __host__ __device__ constexpr int vel(int j) { return j == 0 ? 0 : ((j & 1) ? (j + 1) / 2 : -(j / 2)); }
 // Largest |e_j| of the lattice
@@ -432,9 +435,9 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 4 && B == 5) ? 4 : 1) k_stre
 //   ring (HALO = false): the window is the whole periodic instance and stays resident for
 //     all nsteps; the wrap-around uses
 //       tail: the last |e| nodes of the instance (read by thread 0),
-//       head = thread 0's L window (read by the threads at the end of the instance),
-//       wrap: a copy of the last two threads' own values (their gather runs through shared
-//             memory, since the last thread's node count is only known at run time).
+//       head = thread 0's L window (read by the threads at the end of the instance: a
+//             left-moving source past node N-1 is replaced by its head slot, a run-time
+//             select taken only in the warps that hold such a thread).
 //     Several instances may share a CTA (warp-aligned thread runs).
 //   halo (HALO = true): temporal blocking.  The window is npos = valid + 2H consecutive
 //     nodes (global index taken modulo N) with H = nsteps * max|e|; the window edges read
@@ -469,8 +472,7 @@ __global__ void __launch_bounds__(MAXT, 1)
     T *R = smem;                        // [2][NE][nt]
     T *L = R + 2 * NE * nt;             // [2][NE][nt]
     T *tail = L + 2 * NE * nt;          // [2][NE][max_inst]                (ring; max_inst % 4 == 0)
-    T *wrap = tail + 2 * NE * max_inst; // [max_inst][2][B-1][K]            (ring)
-    T *scoef = HALO ? tail : wrap + 2 * (B - 1) * K * max_inst;
+    T *scoef = HALO ? tail : tail + 2 * NE * max_inst;
 
     const int first = cta_first[blockIdx.x], last = cta_first[blockIdx.x + 1];
     const int tid = threadIdx.x;
@@ -500,11 +502,13 @@ __global__ void __launch_bounds__(MAXT, 1)
     const int npos = I.npos;
     const bool near_end = !HALO && has && (t + 1) * K + wmax(B) > N;  // ring: threads nthr-2, nthr-1
     const int xb = t * K;
-    T *Sx = wrap + ((I.il * 2 + (t == I.nthr - 1 ? 1 : 0)) * (B - 1)) * K;
-    // halo windows: the outermost threads have no neighbour; they read their own edge slot
-    // (in bounds, stale) instead
+    // ring: the warps that hold a near-end thread take the gather with the wrap-around select
+    const bool wrap_warp = !HALO && __any_sync(0xffffffffu, near_end);
+    // the outermost threads have no neighbour on that side (halo: window edge; ring: the
+    // last thread, whose reads past node N-1 are replaced by the head); they read their own
+    // edge slot (in bounds, stale) instead
     const int left_nb = (HALO && t == 0) ? tid : tid - 1;
-    const int right_nb = (HALO && t + 1 >= I.nthr) ? tid : tid + 1;
+    const int right_nb = (t + 1 >= I.nthr) ? tid : tid + 1;
 
     T phi[K], v[B][K];
 #pragma unroll
@@ -563,9 +567,11 @@ __global__ void __launch_bounds__(MAXT, 1)
             T d[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) d[k] = T(0);
-            if (!near_end) {
-                // f_j(x) = s_j(x - e_j) from own registers or a neighbour's published edge
-                // (ring: thread 0 takes its right-moving inflow from the tail buffer)
+            // f_j(x) = s_j(x - e_j) from own registers or a neighbour's published edge
+            // (ring: thread 0 takes its right-moving inflow from the tail buffer, and a
+            // left-moving source past node N-1 wraps to thread 0's head window)
+            auto pull = [&](auto wrapc) {
+                constexpr bool WRAP = decltype(wrapc)::value;
 #pragma unroll
                 for (int j = 1; j < B; ++j) {
                     const int e = vel(j);
@@ -589,46 +595,23 @@ __global__ void __launch_bounds__(MAXT, 1)
                         const int a = -e;
 #pragma unroll
                         for (int k = 0; k < K; ++k) {  // ascending: v[j][k + a] still old
-                            const T nv = (k + a < K) ? v[j][k + a] : Lb[(eslot(a) + k + a - K) * nt + right_nb];
+                            T nv = (k + a < K) ? v[j][k + a] : Lb[(eslot(a) + k + a - K) * nt + right_nb];
+                            if constexpr (WRAP) {
+                                // positions past N-1 (last thread's padding) clamp to the
+                                // last head slot: in bounds, never written back
+                                const int src = xb + k + a;
+                                if (src >= N) nv = Lb[(eslot(a) + min(src - N, a - 1)) * nt + I.tbase];
+                            }
                             d[k] += nv - v[j][k];
                             v[j][k] = nv;
                         }
                     }
                 }
-            } else {
-                // ring, last one or two threads (the last may own fewer than K nodes): stage own
-                // values in shared memory, then take every source with one load from a computed
-                // address; sources past node N-1 wrap to thread 0's head window.
-#pragma unroll
-                for (int j = 1; j < B; ++j)
-#pragma unroll
-                    for (int k = 0; k < K; ++k) Sx[(j - 1) * K + k] = v[j][k];
-#pragma unroll
-                for (int j = 1; j < B; ++j) {
-                    const int e = vel(j);
-#pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        const T *q;
-                        if (e > 0) {
-                            if (k >= e)
-                                q = &Sx[(j - 1) * K + k - e];
-                            else
-                                q = t > 0 ? &Rb[(eslot(e) + k) * nt + tid - 1] : &Tb[(eslot(e) + k) * max_inst + I.il];
-                        } else {
-                            const int a = -e, src = xb + k + a;
-                            if (src >= N)
-                                q = &Lb[(eslot(a) + min(src - N, a - 1)) * nt + I.tbase];
-                            else if (k + a < K)
-                                q = &Sx[(j - 1) * K + k + a];
-                            else
-                                q = &Lb[(eslot(a) + k + a - K) * nt + tid + 1];
-                        }
-                        const T nv = *q;
-                        d[k] += nv - v[j][k];
-                        v[j][k] = nv;
-                    }
-                }
-            }
+            };
+            if (wrap_warp)
+                pull(BoolC<true>{});
+            else
+                pull(BoolC<false>{});
 #pragma unroll
             for (int k = 0; k < K; ++k) phi[k] += d[k];
             // relax: s'_j = (1 - omega) f_j + P_j(phi'), Horner with coefficients from shared memory
