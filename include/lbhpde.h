@@ -229,6 +229,14 @@ int lbhpde_set_kernel(lbhpde_t h, int kernel, int nodes_per_thread, int steps_pe
 int lbhpde_autotune(int precision, int lattice, int degree, int *nodes_per_thread, int *steps_per_launch,
                     double *node_updates_per_s);
 
+/* Records a tuned (nodes per thread, steps per window) pair for one precision, lattice and f^eq
+ * degree without timing anything, as lbhpde_autotune would have left it: e.g. a pair found in
+ * an earlier process, or a fixed choice for a profiling run.  Host only (no device work).
+ * LBHPDE_ERR_ARG for an invalid precision, lattice or degree, or steps_per_launch < 1;
+ * LBHPDE_ERR_UNSUPPORTED for nodes per thread the library was not built with, or a window
+ * whose halo (2 * steps * max|e|) leaves fewer than half of its nodes valid. */
+int lbhpde_set_tuning(int precision, int lattice, int degree, int nodes_per_thread, int steps_per_launch);
+
 int lbhpde_get_model(lbhpde_t h, lbhpde_model_info *out);
 int lbhpde_destroy(lbhpde_t h);
 const char *lbhpde_strerror(int code);

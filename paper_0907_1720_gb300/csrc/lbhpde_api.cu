@@ -542,6 +542,22 @@ extern "C" int lbhpde_autotune(int precision, int lattice, int degree, int *node
     return LBHPDE_OK;
 }
 
+extern "C" int lbhpde_set_tuning(int precision, int lattice, int degree, int nodes_per_thread, int steps_per_launch) {
+    if ((precision != LBHPDE_FP64 && precision != LBHPDE_FP32_DEV) || (lattice != 5 && lattice != 7) || degree < 1 ||
+        degree > LBHPDE_MAX_DEG || steps_per_launch < 1)
+        return LBHPDE_ERR_ARG;
+    const size_t esz = precision == LBHPDE_FP64 ? 8 : 4;
+    const int b = lattice, K = nodes_per_thread;
+    const int maxt = lbh::onchip_maxt(esz, b, K);
+    if (maxt == 0 || K < lbk::wmax(b)) return LBHPDE_ERR_UNSUPPORTED;
+    // the same bound as the autotuner's candidates: the halo leaves at least half the window valid
+    if ((long long)maxt * K - 2LL * steps_per_launch * lbk::wmax(b) < (long long)maxt * K / 2)
+        return LBHPDE_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[std::make_tuple((int)esz, b, lbh::onchip_dc(b, degree))] = std::make_pair(K, steps_per_launch);
+    return LBHPDE_OK;
+}
+
 // ============================================================================= batches
 
 namespace {

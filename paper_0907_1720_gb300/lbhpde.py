@@ -125,6 +125,7 @@ _SIGS = {
     "lbhpde_set_kernel": (_I, [_V, _I, _I, _I]),
     "lbhpde_get_model": (_I, [_V, _P(lbhpde_model_info)]),
     "lbhpde_autotune": (_I, [_I, _I, _I, _P(_I), _P(_I), _P(_D)]),
+    "lbhpde_set_tuning": (_I, [_I, _I, _I, _I, _I]),
     "lbhpde_destroy": (_I, [_V]),
     "lbhpde_strerror": (ctypes.c_char_p, [_I]),
     "lbhpde_batch_create": (_I, [_P(_V), _I, _P(lbhpde_instance), _I, _V, _P(lbhpde_allocator)]),
@@ -276,6 +277,12 @@ def autotune(precision, lattice, degree):
     _check(lib().lbhpde_autotune(int(precision), int(lattice), int(degree), ctypes.byref(K), ctypes.byref(T),
                                  ctypes.byref(r)), "lbhpde_autotune")
     return K.value, T.value, r.value
+
+
+def set_tuning(precision, lattice, degree, nodes_per_thread, steps_per_launch):
+    """lbhpde_set_tuning: record a tuned on-chip pair without timing (later batches use it)."""
+    _check(lib().lbhpde_set_tuning(int(precision), int(lattice), int(degree), int(nodes_per_thread),
+                                   int(steps_per_launch)), "lbhpde_set_tuning")
 
 
 def tau_sweep(problem, taus, precision=FP64, nsteps=None, phib=None):

@@ -216,3 +216,18 @@ def test_real_exponent_argument_errors(lib):
     P = (L.lbhpde_pi * 3)(L.make_pi((0, 0, 0.5), 1.5, (0, 1.0)), L.make_pi((0, 1.0)),
                           L.make_pi((0, 0.0), 2.5, (0, 1.0)))
     assert lib.lbhpde_model(3, a, P, 0.1, 1e-4, 1.3, 0, 1, ctypes.byref(info)) == L.ERR_ARG
+
+
+def test_set_tuning_argument_checks(lib):
+    """lbhpde_set_tuning records a pair on the host only; it rejects what the autotuner would
+    never choose."""
+    f = lib.lbhpde_set_tuning
+    assert f(7, 5, 5, 8, 128) == L.ERR_ARG             # precision
+    assert f(L.FP32_DEV, 6, 5, 8, 128) == L.ERR_ARG     # lattice
+    assert f(L.FP32_DEV, 5, 0, 8, 128) == L.ERR_ARG     # degree
+    assert f(L.FP32_DEV, 5, 5, 8, 0) == L.ERR_ARG       # steps per window
+    assert f(L.FP32_DEV, 5, 5, 3, 128) == L.ERR_UNSUPPORTED   # not a compiled width
+    assert f(L.FP64, 7, 7, 8, 16) == L.ERR_UNSUPPORTED        # FP64 D1Q7 has K = 4 only
+    assert f(L.FP32_DEV, 5, 5, 8, 600) == L.ERR_UNSUPPORTED   # halo 2400 of a 4096-node window
+    # a run-time-degree FP64 D1Q7 pair (valid for every model of that class)
+    assert f(L.FP64, 7, 9, 4, 16) == L.OK
