@@ -510,20 +510,54 @@ __global__ void __launch_bounds__(MAXT, 1)
     const int left_nb = (HALO && t == 0) ? tid : tid - 1;
     const int right_nb = (t + 1 >= I.nthr) ? tid : tid + 1;
 
-    T phi[K], v[B][K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int p = xb + k;
-        const bool ok = has && p < npos;
+    // global node of window position p (halo: taken modulo N)
+    auto gnode = [&](int p) -> long long {
         long long x = p;
         if (HALO) {
             x = (long long)I.x0 + p;
             x %= N;
             x += x < 0 ? N : 0;
         }
-        phi[k] = ok ? st_in[I.off + x] : T(0);
+        return x;
+    };
+    // a thread whose K positions are consecutive global nodes on 16-byte boundaries moves
+    // them with vector loads and stores (VW elements each)
+    constexpr int VW = 16 / (int)sizeof(T);
+    auto vec_ok = [&](const T *base, long long x) {
+        return K % VW == 0 && x + K <= N && ((uintptr_t)(base + x) & 15) == 0 && ((I.ld * (long long)sizeof(T)) & 15) == 0;
+    };
+    T phi[K], v[B][K];
+    const long long xv = has ? gnode(xb) : 0;
+    if (has && xb + K <= npos && vec_ok(st_in + I.off, xv)) {
+        const T *src = st_in + I.off + xv;
 #pragma unroll
-        for (int j = 1; j < B; ++j) v[j][k] = ok ? st_in[I.off + (long long)j * I.ld + x] : T(0);
+        for (int j = 0; j < B; ++j) {
+            T *dst = j == 0 ? phi : v[j];
+#pragma unroll
+            for (int q = 0; q < K / VW; ++q) {
+                if constexpr (sizeof(T) == 4) {
+                    const float4 w = reinterpret_cast<const float4 *>(src + (long long)j * I.ld)[q];
+                    dst[4 * q] = w.x;
+                    dst[4 * q + 1] = w.y;
+                    dst[4 * q + 2] = w.z;
+                    dst[4 * q + 3] = w.w;
+                } else {
+                    const double2 w = reinterpret_cast<const double2 *>(src + (long long)j * I.ld)[q];
+                    dst[2 * q] = w.x;
+                    dst[2 * q + 1] = w.y;
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int p = xb + k;
+            const bool ok = has && p < npos;
+            const long long x = gnode(p);
+            phi[k] = ok ? st_in[I.off + x] : T(0);
+#pragma unroll
+            for (int j = 1; j < B; ++j) v[j][k] = ok ? st_in[I.off + (long long)j * I.ld + x] : T(0);
+        }
     }
     __syncthreads();
     const T *sc = scoef + I.scoef;
@@ -643,19 +677,30 @@ __global__ void __launch_bounds__(MAXT, 1)
             }
         }
     }
+    if (has && xb >= I.vlo && xb + K <= I.vhi && vec_ok(st_out + I.off2, xv)) {
+        T *dst = st_out + I.off2 + xv;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const int p = xb + k;
-        if (has && p >= I.vlo && p < I.vhi) {
-            long long x = p;
-            if (HALO) {
-                x = (long long)I.x0 + p;
-                x %= N;
-                x += x < 0 ? N : 0;
+        for (int j = 0; j < B; ++j) {
+            const T *src = j == 0 ? phi : v[j];
+#pragma unroll
+            for (int q = 0; q < K / VW; ++q) {
+                if constexpr (sizeof(T) == 4)
+                    reinterpret_cast<float4 *>(dst + (long long)j * I.ld)[q] =
+                        make_float4(src[4 * q], src[4 * q + 1], src[4 * q + 2], src[4 * q + 3]);
+                else
+                    reinterpret_cast<double2 *>(dst + (long long)j * I.ld)[q] = make_double2(src[2 * q], src[2 * q + 1]);
             }
-            st_out[I.off2 + x] = phi[k];
+        }
+    } else {
 #pragma unroll
-            for (int j = 1; j < B; ++j) st_out[I.off2 + (long long)j * I.ld + x] = v[j][k];
+        for (int k = 0; k < K; ++k) {
+            const int p = xb + k;
+            if (has && p >= I.vlo && p < I.vhi) {
+                const long long x = gnode(p);
+                st_out[I.off2 + x] = phi[k];
+#pragma unroll
+                for (int j = 1; j < B; ++j) st_out[I.off2 + (long long)j * I.ld + x] = v[j][k];
+            }
         }
     }
 }
