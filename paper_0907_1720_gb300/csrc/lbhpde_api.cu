@@ -192,11 +192,21 @@ namespace lbh {
 
 int onchip_maxt(size_t esz, int b, int K) {
     if (esz == 4) {
-        if (b == 5) return K == 8 ? 512 : (K == 4 ? 1024 : (K == 2 ? 1024 : 0));
+        if (b == 5) return K == 8 ? 512 : (K == 4 ? 1024 : (K == 2 ? 1024 : 0));  // resident CTAs
         return K == 8 ? 256 : (K == 4 ? 512 : 0);
     }
     if (b == 5) return K == 4 ? 512 : (K == 2 ? 1024 : 0);
     return K == 4 ? 256 : 0;
+}
+
+// Threads of a window CTA.  FP32 D1Q5 windows with K = 8 take 128 threads (96 registers), so
+// five CTAs share an SM: some load or write back their windows while others compute, and their
+// per-step barriers fall at different times.  (Measured on GB300: 5.92e11 node-updates/s on the
+// ensemble against 5.80e11 with 256 threads and 5.61e11 with 512; the D1Q7 and FP64 windows
+// were slower with 128 threads than with their resident CTA size.)
+int onchip_maxt_halo(size_t esz, int b, int K) {
+    if (esz == 4 && b == 5 && K == 8) return kHaloThreadsF32Q5;
+    return onchip_maxt(esz, b, K);
 }
 
 int default_K(size_t esz, int b) { return esz == 4 && b == 5 ? 8 : 4; }
@@ -281,9 +291,9 @@ int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Pa
     return LBHPDE_OK;
 }
 
-int pack_halo(int b, size_t esz, int K, int dc, int H, const std::vector<Member> &m, Packed &out) {
+int pack_halo(int b, size_t esz, int K, int dc, int H, const std::vector<Member> &m, Packed &out, bool wide) {
     out = Packed{};
-    const int maxt = onchip_maxt(esz, b, K);
+    const int maxt = wide ? onchip_maxt(esz, b, K) : onchip_maxt_halo(esz, b, K);
     if (maxt == 0) return LBHPDE_ERR_UNSUPPORTED;
     const int valid = maxt * K - 2 * H;
     if (valid < 32) return LBHPDE_ERR_UNSUPPORTED;
@@ -365,7 +375,13 @@ template <typename T, int B, bool HALO>
 int launch_onchip_b(int K, int dc, const OnchipArgs &a) {
     if constexpr (sizeof(T) == 4) {
         if constexpr (B == 5) {
-            if (K == 8) return launch_onchip_d<T, B, 8, 512, HALO>(dc, a);
+            if (K == 8) {
+                if constexpr (HALO) {  // window CTAs: small (batches) or as wide as a resident CTA
+                    if (a.p->nthreads <= kHaloThreadsF32Q5)
+                        return launch_onchip_d<T, B, 8, kHaloThreadsF32Q5, HALO>(dc, a);
+                }
+                return launch_onchip_d<T, B, 8, 512, HALO>(dc, a);
+            }
             if (K == 4) return launch_onchip_d<T, B, 4, 1024, HALO>(dc, a);
             if (K == 2) return launch_onchip_d<T, B, 2, 1024, HALO>(dc, a);
         } else {
@@ -510,7 +526,7 @@ extern "C" int lbhpde_autotune(int precision, int lattice, int degree, int *node
     double best = 0.0;
     for (int K : {2, 4, 8}) {
         if (rc != LBHPDE_OK) break;
-        const int maxt = lbh::onchip_maxt(esz, b, K);
+        const int maxt = lbh::onchip_maxt_halo(esz, b, K);
         if (maxt == 0 || K < lbk::wmax(b)) continue;
         for (int tblk : {16, 32, 64, 96, 128}) {
             if (maxt * K - 2 * tblk * lbk::wmax(b) < maxt * K / 2) continue;
@@ -548,7 +564,7 @@ extern "C" int lbhpde_set_tuning(int precision, int lattice, int degree, int nod
         return LBHPDE_ERR_ARG;
     const size_t esz = precision == LBHPDE_FP64 ? 8 : 4;
     const int b = lattice, K = nodes_per_thread;
-    const int maxt = lbh::onchip_maxt(esz, b, K);
+    const int maxt = lbh::onchip_maxt_halo(esz, b, K);
     if (maxt == 0 || K < lbk::wmax(b)) return LBHPDE_ERR_UNSUPPORTED;
     // the same bound as the autotuner's candidates: the halo leaves at least half the window valid
     if ((long long)maxt * K - 2LL * steps_per_launch * lbk::wmax(b) < (long long)maxt * K / 2)
@@ -616,11 +632,11 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
     const int maxt = lbh::onchip_maxt(bt->esz, g.b, K);
     if (maxt == 0 || K < lbk::wmax(g.b)) return LBHPDE_ERR_UNSUPPORTED;
     const int W = lbk::wmax(g.b);
-    const int cap = maxt * K;
+    const int cap = maxt * K, cap_h = lbh::onchip_maxt_halo(bt->esz, g.b, K) * K;
     g.dc = lbh::onchip_dc(g.b, g.maxD);
-    if (tblk <= 0) tblk = lbh::default_tblk(cap, W);
+    if (tblk <= 0) tblk = lbh::default_tblk(cap_h, W);
     const int H = tblk * W;
-    if (cap - 2 * H < 32) return LBHPDE_ERR_UNSUPPORTED;
+    if (cap_h - 2 * H < 32) return LBHPDE_ERR_UNSUPPORTED;
     std::vector<lbh::Member> ring, halo;
     for (int i : g.members) {
         const lbh::Member mb{bt->segs_h[i], bt->segs_h[i].off, 1 << 30};

@@ -34,7 +34,11 @@ struct Packed {
 
 // Largest CTA (threads) of the compiled on-chip variant for (element size, lattice, nodes per
 // thread); 0 when no variant exists.
+// Threads per CTA of the on-chip kernels: resident instances (capacity = threads * K nodes)
+// and temporally blocked windows (FP32 D1Q5 with K = 8 uses smaller window CTAs).
+constexpr int kHaloThreadsF32Q5 = 128;
 int onchip_maxt(size_t esz, int b, int K);
+int onchip_maxt_halo(size_t esz, int b, int K);
 int default_K(size_t esz, int b);
 // Steps per halo window such that the halo (steps * max|e| on each side) leaves at least three
 // quarters of a window of `capacity` nodes valid.
@@ -45,7 +49,10 @@ int onchip_dc(int b, int maxD);
 // Resident instances (N <= capacity): first fit, largest first, warp-aligned runs, <= 32 per CTA.
 int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Packed &out);
 // Temporally blocked windows with halo H: one window per CTA.
-int pack_halo(int b, size_t esz, int K, int dc, int H, const std::vector<Member> &m, Packed &out);
+// wide: windows as large as a resident CTA (fewer, longer windows: the server, whose step
+// blocks fix the steps per window) instead of the smaller window CTAs.
+int pack_halo(int b, size_t esz, int K, int dc, int H, const std::vector<Member> &m, Packed &out,
+              bool wide = false);
 
 int launch_onchip(int b, size_t esz, int K, int dc, bool halo, const Packed &p, const lbk::OnchipInst *insts_d,
                   const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st);

@@ -460,8 +460,17 @@ struct OnchipInst {
                         // frozen after them while the CTA's barriers continue)
 };
 
+// threads per SM at each configuration's register budget (FP32 D1Q5 with K = 8: 128 registers);
+// a CTA smaller than that asks for the registers of budget / MAXT CTAs per SM
+__host__ __device__ constexpr int onchip_budget(int esz, int B, int K) {
+    return esz == 4 ? (B == 5 ? (K == 8 ? 512 : 1024) : (K == 8 ? 256 : 512)) : (B == 5 ? (K == 4 ? 512 : 1024) : 256);
+}
+__host__ __device__ constexpr int onchip_minb(int esz, int B, int K, int MAXT) {
+    return onchip_budget(esz, B, K) / MAXT > 1 ? onchip_budget(esz, B, K) / MAXT : 1;
+}
+
 template <typename T, int B, int K, int MAXT, bool HALO, int DC>
-__global__ void __launch_bounds__(MAXT, 1)
+__global__ void __launch_bounds__(MAXT, onchip_minb(sizeof(T), B, K, MAXT))
     k_onchip(const T *__restrict__ st_in, T *__restrict__ st_out, const OnchipInst *__restrict__ insts,
              const int *__restrict__ cta_first, const T *__restrict__ coefs, int nsteps, int max_inst) {
     static_assert(K >= wmax(B), "a thread must own at least max|e| nodes");

@@ -285,7 +285,7 @@ int advance(lbhpde_server_s *S) {
         const int K = lbh::default_K(S->esz, b);
         const int maxt = lbh::onchip_maxt(S->esz, b, K);
         const int cap = maxt * K, W = (b - 1) / 2;
-        const int tblk = lbh::default_tblk(cap, W);
+        const int tblk = lbh::default_tblk(cap, W);  // windows as wide as a resident CTA
         std::vector<Req *> ring, halo;
         int maxD = 0;
         for (Req *r : S->active)
@@ -326,7 +326,7 @@ int advance(lbhpde_server_s *S) {
                 }
                 if (m.empty()) break;
                 Planned pl{b, K, dc, true, 2 * cls + 1, n, {}};
-                SRC(lbh::pack_halo(b, S->esz, K, dc, tblk * W, m, pl.p));
+                SRC(lbh::pack_halo(b, S->esz, K, dc, tblk * W, m, pl.p, true));
                 plan.push_back(std::move(pl));
             }
         }

@@ -228,6 +228,6 @@ def test_set_tuning_argument_checks(lib):
     assert f(L.FP32_DEV, 5, 5, 8, 0) == L.ERR_ARG       # steps per window
     assert f(L.FP32_DEV, 5, 5, 3, 128) == L.ERR_UNSUPPORTED   # not a compiled width
     assert f(L.FP64, 7, 7, 8, 16) == L.ERR_UNSUPPORTED        # FP64 D1Q7 has K = 4 only
-    assert f(L.FP32_DEV, 5, 5, 8, 600) == L.ERR_UNSUPPORTED   # halo 2400 of a 4096-node window
+    assert f(L.FP32_DEV, 5, 5, 8, 600) == L.ERR_UNSUPPORTED   # halo 2400 nodes: more than half a window
     # a run-time-degree FP64 D1Q7 pair (valid for every model of that class)
     assert f(L.FP64, 7, 9, 4, 16) == L.OK
