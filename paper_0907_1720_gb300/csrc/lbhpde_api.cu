@@ -59,7 +59,7 @@ struct Group {
         OnchipInst *insts = nullptr;
         int *cta_first = nullptr;
         int ncta() const { return host.ncta(); }
-    } ring, halo;
+    } ring[lbh::kRingClasses], halo;  // resident instances by CTA size class; windows
     int K = 0, maxt = 0, tblk = 0;
     int dc = 0;  // compile-time degree of the on-chip kernel variant (0 = run time)
     bool uniform = false;  // every member has the same model (coefficients and omega)
@@ -83,8 +83,8 @@ struct lbhpde_batch_s {
     cudaStream_t stream = nullptr;
     // resident instances run on `side`, forked from and joined back into `stream` with events,
     // so that the window launches fill the SMs the resident launch leaves idle
-    cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t side[lbh::kRingClasses] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[lbh::kRingClasses] = {};
     // streaming path: kGraphSteps one-step launches captured once per buffer parity and replayed
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool has_alloc = false;
@@ -173,11 +173,14 @@ struct lbhpde_batch_s {
         for (auto &gx : graph)
             if (gx) cudaGraphExecDestroy(gx);
         graph[0] = graph[1] = nullptr;
-        if (side) cudaStreamDestroy(side);
+        for (int c = 0; c < lbh::kRingClasses; ++c) {
+            if (side[c]) cudaStreamDestroy(side[c]);
+            if (ev_join[c]) cudaEventDestroy(ev_join[c]);
+            side[c] = nullptr;
+            ev_join[c] = nullptr;
+        }
         if (ev_fork) cudaEventDestroy(ev_fork);
-        if (ev_join) cudaEventDestroy(ev_join);
-        side = nullptr;
-        ev_fork = ev_join = nullptr;
+        ev_fork = nullptr;
         stream = nullptr;
     }
 };
@@ -211,6 +214,52 @@ int onchip_maxt_halo(size_t esz, int b, int K) {
 
 int default_K(size_t esz, int b) { return esz == 4 && b == 5 ? 8 : 4; }
 
+// Resident size classes.  FP32 D1Q5 with K = 8 puts an instance in the smallest of 128-, 256- and
+// 512-thread CTAs that holds it (classes 0, 1, 2): small CTAs share an SM (128 registers a
+// thread) and step on their own barriers.  (GB300, 1000 steps: 1024-node instances 6.77e11
+// node-updates/s in 128-thread CTAs against 5.73e11 packed four to a 512-thread CTA; 2048-node
+// ones 6.52e11 against 6.24e11.)  Other configurations have class 2 only.
+int ring_class(size_t esz, int b, int K, long long N) {
+    if (esz == 4 && b == 5 && K == 8) return N <= 128 * K ? 0 : (N <= 256 * K ? 1 : 2);
+    return 2;
+}
+int ring_class_threads(size_t esz, int b, int K, int cls) {
+    if (esz == 4 && b == 5 && K == 8) return cls == 0 ? 128 : (cls == 1 ? 256 : 512);
+    return onchip_maxt(esz, b, K);
+}
+
+void split_ring_classes(size_t esz, int b, int K, const std::vector<Member> &m, std::vector<Member> (&out)[kRingClasses]) {
+    for (auto &v : out) v.clear();
+    auto pad = [&](long long n) { return (int)(((n + K - 1) / K + 31) & ~31); };
+    std::vector<int> order(m.size());
+    for (size_t i = 0; i < m.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return pad(m[a].seg.N) > pad(m[c].seg.N); });
+    // the largest class first, first fit, as pack_ring will place it; then a smaller instance
+    // joins it where it fills a gap (an idle warp costs as much as a busy one) and takes a CTA
+    // of its own class otherwise
+    const int top = kRingClasses - 1, cap = ring_class_threads(esz, b, K, top);
+    struct Gap {
+        int free, n;
+    };
+    std::vector<Gap> ctas;
+    for (int i : order) {
+        const int c = ring_class(esz, b, K, m[i].seg.N), t = pad(m[i].seg.N);
+        bool placed = false;
+        for (auto &g : ctas)
+            if (g.free >= t && g.n < 32) {
+                g.free -= t;
+                ++g.n;
+                placed = true;
+                break;
+            }
+        if (!placed && c == top) {
+            ctas.push_back(Gap{cap - t, 1});
+            placed = true;
+        }
+        out[placed ? top : c].push_back(m[i]);
+    }
+}
+
 int default_tblk(int capacity, int W) {
     int t = 64;
     while (t > 1 && capacity - 2 * t * W < capacity * 3 / 4) t /= 2;
@@ -219,9 +268,9 @@ int default_tblk(int capacity, int W) {
 
 int onchip_dc(int b, int maxD) { return maxD == (b == 5 ? 5 : 7) ? maxD : 0; }
 
-int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Packed &out) {
+int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Packed &out, int threads) {
     out = Packed{};
-    const int maxt = onchip_maxt(esz, b, K);
+    const int maxt = threads > 0 ? threads : onchip_maxt(esz, b, K);
     if (maxt == 0) return LBHPDE_ERR_UNSUPPORTED;
     auto thr = [&](long long n) { return (int)((n + K - 1) / K); };
     auto pad = [&](long long n) { return (thr(n) + 31) & ~31; };
@@ -375,10 +424,10 @@ template <typename T, int B, bool HALO>
 int launch_onchip_b(int K, int dc, const OnchipArgs &a) {
     if constexpr (sizeof(T) == 4) {
         if constexpr (B == 5) {
-            if (K == 8) {
-                if constexpr (HALO) {  // window CTAs: small (batches) or as wide as a resident CTA
-                    if (a.p->nthreads <= kHaloThreadsF32Q5)
-                        return launch_onchip_d<T, B, 8, kHaloThreadsF32Q5, HALO>(dc, a);
+            if (K == 8) {  // CTAs of 128, 256 (resident only) or 512 threads: the plan's size class
+                if (a.p->nthreads <= 128) return launch_onchip_d<T, B, 8, 128, HALO>(dc, a);
+                if constexpr (!HALO) {
+                    if (a.p->nthreads <= 256) return launch_onchip_d<T, B, 8, 256, HALO>(dc, a);
                 }
                 return launch_onchip_d<T, B, 8, 512, HALO>(dc, a);
             }
@@ -636,22 +685,29 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
     g.dc = lbh::onchip_dc(g.b, g.maxD);
     if (tblk <= 0) tblk = lbh::default_tblk(cap_h, W);
     const int H = tblk * W;
-    if (cap_h - 2 * H < 32) return LBHPDE_ERR_UNSUPPORTED;
-    std::vector<lbh::Member> ring, halo;
+    std::vector<lbh::Member> resident, ring[lbh::kRingClasses], halo;
     for (int i : g.members) {
         const lbh::Member mb{bt->segs_h[i], bt->segs_h[i].off, 1 << 30};
-        (bt->N[i] <= cap && !force_halo ? ring : halo).push_back(mb);
+        (bt->N[i] <= cap && !force_halo ? resident : halo).push_back(mb);
     }
+    lbh::split_ring_classes(bt->esz, g.b, K, resident, ring);
+    // windows must keep some valid nodes; resident members only chunk their launches by tblk
+    if (!halo.empty() && cap_h - 2 * H < 32) return LBHPDE_ERR_UNSUPPORTED;
     // the previous plan's device tables (a re-plan after lbhpde_batch_set_kernel)
-    bt->dev_free(g.ring.insts);
-    bt->dev_free(g.ring.cta_first);
+    for (auto &pl : g.ring) {
+        bt->dev_free(pl.insts);
+        bt->dev_free(pl.cta_first);
+        pl = Group::Plan{};
+    }
     bt->dev_free(g.halo.insts);
     bt->dev_free(g.halo.cta_first);
-    g.ring = Group::Plan{};
     g.halo = Group::Plan{};
-    if (!ring.empty()) RC(lbh::pack_ring(g.b, bt->esz, K, g.dc, ring, g.ring.host));
+    for (int c = 0; c < lbh::kRingClasses; ++c) {
+        if (ring[c].empty()) continue;
+        RC(lbh::pack_ring(g.b, bt->esz, K, g.dc, ring[c], g.ring[c].host, lbh::ring_class_threads(bt->esz, g.b, K, c)));
+        RC(upload_plan(bt, g.ring[c]));
+    }
     if (!halo.empty()) RC(lbh::pack_halo(g.b, bt->esz, K, g.dc, H, halo, g.halo.host));
-    RC(upload_plan(bt, g.ring));
     RC(upload_plan(bt, g.halo));
     g.K = K;
     g.maxt = maxt;
@@ -660,8 +716,9 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
     return LBHPDE_OK;
 }
 
-int launch_group(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *out, int nsteps, cudaStream_t st) {
-    Group::Plan &pl = halo ? g.halo : g.ring;
+int launch_group(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *out, int nsteps, cudaStream_t st,
+                 int cls = lbh::kRingClasses - 1) {
+    Group::Plan &pl = halo ? g.halo : g.ring[cls];
     return lbh::launch_onchip(g.b, bt->esz, g.K, g.dc, halo, pl.host, pl.insts, pl.cta_first, in, out, bt->coefT,
                               nsteps, st);
 }
@@ -927,35 +984,45 @@ int step_periodic(lbhpde_batch_s *bt, long nsteps) {
         if (!g.members.empty() && g.halo.ncta()) tb = std::min(tb, g.tblk);
     const long nchunks = any_halo ? (nsteps + tb - 1) / tb : 0;
     const int cur0 = bt->cur, cur1 = bt->cur ^ (int)(nchunks & 1);
-    bool any_ring = false;
-    for (auto &g : bt->groups)
-        if (!g.members.empty() && g.ring.ncta()) any_ring = true;
-    // resident instances and windows touch disjoint rows: run them concurrently
-    const bool fork = any_ring && any_halo;
-    cudaStream_t rs = bt->stream;
+    // resident instances (each size class) and windows touch disjoint rows: when there is more
+    // than one kind, they run concurrently, the resident classes on streams of their own
+    bool used[lbh::kRingClasses] = {};
+    int kinds = any_halo ? 1 : 0;
+    for (int c = 0; c < lbh::kRingClasses; ++c) {
+        for (auto &g : bt->groups)
+            if (!g.members.empty() && g.ring[c].ncta()) used[c] = true;
+        kinds += used[c] ? 1 : 0;
+    }
+    const bool fork = kinds > 1;
     if (fork) {
-        if (!bt->side) {
-            CK(cudaStreamCreateWithFlags(&bt->side, cudaStreamNonBlocking));
-            CK(cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming));
-            CK(cudaEventCreateWithFlags(&bt->ev_join, cudaEventDisableTiming));
-        }
+        if (!bt->ev_fork) CK(cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming));
         CK(cudaEventRecord(bt->ev_fork, bt->stream));
-        CK(cudaStreamWaitEvent(bt->side, bt->ev_fork, 0));
-        rs = bt->side;
     }
-    for (auto &g : bt->groups) {
-        if (g.members.empty() || !g.ring.ncta()) continue;
-        const long spl = bt->spl_req > 0 ? bt->spl_req : (1L << 30);
-        long left = nsteps;
-        bool firstl = true;
-        while (left > 0) {
-            const int n = (int)std::min(left, spl);
-            RC(launch_group(bt, g, false, bt->st[firstl ? cur0 : cur1], bt->st[cur1], n, rs));
-            firstl = false;
-            left -= n;
+    for (int c = 0; c < lbh::kRingClasses; ++c) {
+        if (!used[c]) continue;
+        cudaStream_t rs = bt->stream;
+        if (fork) {
+            if (!bt->side[c]) {
+                CK(cudaStreamCreateWithFlags(&bt->side[c], cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&bt->ev_join[c], cudaEventDisableTiming));
+            }
+            CK(cudaStreamWaitEvent(bt->side[c], bt->ev_fork, 0));
+            rs = bt->side[c];
         }
+        for (auto &g : bt->groups) {
+            if (g.members.empty() || !g.ring[c].ncta()) continue;
+            const long spl = bt->spl_req > 0 ? bt->spl_req : (1L << 30);
+            long left = nsteps;
+            bool firstl = true;
+            while (left > 0) {
+                const int n = (int)std::min(left, spl);
+                RC(launch_group(bt, g, false, bt->st[firstl ? cur0 : cur1], bt->st[cur1], n, rs, c));
+                firstl = false;
+                left -= n;
+            }
+        }
+        if (fork) CK(cudaEventRecord(bt->ev_join[c], bt->side[c]));
     }
-    if (fork) CK(cudaEventRecord(bt->ev_join, bt->side));
     long left = nsteps;
     for (long c = 0; c < nchunks; ++c) {
         const int n = (int)std::min<long>(left, tb);
@@ -965,7 +1032,9 @@ int step_periodic(lbhpde_batch_s *bt, long nsteps) {
         bt->cur ^= 1;
         left -= n;
     }
-    if (fork) CK(cudaStreamWaitEvent(bt->stream, bt->ev_join, 0));
+    if (fork)
+        for (int c = 0; c < lbh::kRingClasses; ++c)
+            if (used[c]) CK(cudaStreamWaitEvent(bt->stream, bt->ev_join[c], 0));
     bt->cur = cur1;
     return LBHPDE_OK;
 }

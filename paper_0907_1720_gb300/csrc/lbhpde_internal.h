@@ -46,8 +46,16 @@ int default_tblk(int capacity, int W);
 // Compile-time degree variant the on-chip kernel uses for a set of members of maximum degree D.
 int onchip_dc(int b, int maxD);
 
-// Resident instances (N <= capacity): first fit, largest first, warp-aligned runs, <= 32 per CTA.
-int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Packed &out);
+// Resident instances (N <= capacity): first fit, largest first, warp-aligned runs, <= 32 per CTA,
+// in CTAs of `threads` threads (0: the configuration's resident CTA size).
+int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Packed &out, int threads = 0);
+// Resident size class of an instance of N nodes (0, 1, 2) and the CTA size of a class.
+constexpr int kRingClasses = 3;
+int ring_class(size_t esz, int b, int K, long long N);
+int ring_class_threads(size_t esz, int b, int K, int cls);
+// Resident members by the CTA size class they take: their own class, or the largest one where
+// they fill a gap left by larger instances.
+void split_ring_classes(size_t esz, int b, int K, const std::vector<Member> &m, std::vector<Member> (&out)[kRingClasses]);
 // Temporally blocked windows with halo H: one window per CTA.
 // wide: windows as large as a resident CTA (fewer, longer windows: the server, whose step
 // blocks fix the steps per window) instead of the smaller window CTAs.

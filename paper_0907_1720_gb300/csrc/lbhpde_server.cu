@@ -141,10 +141,11 @@ struct lbhpde_server_s {
     size_t esz = 4;
     int device = 0, max_active = 0, block = 256;
     cudaStream_t stream = nullptr;
-    // A step block's independent launch chains (per lattice and degree class: the resident launch,
-    // and the window launches, which follow each other) run on lanes of their own, after the
-    // table uploads on `stream`, and join it before the block's one synchronisation.
-    static constexpr int kLanes = 8;
+    // A step block's independent launch chains (per lattice and degree class: one resident launch
+    // per CTA size class, and the window launches, which follow each other) run on lanes of
+    // their own, after the table uploads on `stream`, and join it before the block's one
+    // synchronisation.
+    static constexpr int kLanes = 16;
     cudaStream_t lane[kLanes] = {};
     cudaEvent_t ev_up = nullptr, ev_done[kLanes] = {};
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // timing of one step block
@@ -264,7 +265,7 @@ int setup_admitted(lbhpde_server_s *S, std::vector<Req *> &adm) {
 struct Planned {
     int b, K, dc;
     bool halo;
-    int lane;    // stream lane: 2 * (lattice, degree class) + (windows ? 1 : 0)
+    int lane;    // stream lane: 4 * (lattice, degree class) + (windows ? 3 : resident size class)
     int nsteps;
     lbh::Packed p;
     size_t ioff = 0, foff = 0;  // offsets of its tables in the block's device arrays
@@ -304,9 +305,15 @@ int advance(lbhpde_server_s *S) {
                 n = std::max(n, st);
                 r->done += st;
             }
-            Planned pl{b, K, dc, false, 2 * cls, n, {}};
-            SRC(lbh::pack_ring(b, S->esz, K, dc, m, pl.p));
-            plan.push_back(std::move(pl));
+            // one launch per resident size class, each on a lane of its own
+            std::vector<lbh::Member> mc[lbh::kRingClasses];
+            lbh::split_ring_classes(S->esz, b, K, m, mc);
+            for (int c = 0; c < lbh::kRingClasses; ++c) {
+                if (mc[c].empty()) continue;
+                Planned pl{b, K, dc, false, 4 * cls + c, n, {}};
+                SRC(lbh::pack_ring(b, S->esz, K, dc, mc[c], pl.p, lbh::ring_class_threads(S->esz, b, K, c)));
+                plan.push_back(std::move(pl));
+            }
         }
         if (!halo.empty()) {
             std::vector<long> left(halo.size());
@@ -325,7 +332,7 @@ int advance(lbhpde_server_s *S) {
                     left[q] -= st;
                 }
                 if (m.empty()) break;
-                Planned pl{b, K, dc, true, 2 * cls + 1, n, {}};
+                Planned pl{b, K, dc, true, 4 * cls + 3, n, {}};
                 SRC(lbh::pack_halo(b, S->esz, K, dc, tblk * W, m, pl.p, true));
                 plan.push_back(std::move(pl));
             }

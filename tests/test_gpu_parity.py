@@ -150,6 +150,20 @@ def test_onchip_step_chunks_are_seamless(L):
     assert np.array_equal(a, b)
 
 
+def test_resident_launch_longer_than_a_window_allows(L):
+    """Resident-only batches accept a steps-per-launch whose halo would not fit a window (it
+    only chunks the resident launches); a batch that needs windows refuses it."""
+    p = problem(W.kdv_burgers(2.0, 0.05, 0.9), 1800, 0.1, 1e-4, 1.3, 300, seed=8)
+    for P, K in ((L.FP32_DEV, 8), (L.FP64, 4)):
+        got = run_gpu(L, p, P, L.KERNEL_ONCHIP, K, 1000)
+        assert normwise(got, oracle.run_problem(p)) <= (FP64_TOL if P == L.FP64 else FP32_TOL(300))
+    s = L.Solver.for_problem(p, precision=L.FP32_DEV)
+    with pytest.raises(L.LbhpdeError) as e:
+        s.set_kernel(L.KERNEL_HALO, 8, 1000)
+    assert e.value.code == L.ERR_UNSUPPORTED
+    s.close()
+
+
 def test_step_zero_and_incremental(L):
     p = problem(W.kdv(), 128, 0.1, 1e-4, 1.3, 40, seed=9)
     s = L.Solver.for_problem(p, precision=L.FP64)
