@@ -1,7 +1,8 @@
 """Build the CUDA library in-tree: paper_0907_1720_gb300/_build/liblbhpde.so (sm_103a only).
 
-Two translation units are compiled in parallel with nvcc and linked into one shared object
-that exports the C ABI of include/lbhpde.h.  The library depends on the CUDA runtime only.
+The translation units (the on-chip kernels of each precision in units of their own) compile
+in parallel with nvcc and link into one shared object that exports the C ABI of
+include/lbhpde.h.  The library depends on the CUDA runtime only.
 """
 from __future__ import annotations
 
@@ -17,8 +18,9 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "liblbhpde.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lbhpde_model.cpp", "lbhpde_api.cu", "lbhpde_bounded.cu", "lbhpde_noalloc.cu", "lbhpde_server.cu"]
-HEADERS = ["lbhpde_kernels.cuh", "lbhpde_bounded.cuh", "lbhpde_internal.h"]
+SOURCES = ["lbhpde_model.cpp", "lbhpde_api.cu", "lbhpde_onchip_f32.cu", "lbhpde_onchip_f64.cu", "lbhpde_bounded.cu",
+           "lbhpde_noalloc.cu", "lbhpde_server.cu"]
+HEADERS = ["lbhpde_kernels.cuh", "lbhpde_bounded.cuh", "lbhpde_internal.h", "lbhpde_onchip_launch.cuh"]
 
 
 def _nvcc():

@@ -260,9 +260,9 @@ void split_ring_classes(size_t esz, int b, int K, const std::vector<Member> &m, 
     }
 }
 
-int default_tblk(int capacity, int W) {
+int default_tblk(int capacity, int W, int valid_eighths) {
     int t = 64;
-    while (t > 1 && capacity - 2 * t * W < capacity * 3 / 4) t /= 2;
+    while (t > 1 && capacity - 2 * t * W < capacity * valid_eighths / 8) t /= 2;
     return t;
 }
 
@@ -324,6 +324,9 @@ int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Pa
             I.vlo = 0;
             I.vhi = s.N;
             I.steps = m[i].steps;
+            I.A = s.A;
+            I.Dg = s.Dg;
+            I.nu = s.nu;
             out.insts.push_back(I);
             sco += lbk::cblock(b, dc > 0 ? dc : s.D);
             tb += pad(s.N);
@@ -367,6 +370,9 @@ int pack_halo(int b, size_t esz, int K, int dc, int H, const std::vector<Member>
             I.vlo = H;
             I.vhi = H + v;
             I.steps = mb.steps;
+            I.A = s.A;
+            I.Dg = s.Dg;
+            I.nu = s.nu;
             out.first.push_back((int)out.insts.size());
             out.insts.push_back(I);
             coef_max = std::max(coef_max, (size_t)lbk::cblock(b, dc > 0 ? dc : s.D));
@@ -390,77 +396,13 @@ namespace {
         }                                 \
     } while (0)
 
-struct OnchipArgs {
-    const Packed *p;
-    const OnchipInst *insts;
-    const int *first;
-    const void *in;
-    void *out;
-    const void *coefT;
-    int nsteps;
-    cudaStream_t st;
-};
-
-template <typename T, int B, int K, int MAXT, bool HALO, int DC>
-int launch_onchip_t(const OnchipArgs &a) {
-    auto fn = lbk::k_onchip<T, B, K, MAXT, HALO, DC>;
-    LBH_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)a.p->smem));
-    fn<<<a.p->ncta(), a.p->nthreads, a.p->smem, a.st>>>((const T *)a.in, (T *)a.out, a.insts, a.first,
-                                                         (const T *)a.coefT, a.nsteps, a.p->max_inst);
-    LBH_CK(cudaGetLastError());
-    return LBHPDE_OK;
-}
-
-// compile-time polynomial degree: D = 5 on D1Q5 and D = 7 on D1Q7 (the KdV/KS/KdV-Burgers and
-// Kawahara families), run-time degree otherwise
-template <typename T, int B, int K, int MAXT, bool HALO>
-int launch_onchip_d(int dc, const OnchipArgs &a) {
-    constexpr int DC = B == 5 ? 5 : 7;
-    if (dc == DC) return launch_onchip_t<T, B, K, MAXT, HALO, DC>(a);
-    return launch_onchip_t<T, B, K, MAXT, HALO, 0>(a);
-}
-
-template <typename T, int B, bool HALO>
-int launch_onchip_b(int K, int dc, const OnchipArgs &a) {
-    if constexpr (sizeof(T) == 4) {
-        if constexpr (B == 5) {
-            if (K == 8) {  // CTAs of 128, 256 (resident only) or 512 threads: the plan's size class
-                if (a.p->nthreads <= 128) return launch_onchip_d<T, B, 8, 128, HALO>(dc, a);
-                if constexpr (!HALO) {
-                    if (a.p->nthreads <= 256) return launch_onchip_d<T, B, 8, 256, HALO>(dc, a);
-                }
-                return launch_onchip_d<T, B, 8, 512, HALO>(dc, a);
-            }
-            if (K == 4) return launch_onchip_d<T, B, 4, 1024, HALO>(dc, a);
-            if (K == 2) return launch_onchip_d<T, B, 2, 1024, HALO>(dc, a);
-        } else {
-            if (K == 8) return launch_onchip_d<T, B, 8, 256, HALO>(dc, a);
-            if (K == 4) return launch_onchip_d<T, B, 4, 512, HALO>(dc, a);
-        }
-    } else {
-        if constexpr (B == 5) {
-            if (K == 4) return launch_onchip_d<T, B, 4, 512, HALO>(dc, a);
-            if (K == 2) return launch_onchip_d<T, B, 2, 1024, HALO>(dc, a);
-        } else {
-            if (K == 4) return launch_onchip_d<T, B, 4, 256, HALO>(dc, a);
-        }
-    }
-    return LBHPDE_ERR_UNSUPPORTED;
-}
-
 }  // namespace
 
 int launch_onchip(int b, size_t esz, int K, int dc, bool halo, const Packed &p, const OnchipInst *insts_d,
                   const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st) {
     if (p.ncta() == 0 || nsteps <= 0) return LBHPDE_OK;
-    const OnchipArgs a{&p, insts_d, first_d, in, out, coefT, nsteps, st};
-    if (esz == 4) {
-        if (b == 5)
-            return halo ? launch_onchip_b<float, 5, true>(K, dc, a) : launch_onchip_b<float, 5, false>(K, dc, a);
-        return halo ? launch_onchip_b<float, 7, true>(K, dc, a) : launch_onchip_b<float, 7, false>(K, dc, a);
-    }
-    if (b == 5) return halo ? launch_onchip_b<double, 5, true>(K, dc, a) : launch_onchip_b<double, 5, false>(K, dc, a);
-    return halo ? launch_onchip_b<double, 7, true>(K, dc, a) : launch_onchip_b<double, 7, false>(K, dc, a);
+    return esz == 4 ? launch_onchip_f32(b, K, dc, halo, p, insts_d, first_d, in, out, coefT, nsteps, st)
+                    : launch_onchip_f64(b, K, dc, halo, p, insts_d, first_d, in, out, coefT, nsteps, st);
 }
 
 int launch_init(int b, size_t esz, void *st, const Seg *segs, const int2 *blocks, int nb, const double *coefd,
@@ -682,7 +624,7 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
     if (maxt == 0 || K < lbk::wmax(g.b)) return LBHPDE_ERR_UNSUPPORTED;
     const int W = lbk::wmax(g.b);
     const int cap = maxt * K, cap_h = lbh::onchip_maxt_halo(bt->esz, g.b, K) * K;
-    g.dc = lbh::onchip_dc(g.b, g.maxD);
+    g.dc = g.has_nu ? -1 : lbh::onchip_dc(g.b, g.maxD);  // real exponents: their own variant
     if (tblk <= 0) tblk = lbh::default_tblk(cap_h, W);
     const int H = tblk * W;
     std::vector<lbh::Member> resident, ring[lbh::kRingClasses], halo;
@@ -905,14 +847,15 @@ int choose_kernels(lbhpde_batch_s *bt) {
     for (auto &g : bt->groups) {
         if (g.members.empty()) continue;
         g.onchip_ok = false;
-        if (bt->kernel == LBHPDE_KERNEL_STREAM || g.has_nu) continue;
+        if (bt->kernel == LBHPDE_KERNEL_STREAM) continue;
         int K = bt->K_req > 0 ? bt->K_req : lbh::default_K(bt->esz, g.b);
         int tblk = bt->spl_req;
         int tk = 0, tt = 0;
-        if (tuned_choice(bt->esz, g.b, lbh::onchip_dc(g.b, g.maxD), &tk, &tt)) {
+        if (tuned_choice(bt->esz, g.b, g.has_nu ? -1 : lbh::onchip_dc(g.b, g.maxD), &tk, &tt)) {
             if (bt->K_req == 0) K = tk;
             if (bt->spl_req == 0) tblk = tt;
         }
+        if (g.has_nu && K < 4) continue;  // the real-exponent on-chip variants hold 4 or more nodes a thread
         int rc = plan_onchip(bt, g, K, tblk, bt->kernel == LBHPDE_KERNEL_HALO);
         if (rc != LBHPDE_OK) return rc;
     }

@@ -40,9 +40,11 @@ constexpr int kHaloThreadsF32Q5 = 128;
 int onchip_maxt(size_t esz, int b, int K);
 int onchip_maxt_halo(size_t esz, int b, int K);
 int default_K(size_t esz, int b);
-// Steps per halo window such that the halo (steps * max|e| on each side) leaves at least three
-// quarters of a window of `capacity` nodes valid.
-int default_tblk(int capacity, int W);
+// Steps per halo window (a power of two up to 64) such that the halo (steps * max|e| on each
+// side) leaves at least valid_eighths / 8 of a window of `capacity` nodes valid.  Batches take
+// 7/8 (the autotuner's picks on GB300: 32 for FP32 windows, 16 for FP64 D1Q7); the server takes
+// 6/8, since each window chunk of a step block is another launch.
+int default_tblk(int capacity, int W, int valid_eighths = 7);
 // Compile-time degree variant the on-chip kernel uses for a set of members of maximum degree D.
 int onchip_dc(int b, int maxD);
 
@@ -64,6 +66,11 @@ int pack_halo(int b, size_t esz, int K, int dc, int H, const std::vector<Member>
 
 int launch_onchip(int b, size_t esz, int K, int dc, bool halo, const Packed &p, const lbk::OnchipInst *insts_d,
                   const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st);
+// the same for one precision (lbhpde_onchip_f32.cu, lbhpde_onchip_f64.cu)
+int launch_onchip_f32(int b, int K, int dc, bool halo, const Packed &p, const lbk::OnchipInst *insts_d,
+                      const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st);
+int launch_onchip_f64(int b, int K, int dc, bool halo, const Packed &p, const lbk::OnchipInst *insts_d,
+                      const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st);
 int launch_init(int b, size_t esz, void *st, const lbk::Seg *segs, const int2 *blocks, int nb, const double *coefd,
                 const double *phi0, const long long *blk_off, cudaStream_t stream);
 

@@ -110,65 +110,65 @@ __device__ __forceinline__ T gen_eval(const T *c, int A, int Dg, T phi, T w) {
     return acc;
 }
 
-// gen_eval for the four nodes of a k_stream group at once: each coefficient is loaded once and
-// feeds four independent accumulators.  DG: the row degree at compile time (the rows unroll);
-// DG < 0: run time.
-template <typename T, int DG>
-__device__ __forceinline__ void gen_eval4(const T *c, int A, int Dg, const T (&phi)[4], const T (&w)[4],
-                                          T (&out)[4]) {
+// gen_eval for NN nodes at once (a k_stream group of four, an on-chip thread's K): each
+// coefficient is loaded once and feeds NN independent accumulators.  DG: the row degree at
+// compile time (the rows unroll); DG < 0: run time.
+template <typename T, int DG, int NN>
+__device__ __forceinline__ void gen_evalN(const T *c, int A, int Dg, const T (&phi)[NN], const T (&w)[NN],
+                                          T (&out)[NN]) {
     const int dg = DG >= 0 ? DG : Dg;
     for (int a = A; a >= 0; --a) {
         const T *r = c + a * (dg + 1);
-        T h[4];
+        T h[NN];
         if constexpr (DG >= 0) {
             T cr[DG + 1];
 #pragma unroll
             for (int p = 0; p <= DG; ++p) cr[p] = r[p];
 #pragma unroll
-            for (int n = 0; n < 4; ++n) h[n] = cr[DG];
+            for (int n = 0; n < NN; ++n) h[n] = cr[DG];
 #pragma unroll
             for (int p = DG - 1; p >= 0; --p)
 #pragma unroll
-                for (int n = 0; n < 4; ++n) h[n] = fma_t(h[n], phi[n], cr[p]);
+                for (int n = 0; n < NN; ++n) h[n] = fma_t(h[n], phi[n], cr[p]);
         } else {
             const T cD = r[dg];
 #pragma unroll
-            for (int n = 0; n < 4; ++n) h[n] = cD;
+            for (int n = 0; n < NN; ++n) h[n] = cD;
             for (int p = dg - 1; p >= 0; --p) {
                 const T cp = r[p];
 #pragma unroll
-                for (int n = 0; n < 4; ++n) h[n] = fma_t(h[n], phi[n], cp);
+                for (int n = 0; n < NN; ++n) h[n] = fma_t(h[n], phi[n], cp);
             }
         }
 #pragma unroll
-        for (int n = 0; n < 4; ++n) out[n] = a == A ? h[n] : fma_t(out[n], w[n], h[n]);
+        for (int n = 0; n < NN; ++n) out[n] = a == A ? h[n] : fma_t(out[n], w[n], h[n]);
     }
 }
 
-// gen_eval4 with the row degree dispatched to a compile-time variant (0..7 in FP32, 0..3 in FP64,
+// gen_evalN with the row degree dispatched to a compile-time variant (0..7 in FP32, 0..3 in FP64,
 // where more would spill), else run time.
-template <typename T>
-__device__ __forceinline__ void gen_eval4_any(const T *c, int A, int Dg, const T (&phi)[4], const T (&w)[4],
-                                              T (&out)[4]) {
+template <typename T, int NN = 4>
+__device__ __forceinline__ void gen_eval4_any(const T *c, int A, int Dg, const T (&phi)[NN], const T (&w)[NN],
+                                              T (&out)[NN]) {
     if constexpr (sizeof(T) == 8) {
         switch (Dg) {
-        case 0: gen_eval4<T, 0>(c, A, Dg, phi, w, out); break;
-        case 1: gen_eval4<T, 1>(c, A, Dg, phi, w, out); break;
-        case 2: gen_eval4<T, 2>(c, A, Dg, phi, w, out); break;
-        case 3: gen_eval4<T, 3>(c, A, Dg, phi, w, out); break;
-        default: gen_eval4<T, -1>(c, A, Dg, phi, w, out); break;
+        case 0: gen_evalN<T, 0, NN>(c, A, Dg, phi, w, out); break;
+        case 1: gen_evalN<T, 1, NN>(c, A, Dg, phi, w, out); break;
+        case 2: gen_evalN<T, 2, NN>(c, A, Dg, phi, w, out); break;
+        case 3: gen_evalN<T, 3, NN>(c, A, Dg, phi, w, out); break;
+        default: gen_evalN<T, -1, NN>(c, A, Dg, phi, w, out); break;
         }
     } else {
         switch (Dg) {
-        case 0: gen_eval4<T, 0>(c, A, Dg, phi, w, out); break;
-        case 1: gen_eval4<T, 1>(c, A, Dg, phi, w, out); break;
-        case 2: gen_eval4<T, 2>(c, A, Dg, phi, w, out); break;
-        case 3: gen_eval4<T, 3>(c, A, Dg, phi, w, out); break;
-        case 4: gen_eval4<T, 4>(c, A, Dg, phi, w, out); break;
-        case 5: gen_eval4<T, 5>(c, A, Dg, phi, w, out); break;
-        case 6: gen_eval4<T, 6>(c, A, Dg, phi, w, out); break;
-        case 7: gen_eval4<T, 7>(c, A, Dg, phi, w, out); break;
-        default: gen_eval4<T, -1>(c, A, Dg, phi, w, out); break;
+        case 0: gen_evalN<T, 0, NN>(c, A, Dg, phi, w, out); break;
+        case 1: gen_evalN<T, 1, NN>(c, A, Dg, phi, w, out); break;
+        case 2: gen_evalN<T, 2, NN>(c, A, Dg, phi, w, out); break;
+        case 3: gen_evalN<T, 3, NN>(c, A, Dg, phi, w, out); break;
+        case 4: gen_evalN<T, 4, NN>(c, A, Dg, phi, w, out); break;
+        case 5: gen_evalN<T, 5, NN>(c, A, Dg, phi, w, out); break;
+        case 6: gen_evalN<T, 6, NN>(c, A, Dg, phi, w, out); break;
+        case 7: gen_evalN<T, 7, NN>(c, A, Dg, phi, w, out); break;
+        default: gen_evalN<T, -1, NN>(c, A, Dg, phi, w, out); break;
         }
     }
 }
@@ -458,7 +458,15 @@ struct OnchipInst {
     int vlo, vhi;       // positions written back: [vlo, vhi)
     int steps;          // steps this instance takes in the launch (<= nsteps; the state is
                         // frozen after them while the CTA's barriers continue)
+    int A, Dg;          // real-exponent models (run-time degree variant only): P_j =
+    double nu;          //   sum_{a<=A} (phi^nu)^a sum_{i<=Dg} c[a(Dg+1)+i] phi^i; A = 0: polynomial
 };
+
+// gen_eval for the K nodes of a thread, every coefficient loaded once for all K
+template <typename T, int K>
+__device__ __forceinline__ void gen_evalK(const T *c, int A, int Dg, const T (&phi)[K], const T (&w)[K], T (&out)[K]) {
+    gen_eval4_any<T, K>(c, A, Dg, phi, w, out);
+}
 
 // threads per SM at each configuration's register budget (FP32 D1Q5 with K = 8: 128 registers);
 // a CTA smaller than that asks for the registers of budget / MAXT CTAs per SM
@@ -469,6 +477,8 @@ __host__ __device__ constexpr int onchip_minb(int esz, int B, int K, int MAXT) {
     return onchip_budget(esz, B, K) / MAXT > 1 ? onchip_budget(esz, B, K) / MAXT : 1;
 }
 
+// DC: the f^eq degree at compile time; 0: run time; -1: run time with real-exponent terms
+// (P_j evaluated in phi and w = phi^nu for the instances with A > 0).
 template <typename T, int B, int K, int MAXT, bool HALO, int DC>
 __global__ void __launch_bounds__(MAXT, onchip_minb(sizeof(T), B, K, MAXT))
     k_onchip(const T *__restrict__ st_in, T *__restrict__ st_out, const OnchipInst *__restrict__ insts,
@@ -658,6 +668,14 @@ __global__ void __launch_bounds__(MAXT, onchip_minb(sizeof(T), B, K, MAXT))
 #pragma unroll
             for (int k = 0; k < K; ++k) phi[k] += d[k];
             // relax: s'_j = (1 - omega) f_j + P_j(phi'), Horner with coefficients from shared memory
+            // (real exponents: w = phi^nu once per node, then the rows in phi and w)
+            T w[K];
+            if constexpr (DC < 0) {
+                if (I.A > 0) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) w[k] = nu_pow<T>(phi[k], I.nu);
+                }
+            }
 #pragma unroll
             for (int j = 1; j < B; ++j) {
                 const T *c = sc + (j - 1) * cs;
@@ -672,13 +690,23 @@ __global__ void __launch_bounds__(MAXT, onchip_minb(sizeof(T), B, K, MAXT))
 #pragma unroll
                         for (int k = 0; k < K; ++k) acc[k] = fma_t(acc[k], phi[k], cr[p]);
                 } else {
-                    const T cD = c[D];
+                    auto horner = [&] {
+                        const T cD = c[D];
 #pragma unroll
-                    for (int k = 0; k < K; ++k) acc[k] = cD;
-                    for (int p = D - 1; p >= 0; --p) {
-                        const T cp = c[p];
+                        for (int k = 0; k < K; ++k) acc[k] = cD;
+                        for (int p = D - 1; p >= 0; --p) {
+                            const T cp = c[p];
 #pragma unroll
-                        for (int k = 0; k < K; ++k) acc[k] = fma_t(acc[k], phi[k], cp);
+                            for (int k = 0; k < K; ++k) acc[k] = fma_t(acc[k], phi[k], cp);
+                        }
+                    };
+                    if constexpr (DC < 0) {
+                        if (I.A > 0)
+                            gen_evalK<T, K>(c, I.A, I.Dg, phi, w, acc);
+                        else
+                            horner();
+                    } else {
+                        horner();
                     }
                 }
 #pragma unroll

@@ -286,7 +286,7 @@ int advance(lbhpde_server_s *S) {
         const int K = lbh::default_K(S->esz, b);
         const int maxt = lbh::onchip_maxt(S->esz, b, K);
         const int cap = maxt * K, W = (b - 1) / 2;
-        const int tblk = lbh::default_tblk(cap, W);  // windows as wide as a resident CTA
+        const int tblk = lbh::default_tblk(cap, W, 6);  // windows as wide as a resident CTA
         std::vector<Req *> ring, halo;
         int maxD = 0;
         for (Req *r : S->active)

@@ -1,6 +1,6 @@
 """Real-exponent flux functions on the GPU (class (1) of Sec. III C with u^n u_x, real n)
-against the oracle, through the C ABI.  Such models take the streaming kernel's run-time
-degree path (w = phi^nu once per node, then a Horner evaluation in phi and w).
+against the oracle, through the C ABI.  Such models take the run-time degree paths of the
+streaming and on-chip kernels (w = phi^nu once per node, then a Horner evaluation in phi and w).
 
 FP64 tolerance 1e-12 normwise on problems whose rounding growth the oracle measures below 2
 (a 1e-13 perturbation of phi0). Where n < 1, phi stays away from 0: phi^n has an infinite
@@ -59,16 +59,38 @@ def problems():
     }
 
 
+KERNELS = {"auto": 0, "stream": 1, "onchip": 2, "halo": 3, "onchip_k2": 2}
+
+
 @pytest.mark.parametrize("name", list(problems()))
-@pytest.mark.parametrize("kernel", ["auto", "stream"])
+@pytest.mark.parametrize("kernel", list(KERNELS))
 def test_fp64_matches_oracle(L, name, kernel):
+    """Every kernel: the streaming step, the resident and windowed on-chip variants with the
+    real-exponent evaluation, and 2 nodes a thread (which real exponents take by streaming)."""
     p = problems()[name]
     want = oracle_periodic(p)
     s = L.Solver.for_problem(p, precision=L.FP64)
-    s.set_kernel(L.KERNEL_STREAM if kernel == "stream" else L.KERNEL_AUTO)
+    K = 2 if kernel == "onchip_k2" else 0
+    if kernel == "onchip_k2" and p.eq.lattice == 7:
+        pytest.skip("D1Q7 needs at least 3 nodes a thread")
+    s.set_kernel(KERNELS[kernel], K)
     got = s.set_phi(p.phi0).step(p.nsteps).read_phi()
     s.close()
     assert normwise(got, want) <= FP64_TOL
+
+
+@pytest.mark.parametrize("kernel", ["onchip", "halo"])
+def test_fp32_onchip_matches_fp64(L, kernel):
+    """FP32 on the on-chip variants stays within the FP32 bound of the parity tests (64 eps32
+    sqrt(steps) + 1e-6, a random walk of per-step roundings) of the FP64 oracle: gKdV soliton,
+    2000 steps, with phi^nu by the FP32 intrinsic."""
+    p = problems()["gkdv_1.5_soliton"]
+    want = oracle_periodic(p)
+    s = L.Solver.for_problem(p, precision=L.FP32_DEV)
+    s.set_kernel(KERNELS[kernel])
+    got = s.set_phi(p.phi0).step(p.nsteps).read_phi()
+    s.close()
+    assert normwise(got, want) <= 64 * np.finfo(np.float32).eps * np.sqrt(p.nsteps) + 1e-6
 
 
 def test_batch_with_real_exponent_and_polynomial_members(L):
