@@ -856,6 +856,9 @@ int choose_kernels(lbhpde_batch_s *bt) {
             if (bt->spl_req == 0) tblk = tt;
         }
         if (g.has_nu && K < 4) continue;  // the real-exponent on-chip variants hold 4 or more nodes a thread
+        // FP64 real exponents: the FP64 pow binds both kernels, and streaming was faster on GB300
+        // (3.88e9 node-updates/s against 3.62e9 in windows on a 2^24-node gKdV grid)
+        if (g.has_nu && bt->esz == 8 && bt->kernel == LBHPDE_KERNEL_AUTO) continue;
         int rc = plan_onchip(bt, g, K, tblk, bt->kernel == LBHPDE_KERNEL_HALO);
         if (rc != LBHPDE_OK) return rc;
     }

@@ -117,9 +117,8 @@ template <typename T, int DG, int NN>
 __device__ __forceinline__ void gen_evalN(const T *c, int A, int Dg, const T (&phi)[NN], const T (&w)[NN],
                                           T (&out)[NN]) {
     const int dg = DG >= 0 ? DG : Dg;
-    for (int a = A; a >= 0; --a) {
+    auto row = [&](int a, T (&h)[NN]) {  // Q_a(phi) for every node
         const T *r = c + a * (dg + 1);
-        T h[NN];
         if constexpr (DG >= 0) {
             T cr[DG + 1];
 #pragma unroll
@@ -140,8 +139,14 @@ __device__ __forceinline__ void gen_evalN(const T *c, int A, int Dg, const T (&p
                 for (int n = 0; n < NN; ++n) h[n] = fma_t(h[n], phi[n], cp);
             }
         }
+    };
+    row(A, out);  // the top row starts the Horner recursion in w
+#pragma unroll 2
+    for (int a = A - 1; a >= 0; --a) {
+        T h[NN];
+        row(a, h);
 #pragma unroll
-        for (int n = 0; n < NN; ++n) out[n] = a == A ? h[n] : fma_t(out[n], w[n], h[n]);
+        for (int n = 0; n < NN; ++n) out[n] = fma_t(out[n], w[n], h[n]);
     }
 }
 
