@@ -141,6 +141,39 @@ def bounded_problems(members):
     return probs
 
 
+def workload_problems(args, rank=0):
+    """(problems, steps per benchmark step, description) of the workload; both arms name the
+    workload by this description."""
+    if args.workload == "ensemble":
+        probs = ensemble_problems(rank, args.members)
+        nsteps = W.ENSEMBLE_STEPS
+        desc = (f"kdv_burgers_ensemble_{args.members}: {args.members} x N~U{{256..8192}} "
+                f"(sum N = {sum(p.N for p in probs)}), "
+                f"D1Q5 scheme 1, dx={W.ENSEMBLE_DX}, dt={W.ENSEMBLE_DT}, tau={W.ENSEMBLE_TAU}, "
+                f"{nsteps} steps per benchmark step")
+    elif args.workload == "bounded":
+        probs = bounded_problems(args.sweep_members)
+        nsteps = BOUNDED_STEPS
+        desc = (f"ks_shock_tau_sweep_{args.sweep_members}: {args.sweep_members} x N=601 (Example 4.1 on "
+                f"[-30, 30], bounded grid, non-equilibrium extrapolation depth 2), D1Q5 scheme 1 without "
+                f"A_40, dx=0.1, dt=1e-3, tau in [{BOUNDED_TAU[0]}, {BOUNDED_TAU[1]}], {nsteps} steps per "
+                f"benchmark step, one resident CTA per instance")
+    elif args.workload == "nu_grid":
+        p = W.gkdv_grid_config(N=args.nodes, nsteps=1000)
+        probs, nsteps = [p], p.nsteps
+        desc = (f"gkdv_real_exponent_grid: N={args.nodes}, u_t + u^1.5 u_x + u_xxx = 0, D1Q5 scheme 1, "
+                f"dx=0.1, dt=1e-4, tau=1.3, {nsteps} steps per benchmark step ("
+                f"{'streaming kernel' if args.kernel == 'stream' else 'temporally blocked windows'}, "
+                f"phi^nu once per node)")
+    else:
+        p = W.long_grid_config(N=args.nodes, nsteps=1000)
+        probs, nsteps = [p], p.nsteps
+        desc = (f"kawahara_long_grid: N={args.nodes}, D1Q7 scheme 1, dx=0.1, dt=1e-4, tau=2.02, "
+                f"{nsteps} steps per benchmark step "
+                f"({'streaming kernel' if args.kernel == 'stream' else 'temporally blocked windows'})")
+    return probs, nsteps, desc
+
+
 def flops_per_node_update(b, D):
     """Algorithmic FP operations of one node-update in the kernels' formulation: per moving
     population one Horner polynomial of degree D plus the relaxation (D + 1 multiply-adds,
@@ -213,47 +246,11 @@ def run_ours(args, rank, world):
             b0, d0 = (5, 5) if args.workload == "ensemble" else (7, 7)
             K_t, T_t, r_t = L.autotune(prec0, b0, d0)
             tuned = {"nodes_per_thread": K_t, "steps_per_window": T_t, "tuning_rate": r_t}
-        if args.workload == "ensemble":
-            probs = ensemble_problems(rank, args.members)
-            nsteps = W.ENSEMBLE_STEPS
-            prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
-            solver = L.Batch(probs, precision=prec)
-            workload = (f"kdv_burgers_ensemble_{args.members}: {args.members} x N~U{{256..8192}} "
-                        f"(sum N = {sum(p.N for p in probs)}), "
-                        f"D1Q5 scheme 1, dx={W.ENSEMBLE_DX}, dt={W.ENSEMBLE_DT}, tau={W.ENSEMBLE_TAU}, "
-                        f"{nsteps} steps per benchmark step")
-        elif args.workload == "bounded":
-            probs = bounded_problems(args.sweep_members)
-            nsteps = BOUNDED_STEPS
-            prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
-            solver = L.Batch(probs, precision=prec)
-            workload = (f"ks_shock_tau_sweep_{args.sweep_members}: {args.sweep_members} x N=601 (Example 4.1 on "
-                        f"[-30, 30], bounded grid, non-equilibrium extrapolation depth 2), D1Q5 scheme 1 without "
-                        f"A_40, dx=0.1, dt=1e-3, tau in [{BOUNDED_TAU[0]}, {BOUNDED_TAU[1]}], {nsteps} steps per "
-                        f"benchmark step, one resident CTA per instance")
-        elif args.workload == "nu_grid":
-            p = W.gkdv_grid_config(N=args.nodes, nsteps=1000)
-            probs = [p]
-            nsteps = p.nsteps
-            prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
-            solver = L.Batch(probs, precision=prec)
-            if args.kernel == "stream":
-                solver.set_kernel(L.KERNEL_STREAM)
-            workload = (f"gkdv_real_exponent_grid: N={args.nodes}, u_t + u^1.5 u_x + u_xxx = 0, D1Q5 scheme 1, "
-                        f"dx=0.1, dt=1e-4, tau=1.3, {nsteps} steps per benchmark step ("
-                        f"{'streaming kernel' if args.kernel == 'stream' else 'temporally blocked windows'}, "
-                        f"phi^nu once per node)")
-        else:
-            p = W.long_grid_config(N=args.nodes, nsteps=1000)
-            probs = [p]
-            nsteps = p.nsteps
-            prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
-            solver = L.Batch(probs, precision=prec)
-            if args.kernel == "stream":
-                solver.set_kernel(L.KERNEL_STREAM)
-            workload = (f"kawahara_long_grid: N={args.nodes}, D1Q7 scheme 1, dx=0.1, dt=1e-4, tau=2.02, "
-                        f"{nsteps} steps per benchmark step "
-                        f"({'streaming kernel' if args.kernel == 'stream' else 'temporally blocked windows'})")
+        probs, nsteps, workload = workload_problems(args, rank)
+        prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
+        solver = L.Batch(probs, precision=prec)
+        if args.kernel == "stream" and args.workload in ("nu_grid", "long_grid"):
+            solver.set_kernel(L.KERNEL_STREAM)
         total = sum(p.N for p in probs)
         b = 5 if args.workload in ("ensemble", "bounded", "nu_grid") else 7
         bounded = args.workload == "bounded"
@@ -402,6 +399,12 @@ def run_ours(args, rank, world):
     return line
 
 
+def serving_description(args):
+    return (f"serving: Poisson arrivals (mean {args.rate:g} req/s) of mixed KdV / mKdV / K(2,2) / KS / Kawahara "
+            f"requests, N log-uniform [128, 65536], steps uniform [1e3, 1e5], FP32 deviation storage, "
+            f"memory-admitted")
+
+
 def run_serving(args):
     """Continuous batching: Poisson arrivals of mixed requests submitted from a host thread
     while the server runs; latency = finish - submit on the server's clock."""
@@ -460,9 +463,7 @@ def run_serving(args):
             "steps": 1, "warmup": 0, "ms_per_step": head["makespan_s"] * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic (seeded Poisson request stream)",
-            "config": {"workload": f"serving: Poisson arrivals (mean {args.rate:g} req/s) of mixed KdV / mKdV / "
-                                   f"K(2,2) / KS / Kawahara requests, N log-uniform [128, 65536], steps uniform "
-                                   f"[1e3, 1e5], FP32 deviation storage, memory-admitted",
+            "config": {"workload": serving_description(args),
                        "window_requests": head["requests"], "steps_per_block": args.block},
             "p50_latency_s": head["p50_latency_s"], "p99_latency_s": head["p99_latency_s"],
             "clocks": head["clocks"], "sweep": out}
@@ -644,6 +645,21 @@ def cpu_oracle_rate(args, sample_s=15.0):
         el = time.perf_counter() - t0
         upd = sum(p.N for p in probs) * steps
         sample = f"{len(probs)} tau-sweep members x {steps} steps, one member per thread"
+    elif args.workload == "serving":
+        # the first requests of the same seeded stream, one per thread, each advanced by the
+        # same number of steps (a bounded sample of their work)
+        count = min(args.requests, max(64, int(args.window * args.rate)))
+        probs = [q for _, q in W.serving_requests(count, rate=args.rate, seed=W.SEED + int(args.rate))][: 2 * cores]
+        t0 = time.perf_counter()
+        oracle.run_problem(probs[0], nsteps=5)
+        dt1 = max((time.perf_counter() - t0) / 5 / max(probs[0].N, 1), 1e-12)  # seconds per node-update
+        steps = int(max(5, min(1000, sample_s * cores / (dt1 * sum(p.N for p in probs)))))
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(cores) as ex:
+            list(ex.map(lambda p: oracle.run_problem(p, nsteps=steps), probs))
+        el = time.perf_counter() - t0
+        upd = sum(p.N for p in probs) * steps
+        sample = f"the first {len(probs)} requests of the stream x {steps} steps each, one request per thread"
     elif args.workload == "nu_grid":
         p = W.gkdv_grid_config(N=1 << 16, nsteps=1)
         M = oracle.Model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, nu=p.eq.nu, pi_nu=p.eq.pi_nu)
@@ -684,7 +700,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": float(np.mean([r["seconds"] for r in vals])) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "sample": vals[-1]["sample"]},
+            "config": {"workload": serving_description(args) if args.workload == "serving"
+                       else workload_problems(args)[2], "sample": vals[-1]["sample"]},
             "cpu_baseline": {"value": v, "unit": "node-updates/s", "cores": vals[-1]["cores"], "kind": "oracle",
                              "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": "node-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
