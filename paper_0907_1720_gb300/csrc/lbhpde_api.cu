@@ -63,7 +63,7 @@ struct Group {
     int K = 0, maxt = 0, tblk = 0;
     int dc = 0;  // compile-time degree of the on-chip kernel variant (0 = run time)
     bool uniform = false;  // every member has the same model (coefficients and omega)
-    bool has_nu = false;   // a member has real-exponent terms: streaming kernel, run-time degree
+    bool has_nu = false;   // a member has real-exponent terms: the real-exponent variants (on chip: degree code -1)
     // bounded groups (LBHPDE_NEE): resident members, one CTA each, and streaming members
     std::vector<lbk::BoundedInst> bnd_h;
     lbk::BoundedInst *bnd = nullptr;
