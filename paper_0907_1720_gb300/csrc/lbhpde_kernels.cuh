@@ -113,10 +113,11 @@ __device__ __forceinline__ T gen_eval(const T *c, int A, int Dg, T phi, T w) {
 // gen_eval for NN nodes at once (a k_stream group of four, an on-chip thread's K): each
 // coefficient is loaded once and feeds NN independent accumulators.  DG: the row degree at
 // compile time (the rows unroll); DG < 0: run time.
-template <typename T, int DG, int NN>
-__device__ __forceinline__ void gen_evalN(const T *c, int A, int Dg, const T (&phi)[NN], const T (&w)[NN],
+template <typename T, int DG, int NN, int AA = -1>
+__device__ __forceinline__ void gen_evalN(const T *c, int A_, int Dg, const T (&phi)[NN], const T (&w)[NN],
                                           T (&out)[NN]) {
     const int dg = DG >= 0 ? DG : Dg;
+    const int A = AA >= 0 ? AA : A_;  // AA >= 0: the row count at compile time (the rows unroll)
     auto row = [&](int a, T (&h)[NN]) {  // Q_a(phi) for every node
         const T *r = c + a * (dg + 1);
         if constexpr (DG >= 0) {
@@ -141,12 +142,47 @@ __device__ __forceinline__ void gen_evalN(const T *c, int A, int Dg, const T (&p
         }
     };
     row(A, out);  // the top row starts the Horner recursion in w
-#pragma unroll 2
-    for (int a = A - 1; a >= 0; --a) {
-        T h[NN];
-        row(a, h);
+    if constexpr (AA >= 0) {
 #pragma unroll
-        for (int n = 0; n < NN; ++n) out[n] = fma_t(out[n], w[n], h[n]);
+        for (int a = AA - 1; a >= 0; --a) {
+            T h[NN];
+            row(a, h);
+#pragma unroll
+            for (int n = 0; n < NN; ++n) out[n] = fma_t(out[n], w[n], h[n]);
+        }
+    } else {
+#pragma unroll 2
+        for (int a = A - 1; a >= 0; --a) {
+            T h[NN];
+            row(a, h);
+#pragma unroll
+            for (int n = 0; n < NN; ++n) out[n] = fma_t(out[n], w[n], h[n]);
+        }
+    }
+}
+
+// gen_evalN with both the row count (1..4 rows above the first) and the row degree (0..3) at
+// compile time: the on-chip FP32 real-exponent path, where the loads of a fully unrolled
+// evaluation can be scheduled ahead.  Other shapes take gen_eval4_any.
+template <typename T, int NN, int AA>
+__device__ __forceinline__ bool gen_eval_rows(const T *c, int Dg, const T (&phi)[NN], const T (&w)[NN], T (&out)[NN]) {
+    switch (Dg) {
+    case 0: gen_evalN<T, 0, NN, AA>(c, AA, 0, phi, w, out); return true;
+    case 1: gen_evalN<T, 1, NN, AA>(c, AA, 1, phi, w, out); return true;
+    case 2: gen_evalN<T, 2, NN, AA>(c, AA, 2, phi, w, out); return true;
+    case 3: gen_evalN<T, 3, NN, AA>(c, AA, 3, phi, w, out); return true;
+    default: return false;
+    }
+}
+template <typename T, int NN>
+__device__ __forceinline__ bool gen_eval_fixed(const T *c, int A, int Dg, const T (&phi)[NN], const T (&w)[NN],
+                                               T (&out)[NN]) {
+    switch (A) {
+    case 1: return gen_eval_rows<T, NN, 1>(c, Dg, phi, w, out);
+    case 2: return gen_eval_rows<T, NN, 2>(c, Dg, phi, w, out);
+    case 3: return gen_eval_rows<T, NN, 3>(c, Dg, phi, w, out);
+    case 4: return gen_eval_rows<T, NN, 4>(c, Dg, phi, w, out);
+    default: return false;
     }
 }
 
@@ -467,9 +503,13 @@ struct OnchipInst {
     double nu;          //   sum_{a<=A} (phi^nu)^a sum_{i<=Dg} c[a(Dg+1)+i] phi^i; A = 0: polynomial
 };
 
-// gen_eval for the K nodes of a thread, every coefficient loaded once for all K
+// gen_eval for the K nodes of a thread, every coefficient loaded once for all K (FP32: the common
+// shapes with the row count and degree at compile time)
 template <typename T, int K>
 __device__ __forceinline__ void gen_evalK(const T *c, int A, int Dg, const T (&phi)[K], const T (&w)[K], T (&out)[K]) {
+    if constexpr (sizeof(T) == 4) {
+        if (gen_eval_fixed<T, K>(c, A, Dg, phi, w, out)) return;
+    }
     gen_eval4_any<T, K>(c, A, Dg, phi, w, out);
 }
 
