@@ -286,6 +286,7 @@ def run_ours(args, rank, world):
         if world > 1:
             torch.distributed.barrier()
         kernel_ms = []
+        launches0 = solver.kernel_launches()
         with ClockSampler(dev) as clk:
             torch.cuda.synchronize()
             ev[2].record(stream)
@@ -296,6 +297,7 @@ def run_ours(args, rank, world):
             ev[3].record(stream)
             torch.cuda.synchronize()
         total_ms = ev[2].elapsed_time(ev[3])
+        launches_timed = solver.kernel_launches() - launches0  # counted by the library
         kern = [a.elapsed_time(c) for a, c in kernel_ms]
         upd_step = total * nsteps
         value, t_max = aggregate(total_ms / 1e3, upd_step * args.steps, world, device="cuda")
@@ -377,8 +379,6 @@ def run_ours(args, rank, world):
                         "flops_per_node_update": fl, "peak_source": src,
                         "hbm": {"achieved_gbs": achieved, "frac": achieved / peaks["hbm_gbs"],
                                 "bytes_per_node_update": by}}
-        tblk = tuned["steps_per_window"] if tuned else (64 if args.workload == "ensemble" else 32)
-        launches_per_step = 1 + 2 + solver_kernel_launches(args, nsteps, tblk)  # init, diagnostics x2, steps
         line = {
             "metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
@@ -390,7 +390,7 @@ def run_ours(args, rank, world):
                               if bounded else
                               f"inputs larger than L2: state {2 * total * b * esz / 2**20:.0f} MiB (two buffers)"),
                        "parallelism": f"replicas x{world} (independent ensembles)"},
-            "roofline": roof, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "clocks": clocks,
+            "roofline": roof, "e2e": e2e, "gpu_launches": launches_timed, "clocks": clocks,
             "kernel_ms_per_step": kern_ms, "accuracy": accuracy,
         }
         if fp64 is not None:
@@ -466,6 +466,7 @@ def run_serving(args):
             "config": {"workload": serving_description(args),
                        "window_requests": head["requests"], "steps_per_block": args.block},
             "p50_latency_s": head["p50_latency_s"], "p99_latency_s": head["p99_latency_s"],
+            "gpu_launches": head["launches"],
             "clocks": head["clocks"], "sweep": out}
     if fp64 is not None:
         line["fp64_plain"] = fp64
@@ -499,21 +500,6 @@ def serving_fp64_plain(L, reqs, max_updates=2e9):
     return {"value": work / t.sum(), "unit": "node-updates/s", "requests": len(t),
             "service_s_p50": float(np.percentile(t, 50)), "service_s_p99": float(np.percentile(t, 99)),
             "path": "one handle per request, FP64, k_stream one launch per step (graph-replayed), back to back"}
-
-
-def solver_kernel_launches(args, nsteps, tblk):
-    """Kernel launches of one lbhpde_batch_step(nsteps) call: the streaming kernel launches once
-    per step; resident instances launch once and temporally blocked windows once per tblk steps;
-    bounded instances launch once per 1024 steps."""
-    if args.workload == "bounded":
-        return (nsteps + 1023) // 1024
-    if args.workload == "nu_grid" and args.kernel == "stream":
-        return nsteps
-    if args.workload == "ensemble":
-        return 1 + (nsteps + tblk - 1) // tblk
-    if args.kernel == "stream":
-        return nsteps
-    return (nsteps + tblk - 1) // tblk
 
 
 def solver_model_degree(L, probs):

@@ -211,6 +211,11 @@ typedef struct {
 /* phistar: [N] doubles in device memory, or NULL.  Synchronises the stream. */
 int lbhpde_diagnostics(lbhpde_t h, const double *phistar_device, lbhpde_diag *out);
 
+/* Kernels the handle has launched since it was made, into *count: every step, initialisation,
+ * readout and diagnostics kernel (a replay of a captured graph counts each kernel in it).
+ * Host only; LBHPDE_ERR_ARG for a NULL argument. */
+int lbhpde_kernel_launches(lbhpde_t h, long long *count);
+
 /* Which kernel lbhpde_step uses (LBHPDE_KERNEL_*).  For the on-chip kernels: the nodes each
  * thread holds (FP32: 2, 4 or 8 on D1Q5, 4 or 8 on D1Q7; FP64: 2 or 4 on D1Q5, 4 on D1Q7) and
  * the steps per launch (resident instances: launch chunk; windows: steps per window, which
@@ -276,6 +281,8 @@ int lbhpde_batch_step_nee(lbhpde_batch_t b, long nsteps, const double *phib, lon
 int lbhpde_batch_read_phi(lbhpde_batch_t b, double *phi_out, int out_on_device);
 /* out: [count] records.  phistar: [sum N] doubles in device memory, or NULL. */
 int lbhpde_batch_diagnostics(lbhpde_batch_t b, const double *phistar_device, lbhpde_diag *out);
+/* As lbhpde_kernel_launches, for a batch. */
+int lbhpde_batch_kernel_launches(lbhpde_batch_t b, long long *count);
 int lbhpde_batch_set_kernel(lbhpde_batch_t b, int kernel, int nodes_per_thread, int steps_per_launch);
 /* Total node count (sum N) and device bytes held. */
 int lbhpde_batch_size(lbhpde_batch_t b, long *total_nodes, size_t *device_bytes);

@@ -118,6 +118,8 @@ struct lbhpde_batch_s {
     size_t phib_cap = 0;           // its capacity in doubles
     int kernel = LBHPDE_KERNEL_AUTO;
     int K_req = 0, spl_req = 0;
+    long long launches = 0;          // kernels launched (a graph replay counts its kernels)
+    long long graph_launches[2] = {0, 0};  // kernels in each captured graph
     long steps = 0;
     bool initialised = false;
     std::vector<std::pair<void *, size_t>> allocations;
@@ -589,6 +591,7 @@ int launch_stream_t(lbhpde_batch_s *bt, Group &g, const int2 *blocks, int nb, co
         lbk::k_stream<T, B, DC, kStreamThreads, PARAMC><<<nb, kStreamThreads, 0, bt->stream>>>(
             in, out, bt->segs, blocks, (const T *)bt->coefT, pc);
     CK(cudaGetLastError());
+    ++bt->launches;
     return LBHPDE_OK;
 }
 
@@ -661,6 +664,7 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
 int launch_group(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *out, int nsteps, cudaStream_t st,
                  int cls = lbh::kRingClasses - 1) {
     Group::Plan &pl = halo ? g.halo : g.ring[cls];
+    if (pl.ncta() > 0 && nsteps > 0) ++bt->launches;
     return lbh::launch_onchip(g.b, bt->esz, g.K, g.dc, halo, pl.host, pl.insts, pl.cta_first, in, out, bt->coefT,
                               nsteps, st);
 }
@@ -899,9 +903,12 @@ int step_periodic(lbhpde_batch_s *bt, long nsteps) {
                 cudaGraph_t gr = nullptr;
                 CK(cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal));
                 int rc = LBHPDE_OK;
+                const long long before = bt->launches;
                 for (int s = 0; s < kGraphSteps && rc == LBHPDE_OK; ++s) rc = one_step();
                 const cudaError_t ec = cudaStreamEndCapture(bt->stream, &gr);
                 bt->cur = par;  // capture launched nothing
+                bt->graph_launches[par] = bt->launches - before;
+                bt->launches = before;
                 RC(rc);
                 if (ec != cudaSuccess) {
                     (void)cudaGetLastError();
@@ -917,6 +924,7 @@ int step_periodic(lbhpde_batch_s *bt, long nsteps) {
             }
             while (left >= kGraphSteps) {
                 CK(cudaGraphLaunch(bt->graph[par], bt->stream));
+                bt->launches += bt->graph_launches[par];
                 left -= kGraphSteps;
             }
         }
@@ -1035,6 +1043,7 @@ int step_bounded(lbhpde_batch_s *bt, long nsteps, const double *pbd, long long s
                 RC(launch_stream(bt, g, g.sblocks, (int)g.sblocks_h.size(), bt->st[a], bt->st[a ^ 1]));
                 RC(lbh::launch_nee_fix(g.b, bt->esz, bt->st[a ^ 1], bt->segs, g.smembers, (int)g.smembers_h.size(),
                                        bt->coefT, pbd, stride, s, bt->stream));
+                ++bt->launches;
             }
             a ^= 1;
         }
@@ -1049,6 +1058,7 @@ int step_bounded(lbhpde_batch_s *bt, long nsteps, const double *pbd, long long s
                 RC(lbh::launch_bounded(g.b, bt->esz, g.bnd_dc, (int)g.bnd_h.size(), g.bnd_threads, smem, g.bnd,
                                        bt->st[done == 0 ? cur0 : target], bt->st[target], bt->coefT, pbd, stride,
                                        done, n, bt->stream));
+                ++bt->launches;
                 done += n;
             }
         }
@@ -1097,6 +1107,7 @@ int batch_set_phi(lbhpde_batch_s *bt, const double *phi0, int on_device) {
         if (g.members.empty()) continue;
         RC(lbh::launch_init(g.b, bt->esz, bt->st[0], bt->segs, g.blocks, (int)g.blocks_h.size(), bt->coefD, src,
                             g.blk_off, bt->stream));
+        if (!g.blocks_h.empty()) ++bt->launches;
     }
     bt->steps = 0;
     bt->initialised = true;
@@ -1117,6 +1128,7 @@ int batch_read_phi(lbhpde_batch_s *bt, double *out, int on_device) {
         lbk::k_read_phi<double><<<nb, kGenericThreads, 0, bt->stream>>>((const double *)bt->st[bt->cur], bt->segs,
                                                                         bt->all_blocks, dst, bt->blk_off, kChunk, flag);
     CK(cudaGetLastError());
+    ++bt->launches;
     if (!on_device) {
         int bad = 0;
         CK(cudaMemcpyAsync(out, bt->phi_buf, sizeof(double) * bt->total, cudaMemcpyDeviceToHost, bt->stream));
@@ -1141,6 +1153,7 @@ int batch_diag(lbhpde_batch_s *bt, const double *phistar, lbhpde_diag *out) {
     lbk::k_diag_final<<<(bt->count + 127) / 128, 128, 0, bt->stream>>>(bt->part, bt->part_first, bt->count,
                                                                       bt->diag_out);
     CK(cudaGetLastError());
+    bt->launches += 2;
     std::vector<DiagPart> h(bt->count);
     CK(cudaMemcpyAsync(h.data(), bt->diag_out, sizeof(DiagPart) * bt->count, cudaMemcpyDeviceToHost, bt->stream));
     CK(cudaStreamSynchronize(bt->stream));
@@ -1224,6 +1237,11 @@ extern "C" int lbhpde_batch_read_phi(lbhpde_batch_t b, double *out, int on_devic
 extern "C" int lbhpde_batch_diagnostics(lbhpde_batch_t b, const double *phistar, lbhpde_diag *out) {
     return b ? batch_diag(b, phistar, out) : LBHPDE_ERR_ARG;
 }
+extern "C" int lbhpde_batch_kernel_launches(lbhpde_batch_t b, long long *count) {
+    if (!b || !count) return LBHPDE_ERR_ARG;
+    *count = b->launches;
+    return LBHPDE_OK;
+}
 extern "C" int lbhpde_batch_set_kernel(lbhpde_batch_t b, int kernel, int nodes_per_thread, int steps_per_launch) {
     if (!b || kernel < LBHPDE_KERNEL_AUTO || kernel > LBHPDE_KERNEL_HALO || nodes_per_thread < 0 ||
         steps_per_launch < 0)
@@ -1289,6 +1307,9 @@ extern "C" int lbhpde_read_phi(lbhpde_t h, double *out, int on_device) {
 }
 extern "C" int lbhpde_diagnostics(lbhpde_t h, const double *phistar, lbhpde_diag *out) {
     return h ? batch_diag(h->b, phistar, out) : LBHPDE_ERR_ARG;
+}
+extern "C" int lbhpde_kernel_launches(lbhpde_t h, long long *count) {
+    return h ? lbhpde_batch_kernel_launches(h->b, count) : LBHPDE_ERR_ARG;
 }
 extern "C" int lbhpde_set_kernel(lbhpde_t h, int kernel, int nodes_per_thread, int steps_per_launch) {
     return h ? lbhpde_batch_set_kernel(h->b, kernel, nodes_per_thread, steps_per_launch) : LBHPDE_ERR_ARG;

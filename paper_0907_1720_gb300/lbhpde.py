@@ -122,6 +122,7 @@ _SIGS = {
     "lbhpde_step_nee": (_I, [_V, _L, _V, _I]),
     "lbhpde_read_phi": (_I, [_V, _V, _I]),
     "lbhpde_diagnostics": (_I, [_V, _V, _P(lbhpde_diag)]),
+    "lbhpde_kernel_launches": (_I, [_V, _P(ctypes.c_longlong)]),
     "lbhpde_set_kernel": (_I, [_V, _I, _I, _I]),
     "lbhpde_get_model": (_I, [_V, _P(lbhpde_model_info)]),
     "lbhpde_autotune": (_I, [_I, _I, _I, _P(_I), _P(_I), _P(_D)]),
@@ -134,6 +135,7 @@ _SIGS = {
     "lbhpde_batch_step_nee": (_I, [_V, _L, _V, _L, _I]),
     "lbhpde_batch_read_phi": (_I, [_V, _V, _I]),
     "lbhpde_batch_diagnostics": (_I, [_V, _V, _P(lbhpde_diag)]),
+    "lbhpde_batch_kernel_launches": (_I, [_V, _P(ctypes.c_longlong)]),
     "lbhpde_batch_set_kernel": (_I, [_V, _I, _I, _I]),
     "lbhpde_batch_size": (_I, [_V, _P(_L), _P(_S)]),
     "lbhpde_batch_destroy": (_I, [_V]),
@@ -416,6 +418,12 @@ class Solver:
             _check(rc, "lbhpde_diagnostics")
         return d.as_dict()
 
+    def kernel_launches(self) -> int:
+        """lbhpde_kernel_launches: kernels launched since the handle was made."""
+        n = ctypes.c_longlong()
+        _check(lib().lbhpde_kernel_launches(self.h, ctypes.byref(n)), "lbhpde_kernel_launches")
+        return n.value
+
     def model(self) -> lbhpde_model_info:
         out = lbhpde_model_info()
         _check(lib().lbhpde_get_model(self.h, ctypes.byref(out)), "lbhpde_get_model")
@@ -498,6 +506,12 @@ class Batch:
         if rc not in (OK, ERR_DIVERGED):
             _check(rc, "lbhpde_batch_diagnostics")
         return np.ctypeslib.as_array(out)
+
+    def kernel_launches(self) -> int:
+        """lbhpde_batch_kernel_launches: kernels launched since the batch was made."""
+        n = ctypes.c_longlong()
+        _check(lib().lbhpde_batch_kernel_launches(self.h, ctypes.byref(n)), "lbhpde_batch_kernel_launches")
+        return n.value
 
     def size(self):
         n, b = ctypes.c_long(), ctypes.c_size_t()

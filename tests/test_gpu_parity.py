@@ -315,6 +315,27 @@ def test_autotune_then_parity(L):
         bt.close()
 
 
+def test_kernel_launch_count(L):
+    """lbhpde_kernel_launches counts every kernel: graph replays count the kernels they hold."""
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        p = problem(W.kawahara(), 2049, 0.1, 1e-3, 2.5, 200, seed=21)
+        s = L.Solver.for_problem(p, precision=L.FP32_DEV).set_kernel(L.KERNEL_STREAM)
+        n0 = s.kernel_launches()
+        s.set_phi(p.phi0).step(200)  # initialisation, then 3 replays of a 64-step graph + 8 launches
+        assert s.kernel_launches() - n0 == 1 + 200
+        s.read_phi()
+        s.diagnostics()
+        assert s.kernel_launches() - n0 == 1 + 200 + 1 + 2
+        s.close()
+        q = problem(W.kdv(), 400, 0.1, 2e-5, 1.07, 100)
+        r = L.Solver.for_problem(q, precision=L.FP32_DEV).set_kernel(L.KERNEL_ONCHIP)
+        m0 = r.kernel_launches()
+        r.set_phi(q.phi0).step(100)  # initialisation and one resident launch
+        assert r.kernel_launches() - m0 == 2
+        r.close()
+
+
 def test_stream_graph_replay_matches_single_launches(L):
     """On a non-default stream, long streaming runs replay a captured graph of 64 one-step
     launches; the result equals 200 individual launches bit for bit and matches the oracle."""
