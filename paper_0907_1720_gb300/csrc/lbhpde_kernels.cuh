@@ -161,31 +161,6 @@ __device__ __forceinline__ void gen_evalN(const T *c, int A_, int Dg, const T (&
     }
 }
 
-// gen_evalN with both the row count (1..4 rows above the first) and the row degree (0..3) at
-// compile time: the on-chip FP32 real-exponent path, where the loads of a fully unrolled
-// evaluation can be scheduled ahead.  Other shapes take gen_eval4_any.
-template <typename T, int NN, int AA>
-__device__ __forceinline__ bool gen_eval_rows(const T *c, int Dg, const T (&phi)[NN], const T (&w)[NN], T (&out)[NN]) {
-    switch (Dg) {
-    case 0: gen_evalN<T, 0, NN, AA>(c, AA, 0, phi, w, out); return true;
-    case 1: gen_evalN<T, 1, NN, AA>(c, AA, 1, phi, w, out); return true;
-    case 2: gen_evalN<T, 2, NN, AA>(c, AA, 2, phi, w, out); return true;
-    case 3: gen_evalN<T, 3, NN, AA>(c, AA, 3, phi, w, out); return true;
-    default: return false;
-    }
-}
-template <typename T, int NN>
-__device__ __forceinline__ bool gen_eval_fixed(const T *c, int A, int Dg, const T (&phi)[NN], const T (&w)[NN],
-                                               T (&out)[NN]) {
-    switch (A) {
-    case 1: return gen_eval_rows<T, NN, 1>(c, Dg, phi, w, out);
-    case 2: return gen_eval_rows<T, NN, 2>(c, Dg, phi, w, out);
-    case 3: return gen_eval_rows<T, NN, 3>(c, Dg, phi, w, out);
-    case 4: return gen_eval_rows<T, NN, 4>(c, Dg, phi, w, out);
-    default: return false;
-    }
-}
-
 // gen_evalN with the row degree dispatched to a compile-time variant (0..7 in FP32, 0..3 in FP64,
 // where more would spill), else run time.
 template <typename T, int NN = 4>
@@ -503,14 +478,48 @@ struct OnchipInst {
     double nu;          //   sum_{a<=A} (phi^nu)^a sum_{i<=Dg} c[a(Dg+1)+i] phi^i; A = 0: polynomial
 };
 
-// gen_eval for the K nodes of a thread, every coefficient loaded once for all K (FP32: the common
-// shapes with the row count and degree at compile time)
+// gen_eval for the K nodes of a thread, every coefficient loaded once for all K
 template <typename T, int K>
 __device__ __forceinline__ void gen_evalK(const T *c, int A, int Dg, const T (&phi)[K], const T (&w)[K], T (&out)[K]) {
-    if constexpr (sizeof(T) == 4) {
-        if (gen_eval_fixed<T, K>(c, A, Dg, phi, w, out)) return;
-    }
     gen_eval4_any<T, K>(c, A, Dg, phi, w, out);
+}
+
+// The relaxation of every moving population of a thread's K nodes for a real-exponent model
+// whose row count (AA + 1) and row degree DG are known at compile time: one dispatch per step
+// instead of one per population.  Rows of P_j start at sc + (j - 1) cs.
+template <typename T, int B, int K, int AA, int DG>
+__device__ __forceinline__ void relax_rows(const T *sc, int cs, const T (&phi)[K], const T (&w)[K], T (&v)[B][K],
+                                           T omw) {
+#pragma unroll
+    for (int j = 1; j < B; ++j) {
+        T acc[K];
+        gen_evalN<T, DG, K, AA>(sc + (j - 1) * cs, AA, DG, phi, w, acc);
+#pragma unroll
+        for (int k = 0; k < K; ++k) v[j][k] = fma_t(omw, v[j][k], acc[k]);
+    }
+}
+template <typename T, int B, int K, int AA>
+__device__ __forceinline__ bool relax_rows_dg(int Dg, const T *sc, int cs, const T (&phi)[K], const T (&w)[K],
+                                              T (&v)[B][K], T omw) {
+    switch (Dg) {
+    case 0: relax_rows<T, B, K, AA, 0>(sc, cs, phi, w, v, omw); return true;
+    case 1: relax_rows<T, B, K, AA, 1>(sc, cs, phi, w, v, omw); return true;
+    case 2: relax_rows<T, B, K, AA, 2>(sc, cs, phi, w, v, omw); return true;
+    case 3: relax_rows<T, B, K, AA, 3>(sc, cs, phi, w, v, omw); return true;
+    default: return false;
+    }
+}
+// the common shapes (2..5 rows, degree 0..3); false for the others
+template <typename T, int B, int K>
+__device__ __forceinline__ bool relax_rows_fixed(int A, int Dg, const T *sc, int cs, const T (&phi)[K],
+                                                 const T (&w)[K], T (&v)[B][K], T omw) {
+    switch (A) {
+    case 1: return relax_rows_dg<T, B, K, 1>(Dg, sc, cs, phi, w, v, omw);
+    case 2: return relax_rows_dg<T, B, K, 2>(Dg, sc, cs, phi, w, v, omw);
+    case 3: return relax_rows_dg<T, B, K, 3>(Dg, sc, cs, phi, w, v, omw);
+    case 4: return relax_rows_dg<T, B, K, 4>(Dg, sc, cs, phi, w, v, omw);
+    default: return false;
+    }
 }
 
 // threads per SM at each configuration's register budget (FP32 D1Q5 with K = 8: 128 registers);
@@ -715,14 +724,16 @@ __global__ void __launch_bounds__(MAXT, onchip_minb(sizeof(T), B, K, MAXT))
             // relax: s'_j = (1 - omega) f_j + P_j(phi'), Horner with coefficients from shared memory
             // (real exponents: w = phi^nu once per node, then the rows in phi and w)
             T w[K];
+            bool relaxed = false;
             if constexpr (DC < 0) {
                 if (I.A > 0) {
 #pragma unroll
                     for (int k = 0; k < K; ++k) w[k] = nu_pow<T>(phi[k], I.nu);
+                    if constexpr (sizeof(T) == 4) relaxed = relax_rows_fixed<T, B, K>(I.A, I.Dg, sc, cs, phi, w, v, omw);
                 }
             }
 #pragma unroll
-            for (int j = 1; j < B; ++j) {
+            for (int j = 1; j < B && !relaxed; ++j) {
                 const T *c = sc + (j - 1) * cs;
                 T acc[K];
                 if constexpr (DC > 0) {
