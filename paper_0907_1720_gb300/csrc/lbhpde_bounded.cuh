@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(MAXT, 1)
     const int N = I.N;
     const int x0 = tid * K - I.shift;  // node of this thread's first position
     const int kL = W - 1 + I.depth, kR = N - W - I.depth;
-    const int lane = tid & 31, warp = tid >> 5;
+    const int warp = tid >> 5;
     // the warps and lanes of the two ends (fixed for the launch)
     const int wL = ((kL + I.shift) / K) >> 5, wR = ((N - 1 + I.shift) / K) >> 5;
     const int srcL = ((kL + I.shift) / K) & 31, srcR = ((kR + I.shift) / K) & 31;

@@ -292,8 +292,10 @@ __device__ __forceinline__ void stream_body(const T *__restrict__ in, T *__restr
     auto coef = [&](int j, int p) -> T {  // coefficient p of P_j, compile-time indices
         if constexpr (PARAMC)
             return pc.c[(j - 1) * (DC + 1) + p];
+        else if constexpr (DC > 0)
+            return creg[(j - 1) * (DC + 1) + p];
         else
-            return creg[(j - 1) * ((DC > 0 ? DC : 0) + 1) + p];
+            return T(0);  // run-time degree: the coefficients come from shared memory instead
     };
     // real-exponent models (run-time degree path only): w = phi^nu once per node
     const int A = DC > 0 ? 0 : s.A;
