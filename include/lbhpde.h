@@ -335,8 +335,10 @@ typedef struct {
  * bounds the admitted requests; steps_per_block (0 = 256) is the admission granularity. */
 int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t device_bytes, int max_active,
                          int steps_per_block, int device);
-/* Step a0 runs here on the caller's thread.  Errors: LBHPDE_ERR_ARG (invalid request),
- * LBHPDE_ERR_OOM (larger than the whole arena), LBHPDE_ERR_CUDA (the server has failed). */
+/* Step a0 runs here on the caller's thread.  Any model lbhpde_model accepts, real exponents
+ * included (served by the on-chip kernels' real-exponent variant).  Errors: LBHPDE_ERR_ARG
+ * (invalid request), LBHPDE_ERR_OOM (larger than the whole arena), LBHPDE_ERR_CUDA (the server
+ * has failed). */
 int lbhpde_submit(lbhpde_server_t s, const lbhpde_request *req, uint64_t *id);
 /* Non-blocking.  LBHPDE_PENDING while the request is queued or running (info is filled);
  * otherwise its final status, phi copied to phi_out ([N] host doubles, may be NULL), and the

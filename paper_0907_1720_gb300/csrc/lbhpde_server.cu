@@ -34,8 +34,9 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 constexpr size_t kGrain = 256;        // arena allocation granularity (bytes)
-constexpr int kCoefStride = 388;      // coefficient slot: 2 (b-1)(D+1) + 1 <= 385 values, padded
+constexpr int kCoefStride = 772;      // coefficient slot: 2 (b-1)(D+1) + 1 <= 769 values (D+1 <= 64), padded
 constexpr int kLookahead = 64;        // queued requests examined per admission pass
+constexpr int kClasses = 6;           // (D1Q5, D1Q7) x (compiled degree, run-time degree, real exponents)
 
 size_t round_up(size_t n, size_t g) { return (n + g - 1) / g * g; }
 
@@ -105,6 +106,9 @@ struct Req {
         s.ld = ld;
         s.N = (int)N;
         s.D = mi.D;
+        s.A = mi.nu_rows - 1;  // real-exponent rows (0: an ordinary polynomial)
+        s.Dg = mi.nu_deg;
+        s.nu = mi.nu;
         s.coef = slot * kCoefStride;
         return s;
     }
@@ -145,7 +149,7 @@ struct lbhpde_server_s {
     // per CTA size class, and the window launches, which follow each other) run on lanes of
     // their own, after the table uploads on `stream`, and join it before the block's one
     // synchronisation.
-    static constexpr int kLanes = 16;
+    static constexpr int kLanes = 4 * 6;  // 4 per (lattice, class)
     cudaStream_t lane[kLanes] = {};
     cudaEvent_t ev_up = nullptr, ev_done[kLanes] = {};
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // timing of one step block
@@ -205,10 +209,12 @@ int setup_admitted(lbhpde_server_s *S, std::vector<Req *> &adm) {
         const Req &r = *adm[q];
         double *c = cd.data() + q * kCoefStride;
         int k = 0;
+        // the generalised tables: the degree-D coefficients of an ordinary polynomial model, the
+        // flattened (A + 1)(Dg + 1) = D + 1 entries of a real-exponent one
         for (int j = 1; j < r.mi.b; ++j)
-            for (int p = 0; p <= r.mi.D; ++p) c[k++] = r.mi.coef[j][p];
+            for (int p = 0; p <= r.mi.D; ++p) c[k++] = r.mi.gcoef[j][p];
         for (int j = 1; j < r.mi.b; ++j)
-            for (int p = 0; p <= r.mi.D; ++p) c[k++] = r.mi.feq[j][p];
+            for (int p = 0; p <= r.mi.D; ++p) c[k++] = r.mi.gfeq[j][p];
         c[k] = 1.0 - r.mi.omega;
         phi_total += r.N;
     }
@@ -265,7 +271,7 @@ int setup_admitted(lbhpde_server_s *S, std::vector<Req *> &adm) {
 struct Planned {
     int b, K, dc;
     bool halo;
-    int lane;    // stream lane: 4 * (lattice, degree class) + (windows ? 3 : resident size class)
+    int lane;    // stream lane: 4 * (lattice, class) + (windows ? 3 : resident size class)
     int nsteps;
     lbh::Packed p;
     size_t ioff = 0, foff = 0;  // offsets of its tables in the block's device arrays
@@ -276,12 +282,13 @@ struct Planned {
 // in one copy each, launch them in order on the server stream and wait once.
 int advance(lbhpde_server_s *S) {
     std::vector<Planned> plan;
-    // per lattice, two degree classes: requests whose f^eq degree the compiled variant covers
-    // (D <= 5 on D1Q5, <= 7 on D1Q7) and the rest, each with its own launches, so that one
-    // high-degree request does not send the whole lattice to the run-time-degree variant
-    for (int cls = 0; cls < 4; ++cls) {
-        const int b = cls < 2 ? 5 : 7;
-        const bool high = (cls & 1) != 0;
+    // per lattice, three classes: requests whose f^eq degree the compiled variant covers (D <= 5
+    // on D1Q5, <= 7 on D1Q7), higher-degree polynomials, and real-exponent models, each with its
+    // own launches, so that one high-degree or real-exponent request does not send the whole
+    // lattice to a slower variant
+    for (int cls = 0; cls < kClasses; ++cls) {
+        const int b = cls < kClasses / 2 ? 5 : 7;
+        const int kind = cls % 3;  // 0: compiled degree, 1: run-time degree, 2: real exponents
         const int dcmax = b == 5 ? 5 : 7;
         const int K = lbh::default_K(S->esz, b);
         const int maxt = lbh::onchip_maxt(S->esz, b, K);
@@ -290,12 +297,13 @@ int advance(lbhpde_server_s *S) {
         std::vector<Req *> ring, halo;
         int maxD = 0;
         for (Req *r : S->active)
-            if (r->mi.b == b && r->done < r->nsteps && (r->mi.D > dcmax) == high) {
+            if (r->mi.b == b && r->done < r->nsteps &&
+                (r->mi.nu_rows > 1 ? 2 : (r->mi.D > dcmax ? 1 : 0)) == kind) {
                 (r->N <= cap ? ring : halo).push_back(r);
                 maxD = std::max(maxD, r->mi.D);
             }
         if (ring.empty() && halo.empty()) continue;
-        const int dc = lbh::onchip_dc(b, maxD);
+        const int dc = kind == 2 ? -1 : lbh::onchip_dc(b, maxD);
         if (!ring.empty()) {
             std::vector<lbh::Member> m;
             int n = 0;
@@ -561,8 +569,8 @@ extern "C" int lbhpde_submit(lbhpde_server_t S, const lbhpde_request *q, uint64_
     int rc = lbhpde_model(q->m, q->alpha, q->pi, q->dx, q->dt, q->tau, q->lattice, q->scheme, &r->mi);
     const int W = (r->mi.b - 1) / 2;
     if (rc == LBHPDE_OK && (q->N < 2 * W || q->N > (1L << 26))) rc = LBHPDE_ERR_ARG;
-    // the server's kernels are the on-chip ones, which take ordinary polynomial models only
-    if (rc == LBHPDE_OK && r->mi.nu_rows > 1) rc = LBHPDE_ERR_UNSUPPORTED;
+    // real-exponent models take the on-chip variant that evaluates four or more nodes a thread
+    if (rc == LBHPDE_OK && r->mi.nu_rows > 1 && lbh::default_K(S->esz, r->mi.b) < 4) rc = LBHPDE_ERR_UNSUPPORTED;
     if (rc != LBHPDE_OK) {
         delete r;
         return rc;

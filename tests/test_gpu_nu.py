@@ -143,13 +143,33 @@ def test_fp32_accuracy(L):
     assert errs[L.FP32_DEV] <= 2.0 * errs[L.FP64]
 
 
-def test_server_rejects_real_exponent_requests(L):
-    srv = L.Server(precision=L.FP32_DEV, device_bytes=1 << 24, max_active=4, steps_per_block=64)
-    p = problems()["gkdv_1.5_soliton"]
-    with pytest.raises(L.LbhpdeError) as e:
-        srv.submit(p.eq, p.N, p.dx, p.dt, p.tau, 10, p.phi0)
-    assert e.value.code == L.ERR_UNSUPPORTED
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_server_serves_real_exponent_requests(L, precision):
+    """Real-exponent requests mixed with polynomial ones in the server: each result equals, bit
+    for bit, the same request solved alone on the on-chip kernels, and matches the oracle."""
+    P = L.FP32_DEV if precision == "fp32" else L.FP64
+    ps = problems()
+    xw = W.grid(-450.0, 9000, DX)  # longer than a resident CTA holds: windows
+    wide = W.Problem(W.gkdv(1.5), 9000, DX, 1e-4, 1.3, 0, W.gkdv_soliton(xw, 0.0, 1.5, L=900.0), xl=-450.0)
+    reqs = [ps["gkdv_1.5_soliton"], W.kdv_config(N=400, dt=1e-4, tau=1.3, t_end=0.0), ps["ks_real_d1q5"],
+            ps["kawahara_real_d1q7"], ps["gkdv_0.5_offset"], wide]
+    for i, p in enumerate(reqs):
+        p.nsteps = 300 + 37 * i
+    srv = L.Server(precision=P, device_bytes=64 << 20, max_active=16, steps_per_block=128)
+    ids = [srv.submit_problem(p) for p in reqs]
+    got = [srv.wait(i, 120.0) for i in ids]
+    st = srv.stats()
     srv.close()
+    assert st["error"] == 0
+    for (rc, phi, info), p in zip(got, reqs):
+        assert rc == L.OK, (p.eq.name, rc)
+        s = L.Solver.for_problem(p, precision=P).set_kernel(L.KERNEL_ONCHIP)
+        alone = s.set_phi(p.phi0).step(p.nsteps).read_phi()
+        s.close()
+        assert np.array_equal(phi, alone), p.eq.name
+        want = oracle_periodic(p) if p.eq.pi_nu is not None else oracle.run_problem(p)
+        tol = FP64_TOL if P == L.FP64 else 64 * np.finfo(np.float32).eps * np.sqrt(p.nsteps) + 1e-6
+        assert normwise(phi, want) <= tol, p.eq.name
 
 
 def test_replan_discards_captured_graphs(L):
