@@ -211,9 +211,9 @@ typedef struct {
 /* phistar: [N] doubles in device memory, or NULL.  Synchronises the stream. */
 int lbhpde_diagnostics(lbhpde_t h, const double *phistar_device, lbhpde_diag *out);
 
-/* Kernels the handle has launched since it was made, into *count: every step, initialisation,
- * readout and diagnostics kernel (a replay of a captured graph counts each kernel in it).
- * Host only; LBHPDE_ERR_ARG for a NULL argument. */
+/* Kernels the handle has launched since it was made (instrumentation; no counterpart in the
+ * paper), into *count: every step, initialisation, readout and diagnostics kernel (a replay of
+ * a captured graph counts each kernel in it).  Host only; LBHPDE_ERR_ARG for a NULL argument. */
 int lbhpde_kernel_launches(lbhpde_t h, long long *count);
 
 /* Which kernel lbhpde_step uses (LBHPDE_KERNEL_*).  For the on-chip kernels: the nodes each
@@ -235,8 +235,9 @@ int lbhpde_autotune(int precision, int lattice, int degree, int *nodes_per_threa
                     double *node_updates_per_s);
 
 /* Records a tuned (nodes per thread, steps per window) pair for one precision, lattice and f^eq
- * degree without timing anything, as lbhpde_autotune would have left it: e.g. a pair found in
- * an earlier process, or a fixed choice for a profiling run.  Host only (no device work).
+ * degree without timing anything (no counterpart in the paper), as lbhpde_autotune would have
+ * left it: e.g. a pair found in an earlier process, or a fixed choice for a profiling run.
+ * Host only (no device work).
  * LBHPDE_ERR_ARG for an invalid precision, lattice or degree, or steps_per_launch < 1;
  * LBHPDE_ERR_UNSUPPORTED for nodes per thread the library was not built with, or a window
  * whose halo (2 * steps * max|e|) leaves fewer than half of its nodes valid. */
