@@ -455,6 +455,8 @@ def run_serving(args):
                     "achieved_node_updates_s": work / (t1 - t0), "makespan_s": t1 - t0,
                     "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                     "launches": st["launches"], "gpu_busy_s": st["gpu_busy_s"],
+                    "host_s": {k[5:-2]: st[k] for k in ("host_admit_s", "host_setup_s", "host_plan_s",
+                                                         "host_launch_s", "host_wait_s", "host_retire_s")},
                     "gpu_busy_frac": st["gpu_busy_s"] / (t1 - t0), "clocks": clk.summary()})
     head = out[0]
     fp64 = None if args.quick else serving_fp64_plain(L, W.serving_requests(

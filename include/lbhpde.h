@@ -329,6 +329,10 @@ typedef struct {
     int error;             /* sticky status of the scheduler (LBHPDE_OK unless a CUDA call failed) */
     double gpu_busy_s;     /* summed GPU time of the step blocks, from their uploads to their last
                             * launch (CUDA events): busy / wall time is the device's share of work */
+    /* host time of the scheduler thread by phase (seconds, summed over step blocks): admission,
+     * set-up of admitted requests (uploads, initialisation), planning (packing and table
+     * uploads), issuing the launches, waiting for the block, retiring finished requests */
+    double host_admit_s, host_setup_s, host_plan_s, host_launch_s, host_wait_s, host_retire_s;
 } lbhpde_server_info;
 
 /* device_bytes (>= 1 MiB) is the state arena, allocated at creation; each request holds

@@ -154,6 +154,8 @@ struct lbhpde_server_s {
     cudaEvent_t ev_up = nullptr, ev_done[kLanes] = {};
     cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // timing of one step block
     double gpu_busy = 0.0;
+    // host time of the scheduler thread by phase (written by that thread, under mu)
+    double t_admit = 0.0, t_setup = 0.0, t_plan = 0.0, t_launch = 0.0, t_wait = 0.0, t_retire = 0.0;
     void *arena_d = nullptr;
     Arena arena;
     void *coefT_d = nullptr;
@@ -281,6 +283,7 @@ struct Planned {
 // (resident instances once per lattice, windows in chunks of tblk steps), upload their tables
 // in one copy each, launch them in order on the server stream and wait once.
 int advance(lbhpde_server_s *S) {
+    const auto t_enter = Clock::now();
     std::vector<Planned> plan;
     // per lattice, three classes: requests whose f^eq degree the compiled variant covers (D <= 5
     // on D1Q5, <= 7 on D1Q7), higher-degree polynomials, and real-exponent models, each with its
@@ -357,6 +360,7 @@ int advance(lbhpde_server_s *S) {
     }
     SRC(S->insts_d.ensure(insts.size()));
     SRC(S->first_d.ensure(first.size()));
+    const auto tp = Clock::now();
     SCK(cudaEventRecord(S->ev_t0, S->stream));
     SCK(cudaMemcpyAsync(S->insts_d.p, insts.data(), sizeof(lbk::OnchipInst) * insts.size(), cudaMemcpyHostToDevice,
                         S->stream));
@@ -378,11 +382,16 @@ int advance(lbhpde_server_s *S) {
             SCK(cudaStreamWaitEvent(S->stream, S->ev_done[i], 0));
         }
     SCK(cudaEventRecord(S->ev_t1, S->stream));
+    const auto tl = Clock::now();
     SCK(cudaStreamSynchronize(S->stream));
+    const auto tw = Clock::now();
     float ms = 0.0f;
     SCK(cudaEventElapsedTime(&ms, S->ev_t0, S->ev_t1));
     std::lock_guard<std::mutex> lk(S->mu);
     S->gpu_busy += ms * 1e-3;
+    S->t_plan += std::chrono::duration<double>(tp - t_enter).count();
+    S->t_launch += std::chrono::duration<double>(tl - tp).count();
+    S->t_wait += std::chrono::duration<double>(tw - tl).count();
     return LBHPDE_OK;
 }
 
@@ -431,6 +440,7 @@ void worker_main(lbhpde_server_s *S) {
     }
     for (;;) {
         std::vector<Req *> adm;
+        const auto ta = Clock::now();
         {
             std::unique_lock<std::mutex> lk(S->mu);
             if (S->stop) break;
@@ -461,10 +471,18 @@ void worker_main(lbhpde_server_s *S) {
                 continue;
             }
         }
+        const auto ts = Clock::now();
         int rc = setup_admitted(S, adm);
         for (Req *r : adm) S->active.push_back(r);
+        const auto tv = Clock::now();
         if (rc == LBHPDE_OK) rc = advance(S);
         if (rc == LBHPDE_OK) rc = cudaStreamSynchronize(S->stream) == cudaSuccess ? LBHPDE_OK : LBHPDE_ERR_CUDA;
+        const auto tr = Clock::now();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->t_admit += std::chrono::duration<double>(ts - ta).count();
+            S->t_setup += std::chrono::duration<double>(tv - ts).count();
+        }
         std::vector<Req *> still;
         for (Req *r : S->active) {
             if (rc == LBHPDE_OK && r->done >= r->nsteps) {
@@ -475,6 +493,10 @@ void worker_main(lbhpde_server_s *S) {
             }
         }
         S->active.swap(still);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->t_retire += std::chrono::duration<double>(Clock::now() - tr).count();
+        }
         if (rc != LBHPDE_OK) {
             std::lock_guard<std::mutex> lk(S->mu);
             S->error = rc;
@@ -644,6 +666,12 @@ extern "C" int lbhpde_server_stats(lbhpde_server_t S, lbhpde_server_info *out) {
     out->launches = S->launches;
     out->error = S->error;
     out->gpu_busy_s = S->gpu_busy;
+    out->host_admit_s = S->t_admit;
+    out->host_setup_s = S->t_setup;
+    out->host_plan_s = S->t_plan;
+    out->host_launch_s = S->t_launch;
+    out->host_wait_s = S->t_wait;
+    out->host_retire_s = S->t_retire;
     return LBHPDE_OK;
 }
 

@@ -94,7 +94,9 @@ class lbhpde_server_info(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_long), ("in_flight", ctypes.c_long), ("completed", ctypes.c_long),
                 ("node_updates", ctypes.c_double), ("bytes_in_use", ctypes.c_size_t),
                 ("bytes_total", ctypes.c_size_t), ("launches", ctypes.c_long), ("error", ctypes.c_int),
-                ("gpu_busy_s", ctypes.c_double)]
+                ("gpu_busy_s", ctypes.c_double), ("host_admit_s", ctypes.c_double), ("host_setup_s", ctypes.c_double),
+                ("host_plan_s", ctypes.c_double), ("host_launch_s", ctypes.c_double), ("host_wait_s", ctypes.c_double),
+                ("host_retire_s", ctypes.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
