@@ -91,7 +91,9 @@ struct Req {
     uint64_t id = 0;
     lbhpde_model_info mi{};
     long long N = 0;
-    long nsteps = 0, done = 0;
+    long nsteps = 0, done = 0;        // steps to take; steps planned into step blocks so far
+    long done_gpu = 0;                // steps of blocks that have completed on the GPU
+    long long final_block = -1;       // the block that holds its last steps (-1: none)
     std::vector<double> phi0, phi;
     int status = LBHPDE_PENDING;
     long nonfinite = 0;
@@ -145,6 +147,10 @@ struct lbhpde_server_s {
     size_t esz = 4;
     int device = 0, max_active = 0, block = 256;
     cudaStream_t stream = nullptr;
+    // set-up of admitted requests (uploads, initialisation) runs on `up`, beside a block in
+    // flight on `stream`; `stream` waits for it through ev_setup
+    cudaStream_t up = nullptr;
+    cudaEvent_t ev_setup = nullptr;
     // A step block's independent launch chains (per lattice and degree class: one resident launch
     // per CTA size class, and the window launches, which follow each other) run on lanes of
     // their own, after the table uploads on `stream`, and join it before the block's one
@@ -152,7 +158,8 @@ struct lbhpde_server_s {
     static constexpr int kLanes = 4 * 6;  // 4 per (lattice, class)
     cudaStream_t lane[kLanes] = {};
     cudaEvent_t ev_up = nullptr, ev_done[kLanes] = {};
-    cudaEvent_t ev_t0 = nullptr, ev_t1 = nullptr;  // timing of one step block
+    cudaEvent_t ev_t0[2] = {}, ev_t1[2] = {};  // timing of the step blocks (by block parity)
+    long long next_block = 0;                  // id of the next block to plan
     double gpu_busy = 0.0;
     // host time of the scheduler thread by phase (written by that thread, under mu)
     double t_admit = 0.0, t_setup = 0.0, t_plan = 0.0, t_launch = 0.0, t_wait = 0.0, t_retire = 0.0;
@@ -224,11 +231,11 @@ int setup_admitted(lbhpde_server_s *S, std::vector<Req *> &adm) {
         const Req &r = *adm[q];
         const double *c = cd.data() + q * kCoefStride;
         SCK(cudaMemcpyAsync(S->coefD_d + (size_t)r.slot * kCoefStride, c, sizeof(double) * kCoefStride,
-                            cudaMemcpyHostToDevice, S->stream));
+                            cudaMemcpyHostToDevice, S->up));
         if (S->esz == 4) {
             std::vector<float> cf(c, c + kCoefStride);
             SCK(cudaMemcpyAsync((float *)S->coefT_d + (size_t)r.slot * kCoefStride, cf.data(),
-                                sizeof(float) * kCoefStride, cudaMemcpyHostToDevice, S->stream));
+                                sizeof(float) * kCoefStride, cudaMemcpyHostToDevice, S->up));
         }
     }
     SRC(S->phi0_d.ensure(phi_total));
@@ -236,7 +243,7 @@ int setup_admitted(lbhpde_server_s *S, std::vector<Req *> &adm) {
     long long o = 0;
     for (Req *r : adm) {
         SCK(cudaMemcpyAsync(S->phi0_d.p + o, r->phi0.data(), sizeof(double) * r->N, cudaMemcpyHostToDevice,
-                            S->stream));
+                            S->up));
         segs.push_back(r->seg());
         o += r->N;
     }
@@ -256,16 +263,20 @@ int setup_admitted(lbhpde_server_s *S, std::vector<Req *> &adm) {
         SRC(S->segs_d.ensure(segs.size()));
         SRC(S->blocks_d.ensure(blocks.size()));
         SRC(S->boff_d.ensure(boff.size()));
-        SCK(cudaMemcpyAsync(S->segs_d.p, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, S->stream));
+        SCK(cudaMemcpyAsync(S->segs_d.p, segs.data(), sizeof(Seg) * segs.size(), cudaMemcpyHostToDevice, S->up));
         SCK(cudaMemcpyAsync(S->blocks_d.p, blocks.data(), sizeof(int2) * blocks.size(), cudaMemcpyHostToDevice,
-                            S->stream));
+                            S->up));
         SCK(cudaMemcpyAsync(S->boff_d.p, boff.data(), sizeof(long long) * boff.size(), cudaMemcpyHostToDevice,
-                            S->stream));
+                            S->up));
         SRC(lbh::launch_init(b, S->esz, S->arena_d, S->segs_d.p, S->blocks_d.p, (int)blocks.size(), S->coefD_d,
-                             S->phi0_d.p, S->boff_d.p, S->stream));
-        // the next lattice reuses the tables: order the copies after this launch
-        SCK(cudaStreamSynchronize(S->stream));
+                             S->phi0_d.p, S->boff_d.p, S->up));
+        // the next lattice reuses the tables: order the copies after this launch (the set-up
+        // stream holds only set-up work, so this does not wait for a block in flight)
+        SCK(cudaStreamSynchronize(S->up));
     }
+    // the next block (and the wait before retiring) come after the new requests' initialisation
+    SCK(cudaEventRecord(S->ev_setup, S->up));
+    SCK(cudaStreamWaitEvent(S->stream, S->ev_setup, 0));
     return LBHPDE_OK;
 }
 
@@ -279,12 +290,21 @@ struct Planned {
     size_t ioff = 0, foff = 0;  // offsets of its tables in the block's device arrays
 };
 
-// Advance every active request by up to one block of steps: plan all launches of the block
-// (resident instances once per lattice, windows in chunks of tblk steps), upload their tables
-// in one copy each, launch them in order on the server stream and wait once.
-int advance(lbhpde_server_s *S) {
-    const auto t_enter = Clock::now();
+// A planned step block: its launches and, per request, the steps it advances.
+struct Block {
+    long long id = -1;
     std::vector<Planned> plan;
+    std::vector<std::pair<Req *, int>> members;
+};
+
+// Plan the next step block on the host: every active request advances by up to S->block steps
+// (resident instances once per lattice and class, windows in chunks of tblk steps).  Requests'
+// planned step counts and buffers advance here; the block runs when launch_block issues it.
+int plan_block(lbhpde_server_s *S, Block &blk) {
+    const auto t_enter = Clock::now();
+    blk = Block{};
+    blk.id = S->next_block;
+    std::vector<Planned> &plan = blk.plan;
     // per lattice, three classes: requests whose f^eq degree the compiled variant covers (D <= 5
     // on D1Q5, <= 7 on D1Q7), higher-degree polynomials, and real-exponent models, each with its
     // own launches, so that one high-degree or real-exponent request does not send the whole
@@ -315,6 +335,7 @@ int advance(lbhpde_server_s *S) {
                 m.push_back(lbh::Member{r->seg(), r->off[r->cur], st});
                 n = std::max(n, st);
                 r->done += st;
+                blk.members.emplace_back(r, st);
             }
             // one launch per resident size class, each on a lane of its own
             std::vector<lbh::Member> mc[lbh::kRingClasses];
@@ -338,6 +359,7 @@ int advance(lbhpde_server_s *S) {
                     Req *r = halo[q];
                     m.push_back(lbh::Member{r->seg(), r->off[r->cur ^ 1], st});
                     n = std::max(n, st);
+                    blk.members.emplace_back(r, st);
                     r->cur ^= 1;  // the launch writes the other buffer
                     r->done += st;
                     left[q] -= st;
@@ -349,7 +371,25 @@ int advance(lbhpde_server_s *S) {
             }
         }
     }
-    if (plan.empty()) return LBHPDE_OK;
+    if (plan.empty()) {
+        blk.id = -1;
+        return LBHPDE_OK;
+    }
+    ++S->next_block;
+    for (auto &mr : blk.members)
+        if (mr.first->done >= mr.first->nsteps) mr.first->final_block = blk.id;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->t_plan += std::chrono::duration<double>(Clock::now() - t_enter).count();
+    return LBHPDE_OK;
+}
+
+// Issue a planned block: its tables in one upload each, then its launches on the stream lanes,
+// joined back into `stream` (no wait).  The next block's tables are uploaded on `stream` after
+// this block's join, so one set of table buffers serves every block.
+int launch_block(lbhpde_server_s *S, Block &blk) {
+    const auto t_enter = Clock::now();
+    std::vector<Planned> &plan = blk.plan;
+    const int par = (int)(blk.id & 1);
     std::vector<lbk::OnchipInst> insts;
     std::vector<int> first;
     for (Planned &pl : plan) {
@@ -360,8 +400,7 @@ int advance(lbhpde_server_s *S) {
     }
     SRC(S->insts_d.ensure(insts.size()));
     SRC(S->first_d.ensure(first.size()));
-    const auto tp = Clock::now();
-    SCK(cudaEventRecord(S->ev_t0, S->stream));
+    SCK(cudaEventRecord(S->ev_t0[par], S->stream));
     SCK(cudaMemcpyAsync(S->insts_d.p, insts.data(), sizeof(lbk::OnchipInst) * insts.size(), cudaMemcpyHostToDevice,
                         S->stream));
     SCK(cudaMemcpyAsync(S->first_d.p, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, S->stream));
@@ -381,17 +420,21 @@ int advance(lbhpde_server_s *S) {
             SCK(cudaEventRecord(S->ev_done[i], S->lane[i]));
             SCK(cudaStreamWaitEvent(S->stream, S->ev_done[i], 0));
         }
-    SCK(cudaEventRecord(S->ev_t1, S->stream));
-    const auto tl = Clock::now();
-    SCK(cudaStreamSynchronize(S->stream));
-    const auto tw = Clock::now();
+    SCK(cudaEventRecord(S->ev_t1[par], S->stream));
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->t_launch += std::chrono::duration<double>(Clock::now() - t_enter).count();
+    return LBHPDE_OK;
+}
+
+// After `stream` has drained: a launched block's GPU time, and its steps as done.
+int complete_block(lbhpde_server_s *S, Block &blk) {
+    if (blk.id < 0) return LBHPDE_OK;
+    const int par = (int)(blk.id & 1);
     float ms = 0.0f;
-    SCK(cudaEventElapsedTime(&ms, S->ev_t0, S->ev_t1));
+    SCK(cudaEventElapsedTime(&ms, S->ev_t0[par], S->ev_t1[par]));
+    for (auto &mr : blk.members) mr.first->done_gpu += mr.second;
     std::lock_guard<std::mutex> lk(S->mu);
     S->gpu_busy += ms * 1e-3;
-    S->t_plan += std::chrono::duration<double>(tp - t_enter).count();
-    S->t_launch += std::chrono::duration<double>(tl - tp).count();
-    S->t_wait += std::chrono::duration<double>(tw - tl).count();
     return LBHPDE_OK;
 }
 
@@ -438,6 +481,7 @@ void worker_main(lbhpde_server_s *S) {
         S->cv_done.notify_all();
         return;
     }
+    Block inflight;  // launched and not yet waited for (id -1: none)
     for (;;) {
         std::vector<Req *> adm;
         const auto ta = Clock::now();
@@ -466,26 +510,36 @@ void worker_main(lbhpde_server_s *S) {
                 adm.push_back(r);
                 it = S->queue.erase(it);
             }
-            if (S->active.empty() && adm.empty()) {
+            if (S->active.empty() && adm.empty() && inflight.id < 0) {
                 S->cv_work.wait_for(lk, std::chrono::milliseconds(20));
                 continue;
             }
         }
+        // admission, set-up and the plan of the next block run while the block in flight runs
         const auto ts = Clock::now();
         int rc = setup_admitted(S, adm);
         for (Req *r : adm) S->active.push_back(r);
         const auto tv = Clock::now();
-        if (rc == LBHPDE_OK) rc = advance(S);
+        Block next;
+        if (rc == LBHPDE_OK) rc = plan_block(S, next);
+        // wait for the block in flight and the set-up of the admitted requests
+        const auto tw = Clock::now();
         if (rc == LBHPDE_OK) rc = cudaStreamSynchronize(S->stream) == cudaSuccess ? LBHPDE_OK : LBHPDE_ERR_CUDA;
         const auto tr = Clock::now();
+        if (rc == LBHPDE_OK) rc = complete_block(S, inflight);
+        const long long done_id = inflight.id;
+        inflight = Block{};
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->t_admit += std::chrono::duration<double>(ts - ta).count();
             S->t_setup += std::chrono::duration<double>(tv - ts).count();
+            S->t_wait += std::chrono::duration<double>(tr - tw).count();
         }
+        // retire the requests whose last block has completed (and those that take no steps);
+        // the ones that finish in the planned block stay until it has run
         std::vector<Req *> still;
         for (Req *r : S->active) {
-            if (rc == LBHPDE_OK && r->done >= r->nsteps) {
+            if (rc == LBHPDE_OK && r->done >= r->nsteps && r->final_block <= done_id) {
                 S->node_updates += (double)r->N * (double)r->nsteps;
                 rc = retire(S, r);
             } else {
@@ -496,6 +550,10 @@ void worker_main(lbhpde_server_s *S) {
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->t_retire += std::chrono::duration<double>(Clock::now() - tr).count();
+        }
+        if (rc == LBHPDE_OK && next.id >= 0) {
+            rc = launch_block(S, next);
+            if (rc == LBHPDE_OK) inflight = std::move(next);
         }
         if (rc != LBHPDE_OK) {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -520,7 +578,7 @@ void worker_main(lbhpde_server_s *S) {
 void fill_result(const Req *r, lbhpde_result *info) {
     if (!info) return;
     info->status = r->status;
-    info->steps_done = r->done;
+    info->steps_done = r->done_gpu;
     info->submit_s = r->t_submit;
     info->admit_s = r->t_admit;
     info->finish_s = r->t_finish;
@@ -549,8 +607,11 @@ extern "C" int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t 
     int prev = 0;
     bool ok = cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(device) == cudaSuccess &&
               cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&S->up, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&S->ev_setup, cudaEventDisableTiming) == cudaSuccess &&
               cudaEventCreateWithFlags(&S->ev_up, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreate(&S->ev_t0) == cudaSuccess && cudaEventCreate(&S->ev_t1) == cudaSuccess &&
+              cudaEventCreate(&S->ev_t0[0]) == cudaSuccess && cudaEventCreate(&S->ev_t1[0]) == cudaSuccess &&
+              cudaEventCreate(&S->ev_t0[1]) == cudaSuccess && cudaEventCreate(&S->ev_t1[1]) == cudaSuccess &&
               cudaMalloc(&S->arena_d, device_bytes) == cudaSuccess &&
               cudaMalloc((void **)&S->coefD_d, sizeof(double) * (size_t)max_active * kCoefStride) == cudaSuccess;
     for (int i = 0; ok && i < lbhpde_server_s::kLanes; ++i)
@@ -567,13 +628,17 @@ extern "C" int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t 
         if (S->coefD_d) cudaFree(S->coefD_d);
         if (S->coefT_d && S->coefT_d != S->coefD_d) cudaFree(S->coefT_d);
         if (S->stream) cudaStreamDestroy(S->stream);
+        if (S->up) cudaStreamDestroy(S->up);
+        if (S->ev_setup) cudaEventDestroy(S->ev_setup);
         for (int i = 0; i < lbhpde_server_s::kLanes; ++i) {
             if (S->lane[i]) cudaStreamDestroy(S->lane[i]);
             if (S->ev_done[i]) cudaEventDestroy(S->ev_done[i]);
         }
         if (S->ev_up) cudaEventDestroy(S->ev_up);
-        if (S->ev_t0) cudaEventDestroy(S->ev_t0);
-        if (S->ev_t1) cudaEventDestroy(S->ev_t1);
+        for (int i = 0; i < 2; ++i) {
+            if (S->ev_t0[i]) cudaEventDestroy(S->ev_t0[i]);
+            if (S->ev_t1[i]) cudaEventDestroy(S->ev_t1[i]);
+        }
         delete S;
         return e == cudaErrorMemoryAllocation ? LBHPDE_ERR_OOM : LBHPDE_ERR_CUDA;
     }
@@ -698,14 +763,19 @@ extern "C" int lbhpde_server_destroy(lbhpde_server_t S) {
     cudaFree(S->arena_d);
     if (S->coefT_d != S->coefD_d) cudaFree(S->coefT_d);
     cudaFree(S->coefD_d);
+    cudaStreamSynchronize(S->up);
     cudaStreamDestroy(S->stream);
+    cudaStreamDestroy(S->up);
+    cudaEventDestroy(S->ev_setup);
     for (int i = 0; i < lbhpde_server_s::kLanes; ++i) {
         cudaStreamDestroy(S->lane[i]);
         cudaEventDestroy(S->ev_done[i]);
     }
     cudaEventDestroy(S->ev_up);
-    cudaEventDestroy(S->ev_t0);
-    cudaEventDestroy(S->ev_t1);
+    for (int i = 0; i < 2; ++i) {
+        cudaEventDestroy(S->ev_t0[i]);
+        cudaEventDestroy(S->ev_t1[i]);
+    }
     cudaSetDevice(prev);
     delete S;
     return LBHPDE_OK;
