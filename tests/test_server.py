@@ -60,6 +60,7 @@ def alone(L, p, precision):
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_results_identical_alone_and_in_the_mix(L, precision):
     P = L.FP32_DEV if precision == "fp32" else L.FP64
+    t_start = time.time()
     srv = L.Server(precision=P, device_bytes=64 << 20, max_active=64, steps_per_block=128)
     first = mixed_requests(20, seed=1)
     ids = [srv.submit_problem(p) for p in first]
@@ -82,6 +83,11 @@ def test_results_identical_alone_and_in_the_mix(L, precision):
     srv.close()
     assert len(results) == len(ids), st
     assert st["error"] == 0 and st["completed"] == len(ids)
+    # the scheduler's phase times (one thread, so they add up to at most the wall time)
+    phases = [st[k] for k in ("host_admit_s", "host_setup_s", "host_plan_s", "host_launch_s", "host_wait_s",
+                              "host_retire_s")]
+    assert min(phases) >= 0 and st["gpu_busy_s"] > 0
+    assert sum(phases) <= time.time() - t_start
     for rid, p in zip(ids, probs):
         rc, phi, info = results[rid]
         assert rc == L.OK, (p.eq.name, p.N, rc)
