@@ -32,10 +32,9 @@ struct Packed {
     int ncta() const { return first.empty() ? 0 : (int)first.size() - 1; }
 };
 
-// Largest CTA (threads) of the compiled on-chip variant for (element size, lattice, nodes per
-// thread); 0 when no variant exists.
-// Threads per CTA of the on-chip kernels: resident instances (capacity = threads * K nodes)
-// and temporally blocked windows (FP32 D1Q5 with K = 8 uses smaller window CTAs).
+// Threads per CTA of the on-chip kernels for (element size, lattice, nodes per thread), 0 when
+// no variant exists: resident instances (capacity = threads * K nodes) and temporally blocked
+// windows (FP32 D1Q5 with K = 8 uses smaller window CTAs).
 constexpr int kHaloThreadsF32Q5 = 128;
 int onchip_maxt(size_t esz, int b, int K);
 int onchip_maxt_halo(size_t esz, int b, int K);

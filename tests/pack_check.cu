@@ -1,0 +1,148 @@
+// Host-side check of the on-chip planning (no GPU): size classes, resident packing and window
+// cutting, called through the library's exported functions on random member sets.  Prints
+// "ok" and exits 0 when every invariant holds; otherwise prints the first violation and exits 1.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <random>
+#include <set>
+#include <vector>
+
+#include "lbhpde_internal.h"
+
+static int fails = 0;
+#define CHECK(c, ...)                                  \
+    do {                                               \
+        if (!(c) && fails++ == 0) {                    \
+            std::printf("FAIL %s:%d: ", __FILE__, __LINE__); \
+            std::printf(__VA_ARGS__);                  \
+            std::printf("\n");                         \
+        }                                              \
+    } while (0)
+
+static std::vector<lbh::Member> members(std::mt19937 &g, int count, long long nmin, long long nmax, int D) {
+    std::vector<lbh::Member> m;
+    long long off = 0;
+    std::uniform_int_distribution<long long> dn(nmin, nmax);
+    for (int i = 0; i < count; ++i) {
+        lbh::Member mb{};
+        mb.seg.N = (int)dn(g);
+        mb.seg.ld = (mb.seg.N + 31) / 32 * 32;
+        mb.seg.off = off;
+        mb.seg.D = D;
+        mb.off2 = off;
+        mb.steps = 1 + i % 7;
+        off += mb.seg.ld * 7;
+        m.push_back(mb);
+    }
+    return m;
+}
+
+static void check_ring(const lbh::Packed &p, const std::vector<lbh::Member> &m, int b, int K, int threads, int dc) {
+    std::map<long long, int> seen;
+    int maxn = 0;
+    for (int c = 0; c < p.ncta(); ++c) {
+        const int i0 = p.first[c], i1 = p.first[c + 1];
+        CHECK(i1 > i0 && i1 - i0 <= 32, "cta %d holds %d instances", c, i1 - i0);
+        maxn = std::max(maxn, i1 - i0);
+        int tb = 0, sco = 0;
+        for (int i = i0; i < i1; ++i) {
+            const lbk::OnchipInst &I = p.insts[i];
+            CHECK(I.tbase == tb && I.tbase % 32 == 0, "instance %d: thread base %d, expected %d", i, I.tbase, tb);
+            CHECK(I.nthr == (I.N + K - 1) / K, "instance %d: %d threads for N = %d", i, I.nthr, I.N);
+            CHECK(I.npos == I.N && I.vlo == 0 && I.vhi == I.N && I.x0 == 0, "instance %d: ring window", i);
+            CHECK(I.il == i - i0, "instance %d: tail slot %d", i, I.il);
+            CHECK(I.scoef == sco && I.scoef % 4 == 0, "instance %d: coefficient offset %d", i, I.scoef);
+            sco += lbk::cblock(b, dc > 0 ? dc : I.D);
+            tb += (I.nthr + 31) / 32 * 32;
+            ++seen[I.off];
+        }
+        CHECK(tb <= threads && tb <= p.nthreads, "cta %d uses %d threads of %d (plan %d)", c, tb, threads, p.nthreads);
+    }
+    CHECK(p.nthreads <= threads, "plan threads %d > %d", p.nthreads, threads);
+    CHECK(p.max_inst % 4 == 0 && p.max_inst >= maxn, "max_inst %d for %d", p.max_inst, maxn);
+    CHECK(seen.size() == m.size(), "%zu of %zu members placed", seen.size(), m.size());
+    for (auto &kv : seen) CHECK(kv.second == 1, "member at %lld placed %d times", kv.first, kv.second);
+}
+
+static void check_halo(const lbh::Packed &p, const std::vector<lbh::Member> &m, int K, int H, int maxt) {
+    std::map<long long, std::vector<int>> cover;  // member offset -> coverage count per node
+    for (const lbh::Member &mb : m) cover[mb.seg.off].assign(mb.seg.N, 0);
+    for (int c = 0; c < p.ncta(); ++c) {
+        CHECK(p.first[c + 1] - p.first[c] == 1, "window cta %d holds %d windows", c, p.first[c + 1] - p.first[c]);
+        const lbk::OnchipInst &I = p.insts[p.first[c]];
+        CHECK(I.vlo == H && I.npos == I.vhi + H && I.vhi > I.vlo, "window %d: [%d, %d) of %d", c, I.vlo, I.vhi, I.npos);
+        CHECK(I.nthr == (I.npos + K - 1) / K && I.nthr <= maxt, "window %d: %d threads", c, I.nthr);
+        auto &cv = cover[I.off];
+        for (int q = I.vlo; q < I.vhi; ++q) {
+            long long x = ((long long)I.x0 + q) % I.N;
+            x += x < 0 ? I.N : 0;
+            ++cv[(size_t)x];
+        }
+    }
+    CHECK(p.nthreads == maxt, "window threads %d, expected %d", p.nthreads, maxt);
+    for (auto &kv : cover)
+        for (size_t x = 0; x < kv.second.size(); ++x)
+            if (kv.second[x] != 1) {
+                CHECK(false, "member at %lld: node %zu covered %d times", kv.first, x, kv.second[x]);
+                break;
+            }
+}
+
+int main() {
+    std::mt19937 g(20260907);
+    struct Cfg {
+        size_t esz;
+        int b, K;
+    };
+    const Cfg cfgs[] = {{4, 5, 8}, {4, 5, 4}, {4, 5, 2}, {4, 7, 8}, {4, 7, 4}, {8, 5, 4}, {8, 5, 2}, {8, 7, 4}};
+    for (const Cfg &cf : cfgs) {
+        const int W = (cf.b - 1) / 2;
+        const int cap = lbh::onchip_maxt(cf.esz, cf.b, cf.K) * cf.K;
+        for (int trial = 0; trial < 20; ++trial) {
+            const int D = trial % 2 ? 5 : 9, dc = lbh::onchip_dc(cf.b, D);
+            // resident members: size classes, then each class packed
+            auto m = members(g, 1 + trial * 9, 2 * W, cap, D);
+            std::vector<lbh::Member> cls[lbh::kRingClasses];
+            lbh::split_ring_classes(cf.esz, cf.b, cf.K, m, cls);
+            size_t total = 0;
+            for (int c = 0; c < lbh::kRingClasses; ++c) {
+                total += cls[c].size();
+                for (const lbh::Member &mb : cls[c])
+                    CHECK(lbh::ring_class(cf.esz, cf.b, cf.K, mb.seg.N) == c || c == lbh::kRingClasses - 1,
+                          "N = %d in class %d", mb.seg.N, c);
+                if (cls[c].empty()) continue;
+                const int thr = lbh::ring_class_threads(cf.esz, cf.b, cf.K, c);
+                lbh::Packed p;
+                CHECK(lbh::pack_ring(cf.b, cf.esz, cf.K, dc, cls[c], p, thr) == LBHPDE_OK, "pack_ring failed");
+                check_ring(p, cls[c], cf.b, cf.K, thr, dc);
+                // the gap fillers of the largest class do not open CTAs of their own
+                if (c == lbh::kRingClasses - 1) {
+                    int own = 0;
+                    for (const lbh::Member &mb : cls[c]) own += lbh::ring_class(cf.esz, cf.b, cf.K, mb.seg.N) == c;
+                    CHECK(own == 0 ? p.ncta() == 0 : p.ncta() <= own, "%d CTAs for %d own members", p.ncta(), own);
+                }
+            }
+            CHECK(total == m.size(), "%zu of %zu members classified", total, m.size());
+            // windows: batch-sized and server-wide, several depths
+            for (bool wide : {false, true}) {
+                const int maxt = wide ? lbh::onchip_maxt(cf.esz, cf.b, cf.K) : lbh::onchip_maxt_halo(cf.esz, cf.b, cf.K);
+                for (int eighths : {6, 7}) {
+                    const int T = lbh::default_tblk(maxt * cf.K, W, eighths), H = T * W;
+                    CHECK(maxt * cf.K - 2 * H >= maxt * cf.K * eighths / 8 && (T & (T - 1)) == 0 && T >= 1,
+                          "default depth %d for %d nodes", T, maxt * cf.K);
+                    auto mh = members(g, 1 + trial % 5, 2 * W, 3 * cap + 17, D);
+                    lbh::Packed p;
+                    CHECK(lbh::pack_halo(cf.b, cf.esz, cf.K, dc, H, mh, p, wide) == LBHPDE_OK, "pack_halo failed");
+                    check_halo(p, mh, cf.K, H, maxt);
+                }
+            }
+        }
+    }
+    if (fails) {
+        std::printf("%d failures\n", fails);
+        return 1;
+    }
+    std::printf("ok\n");
+    return 0;
+}
