@@ -1,5 +1,6 @@
 // Host-side check of the on-chip planning (no GPU): size classes, resident packing and window
-// cutting, called through the library's exported functions on random member sets.  Prints
+// cutting on random member sets, and the position shift of bounded resident instances, called
+// through the library's exported functions.  Prints
 // "ok" and exits 0 when every invariant holds; otherwise prints the first violation and exits 1.
 #include <cstdio>
 #include <cstdlib>
@@ -139,6 +140,28 @@ int main() {
             }
         }
     }
+    // bounded resident instances: the host's position shift puts each end's outer nodes and its
+    // extrapolation node in one warp of live threads, inside the CTA
+    const int KB = lbh::kBoundedK, wpos = 32 * KB;  // positions per warp
+    long long shifted = 0;
+    for (int b : {5, 7}) {
+        const int W = (b - 1) / 2;
+        for (int depth = 1; depth <= 4; ++depth)
+            for (int N = 2 * (W + depth); N <= KB * lbh::kBoundedMaxT; ++N) {
+                const int sh = lbh::bounded_shift(b, N, depth);
+                if (sh < 0) {
+                    // only when the shifted grid would not fit the CTA
+                    CHECK(N + wpos > KB * lbh::kBoundedMaxT, "no shift for N = %d, depth %d, b = %d", N, depth, b);
+                    continue;
+                }
+                ++shifted;
+                const int kL = W - 1 + depth, kR = N - W - depth;
+                CHECK(N + sh <= KB * lbh::kBoundedMaxT, "N = %d + shift %d exceeds the CTA", N, sh);
+                CHECK((0 + sh) / wpos == (kL + sh) / wpos, "left end split, N = %d, depth %d", N, depth);
+                CHECK((kR + sh) / wpos == (N - 1 + sh) / wpos, "right end split, N = %d, depth %d", N, depth);
+            }
+    }
+    CHECK(shifted > 10000, "only %lld bounded cases placed", shifted);
     if (fails) {
         std::printf("%d failures\n", fails);
         return 1;

@@ -5,7 +5,9 @@ resident CTA packing and window cutting, checked on random member sets by a smal
 Invariants: every member placed exactly once; warp-aligned, non-overlapping thread runs within
 the CTA size; at most 32 instances per CTA; 16-byte aligned coefficient offsets; only gap fillers
 move up a size class; the valid nodes of a member's windows cover each of its nodes exactly
-once; window depths leave the stated share of a window valid.
+once; window depths leave the stated share of a window valid; for bounded resident instances,
+the position shift puts each end's outer nodes and extrapolation node in one warp inside the CTA
+(every depth 1-4 and grid size up to the CTA's 2048 nodes).
 """
 import os
 import shutil
