@@ -641,7 +641,8 @@ def cpu_oracle_rate(args, sample_s=15.0):
         t0 = time.perf_counter()
         oracle.run_problem(probs[0], nsteps=5)
         dt1 = max((time.perf_counter() - t0) / 5 / max(probs[0].N, 1), 1e-12)  # seconds per node-update
-        steps = int(max(5, min(1000, sample_s * cores / (dt1 * sum(p.N for p in probs)))))
+        # one request per thread: the largest one sets the wall time of the sample
+        steps = int(max(5, min(1000, sample_s / (dt1 * max(p.N for p in probs)))))
         t0 = time.perf_counter()
         with ThreadPoolExecutor(cores) as ex:
             list(ex.map(lambda p: oracle.run_problem(p, nsteps=steps), probs))
