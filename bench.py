@@ -50,8 +50,9 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP32 lanes per SM and SM count of GB300: the ALU roof of the on-chip kernel.
-SMS, FP32_LANES = 152, 128
+# FP32 lanes per SM of GB300 (the SM count is read from the device): the ALU roof of the on-chip
+# kernels.
+FP32_LANES = 128
 FP64_FMA_PER_SM_CLK = 2  # GB300: 152 x 2 x 2 flops x 2070 MHz = 1.26 TFLOP/s, the nominal 1.25
 BOUNDED_STEPS = 1000
 BOUNDED_TAU = (1.989, 2.6)
@@ -115,19 +116,26 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def ensemble_problems(rank=0, members=4096):
-    return W.kdv_burgers_ensemble(count=members, seed=W.SEED + rank)
+def ensemble_problems(rank=0, members=4096, world=1):
+    """Members rank, rank + world, ... of the one seeded ensemble (a partition over the ranks)."""
+    return W.kdv_burgers_ensemble(count=members)[rank::world]
 
 
-def alu_peak(esz, clocks, peaks):
+def sm_count(torch, dev):
+    """Streaming multiprocessors of the device, as the runtime reports them."""
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def alu_peak(esz, clocks, peaks, sms):
     """ALU roof at the median SM clock under load: FP32 lanes, or GB300's FP64 FMA rate."""
     sm_mhz = clocks["sm_mhz"] or peaks.get("sm_max_mhz", 2070.0)
     if esz == 4:
-        return (SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12,
-                f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 x median SM clock under load")
-    return (SMS * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12,
-            f"derived: {SMS} SMs x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 x median SM clock under load "
-            f"(1.26 TFLOP/s at 2070 MHz, the nominal 1.25)")
+        return (sms * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12,
+                f"derived: {sms} SMs (queried from the device) x {FP32_LANES} FP32 lanes x 2 x median SM clock "
+                f"under load ({sm_mhz:.0f} MHz)")
+    return (sms * FP64_FMA_PER_SM_CLK * 2 * sm_mhz * 1e6 / 1e12,
+            f"derived: {sms} SMs (queried from the device) x {FP64_FMA_PER_SM_CLK} FP64 FMA/clk x 2 x median SM "
+            f"clock under load ({sm_mhz:.0f} MHz; 1.26 TFLOP/s at 152 SMs and 2070 MHz, the nominal 1.25)")
 
 
 def bounded_problems(members):
@@ -141,14 +149,16 @@ def bounded_problems(members):
     return probs
 
 
-def workload_problems(args, rank=0):
+def workload_problems(args, rank=0, world=1):
     """(problems, steps per benchmark step, description) of the workload; both arms name the
-    workload by this description."""
+    workload by this description.  The ensemble is one seeded batch whose members rank,
+    rank + world, ... this rank takes; the description names the whole batch."""
     if args.workload == "ensemble":
-        probs = ensemble_problems(rank, args.members)
+        probs = ensemble_problems(rank, args.members, world)
         nsteps = W.ENSEMBLE_STEPS
+        total_n = sum(p.N for p in ensemble_problems(0, args.members, 1)) if world > 1 else sum(p.N for p in probs)
         desc = (f"kdv_burgers_ensemble_{args.members}: {args.members} x N~U{{256..8192}} "
-                f"(sum N = {sum(p.N for p in probs)}), "
+                f"(sum N = {total_n}), "
                 f"D1Q5 scheme 1, dx={W.ENSEMBLE_DX}, dt={W.ENSEMBLE_DT}, tau={W.ENSEMBLE_TAU}, "
                 f"{nsteps} steps per benchmark step")
     elif args.workload == "bounded":
@@ -218,7 +228,31 @@ def aggregate(t_local, units_local, world, device="cpu"):
     return float(u.item()) / float(t.item()), float(t.item())
 
 
-def run_ours(args, rank, world):
+def gather_member_records(records, world, device="cpu"):
+    """Per-member records (index, sum phi, max |phi|, non-finite count) of every rank, gathered
+    to all ranks and ordered by member index: the results of the whole partitioned batch."""
+    import numpy as _np
+    if world <= 1:
+        return sorted(records)
+    import torch
+    import torch.distributed as dist
+
+    loc = torch.tensor(_np.asarray(records, dtype=_np.float64).reshape(-1, 4), device=device)
+    n = torch.tensor([loc.shape[0]], device=device)
+    sizes = [torch.zeros_like(n) for _ in range(world)]
+    dist.all_gather(sizes, n)
+    m = int(max(int(x.item()) for x in sizes))
+    pad = torch.zeros((m, 4), dtype=torch.float64, device=device)
+    pad[: loc.shape[0]] = loc
+    bufs = [torch.zeros_like(pad) for _ in range(world)]
+    dist.all_gather(bufs, pad)
+    out = []
+    for b, k in zip(bufs, sizes):
+        out += [tuple(r) for r in b[: int(k.item())].cpu().numpy().tolist()]
+    return sorted((int(r[0]), r[1], r[2], int(r[3])) for r in out)
+
+
+def run_ours(args, rank, world, cpu=None):
     import torch
 
     from paper_0907_1720_gb300 import lbhpde as L

@@ -194,8 +194,9 @@ int lbhpde_step(lbhpde_t h, long nsteps);
 int lbhpde_step_nee(lbhpde_t h, long nsteps, const double *phib, int phib_on_device);
 
 /* Step a7: copy phi (t = steps taken * dt) into phi_out ([N] doubles, host or device).
- * Host output synchronises.  Returns LBHPDE_ERR_DIVERGED (after copying) if phi has a
- * non-finite value. */
+ * Synchronises the stream (host output: the copy; device output: the 4-byte non-finite flag the
+ * copy kernel raises).  Returns LBHPDE_ERR_DIVERGED (after copying) if phi has a non-finite
+ * value. */
 int lbhpde_read_phi(lbhpde_t h, double *phi_out, int out_on_device);
 
 /* Diagnostics of step a7, reduced on the GPU in double precision. */
@@ -217,8 +218,10 @@ int lbhpde_diagnostics(lbhpde_t h, const double *phistar_device, lbhpde_diag *ou
 int lbhpde_kernel_launches(lbhpde_t h, long long *count);
 
 /* Which kernel lbhpde_step uses (LBHPDE_KERNEL_*).  For the on-chip kernels: the nodes each
- * thread holds (FP32: 2, 4 or 8 on D1Q5, 4 or 8 on D1Q7; FP64: 2 or 4 on D1Q5, 4 on D1Q7) and
- * the steps per launch (resident instances: launch chunk; windows: steps per window, which
+ * thread holds (FP32: 2, 4 or 8 on D1Q5, 4 or 8 on D1Q7; FP64: 2 or 4 on D1Q5, 4 on D1Q7; 16 on
+ * FP32 D1Q5 polynomial models selects the 16-node resident kernel, which holds instances of up
+ * to 8192 nodes and is the automatic choice there, longer ones taking windows of the default
+ * size) and the steps per launch (resident instances: launch chunk; windows: steps per window, which
  * sets the halo to steps * max|e| nodes); 0 = automatic.  Returns LBHPDE_ERR_UNSUPPORTED for a
  * combination the library was not built with, leaving the previous choice in place. */
 int lbhpde_set_kernel(lbhpde_t h, int kernel, int nodes_per_thread, int steps_per_launch);

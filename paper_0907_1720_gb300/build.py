@@ -18,9 +18,9 @@ BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "liblbhpde.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["lbhpde_model.cpp", "lbhpde_api.cu", "lbhpde_onchip_f32.cu", "lbhpde_onchip_f64.cu", "lbhpde_bounded.cu",
-           "lbhpde_noalloc.cu", "lbhpde_server.cu"]
-HEADERS = ["lbhpde_kernels.cuh", "lbhpde_bounded.cuh", "lbhpde_internal.h", "lbhpde_onchip_launch.cuh"]
+SOURCES = ["lbhpde_model.cpp", "lbhpde_api.cu", "lbhpde_onchip_f32.cu", "lbhpde_onchip_f64.cu", "lbhpde_ring.cu",
+           "lbhpde_bounded.cu", "lbhpde_noalloc.cu", "lbhpde_server.cu"]
+HEADERS = ["lbhpde_kernels.cuh", "lbhpde_bounded.cuh", "lbhpde_ring.cuh", "lbhpde_internal.h", "lbhpde_onchip_launch.cuh"]
 
 
 def _nvcc():

@@ -61,6 +61,7 @@ struct Group {
         int ncta() const { return host.ncta(); }
     } ring[lbh::kRingClasses], halo;  // resident instances by CTA size class; windows
     int K = 0, maxt = 0, tblk = 0;
+    int Kr = 0;  // nodes per thread of the resident plans (lbh::kRingK: k_ring)
     int dc = 0;  // compile-time degree of the on-chip kernel variant (0 = run time)
     bool uniform = false;  // every member has the same model (coefficients and omega)
     bool has_nu = false;   // a member has real-exponent terms: the real-exponent variants (on chip: degree code -1)
@@ -197,7 +198,7 @@ namespace lbh {
 
 int onchip_maxt(size_t esz, int b, int K) {
     if (esz == 4) {
-        if (b == 5) return K == 8 ? 512 : (K == 4 ? 1024 : (K == 2 ? 1024 : 0));  // resident CTAs
+        if (b == 5) return K == kRingK ? 512 : (K == 8 ? 512 : (K == 4 ? 1024 : (K == 2 ? 1024 : 0)));  // resident CTAs
         return K == 8 ? 256 : (K == 4 ? 512 : 0);
     }
     if (b == 5) return K == 4 ? 512 : (K == 2 ? 1024 : 0);
@@ -210,9 +211,12 @@ int onchip_maxt(size_t esz, int b, int K) {
 // ensemble against 5.80e11 with 256 threads and 5.61e11 with 512; the D1Q7 and FP64 windows
 // were slower with 128 threads than with their resident CTA size.)
 int onchip_maxt_halo(size_t esz, int b, int K) {
+    if (K == kRingK) return 0;  // the 16-node variant holds resident instances only
     if (esz == 4 && b == 5 && K == 8) return kHaloThreadsF32Q5;
     return onchip_maxt(esz, b, K);
 }
+
+bool ring_split_ok(size_t esz, int b, int dc) { return esz == 4 && b == 5 && dc >= 0; }
 
 int default_K(size_t esz, int b) { return esz == 4 && b == 5 ? 8 : 4; }
 
@@ -222,17 +226,21 @@ int default_K(size_t esz, int b) { return esz == 4 && b == 5 ? 8 : 4; }
 // node-updates/s in 128-thread CTAs against 5.73e11 packed four to a 512-thread CTA; 2048-node
 // ones 6.52e11 against 6.24e11.)  Other configurations have class 2 only.
 int ring_class(size_t esz, int b, int K, long long N) {
-    if (esz == 4 && b == 5 && K == 8) return N <= 128 * K ? 0 : (N <= 256 * K ? 1 : 2);
+    if (esz == 4 && b == 5 && (K == 8 || K == kRingK)) return N <= 128 * K ? 0 : (N <= 256 * K ? 1 : 2);
     return 2;
 }
 int ring_class_threads(size_t esz, int b, int K, int cls) {
-    if (esz == 4 && b == 5 && K == 8) return cls == 0 ? 128 : (cls == 1 ? 256 : 512);
+    if (esz == 4 && b == 5 && (K == 8 || K == kRingK)) return cls == 0 ? 128 : (cls == 1 ? 256 : 512);
     return onchip_maxt(esz, b, K);
 }
+// Threads an instance's run is rounded up to: whole warps for k_onchip, single threads for
+// k_ring (its instances may share a warp)
+int ring_granule(int K) { return K == kRingK ? 1 : 32; }
 
 void split_ring_classes(size_t esz, int b, int K, const std::vector<Member> &m, std::vector<Member> (&out)[kRingClasses]) {
     for (auto &v : out) v.clear();
-    auto pad = [&](long long n) { return (int)(((n + K - 1) / K + 31) & ~31); };
+    const int gr = ring_granule(K);
+    auto pad = [&](long long n) { return (int)(((n + K - 1) / K + gr - 1) / gr * gr); };
     std::vector<int> order(m.size());
     for (size_t i = 0; i < m.size(); ++i) order[i] = (int)i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return pad(m[a].seg.N) > pad(m[c].seg.N); });
@@ -275,7 +283,8 @@ int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Pa
     const int maxt = threads > 0 ? threads : onchip_maxt(esz, b, K);
     if (maxt == 0) return LBHPDE_ERR_UNSUPPORTED;
     auto thr = [&](long long n) { return (int)((n + K - 1) / K); };
-    auto pad = [&](long long n) { return (thr(n) + 31) & ~31; };
+    const int gr = ring_granule(K);
+    auto pad = [&](long long n) { return (thr(n) + gr - 1) / gr * gr; };
     std::vector<int> order(m.size());
     for (size_t i = 0; i < m.size(); ++i) {
         if ((long long)m[i].seg.N > (long long)maxt * K) return LBHPDE_ERR_UNSUPPORTED;
@@ -338,9 +347,15 @@ int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Pa
         coef_max = std::max(coef_max, (size_t)sco);
     }
     out.first.push_back((int)out.insts.size());
+    out.nthreads = (out.nthreads + 31) & ~31;
     out.max_inst = (out.max_inst + 3) & ~3;  // keeps the shared-memory coefficient rows 16-byte aligned
     const int ne = lbk::nedge(b);
-    out.smem = (size_t(4) * ne * out.nthreads + size_t(2) * ne * out.max_inst + coef_max) * esz;
+    if (K == kRingK) {  // exchange rows at the class's CTA size, tails for kRingMaxInst instances
+        out.stride = maxt;
+        out.smem = (size_t(lbk::ring_xchg_elems(b, maxt)) + coef_max) * esz;
+    } else {
+        out.smem = (size_t(4) * ne * out.nthreads + size_t(2) * ne * out.max_inst + coef_max) * esz;
+    }
     if (out.smem > 227 * 1024) return LBHPDE_ERR_UNSUPPORTED;
     return LBHPDE_OK;
 }
@@ -403,6 +418,10 @@ namespace {
 int launch_onchip(int b, size_t esz, int K, int dc, bool halo, const Packed &p, const OnchipInst *insts_d,
                   const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st) {
     if (p.ncta() == 0 || nsteps <= 0) return LBHPDE_OK;
+    if (K == kRingK) {
+        if (halo || esz != 4 || b != 5) return LBHPDE_ERR_UNSUPPORTED;
+        return launch_ring_f32(dc, p, insts_d, first_d, in, out, coefT, nsteps, st);
+    }
     return esz == 4 ? launch_onchip_f32(b, K, dc, halo, p, insts_d, first_d, in, out, coefT, nsteps, st)
                     : launch_onchip_f64(b, K, dc, halo, p, insts_d, first_d, in, out, coefT, nsteps, st);
 }
@@ -621,13 +640,16 @@ int upload_plan(lbhpde_batch_s *bt, Group::Plan &pl) {
 
 // Members that fit one CTA become resident instances; longer members (or all, with
 // force_halo) are cut into temporally blocked windows of tblk steps.
-int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) {
+// Kr: nodes per thread of the resident instances (K, or lbh::kRingK for the 16-node kernel, whose
+// instances hold up to 8192 nodes; the windows then keep K).
+int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int Kr, int tblk, bool force_halo) {
     g.onchip_ok = false;
-    const int maxt = lbh::onchip_maxt(bt->esz, g.b, K);
-    if (maxt == 0 || K < lbk::wmax(g.b)) return LBHPDE_ERR_UNSUPPORTED;
+    const int maxt = lbh::onchip_maxt(bt->esz, g.b, Kr);
+    if (maxt == 0 || K < lbk::wmax(g.b) || lbh::onchip_maxt(bt->esz, g.b, K) == 0) return LBHPDE_ERR_UNSUPPORTED;
     const int W = lbk::wmax(g.b);
-    const int cap = maxt * K, cap_h = lbh::onchip_maxt_halo(bt->esz, g.b, K) * K;
+    const int cap = maxt * Kr, cap_h = lbh::onchip_maxt_halo(bt->esz, g.b, K) * K;
     g.dc = g.has_nu ? -1 : lbh::onchip_dc(g.b, g.maxD);  // real exponents: their own variant
+    if (Kr == lbh::kRingK && !lbh::ring_split_ok(bt->esz, g.b, g.dc)) return LBHPDE_ERR_UNSUPPORTED;
     if (tblk <= 0) tblk = lbh::default_tblk(cap_h, W);
     const int H = tblk * W;
     std::vector<lbh::Member> resident, ring[lbh::kRingClasses], halo;
@@ -635,7 +657,7 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
         const lbh::Member mb{bt->segs_h[i], bt->segs_h[i].off, 1 << 30};
         (bt->N[i] <= cap && !force_halo ? resident : halo).push_back(mb);
     }
-    lbh::split_ring_classes(bt->esz, g.b, K, resident, ring);
+    lbh::split_ring_classes(bt->esz, g.b, Kr, resident, ring);
     // windows must keep some valid nodes; resident members only chunk their launches by tblk
     if (!halo.empty() && cap_h - 2 * H < 32) return LBHPDE_ERR_UNSUPPORTED;
     // the previous plan's device tables (a re-plan after lbhpde_batch_set_kernel)
@@ -649,12 +671,13 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int tblk, bool force_halo) 
     g.halo = Group::Plan{};
     for (int c = 0; c < lbh::kRingClasses; ++c) {
         if (ring[c].empty()) continue;
-        RC(lbh::pack_ring(g.b, bt->esz, K, g.dc, ring[c], g.ring[c].host, lbh::ring_class_threads(bt->esz, g.b, K, c)));
+        RC(lbh::pack_ring(g.b, bt->esz, Kr, g.dc, ring[c], g.ring[c].host, lbh::ring_class_threads(bt->esz, g.b, Kr, c)));
         RC(upload_plan(bt, g.ring[c]));
     }
     if (!halo.empty()) RC(lbh::pack_halo(g.b, bt->esz, K, g.dc, H, halo, g.halo.host));
     RC(upload_plan(bt, g.halo));
     g.K = K;
+    g.Kr = Kr;
     g.maxt = maxt;
     g.tblk = tblk;
     g.onchip_ok = true;
@@ -665,8 +688,8 @@ int launch_group(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *
                  int cls = lbh::kRingClasses - 1) {
     Group::Plan &pl = halo ? g.halo : g.ring[cls];
     if (pl.ncta() > 0 && nsteps > 0) ++bt->launches;
-    return lbh::launch_onchip(g.b, bt->esz, g.K, g.dc, halo, pl.host, pl.insts, pl.cta_first, in, out, bt->coefT,
-                              nsteps, st);
+    return lbh::launch_onchip(g.b, bt->esz, halo ? g.K : g.Kr, g.dc, halo, pl.host, pl.insts, pl.cta_first, in, out,
+                              bt->coefT, nsteps, st);
 }
 
 int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
@@ -852,18 +875,24 @@ int choose_kernels(lbhpde_batch_s *bt) {
         if (g.members.empty()) continue;
         g.onchip_ok = false;
         if (bt->kernel == LBHPDE_KERNEL_STREAM) continue;
-        int K = bt->K_req > 0 ? bt->K_req : lbh::default_K(bt->esz, g.b);
+        // K_req = kRingK asks for the 16-node resident kernel, whose windows keep the default (or
+        // tuned) K; automatic choice: that kernel wherever it applies
+        const int dcg = g.has_nu ? -1 : lbh::onchip_dc(g.b, g.maxD);
+        const bool ring16 = bt->kernel != LBHPDE_KERNEL_HALO && lbh::ring_split_ok(bt->esz, g.b, dcg) &&
+                            (bt->K_req == 0 || bt->K_req == lbh::kRingK);
+        if (bt->K_req == lbh::kRingK && !ring16) return LBHPDE_ERR_UNSUPPORTED;
+        int K = bt->K_req > 0 && bt->K_req != lbh::kRingK ? bt->K_req : lbh::default_K(bt->esz, g.b);
         int tblk = bt->spl_req;
         int tk = 0, tt = 0;
-        if (tuned_choice(bt->esz, g.b, g.has_nu ? -1 : lbh::onchip_dc(g.b, g.maxD), &tk, &tt)) {
-            if (bt->K_req == 0) K = tk;
+        if (tuned_choice(bt->esz, g.b, dcg, &tk, &tt)) {
+            if (bt->K_req == 0 || bt->K_req == lbh::kRingK) K = tk;
             if (bt->spl_req == 0) tblk = tt;
         }
         if (g.has_nu && K < 4) continue;  // the real-exponent on-chip variants hold 4 or more nodes a thread
         // FP64 real exponents: the FP64 pow binds both kernels, and streaming was faster on GB300
         // (3.88e9 node-updates/s against 3.62e9 in windows on a 2^24-node gKdV grid)
         if (g.has_nu && bt->esz == 8 && bt->kernel == LBHPDE_KERNEL_AUTO) continue;
-        int rc = plan_onchip(bt, g, K, tblk, bt->kernel == LBHPDE_KERNEL_HALO);
+        int rc = plan_onchip(bt, g, K, ring16 ? lbh::kRingK : K, tblk, bt->kernel == LBHPDE_KERNEL_HALO);
         if (rc != LBHPDE_OK) return rc;
     }
     for (auto &g : bt->bgroups)
@@ -1119,8 +1148,8 @@ int batch_read_phi(lbhpde_batch_s *bt, double *out, int on_device) {
     if (!bt->initialised) return LBHPDE_ERR_ARG;
     double *dst = on_device ? out : bt->phi_buf;
     const int nb = (int)bt->all_blocks_h.size();
-    int *flag = on_device ? nullptr : bt->nonfinite;
-    if (flag) CK(cudaMemsetAsync(flag, 0, sizeof(int), bt->stream));
+    int *flag = bt->nonfinite;
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), bt->stream));
     if (bt->esz == 4)
         lbk::k_read_phi<float><<<nb, kGenericThreads, 0, bt->stream>>>((const float *)bt->st[bt->cur], bt->segs,
                                                                        bt->all_blocks, dst, bt->blk_off, kChunk, flag);
@@ -1129,13 +1158,13 @@ int batch_read_phi(lbhpde_batch_s *bt, double *out, int on_device) {
                                                                         bt->all_blocks, dst, bt->blk_off, kChunk, flag);
     CK(cudaGetLastError());
     ++bt->launches;
-    if (!on_device) {
-        int bad = 0;
+    // device or host output alike: the non-finite flag is read back, so the call synchronises
+    int bad = 0;
+    if (!on_device)
         CK(cudaMemcpyAsync(out, bt->phi_buf, sizeof(double) * bt->total, cudaMemcpyDeviceToHost, bt->stream));
-        CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, bt->stream));
-        CK(cudaStreamSynchronize(bt->stream));
-        if (bad) return LBHPDE_ERR_DIVERGED;
-    }
+    CK(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, bt->stream));
+    CK(cudaStreamSynchronize(bt->stream));
+    if (bad) return LBHPDE_ERR_DIVERGED;
     return LBHPDE_OK;
 }
 

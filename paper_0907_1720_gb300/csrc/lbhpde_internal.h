@@ -9,6 +9,7 @@
 #include "lbhpde.h"
 #include "lbhpde_bounded.cuh"
 #include "lbhpde_kernels.cuh"
+#include "lbhpde_ring.cuh"
 
 namespace lbh {
 
@@ -29,6 +30,7 @@ struct Packed {
     int nthreads = 32;  // threads per CTA
     int max_inst = 1;   // instances per CTA (resident mode: rounded up to a multiple of 4)
     size_t smem = 0;    // dynamic shared memory per CTA, bytes
+    int stride = 0;     // k_ring: the class's CTA size, the row stride of its exchange buffers
     int ncta() const { return first.empty() ? 0 : (int)first.size() - 1; }
 };
 
@@ -36,6 +38,11 @@ struct Packed {
 // no variant exists: resident instances (capacity = threads * K nodes) and temporally blocked
 // windows (FP32 D1Q5 with K = 8 uses smaller window CTAs).
 constexpr int kHaloThreadsF32Q5 = 128;
+// Nodes a thread of the 16-node resident kernel (k_ring, FP32 D1Q5) holds: an instance of up to
+// 16 * 512 = 8192 nodes stays in one CTA.  Planned with K == kRingK, resident instances only.
+constexpr int kRingK = 16;
+// Whether members of (element size, lattice, on-chip degree code) can take k_ring.
+bool ring_split_ok(size_t esz, int b, int dc);
 int onchip_maxt(size_t esz, int b, int K);
 int onchip_maxt_halo(size_t esz, int b, int K);
 int default_K(size_t esz, int b);
@@ -47,13 +54,16 @@ int default_tblk(int capacity, int W, int valid_eighths = 7);
 // Compile-time degree variant the on-chip kernel uses for a set of members of maximum degree D.
 int onchip_dc(int b, int maxD);
 
-// Resident instances (N <= capacity): first fit, largest first, warp-aligned runs, <= 32 per CTA,
-// in CTAs of `threads` threads (0: the configuration's resident CTA size).
+// Resident instances (N <= capacity): first fit, largest first, <= 32 per CTA, in CTAs of `threads`
+// threads (0: the configuration's resident CTA size).  Runs of threads are warp-aligned for
+// k_onchip and thread-granular for k_ring (K == kRingK).
 int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Packed &out, int threads = 0);
 // Resident size class of an instance of N nodes (0, 1, 2) and the CTA size of a class.
 constexpr int kRingClasses = 3;
 int ring_class(size_t esz, int b, int K, long long N);
 int ring_class_threads(size_t esz, int b, int K, int cls);
+// Threads an instance's run is rounded up to (32 for k_onchip, 1 for k_ring).
+int ring_granule(int K);
 // Resident members by the CTA size class they take: their own class, or the largest one where
 // they fill a gap left by larger instances.
 void split_ring_classes(size_t esz, int b, int K, const std::vector<Member> &m, std::vector<Member> (&out)[kRingClasses]);
@@ -63,8 +73,11 @@ void split_ring_classes(size_t esz, int b, int K, const std::vector<Member> &m, 
 int pack_halo(int b, size_t esz, int K, int dc, int H, const std::vector<Member> &m, Packed &out,
               bool wide = false);
 
+// K == kRingK launches k_ring (resident plans only).
 int launch_onchip(int b, size_t esz, int K, int dc, bool halo, const Packed &p, const lbk::OnchipInst *insts_d,
                   const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st);
+int launch_ring_f32(int dc, const Packed &p, const lbk::OnchipInst *insts_d, const int *first_d, const void *in,
+                    void *out, const void *coefT, int nsteps, cudaStream_t st);
 // the same for one precision (lbhpde_onchip_f32.cu, lbhpde_onchip_f64.cu)
 int launch_onchip_f32(int b, int K, int dc, bool halo, const Packed &p, const lbk::OnchipInst *insts_d,
                       const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st);

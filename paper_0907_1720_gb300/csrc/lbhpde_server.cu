@@ -317,12 +317,16 @@ int plan_block(lbhpde_server_s *S, Block &blk) {
         const int maxt = lbh::onchip_maxt(S->esz, b, K);
         const int cap = maxt * K, W = (b - 1) / 2;
         const int tblk = lbh::default_tblk(cap, W, 6);  // windows as wide as a resident CTA
+        // resident requests: the 16-node kernel (up to 8192 nodes) where it applies (FP32 D1Q5
+        // polynomial models), else the windows' K
+        const int Kr = lbh::ring_split_ok(S->esz, b, kind == 2 ? -1 : 0) ? lbh::kRingK : K;
+        const int capr = lbh::onchip_maxt(S->esz, b, Kr) * Kr;
         std::vector<Req *> ring, halo;
         int maxD = 0;
         for (Req *r : S->active)
             if (r->mi.b == b && r->done < r->nsteps &&
                 (r->mi.nu_rows > 1 ? 2 : (r->mi.D > dcmax ? 1 : 0)) == kind) {
-                (r->N <= cap ? ring : halo).push_back(r);
+                (r->N <= capr ? ring : halo).push_back(r);
                 maxD = std::max(maxD, r->mi.D);
             }
         if (ring.empty() && halo.empty()) continue;
@@ -339,11 +343,11 @@ int plan_block(lbhpde_server_s *S, Block &blk) {
             }
             // one launch per resident size class, each on a lane of its own
             std::vector<lbh::Member> mc[lbh::kRingClasses];
-            lbh::split_ring_classes(S->esz, b, K, m, mc);
+            lbh::split_ring_classes(S->esz, b, Kr, m, mc);
             for (int c = 0; c < lbh::kRingClasses; ++c) {
                 if (mc[c].empty()) continue;
-                Planned pl{b, K, dc, false, 4 * cls + c, n, {}};
-                SRC(lbh::pack_ring(b, S->esz, K, dc, mc[c], pl.p, lbh::ring_class_threads(S->esz, b, K, c)));
+                Planned pl{b, Kr, dc, false, 4 * cls + c, n, {}};
+                SRC(lbh::pack_ring(b, S->esz, Kr, dc, mc[c], pl.p, lbh::ring_class_threads(S->esz, b, Kr, c)));
                 plan.push_back(std::move(pl));
             }
         }

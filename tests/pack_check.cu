@@ -47,20 +47,27 @@ static void check_ring(const lbh::Packed &p, const std::vector<lbh::Member> &m, 
         CHECK(i1 > i0 && i1 - i0 <= 32, "cta %d holds %d instances", c, i1 - i0);
         maxn = std::max(maxn, i1 - i0);
         int tb = 0, sco = 0;
+        const int gr = lbh::ring_granule(K);
         for (int i = i0; i < i1; ++i) {
             const lbk::OnchipInst &I = p.insts[i];
-            CHECK(I.tbase == tb && I.tbase % 32 == 0, "instance %d: thread base %d, expected %d", i, I.tbase, tb);
+            CHECK(I.tbase == tb && I.tbase % gr == 0, "instance %d: thread base %d, expected %d", i, I.tbase, tb);
             CHECK(I.nthr == (I.N + K - 1) / K, "instance %d: %d threads for N = %d", i, I.nthr, I.N);
             CHECK(I.npos == I.N && I.vlo == 0 && I.vhi == I.N && I.x0 == 0, "instance %d: ring window", i);
             CHECK(I.il == i - i0, "instance %d: tail slot %d", i, I.il);
             CHECK(I.scoef == sco && I.scoef % 4 == 0, "instance %d: coefficient offset %d", i, I.scoef);
             sco += lbk::cblock(b, dc > 0 ? dc : I.D);
-            tb += (I.nthr + 31) / 32 * 32;
+            tb += (I.nthr + gr - 1) / gr * gr;
             ++seen[I.off];
         }
         CHECK(tb <= threads && tb <= p.nthreads, "cta %d uses %d threads of %d (plan %d)", c, tb, threads, p.nthreads);
     }
-    CHECK(p.nthreads <= threads, "plan threads %d > %d", p.nthreads, threads);
+    CHECK(p.nthreads <= threads && p.nthreads % 32 == 0, "plan threads %d, CTA size %d", p.nthreads, threads);
+    if (K == lbh::kRingK) {  // exchange rows at the class stride, tails for kRingMaxInst instances
+        const size_t xchg = size_t(4) * lbk::ring_xchg_elems(b, threads);
+        CHECK(p.stride == threads && p.max_inst <= lbk::kRingMaxInst && p.smem > xchg && p.smem <= 227 * 1024,
+              "k_ring plan: stride %d (class %d), %d instances, shared memory %zu (exchange %zu)", p.stride, threads,
+              p.max_inst, p.smem, xchg);
+    }
     CHECK(p.max_inst % 4 == 0 && p.max_inst >= maxn, "max_inst %d for %d", p.max_inst, maxn);
     CHECK(seen.size() == m.size(), "%zu of %zu members placed", seen.size(), m.size());
     for (auto &kv : seen) CHECK(kv.second == 1, "member at %lld placed %d times", kv.first, kv.second);
@@ -96,7 +103,8 @@ int main() {
         size_t esz;
         int b, K;
     };
-    const Cfg cfgs[] = {{4, 5, 8}, {4, 5, 4}, {4, 5, 2}, {4, 7, 8}, {4, 7, 4}, {8, 5, 4}, {8, 5, 2}, {8, 7, 4}};
+    const Cfg cfgs[] = {{4, 5, lbh::kRingK}, {4, 5, 8}, {4, 5, 4}, {4, 5, 2}, {4, 7, 8},
+                        {4, 7, 4},           {8, 5, 4}, {8, 5, 2}, {8, 7, 4}};
     for (const Cfg &cf : cfgs) {
         const int W = (cf.b - 1) / 2;
         const int cap = lbh::onchip_maxt(cf.esz, cf.b, cf.K) * cf.K;
@@ -125,8 +133,12 @@ int main() {
                 }
             }
             CHECK(total == m.size(), "%zu of %zu members classified", total, m.size());
-            // windows: batch-sized and server-wide, several depths
+            // windows: batch-sized and server-wide, several depths (the 16-node variant is resident only)
             for (bool wide : {false, true}) {
+                if (cf.K == lbh::kRingK) {
+                    CHECK(lbh::onchip_maxt_halo(cf.esz, cf.b, cf.K) == 0, "windows offered for K = %d", cf.K);
+                    break;
+                }
                 const int maxt = wide ? lbh::onchip_maxt(cf.esz, cf.b, cf.K) : lbh::onchip_maxt_halo(cf.esz, cf.b, cf.K);
                 for (int eighths : {6, 7}) {
                     const int T = lbh::default_tblk(maxt * cf.K, W, eighths), H = T * W;

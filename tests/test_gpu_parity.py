@@ -4,12 +4,18 @@ Tolerances (normwise: max_x |phi_gpu - phi_oracle| / max_x |phi_oracle|):
 * FP64: 1e-12, the stated bound.  Both sides round every operation in IEEE double; they
   differ only in evaluation order (Horner with omega folded in, flux-difference update of
   phi, fused multiply-add on the GPU), a few ulp per step.
-* FP32 deviation storage: FP32_TOL(n) = 64 * eps32 * sqrt(n) + 1e-6 -- a random walk of a
-  few float roundings of phi per step (eps32 = 2^-24 relative to max|phi|), plus the
-  one-time rounding of the initial state.  The accuracy bar of the FP32 path (error
-  against the exact solution within twice the FP64 path's) is checked on full runs.
+* FP32 deviation storage: FP32_TOL(n) = 16 * eps32 * sqrt(n) + 4 * eps32 (eps32 = 2^-24,
+  relative to max|phi|).  Model: each step rounds phi and the stored deviations once in
+  float, and these roundings add up like a random walk over the n steps (sqrt(n)); the second
+  term is the one-time rounding of the initial state.  Measured on GB300 over every case
+  below and every kernel, the FP32-minus-oracle gap is at most 4.0 eps32 sqrt(n) (scheme-2
+  KdV) and at most 1.5 eps32 sqrt(n) on the ensemble members at 1000 steps, so the bound is
+  4x the worst measured case and about 10x the ensemble's: an encoding slip or a lost
+  rounding step costing 10x the honest error fails it.  The accuracy bar of the FP32 path
+  (error against the exact solution within twice the FP64 path's) is checked on full runs.
 """
 import math
+import os
 import zlib
 
 import numpy as np
@@ -25,7 +31,7 @@ FP64_TOL = 1e-12
 
 
 def FP32_TOL(n):
-    return 64 * 2.0 ** -24 * math.sqrt(max(n, 1)) + 1e-6
+    return 16 * 2.0 ** -24 * math.sqrt(max(n, 1)) + 4 * 2.0 ** -24
 
 
 @pytest.fixture(scope="module")
@@ -128,7 +134,7 @@ def test_sizes_both_kernels(L, b, N, prec):
     got_s = run_gpu(L, p, P, L.KERNEL_STREAM)
     assert normwise(got_s, want) <= tol
     for kern, K, spl in [(k, K, spl) for k in (L.KERNEL_ONCHIP, L.KERNEL_HALO)
-                         for K in ((2, 4, 8) if b == 5 else (4, 8)) for spl in (0, 13)]:
+                         for K in ((2, 4, 8, 16) if b == 5 else (4, 8)) for spl in (0, 13)]:
         s = L.Solver.for_problem(p, precision=P)
         try:
             s.set_kernel(kern, K, spl)
@@ -281,21 +287,48 @@ def test_long_grid_full_size_sampled(L, prec):
         assert abs(got[x] - want) <= tol * scale, x
 
 
-def test_ensemble_sampled_members(L):
-    """The 4096-member KdV-Burgers ensemble (one launch) at 100 steps; 12 members vs the oracle."""
-    probs = W.kdv_burgers_ensemble(nsteps=100)
+ENSEMBLE_CLASSES = ((0, 2048), (2048, 4096), (4096, 8192))  # nodes held by 128-, 256-, 512-thread CTAs
+
+
+@pytest.fixture(scope="module")
+def ensemble_full(L):
+    """The 4096-member KdV-Burgers ensemble of the benchmark, 1000 steps, and the oracle's phi for
+    sampled members: the smallest, the largest, one from each resident CTA size class and seeded
+    random picks.  The oracle runs one member per thread."""
+    from concurrent.futures import ThreadPoolExecutor
+    probs = W.kdv_burgers_ensemble()
+    Ns = np.array([p.N for p in probs])
+    pick = [int(np.argmin(Ns)), int(np.argmax(Ns))]
+    for lo, hi in ENSEMBLE_CLASSES:
+        pick.append(int(np.where((Ns > lo) & (Ns <= hi))[0][0]))
+    rng = np.random.default_rng(1)
+    pick += [int(i) for i in rng.choice(len(probs), 7, replace=False)]
+    pick = sorted(set(pick))
+    with ThreadPoolExecutor(max(1, min(len(pick), os.cpu_count() or 1))) as ex:
+        want = dict(zip(pick, ex.map(lambda i: oracle.run_problem(probs[i]), pick)))
+    return probs, want
+
+
+@pytest.mark.parametrize("plan", ["bench", "windows"])
+def test_ensemble_full_depth_vs_oracle(L, ensemble_full, plan):
+    """The benchmark's ensemble at its full 1000 steps in the launch configuration the benchmark
+    times (the on-chip pair the autotuner picks on GB300, K = 8 and 32 steps per window,
+    recorded without timing; every member of up to 8192 nodes resident in the split-barrier
+    kernel), and again with every member cut into those temporally blocked windows.  Sampled
+    members against the oracle, normwise, within FP32_TOL(1000) = 16 eps32 sqrt(1000) + 4 eps32
+    = 3.0e-5 (about 10x the gap measured on these members)."""
+    probs, want = ensemble_full
+    L.set_tuning(L.FP32_DEV, 5, 5, 8, 32)
     bt = L.Batch(probs, precision=L.FP32_DEV)
-    bt.set_phi(np.concatenate([p.phi0 for p in probs])).step(100)
+    if plan == "windows":
+        bt.set_kernel(L.KERNEL_HALO, 8, 32)
+    bt.set_phi(np.concatenate([p.phi0 for p in probs])).step(W.ENSEMBLE_STEPS)
     outs = bt.split(bt.read_phi())
     d = bt.diagnostics()
     bt.close()
     assert all(r["nonfinite"] == 0 for r in d)
-    rng = np.random.default_rng(1)
-    pick = list(rng.choice(len(probs), 10, replace=False)) + [int(np.argmax([p.N for p in probs])),
-                                                              int(np.argmin([p.N for p in probs]))]
-    for i in pick:
-        want = oracle.run_problem(probs[i])
-        assert normwise(outs[i], want) <= FP32_TOL(100), i
+    for i, w in want.items():
+        assert normwise(outs[i], w) <= FP32_TOL(W.ENSEMBLE_STEPS), (i, probs[i].N)
 
 
 def test_autotune_then_parity(L):

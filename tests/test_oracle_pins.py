@@ -363,13 +363,14 @@ def test_paper_tables_reproduced(row):
 
 
 def test_kdv_soliton_accuracy():
-    """The KdV soliton (c = 4) on N = 400 stays within 15% (E) of the exact solution at t = 1
-    (E = 0.099 at dt = 1e-5, tau = 1.1); a scheme that recovered another equation would be
-    O(1) off."""
+    """The KdV soliton (c = 4) on N = 400 at t = 1 (dt = 1e-5, tau = 1.1, 100 000 steps): the
+    error against the exact solution is E = 0.0994 (relative L2 0.059).  The pin holds E to
+    within 2.5% of that value on both sides: a scheme that recovered another equation would be
+    O(1) off, and a dropped or mis-scaled term of the equilibria moves E by more than 2.5%."""
     p = W.kdv_config()
     phi = oracle.run_problem(p)
     E = oracle.error_E(phi, p.exact(p.t_end))
-    assert E < 0.15
+    assert 0.097 < E < 0.102
 
 
 def test_error_decreases_with_dt():
