@@ -280,7 +280,7 @@ def run_ours(args, rank, world, cpu=None):
             b0, d0 = (5, 5) if args.workload == "ensemble" else (7, 7)
             K_t, T_t, r_t = L.autotune(prec0, b0, d0)
             tuned = {"nodes_per_thread": K_t, "steps_per_window": T_t, "tuning_rate": r_t}
-        probs, nsteps, workload = workload_problems(args, rank)
+        probs, nsteps, workload = workload_problems(args, rank, world)
         prec = L.FP32_DEV if args.precision == "fp32" else L.FP64
         solver = L.Batch(probs, precision=prec)
         if args.kernel == "stream" and args.workload in ("nu_grid", "long_grid"):
@@ -336,9 +336,25 @@ def run_ours(args, rank, world, cpu=None):
         upd_step = total * nsteps
         value, t_max = aggregate(total_ms / 1e3, upd_step * args.steps, world, device="cuda")
 
+        clocks = clk.summary()
+        # the state after the last timed step: sampled members against the oracle (run on the host
+        # cores before the GPU work, same inputs, same 1000 steps)
+        oracle_cmp = None
+        if cpu is not None and cpu.get("oracle_phi"):
+            outs = solver.split(solver.read_phi())
+            oracle_cmp = compare_members(outs, cpu["oracle_phi"], probs)
+        # per-member results of the whole (partitioned) batch, gathered to every rank
+        records = [(int(p.meta.get("index", i)), d["sum_phi"], d["max_abs_phi"], int(d["nonfinite"]))
+                   for i, (p, d) in enumerate(zip(probs, diag))]
+        members_all = gather_member_records(records, world, device="cuda")
+
         # accuracy beside the number: members against the FP64 path (ensemble) or the exact
         # solution (long grid)
         accuracy = None if args.quick else accuracy_report(L, args, probs, solver, prec, torch)
+        if oracle_cmp is not None:
+            accuracy = dict(accuracy or {})
+            accuracy.update(oracle_cmp)
+            accuracy["clocks"] = clocks
 
         # end to end through the public API, host buffers
         e2e_steps = 0 if args.quick else max(1, min(args.steps, 5))
@@ -353,16 +369,20 @@ def run_ours(args, rank, world, cpu=None):
                                        "h2d_bytes_per_step": total * 8 + (phib_h.nbytes if bounded else 0),
                                        "d2h_bytes_per_step": total * 8}
 
-        # FP64 plain path on the same workload (fewer steps: it is ALU bound on GB300)
+        # FP64 plain path on the same workload (fewer steps: it is ALU bound on GB300); its result
+        # against the oracle on the sampled members
         fp64 = None
         if args.workload == "ensemble" and prec == L.FP32_DEV and not args.no_fp64 and not args.quick:
-            fp64 = fp64_plain(L, probs, phi0_d, nsteps, stream, torch, steps=max(1, min(args.steps, 2)))
+            fp64, outs64 = fp64_plain(L, probs, phi0_d, nsteps, stream, torch, steps=max(1, min(args.steps, 2)))
+            if oracle_cmp is not None:
+                c64 = compare_members(outs64, cpu["oracle_phi"], probs)
+                accuracy["fp64_normwise_vs_oracle"] = c64["normwise_vs_oracle"]
 
         kern_ms = float(np.mean(kern))
-        clocks = clk.summary()
+        sms = sm_count(torch, dev)
         if bounded:
             fl = flops_per_node_update(b, D)
-            peak_tf, src = alu_peak(esz, clocks, peaks)
+            peak_tf, src = alu_peak(esz, clocks, peaks, sms)
             achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                     "frac": achieved / peak_tf, "traffic": None,
@@ -372,7 +392,7 @@ def run_ours(args, rank, world, cpu=None):
         elif args.workload == "nu_grid" and args.kernel != "stream":
             A, Dg = nu_shape(L, probs[0])
             fl = flops_per_node_update_nu(b, A, Dg)
-            peak_tf, src = alu_peak(esz, clocks, peaks)
+            peak_tf, src = alu_peak(esz, clocks, peaks, sms)
             achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                     "frac": achieved / peak_tf, "traffic": None,
@@ -387,12 +407,14 @@ def run_ours(args, rank, world, cpu=None):
                     "bytes_per_node_update": by, "peak_source": peak_src}
         elif args.workload == "ensemble" or args.kernel != "stream":
             fl = flops_per_node_update(b, D)
-            peak_tf, src = alu_peak(esz, clocks, peaks)
+            peak_tf, src = alu_peak(esz, clocks, peaks, sms)
             achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                     "frac": achieved / peak_tf, "traffic": None,
-                    "kernel": f"k_onchip<{'float' if esz == 4 else 'double'},{b},K> "
-                              f"({'resident instances + halo windows' if args.workload == 'ensemble' else 'halo windows'})",
+                    "kernel": (f"k_ring<float,5,16,MAXT,5> (every member resident, 16 nodes a thread)"
+                               if args.workload == "ensemble" and esz == 4 else
+                               f"k_onchip<{'float' if esz == 4 else 'double'},{b},K> "
+                               f"({'resident instances + halo windows' if args.workload == 'ensemble' else 'halo windows'})"),
                     "flops_per_node_update": fl, "peak_source": src}
         else:
             by = bytes_per_node_update(b, esz)
@@ -406,7 +428,7 @@ def run_ours(args, rank, world, cpu=None):
             if esz == 8:
                 # FP64 on GB300: the FP64 units bind long before HBM does
                 fl = flops_per_node_update(b, D)
-                peak_tf, src = alu_peak(esz, clocks, peaks)
+                peak_tf, src = alu_peak(esz, clocks, peaks, sms)
                 alu = fl * upd_step / (kern_ms / 1e3) / 1e12
                 roof = {"bound": "alu", "achieved": alu, "peak": peak_tf, "unit": "TFLOP/s",
                         "frac": alu / peak_tf, "traffic": None, "kernel": roof["kernel"],
@@ -416,27 +438,102 @@ def run_ours(args, rank, world, cpu=None):
         line = {
             "metric": METRIC, "value": value, "unit": "node-updates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "strong" if args.workload == "ensemble" and world > 1 else "weak", "vs_baseline": None,
             "dtype": "f32" if prec == L.FP32_DEV else "f64", "data": "synthetic (seeded, shaped like the paper's test problems)",
             "config": {"workload": workload, "node_updates_per_step": upd_step, "precision": args.precision,
                        "autotuned": tuned,
                        "l2": (f"inputs larger than L2: state {total * b * esz / 2**20:.0f} MiB, updated in place"
                               if bounded else
                               f"inputs larger than L2: state {2 * total * b * esz / 2**20:.0f} MiB (two buffers)"),
-                       "parallelism": f"replicas x{world} (independent ensembles)"},
+                       "parallelism": (f"members r::{world} of one seeded ensemble on rank r (no collective in the "
+                                       f"steps; per-member results gathered once after the timed region)"
+                                       if args.workload == "ensemble" and world > 1 else
+                                       f"replicas x{world} (independent copies of the workload)")},
             "roofline": roof, "e2e": e2e, "gpu_launches": launches_timed, "clocks": clocks,
             "kernel_ms_per_step": kern_ms, "accuracy": accuracy,
         }
         if fp64 is not None:
             line["fp64_plain"] = fp64
+        if world > 1:
+            line["members"] = {"gathered": len(members_all),
+                               "sum_phi_total": float(sum(r[1] for r in members_all)),
+                               "nonfinite": int(sum(r[3] for r in members_all))}
         solver.close()
+        # the small configurations and the serving stream, measured in the same run (rank 0, one
+        # GPU, default workload)
+        if args.workload == "ensemble" and world == 1 and not args.quick and not args.no_legs:
+            line["configs_small"] = small_configs_leg(L, torch, stream, cpu.get("small") if cpu else None)
+            line["serving"] = serving_leg(args, L, torch)
     return line
+
+
+def compare_members(outs, want, probs):
+    """Sampled members of a batch result against the oracle's phi: normwise, relative L2 and E
+    (the paper's L1 ratio), the maximum over the members, and each member's figures."""
+    per = []
+    for i, w in sorted(want.items()):
+        g = np.asarray(outs[i], dtype=np.float64)
+        per.append({"member": int(i), "N": int(probs[i].N),
+                    "normwise": float(np.abs(g - w).max() / np.abs(w).max()),
+                    "l2": float(np.linalg.norm(g - w) / np.linalg.norm(w)),
+                    "E": float(np.abs(g - w).sum() / np.abs(w).sum())})
+    return {"l2_vs_oracle": max(r["l2"] for r in per), "E_vs_oracle": max(r["E"] for r in per),
+            "normwise_vs_oracle": max(r["normwise"] for r in per), "members_vs_oracle": per,
+            "reference": "the FP64 CPU oracle on the host cores, same inputs and steps"}
 
 
 def serving_description(args):
     return (f"serving: Poisson arrivals (mean {args.rate:g} req/s) of mixed KdV / mKdV / K(2,2) / KS / Kawahara "
             f"requests, N log-uniform [128, 65536], steps uniform [1e3, 1e5], FP32 deviation storage, "
             f"memory-admitted")
+
+
+def serve_rate(L, rate, count, precision, arena_gb, block):
+    """One serving run: `count` requests of the seeded Poisson stream at `rate` submitted from a
+    host thread at their arrival times while the server runs, then drained; latency = finish -
+    submit on the server's clock.  Offered vs achieved node-updates/s, p50/p99 latency, the GPU
+    busy fraction and the scheduler's phase times."""
+    reqs = W.serving_requests(count, rate=rate, seed=W.SEED + int(rate))
+    srv = L.Server(precision=L.FP32_DEV if precision == "fp32" else L.FP64,
+                   device_bytes=arena_gb << 30, max_active=4096, steps_per_block=block)
+    ids = [None] * count
+    t_start = time.perf_counter()
+
+    def submitter():
+        for i, (ta, p) in enumerate(reqs):
+            dt_ = ta - (time.perf_counter() - t_start)
+            if dt_ > 0:
+                time.sleep(dt_)
+            ids[i] = srv.submit_problem(p)
+
+    th = threading.Thread(target=submitter)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
+        th.start()
+        done = {}
+        while len(done) < count:
+            for i in range(count):
+                if i in done or ids[i] is None:
+                    continue
+                rc, _, info = srv.poll(ids[i])
+                if rc != L.PENDING:
+                    done[i] = (rc, info)
+            time.sleep(0.002)
+        th.join()
+    st = srv.stats()
+    srv.close()
+    lat = np.array([done[i][1]["finish_s"] - done[i][1]["submit_s"] for i in range(count)])
+    t0 = min(done[i][1]["submit_s"] for i in range(count))
+    t1 = max(done[i][1]["finish_s"] for i in range(count))
+    work = sum(p.N * p.nsteps for _, p in reqs)
+    ok = sum(1 for i in range(count) if done[i][0] == L.OK)
+    return {"rate_req_s": rate, "requests": count, "ok": ok,
+            "offered_node_updates_s": work / reqs[-1][0],
+            "achieved_node_updates_s": work / (t1 - t0), "makespan_s": t1 - t0,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "launches": st["launches"], "gpu_busy_s": st["gpu_busy_s"],
+            "host_s": {k[5:-2]: st[k] for k in ("host_admit_s", "host_setup_s", "host_plan_s",
+                                                 "host_launch_s", "host_wait_s", "host_retire_s")},
+            "gpu_busy_frac": st["gpu_busy_s"] / (t1 - t0), "clocks": clk.summary()}
 
 
 def run_serving(args):
@@ -451,47 +548,7 @@ def run_serving(args):
     rates = [args.rate] + ([args.rate / 4, args.rate / 16] if args.sweep else [])
     for rate in rates:
         count = min(args.requests, max(64, int(args.window * rate)))
-        reqs = W.serving_requests(count, rate=rate, seed=W.SEED + int(rate))
-        srv = L.Server(precision=L.FP32_DEV if args.precision == "fp32" else L.FP64,
-                       device_bytes=args.arena_gb << 30, max_active=4096, steps_per_block=args.block)
-        ids = [None] * count
-        t_start = time.perf_counter()
-
-        def submitter():
-            for i, (ta, p) in enumerate(reqs):
-                dt_ = ta - (time.perf_counter() - t_start)
-                if dt_ > 0:
-                    time.sleep(dt_)
-                ids[i] = srv.submit_problem(p)
-
-        th = threading.Thread(target=submitter)
-        with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clk:
-            th.start()
-            done = {}
-            while len(done) < count:
-                for i in range(count):
-                    if i in done or ids[i] is None:
-                        continue
-                    rc, _, info = srv.poll(ids[i])
-                    if rc != L.PENDING:
-                        done[i] = (rc, info)
-                time.sleep(0.002)
-            th.join()
-        st = srv.stats()
-        srv.close()
-        lat = np.array([done[i][1]["finish_s"] - done[i][1]["submit_s"] for i in range(count)])
-        t0 = min(done[i][1]["submit_s"] for i in range(count))
-        t1 = max(done[i][1]["finish_s"] for i in range(count))
-        work = sum(p.N * p.nsteps for _, p in reqs)
-        ok = sum(1 for i in range(count) if done[i][0] == L.OK)
-        out.append({"rate_req_s": rate, "requests": count, "ok": ok,
-                    "offered_node_updates_s": work / reqs[-1][0],
-                    "achieved_node_updates_s": work / (t1 - t0), "makespan_s": t1 - t0,
-                    "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-                    "launches": st["launches"], "gpu_busy_s": st["gpu_busy_s"],
-                    "host_s": {k[5:-2]: st[k] for k in ("host_admit_s", "host_setup_s", "host_plan_s",
-                                                         "host_launch_s", "host_wait_s", "host_retire_s")},
-                    "gpu_busy_frac": st["gpu_busy_s"] / (t1 - t0), "clocks": clk.summary()})
+        out.append(serve_rate(L, rate, count, args.precision, args.arena_gb, args.block))
     head = out[0]
     fp64 = None if args.quick else serving_fp64_plain(L, W.serving_requests(
         min(args.requests, max(64, int(args.window * args.rate))), rate=args.rate, seed=W.SEED + int(args.rate)))
@@ -507,6 +564,74 @@ def run_serving(args):
     if fp64 is not None:
         line["fp64_plain"] = fp64
     return line
+
+
+SERVING_LEG_RATES = (2000.0, 500.0)  # the configuration's rate, and one below the knee
+
+
+def serving_leg(args, L, torch):
+    """The serving configuration inside the default run: the seeded stream at 2000 requests/s
+    (the configuration's mean rate, beyond one GPU's capacity) and at 500/s (below the knee),
+    each over 1 s of arrivals, drained; then the plain per-request FP64 path on the first
+    requests of the 2000/s stream.  p50/p99 are those of the 2000/s run."""
+    torch.cuda.synchronize()
+    rates = [serve_rate(L, r, int(r * 1.0), "fp32", args.arena_gb, args.block) for r in SERVING_LEG_RATES]
+    fp64 = serving_fp64_plain(L, W.serving_requests(int(SERVING_LEG_RATES[0]), rate=SERVING_LEG_RATES[0],
+                                                    seed=W.SEED + int(SERVING_LEG_RATES[0])))
+    head = rates[0]
+    return {"workload": "Poisson arrivals of mixed KdV / mKdV / K(2,2) / KS / Kawahara requests, N log-uniform "
+                        "[128, 65536], steps uniform [1e3, 1e5], FP32 deviation storage, 1 s of arrivals per rate",
+            "rate_req_s": head["rate_req_s"], "p50_latency_s": head["p50_latency_s"],
+            "p99_latency_s": head["p99_latency_s"], "achieved_node_updates_s": head["achieved_node_updates_s"],
+            "offered_node_updates_s": head["offered_node_updates_s"], "gpu_busy_frac": head["gpu_busy_frac"],
+            "clocks": head["clocks"], "rates": rates, "fp64_plain": fp64,
+            "batched_over_fp64_plain": head["achieved_node_updates_s"] / fp64["value"]}
+
+
+def small_configs_leg(L, torch, stream, refs):
+    """Configurations 1 (KdV soliton, N = 400, t = 1, 100 000 steps) and 2 (Kuramoto-Sivashinsky,
+    N = 1024, t = 10, 100 000 steps), each in FP64 and FP32 on the automatic kernel: the whole
+    instance resident in one CTA (one SM) for every step, since a grid this small has no more
+    parallel work than one CTA holds and more CTAs would need a grid-wide exchange each step.
+    CUDA-event time of the steps, E and relative L2 against the exact solution (KdV) or the
+    ETDRK4 reference (KS), and the oracle's single-thread rate on the host beside it."""
+    out = {}
+    cases = (("kdv_n400_t1", W.kdv_config()), ("ks_n1024_t10", W.ks_config()))
+    with torch.cuda.stream(stream):
+        for name, p in cases:
+            if name.startswith("kdv"):
+                ref, ref_kind = p.exact(p.t_end), "exact soliton"
+            else:
+                ref = refs[name]["reference"] if refs and name in refs else W.ks_spectral_reference(t_end=p.t_end)
+                ref_kind = "Fourier ETDRK4 reference"
+            rec = {"N": p.N, "steps": p.nsteps, "dt": p.dt, "tau": p.tau, "error_against": ref_kind,
+                   "ctas": 1, "sms": 1}
+            for prec, tag in ((L.FP64, "fp64"), (L.FP32_DEV, "fp32")):
+                sv = L.Solver.for_problem(p, precision=prec)
+                sv.set_phi(p.phi0).step(500)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                sv.set_phi(p.phi0)
+                a.record(stream)
+                sv.step(p.nsteps)
+                b.record(stream)
+                b.synchronize()
+                sec = a.elapsed_time(b) / 1e3
+                phi = sv.read_phi()
+                sv.close()
+                rec[tag] = {"us_per_step": sec / p.nsteps * 1e6, "solve_s": sec,
+                            "node_updates_s": p.N * p.nsteps / sec,
+                            "E": float(np.abs(phi - ref).sum() / np.abs(ref).sum()),
+                            "l2": float(np.linalg.norm(phi - ref) / np.linalg.norm(ref)),
+                            "kernel": ("k_ring<float,5,16,128,5>, one CTA" if tag == "fp32" else
+                                       "k_onchip<double,5,4,512,false,5>, one CTA")}
+            rec["fp32_E_over_fp64_E"] = rec["fp32"]["E"] / rec["fp64"]["E"]
+            if refs and name in refs:
+                rec["oracle_single_thread"] = refs[name]["oracle"]
+            out[name] = rec
+    if refs and "kawahara_2^24" in refs:
+        out["kawahara_2^24_oracle_single_thread"] = refs["kawahara_2^24"]["oracle"]
+    return out
 
 
 def serving_fp64_plain(L, reqs, max_updates=2e9):
@@ -562,13 +687,13 @@ def fp64_plain(L, probs, phi0_d, nsteps, stream, torch, steps=2):
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     total = sum(p.N for p in probs)
+    outs = s.split(s.read_phi())
     s.close()
-    return {"value": total * nsteps / (ms / 1e3), "unit": "node-updates/s", "ms_per_step": ms,
-            "kernel": "k_stream<double,5,5> (one fused collide+stream launch per time step, HBM)"}
+    return ({"value": total * nsteps / (ms / 1e3), "unit": "node-updates/s", "ms_per_step": ms,
+             "kernel": "k_stream<double,5,5> (one fused collide+stream launch per time step, HBM)"}, outs)
 
 
 def accuracy_report(L, args, probs, solver, prec, torch):
-    import oracle as _  # noqa: F401  (not used here; accuracy vs the oracle lives in the tests)
     out = {}
     if args.workload == "ensemble":
         # FP32 members against the FP64 path on the same inputs (normwise, max over 8 members)
@@ -622,28 +747,60 @@ def accuracy_report(L, args, probs, solver, prec, torch):
 
 # ------------------------------------------------------------ oracle on the CPU
 
-def cpu_oracle_rate(args, sample_s=15.0):
-    """Oracle node-updates/s on the host cores: one member per thread (ctypes releases the
-    GIL), on a bounded sample of the same workload."""
-    import oracle
+def ensemble_sample(probs, count):
+    """Members the oracle runs on the host cores: the smallest, the largest, the first member of each
+    resident CTA size class (up to 2048, 4096 and 8192 nodes) and seeded random picks, `count` in
+    all."""
+    Ns = np.array([p.N for p in probs])
+    pick = [int(np.argmin(Ns)), int(np.argmax(Ns))]
+    for lo, hi in ((0, 2048), (2048, 4096), (4096, 8192)):
+        sel = np.where((Ns > lo) & (Ns <= hi))[0]
+        if sel.size:
+            pick.append(int(sel[0]))
+    rng = np.random.default_rng(W.SEED)
+    for i in rng.permutation(len(probs)):
+        if len(set(pick)) >= count:
+            break
+        pick.append(int(i))
+    return sorted(set(pick))[:max(count, 5)]
+
+
+def oracle_members(oracle, probs, idx, steps, threads):
+    """phi of members idx after `steps` steps (one member per thread; ctypes releases the GIL) and
+    the wall time."""
     from concurrent.futures import ThreadPoolExecutor
+
+    order = sorted(idx, key=lambda i: -probs[i].N)  # largest first: the threads finish together
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        outs = list(ex.map(lambda i: oracle.run_problem(probs[i], nsteps=steps), order))
+    return dict(zip(order, outs)), time.perf_counter() - t0
+
+
+def cpu_oracle_rate(args, sample_s=15.0, keep=False):
+    """Oracle node-updates/s on the host cores: one member per thread (ctypes releases the GIL), on a
+    bounded sample of the same workload.  Ensemble: 2 members per core (smallest, largest, one per
+    resident size class, seeded random picks) at the full 1000 steps; with keep, their phi is
+    returned too (the accuracy reference of the GPU result)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
 
     cores = os.cpu_count() or 1
     if args.workload == "ensemble":
-        probs = ensemble_problems(0)[: 2 * cores]
-        per_member = 20
-        # calibrate the step count so the sample takes about sample_s
-        t0 = time.perf_counter()
-        oracle.run_problem(probs[0], nsteps=per_member)
-        dt1 = time.perf_counter() - t0
-        steps = max(per_member, int(sample_s * cores / (len(probs) * dt1 / per_member) / 1.0))
-        steps = min(steps, W.ENSEMBLE_STEPS)
-        t0 = time.perf_counter()
-        with ThreadPoolExecutor(cores) as ex:
-            list(ex.map(lambda p: oracle.run_problem(p, nsteps=steps), probs))
-        el = time.perf_counter() - t0
-        upd = sum(p.N for p in probs) * steps
-        sample = f"{len(probs)} ensemble members x {steps} steps, one member per thread"
+        probs = ensemble_problems(0, args.members)
+        idx = ensemble_sample(probs, 2 * cores)
+        steps = W.ENSEMBLE_STEPS
+        outs, el = oracle_members(oracle, probs, idx, steps, min(cores, len(idx)))
+        upd = sum(probs[i].N for i in idx) * steps
+        sizes = sorted(probs[i].N for i in idx)
+        res = {"value": upd / el, "unit": "node-updates/s", "cores": min(cores, len(idx)), "kind": "oracle",
+               "sample": f"{len(idx)} ensemble members (N from {sizes[0]} to {sizes[-1]}: the smallest, the largest, "
+                         f"one per resident CTA size class, seeded random picks) x {steps} steps, one member per thread",
+               "seconds": el}
+        if keep:
+            res["oracle_phi"] = outs
+        return res
     elif args.workload == "bounded":
         p0 = bounded_problems(1)[0]
         pb = W.boundary_values(p0, 2, 0, BOUNDED_STEPS)
@@ -710,6 +867,32 @@ def cpu_oracle_rate(args, sample_s=15.0):
             "seconds": el}
 
 
+def small_refs():
+    """Host side of the small configurations: the oracle's single-thread rate on configurations 1
+    (KdV, N = 400) and 2 (KS, N = 1024) over a bounded number of steps, and on configuration 4 (the
+    2^24-node Kawahara grid) over one step, each extrapolated to the configuration's full step
+    count and labelled so; and the ETDRK4 reference of the KS run."""
+    import oracle
+
+    out = {}
+    for name, p, steps, full_n in (("kdv_n400_t1", W.kdv_config(), 10000, 400),
+                                   ("ks_n1024_t10", W.ks_config(), 4000, 1024),
+                                   ("kawahara_2^24", W.long_grid_config(N=1 << 22, nsteps=1), 2, 1 << 24)):
+        t0 = time.perf_counter()
+        oracle.run_problem(p, nsteps=0)  # set-up and initialisation alone, subtracted below
+        t1 = time.perf_counter()
+        oracle.run_problem(p, nsteps=steps)
+        el = max(time.perf_counter() - t1 - (t1 - t0), 1e-9)
+        full = p.nsteps if name != "kawahara_2^24" else 1000
+        rate = p.N * steps / el
+        out[name] = {"oracle": {"node_updates_s": rate, "threads": 1, "steps_run": steps, "nodes_run": p.N,
+                                "seconds": el, "solve_s_extrapolated": full_n * full / rate,
+                                "note": f"{p.N} nodes x {steps} steps timed (initialisation excluded); the "
+                                        f"{full_n}-node, {full}-step solve time extrapolated from that rate"}}
+    out["ks_n1024_t10"]["reference"] = W.ks_spectral_reference(t_end=W.ks_config().t_end)
+    return out
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle as it stands, on the host cores, bounded sample."""
     cores = os.cpu_count() or 1
@@ -757,6 +940,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="skip the on-chip autotuner")
     ap.add_argument("--onchip", default=None, metavar="K,T",
                     help="ensemble/long grid: record this on-chip choice instead of running the autotuner")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="ensemble: skip the small-configuration and serving legs")
     ap.add_argument("--quick", action="store_true",
                     help="only the timed region: no accuracy check, e2e, FP64 or CPU legs (profiling)")
     args = ap.parse_args()
@@ -776,10 +961,13 @@ def main():
 
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    # the CPU baseline runs before any GPU work so no thread pool is forked after CUDA starts
+    # the CPU legs run before any GPU work: the oracle baseline (for the ensemble also the accuracy
+    # reference of the sampled members) and the host side of the small configurations
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and not args.quick:
-        cpu = cpu_oracle_rate(args)
+        cpu = cpu_oracle_rate(args, keep=True)
+        if args.workload == "ensemble" and not args.no_legs:
+            cpu["small"] = small_refs()
     from paper_0907_1720_gb300 import build as B
 
     B.build()
@@ -787,7 +975,7 @@ def main():
         if rank == 0:
             print(json.dumps(run_serving(args)), flush=True)
         return
-    line = run_ours(args, rank, world)
+    line = run_ours(args, rank, world, cpu)
     if cpu is not None:
         line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     if rank == 0:

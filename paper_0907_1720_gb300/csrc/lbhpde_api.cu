@@ -65,6 +65,7 @@ struct Group {
     int dc = 0;  // compile-time degree of the on-chip kernel variant (0 = run time)
     bool uniform = false;  // every member has the same model (coefficients and omega)
     bool has_nu = false;   // a member has real-exponent terms: the real-exponent variants (on chip: degree code -1)
+    bool waves = false;    // ring[2]: whole waves of full CTAs; ring[0]: the tail, launched after it
     // bounded groups (LBHPDE_NEE): resident members, one CTA each, and streaming members
     std::vector<lbk::BoundedInst> bnd_h;
     lbk::BoundedInst *bnd = nullptr;
@@ -101,7 +102,7 @@ struct lbhpde_batch_s {
     size_t st_bytes = 0;
     int cur = 0;
     void *coefT = nullptr;  // coefficient arena in the state type
-    double *coefD = nullptr;  // the same in double (initialisation)
+    double *coefD = nullptr;  // FP64 batches: the table in double (coefT points to it)
     long long *phi_off_d = nullptr;  // per block of the combined map: offset into a concatenated array
     std::vector<int2> all_blocks_h;  // combined block map over all members (segment order)
     std::vector<int> part_first_h;
@@ -256,7 +257,7 @@ void split_ring_classes(size_t esz, int b, int K, const std::vector<Member> &m, 
         const int c = ring_class(esz, b, K, m[i].seg.N), t = pad(m[i].seg.N);
         bool placed = false;
         for (auto &g : ctas)
-            if (g.free >= t && g.n < 32) {
+            if (g.free >= t && g.n < kRingMaxInstances) {
                 g.free -= t;
                 ++g.n;
                 placed = true;
@@ -277,6 +278,90 @@ int default_tblk(int capacity, int W, int valid_eighths) {
 }
 
 int onchip_dc(int b, int maxD) { return maxD == (b == 5 ? 5 : 7) ? maxD : 0; }
+
+bool split_ring_waves(int b, int K, int sms, const std::vector<Member> &m, std::vector<Member> &full,
+                      std::vector<Member> &tail) {
+    full.clear();
+    tail.clear();
+    if (K != kRingK || sms <= 0) return false;
+    const int cap = ring_class_threads(4, b, K, kRingClasses - 1);
+    auto thr = [&](int i) { return (int)((m[i].seg.N + K - 1) / K); };
+    std::vector<int> order(m.size());
+    long long total = 0;
+    for (size_t i = 0; i < m.size(); ++i) {
+        order[i] = (int)i;
+        total += thr((int)i);
+    }
+    const long long limit = total / ((long long)sms * cap) * sms;  // CTAs of the whole waves
+    if (limit == 0) return false;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return thr(a) > thr(c); });
+    // first fit, largest first, into at most `limit` CTAs; then each member that fitted nowhere
+    // takes the CTA where evicting the fewest smaller members makes room, and the evicted members
+    // (the smallest at hand) form the tail
+    struct Cta {
+        int used = 0;
+        std::vector<int> inst;
+    };
+    std::vector<Cta> ctas;
+    std::vector<int> deferred, evicted;
+    for (int i : order) {
+        const int t = thr(i);
+        bool placed = false;
+        for (auto &c : ctas)
+            if (c.used + t <= cap && (int)c.inst.size() < kRingMaxInstances) {
+                c.inst.push_back(i);
+                c.used += t;
+                placed = true;
+                break;
+            }
+        if (placed) continue;
+        if ((long long)ctas.size() < limit)
+            ctas.push_back(Cta{t, {i}});
+        else
+            deferred.push_back(i);
+    }
+    for (int i : deferred) {
+        const int t = thr(i);
+        int best = -1, best_n = 1 << 30;
+        for (size_t c = 0; c < ctas.size(); ++c) {
+            std::vector<int> small;
+            for (int q : ctas[c].inst)
+                if (thr(q) < t) small.push_back(thr(q));
+            std::sort(small.begin(), small.end());
+            int room = cap - ctas[c].used, n = 0;
+            for (int x : small) {
+                if (room >= t) break;
+                room += x;
+                ++n;
+            }
+            if (room >= t && n < best_n) {
+                best = (int)c;
+                best_n = n;
+                if (n <= 1) break;
+            }
+        }
+        if (best < 0) {
+            evicted.push_back(i);
+            continue;
+        }
+        Cta &c = ctas[best];
+        std::stable_sort(c.inst.begin(), c.inst.end(), [&](int a, int d) { return thr(a) < thr(d); });
+        while (cap - c.used < t) {
+            size_t k = 0;
+            while (thr(c.inst[k]) >= t) ++k;  // the smallest member below t (one exists: room >= t)
+            c.used -= thr(c.inst[k]);
+            evicted.push_back(c.inst[k]);
+            c.inst.erase(c.inst.begin() + (long)k);
+        }
+        c.inst.push_back(i);
+        c.used += t;
+    }
+    if (evicted.empty()) return false;
+    for (auto &c : ctas)
+        for (int q : c.inst) full.push_back(m[q]);
+    for (int q : evicted) tail.push_back(m[q]);
+    return true;
+}
 
 int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Packed &out, int threads) {
     out = Packed{};
@@ -299,7 +384,7 @@ int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Pa
     for (int i : order) {
         bool placed = false;
         for (auto &c : ctas) {
-            if (c.used + pad(m[i].seg.N) <= maxt && (int)c.inst.size() < 32) {
+            if (c.used + pad(m[i].seg.N) <= maxt && (int)c.inst.size() < kRingMaxInstances) {
                 c.inst.push_back(i);
                 c.used += pad(m[i].seg.N);
                 placed = true;
@@ -426,22 +511,24 @@ int launch_onchip(int b, size_t esz, int K, int dc, bool halo, const Packed &p, 
                     : launch_onchip_f64(b, K, dc, halo, p, insts_d, first_d, in, out, coefT, nsteps, st);
 }
 
-int launch_init(int b, size_t esz, void *st, const Seg *segs, const int2 *blocks, int nb, const double *coefd,
+int launch_init(int b, size_t esz, void *st, const Seg *segs, const int2 *blocks, int nb, const void *coefT,
                 const double *phi0, const long long *blk_off, cudaStream_t stream) {
     if (nb == 0) return LBHPDE_OK;
     if (esz == 4) {
+        const float *cf = (const float *)coefT;
         if (b == 5)
-            lbk::k_init<float, 5><<<nb, kGenericThreads, 0, stream>>>((float *)st, segs, blocks, coefd, phi0, blk_off,
+            lbk::k_init<float, 5><<<nb, kGenericThreads, 0, stream>>>((float *)st, segs, blocks, cf, phi0, blk_off,
                                                                        kChunk);
         else
-            lbk::k_init<float, 7><<<nb, kGenericThreads, 0, stream>>>((float *)st, segs, blocks, coefd, phi0, blk_off,
+            lbk::k_init<float, 7><<<nb, kGenericThreads, 0, stream>>>((float *)st, segs, blocks, cf, phi0, blk_off,
                                                                        kChunk);
     } else {
+        const double *cd = (const double *)coefT;
         if (b == 5)
-            lbk::k_init<double, 5><<<nb, kGenericThreads, 0, stream>>>((double *)st, segs, blocks, coefd, phi0,
+            lbk::k_init<double, 5><<<nb, kGenericThreads, 0, stream>>>((double *)st, segs, blocks, cd, phi0,
                                                                         blk_off, kChunk);
         else
-            lbk::k_init<double, 7><<<nb, kGenericThreads, 0, stream>>>((double *)st, segs, blocks, coefd, phi0,
+            lbk::k_init<double, 7><<<nb, kGenericThreads, 0, stream>>>((double *)st, segs, blocks, cd, phi0,
                                                                         blk_off, kChunk);
     }
     LBH_CK(cudaGetLastError());
@@ -657,7 +744,23 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int Kr, int tblk, bool forc
         const lbh::Member mb{bt->segs_h[i], bt->segs_h[i].off, 1 << 30};
         (bt->N[i] <= cap && !force_halo ? resident : halo).push_back(mb);
     }
-    lbh::split_ring_classes(bt->esz, g.b, Kr, resident, ring);
+    // the 16-node kernel: whole waves of full CTAs and a tail of small ones when the members fill a
+    // wave; otherwise (and for the other kernels) CTA size classes
+    std::vector<lbh::Member> full, tail;
+    int sms = 0;
+    if (Kr == lbh::kRingK) {
+        int dev = 0;
+        CK(cudaGetDevice(&dev));
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    g.waves = Kr == lbh::kRingK && lbh::split_ring_waves(g.b, Kr, sms, resident, full, tail);
+    if (g.waves) {
+        for (auto &v : ring) v.clear();
+        ring[lbh::kRingClasses - 1] = full;
+        ring[0] = tail;
+    } else {
+        lbh::split_ring_classes(bt->esz, g.b, Kr, resident, ring);
+    }
     // windows must keep some valid nodes; resident members only chunk their launches by tblk
     if (!halo.empty() && cap_h - 2 * H < 32) return LBHPDE_ERR_UNSUPPORTED;
     // the previous plan's device tables (a re-plan after lbhpde_batch_set_kernel)
@@ -671,7 +774,15 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int Kr, int tblk, bool forc
     g.halo = Group::Plan{};
     for (int c = 0; c < lbh::kRingClasses; ++c) {
         if (ring[c].empty()) continue;
-        RC(lbh::pack_ring(g.b, bt->esz, Kr, g.dc, ring[c], g.ring[c].host, lbh::ring_class_threads(bt->esz, g.b, Kr, c)));
+        int threads = lbh::ring_class_threads(bt->esz, g.b, Kr, c);
+        if (g.waves && c == 0) {  // the tail: the smallest class that holds its largest member
+            long long nmax = 0;
+            for (const auto &mb : ring[c]) nmax = std::max<long long>(nmax, mb.seg.N);
+            int cl = 0;
+            while (cl < lbh::kRingClasses - 1 && nmax > (long long)lbh::ring_class_threads(bt->esz, g.b, Kr, cl) * Kr) ++cl;
+            threads = lbh::ring_class_threads(bt->esz, g.b, Kr, cl);
+        }
+        RC(lbh::pack_ring(g.b, bt->esz, Kr, g.dc, ring[c], g.ring[c].host, threads));
         RC(upload_plan(bt, g.ring[c]));
     }
     if (!halo.empty()) RC(lbh::pack_halo(g.b, bt->esz, K, g.dc, H, halo, g.halo.host));
@@ -755,11 +866,11 @@ int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
     RC(bt->dev_alloc(&bt->st[0], bt->st_bytes));
     RC(bt->dev_alloc(&bt->st[1], bt->st_bytes));
     RC(bt->upload(&bt->segs, segs));
-    RC(bt->upload(&bt->coefD, coefd));
     if (bt->esz == 4) {
         std::vector<float> cf(coefd.begin(), coefd.end());
         RC(bt->upload((float **)&bt->coefT, cf));
     } else {
+        RC(bt->upload(&bt->coefD, coefd));
         bt->coefT = bt->coefD;
     }
 
@@ -969,11 +1080,14 @@ int step_periodic(lbhpde_batch_s *bt, long nsteps) {
     const int cur0 = bt->cur, cur1 = bt->cur ^ (int)(nchunks & 1);
     // resident instances (each size class) and windows touch disjoint rows: when there is more
     // than one kind, they run concurrently, the resident classes on streams of their own
+    // (a group planned in whole waves launches its tail (class 0) after its full CTAs (class 2), on
+    // the same stream)
     bool used[lbh::kRingClasses] = {};
     int kinds = any_halo ? 1 : 0;
     for (int c = 0; c < lbh::kRingClasses; ++c) {
         for (auto &g : bt->groups)
-            if (!g.members.empty() && g.ring[c].ncta()) used[c] = true;
+            if (!g.members.empty() && (g.ring[c].ncta() || (c == lbh::kRingClasses - 1 && g.waves && g.ring[0].ncta())))
+                if (!(g.waves && c == 0)) used[c] = true;
         kinds += used[c] ? 1 : 0;
     }
     const bool fork = kinds > 1;
@@ -993,13 +1107,16 @@ int step_periodic(lbhpde_batch_s *bt, long nsteps) {
             rs = bt->side[c];
         }
         for (auto &g : bt->groups) {
-            if (g.members.empty() || !g.ring[c].ncta()) continue;
+            if (g.members.empty() || (g.waves && c == 0)) continue;
+            const bool tail = g.waves && c == lbh::kRingClasses - 1 && g.ring[0].ncta();
+            if (!g.ring[c].ncta() && !tail) continue;
             const long spl = bt->spl_req > 0 ? bt->spl_req : (1L << 30);
             long left = nsteps;
             bool firstl = true;
             while (left > 0) {
                 const int n = (int)std::min(left, spl);
                 RC(launch_group(bt, g, false, bt->st[firstl ? cur0 : cur1], bt->st[cur1], n, rs, c));
+                if (tail) RC(launch_group(bt, g, false, bt->st[firstl ? cur0 : cur1], bt->st[cur1], n, rs, 0));
                 firstl = false;
                 left -= n;
             }
@@ -1134,7 +1251,7 @@ int batch_set_phi(lbhpde_batch_s *bt, const double *phi0, int on_device) {
     for (int gi = 0; gi < 4; ++gi) {
         Group &g = gi < 2 ? bt->groups[gi] : bt->bgroups[gi - 2];
         if (g.members.empty()) continue;
-        RC(lbh::launch_init(g.b, bt->esz, bt->st[0], bt->segs, g.blocks, (int)g.blocks_h.size(), bt->coefD, src,
+        RC(lbh::launch_init(g.b, bt->esz, bt->st[0], bt->segs, g.blocks, (int)g.blocks_h.size(), bt->coefT, src,
                             g.blk_off, bt->stream));
         if (!g.blocks_h.empty()) ++bt->launches;
     }

@@ -64,6 +64,16 @@ int ring_class(size_t esz, int b, int K, long long N);
 int ring_class_threads(size_t esz, int b, int K, int cls);
 // Threads an instance's run is rounded up to (32 for k_onchip, 1 for k_ring).
 int ring_granule(int K);
+// Instances a CTA holds at most (the tail buffer rows of the on-chip kernels).
+constexpr int kRingMaxInstances = 32;
+// Wave-aware split of the 16-node resident members (K == kRingK) for a GPU of `sms` SMs: `full`
+// packs (first fit, largest first) into whole waves of full-SM CTAs, one CTA per SM at a time;
+// `tail` holds the members that do not fit there (or were evicted from a CTA to make room for a
+// larger one).  The tail runs afterwards in CTAs of its own size class spread over the SMs, so the
+// last, partial wave costs the time of its members' own work instead of a whole wave of full
+// CTAs.  False (both empty) when the members do not fill one wave or all fit.
+bool split_ring_waves(int b, int K, int sms, const std::vector<Member> &m, std::vector<Member> &full,
+                      std::vector<Member> &tail);
 // Resident members by the CTA size class they take: their own class, or the largest one where
 // they fill a gap left by larger instances.
 void split_ring_classes(size_t esz, int b, int K, const std::vector<Member> &m, std::vector<Member> (&out)[kRingClasses]);
@@ -83,7 +93,8 @@ int launch_onchip_f32(int b, int K, int dc, bool halo, const Packed &p, const lb
                       const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st);
 int launch_onchip_f64(int b, int K, int dc, bool halo, const Packed &p, const lbk::OnchipInst *insts_d,
                       const int *first_d, const void *in, void *out, const void *coefT, int nsteps, cudaStream_t st);
-int launch_init(int b, size_t esz, void *st, const lbk::Seg *segs, const int2 *blocks, int nb, const double *coefd,
+// coefT: the coefficient table in the state's type (f^eq rows after the P_j rows, as lbk::Seg::coef).
+int launch_init(int b, size_t esz, void *st, const lbk::Seg *segs, const int2 *blocks, int nb, const void *coefT,
                 const double *phi0, const long long *blk_off, cudaStream_t stream);
 
 // Bounded grids (lbhpde_bounded.cu): instances of up to kBoundedK * kBoundedMaxT nodes stay

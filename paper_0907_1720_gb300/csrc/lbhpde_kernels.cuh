@@ -191,33 +191,34 @@ __device__ __forceinline__ void gen_eval4_any(const T *c, int A, int Dg, const T
 
 // ---------------------------------------------------------------------------- a1: init
 // s_j(x) = f^eq_j(phi0(x)) (post-collision state of an equilibrium, collision leaves it
-// unchanged), phi(x) = phi0(x).  f^eq is evaluated in double and rounded once to T.
+// unchanged), phi(x) = phi0(x).  f^eq is evaluated in the state's type T from the coefficient
+// table of that type (FP32 deviation storage: FP32 arithmetic, as every later step; FP64: double).
 // Grid: blocks[i] = (segment, first node); each block covers `chunk` nodes; phi0_off[i] is
 // the offset of block i's segment in the concatenated phi0 array.
 template <typename T, int B>
 __global__ void k_init(T *__restrict__ st, const Seg *__restrict__ segs, const int2 *__restrict__ blocks,
-                       const double *__restrict__ coefd, const double *__restrict__ phi0,
+                       const T *__restrict__ coef, const double *__restrict__ phi0,
                        const long long *__restrict__ phi0_off, int chunk) {
     const int2 bl = blocks[blockIdx.x];
     const Seg s = segs[bl.x];
-    const double *__restrict__ fe = coefd + s.coef + (B - 1) * (s.D + 1);
+    const T *__restrict__ fe = coef + s.coef + (B - 1) * (s.D + 1);
     const double *__restrict__ p0 = phi0 + phi0_off[blockIdx.x];
     const int xend = min(bl.y + chunk, s.N);
     for (int x = bl.y + threadIdx.x; x < xend; x += blockDim.x) {
-        const double ph = p0[x];
-        st[s.off + x] = (T)ph;
-        const double w = s.A > 0 ? nu_pow<double>(ph, s.nu) : 0.0;
+        const T ph = (T)p0[x];
+        st[s.off + x] = ph;
+        const T w = s.A > 0 ? nu_pow<T>(ph, s.nu) : T(0);
 #pragma unroll
         for (int j = 1; j < B; ++j) {
-            const double *c = fe + (j - 1) * (s.D + 1);
-            double acc;
+            const T *c = fe + (j - 1) * (s.D + 1);
+            T acc;
             if (s.A > 0) {
-                acc = gen_eval<double>(c, s.A, s.Dg, ph, w);
+                acc = gen_eval<T>(c, s.A, s.Dg, ph, w);
             } else {
                 acc = c[s.D];
-                for (int p = s.D - 1; p >= 0; --p) acc = __fma_rn(acc, ph, c[p]);
+                for (int p = s.D - 1; p >= 0; --p) acc = fma_t(acc, ph, c[p]);
             }
-            st[s.off + (long long)j * s.ld + x] = (T)acc;
+            st[s.off + (long long)j * s.ld + x] = acc;
         }
     }
 }

@@ -11,7 +11,7 @@
 // Every thread runs the same step: publish its edge populations, one CTA barrier, then the
 // pulls from its own registers, the pulls from its neighbours' slots and the relaxation of all
 // 16 nodes.  The wrap-around of an instance is folded into the pulls: the registers of the
-// last thread's positions past node N-1 take the head values (thread 0's published first
+// last thread's first positions past node N-1 take the head values (thread 0's published first
 // values) before the pulls, and a neighbour read past node N-1 reads the head slot instead.
 // (A split barrier that relaxed the interior nodes while the edge values were in flight, with an
 // mbarrier per step parity, was slower on GB300: 6.0e11 against 6.9e11 node-updates/s on the
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     constexpr int NE = nedge(B);
     constexpr int PS = NE * MAXT;          // one parity of R (or L)
     constexpr int TS = NE * kRingMaxInst;  // one parity of the tails
-    constexpr int RCH = 12;                // Horner chunk: the interior in one pass, no spills at 128 registers
+    constexpr int RCH = 8;                 // Horner chunk (12 and 16 were slower on GB300; no spills)
     static_assert(K >= 2 * W + 1, "a thread must own interior nodes");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *R = reinterpret_cast<T *>(smem_raw);                   // [2][NE][MAXT]
@@ -240,27 +240,41 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
         __syncthreads();
         if (live) {
             // sources in this thread's registers first, then the neighbours'.  Every left-moving
-            // source past node N-1 is a head slot (thread 0's published first values): the
-            // registers of those positions (the last thread's padding, never written back) take
-            // the head values first, and the neighbour reads past N-1 take the head address.
-            // Positions past the last head slot take the last one (read only by padding).
-            if (near_end) {
-                T hd[NE];
+            // source past node N-1 is a head slot (thread 0's published first values): in the
+            // last thread the registers of the first positions past node N-1 (padding, never
+            // written back) take the head values first, and in the last two threads a neighbour
+            // read past node N-1 takes the head address.  The remainder rem picks one
+            // compile-time case, so the registers are named, not indexed; positions further out
+            // are read only by padding.
+            // the flux differences of a node add up apart from phi (they are of the size of the
+            // deviations, O(phi / c)), and phi takes their sum once: one rounding of phi a step.
+            // The sums start at -0, the identity of IEEE addition, so the first add folds away.
+            T d[K];
 #pragma unroll
-                for (int q = 0; q < NE; ++q) hd[q] = Lhd[P * PS + q * MAXT];
+            for (int k = 0; k < K; ++k) d[k] = T(-0.0);
+            if (near_end && rem < K) {
+                auto put = [&](auto rc) {
+                    constexpr int R = decltype(rc)::value;
 #pragma unroll
-                for (int j = 1; j < B; ++j) {
-                    const int a = -vel(j);
-                    if (a > 0) {
+                    for (int j = 1; j < B; ++j) {
+                        const int a = -vel(j);
 #pragma unroll
-                        for (int p = 0; p < K; ++p) {
-                            T h = hd[eslot(a)];
-#pragma unroll
-                            for (int i = 1; i < a; ++i)
-                                if (p - rem >= i) h = hd[eslot(a) + i];
-                            if (p >= rem) v[j][p] = h;
-                        }
+                        for (int i = 0; i < a; ++i)
+                            if (R + i < K) v[j][R + i] = Lhd[P * PS + (eslot(a) + i) * MAXT];
                     }
+                };
+                static_assert(K <= 16, "remainder cases");
+                switch (rem) {
+#define LBK_RING_REM(R)                        \
+    case R:                                    \
+        put(std::integral_constant<int, R>{}); \
+        break;
+                    LBK_RING_REM(1) LBK_RING_REM(2) LBK_RING_REM(3) LBK_RING_REM(4) LBK_RING_REM(5)
+                    LBK_RING_REM(6) LBK_RING_REM(7) LBK_RING_REM(8) LBK_RING_REM(9) LBK_RING_REM(10)
+                    LBK_RING_REM(11) LBK_RING_REM(12) LBK_RING_REM(13) LBK_RING_REM(14) LBK_RING_REM(15)
+#undef LBK_RING_REM
+                    default:
+                        break;
                 }
             }
 #pragma unroll
@@ -270,7 +284,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
 #pragma unroll
                     for (int k = K - 1; k >= e; --k) {
                         const T nv = v[j][k - e];
-                        phi[k] += nv - v[j][k];
+                        d[k] += nv - v[j][k];
                         v[j][k] = nv;
                     }
                 } else {
@@ -278,7 +292,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
 #pragma unroll
                     for (int k = 0; k + a < K; ++k) {
                         const T nv = v[j][k + a];
-                        phi[k] += nv - v[j][k];
+                        d[k] += nv - v[j][k];
                         v[j][k] = nv;
                     }
                 }
@@ -291,7 +305,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
                     for (int k = 0; k < e; ++k) {
                         const T nv = t > 0 ? Rme[P * PS + (eslot(e) + k) * MAXT - 1]
                                            : Tme[P * TS + (eslot(e) + k) * kRingMaxInst];
-                        phi[k] += nv - v[j][k];
+                        d[k] += nv - v[j][k];
                         v[j][k] = nv;
                     }
                 } else {
@@ -303,11 +317,13 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
                         const T *src = k + a >= rem ? Lhd + P * PS + (eslot(a) + q) * MAXT
                                                     : Lrt + P * PS + (eslot(a) + k + a - K) * MAXT;
                         const T nv = *src;
-                        phi[k] += nv - v[j][k];
+                        d[k] += nv - v[j][k];
                         v[j][k] = nv;
                     }
                 }
             }
+#pragma unroll
+            for (int k = 0; k < K; ++k) phi[k] += d[k];
             ring_relax<T, B, K, DC, RCH, 0, K>(sc, cs, D, omw, phi, v);
         }
     };

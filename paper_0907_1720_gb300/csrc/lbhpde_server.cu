@@ -268,7 +268,7 @@ int setup_admitted(lbhpde_server_s *S, std::vector<Req *> &adm) {
                             S->up));
         SCK(cudaMemcpyAsync(S->boff_d.p, boff.data(), sizeof(long long) * boff.size(), cudaMemcpyHostToDevice,
                             S->up));
-        SRC(lbh::launch_init(b, S->esz, S->arena_d, S->segs_d.p, S->blocks_d.p, (int)blocks.size(), S->coefD_d,
+        SRC(lbh::launch_init(b, S->esz, S->arena_d, S->segs_d.p, S->blocks_d.p, (int)blocks.size(), S->coefT_d,
                              S->phi0_d.p, S->boff_d.p, S->up));
         // the next lattice reuses the tables: order the copies after this launch (the set-up
         // stream holds only set-up work, so this does not wait for a block in flight)

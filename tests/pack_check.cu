@@ -152,6 +152,31 @@ int main() {
             }
         }
     }
+    // whole waves of full CTAs plus a tail (16-node kernel): every member placed once and the full
+    // members pack into the whole waves' CTAs
+    for (int trial = 0; trial < 24; ++trial) {
+        const int sms = trial % 3 == 0 ? 4 : (trial % 3 == 1 ? 19 : 152);
+        auto m = members(g, 50 + trial * 37, 4, 8192, 5);
+        std::vector<lbh::Member> full, tail;
+        const bool split = lbh::split_ring_waves(5, lbh::kRingK, sms, m, full, tail);
+        long long total = 0;
+        for (auto &mb : m) total += (mb.seg.N + lbh::kRingK - 1) / lbh::kRingK;
+        const long long limit = total / (512LL * sms) * sms;
+        if (!split) {
+            CHECK(full.empty() && tail.empty(), "no split, yet members assigned");
+            continue;
+        }
+        CHECK(limit > 0 && full.size() + tail.size() == m.size(), "split of %zu members: %zu + %zu", m.size(),
+              full.size(), tail.size());
+        std::set<long long> seen;
+        for (auto &mb : full) seen.insert(mb.seg.off);
+        for (auto &mb : tail) seen.insert(mb.seg.off);
+        CHECK(seen.size() == m.size(), "%zu distinct members of %zu after the split", seen.size(), m.size());
+        lbh::Packed p;
+        CHECK(lbh::pack_ring(5, 4, lbh::kRingK, 5, full, p, 512) == LBHPDE_OK, "pack of the full members failed");
+        CHECK(p.ncta() <= limit, "%d full CTAs for %lld in the whole waves", p.ncta(), limit);
+        check_ring(p, full, 5, lbh::kRingK, 512, 5);
+    }
     // bounded resident instances: the host's position shift puts each end's outer nodes and its
     // extrapolation node in one warp of live threads, inside the CTA
     const int KB = lbh::kBoundedK, wpos = 32 * KB;  // positions per warp

@@ -106,15 +106,14 @@ def emulate_pull(sizes, rng):
         rem = N - t * K
         assert 0 <= rt < nt
         w = v[tid].copy()
-        if near_end:
-            # registers of positions past node N-1 take the head slots (clamped to the last one)
-            hd = [L[q * MAXT + tb] for q in range(NE)]
+        if near_end and rem < K:
+            # the last thread: positions rem .. rem + a - 1 take the head slots; positions further
+            # out keep their padding, which must never reach a real node
             for j in range(1, B):
                 a = -VEL[j]
-                if a > 0:
-                    for p in range(K):
-                        if p >= rem:
-                            w[j, p] = hd[eslot(a) + min(p - rem, a - 1)]
+                for q in range(max(a, 0)):
+                    if rem + q < K:
+                        w[j, rem + q] = L[(eslot(a) + q) * MAXT + tb]
         for j in range(1, B):
             e = VEL[j]
             for k in range(K):
