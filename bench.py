@@ -591,8 +591,10 @@ def serving_leg(args, L, torch):
 def small_configs_leg(L, torch, stream, refs):
     """Configurations 1 (KdV soliton, N = 400, t = 1, 100 000 steps) and 2 (Kuramoto-Sivashinsky,
     N = 1024, t = 10, 100 000 steps), each in FP64 and FP32 on the automatic kernel: the whole
-    instance resident in one CTA (one SM) for every step, since a grid this small has no more
-    parallel work than one CTA holds and more CTAs would need a grid-wide exchange each step.
+    instance resident in one CTA (one SM) for every step, with as many threads as it has node
+    pairs, since a grid this small has no more parallel work than one CTA holds and more CTAs
+    would need a grid-wide exchange each step (latency-bound: a step is a barrier, an exchange
+    and two nodes' arithmetic per thread).
     CUDA-event time of the steps, E and relative L2 against the exact solution (KdV) or the
     ETDRK4 reference (KS), and the oracle's single-thread rate on the host beside it."""
     out = {}
@@ -623,8 +625,9 @@ def small_configs_leg(L, torch, stream, refs):
                             "node_updates_s": p.N * p.nsteps / sec,
                             "E": float(np.abs(phi - ref).sum() / np.abs(ref).sum()),
                             "l2": float(np.linalg.norm(phi - ref) / np.linalg.norm(ref)),
-                            "kernel": ("k_ring<float,5,16,128,5>, one CTA" if tag == "fp32" else
-                                       "k_onchip<double,5,4,512,false,5>, one CTA")}
+                            "kernel": (f"k_onchip<{'float' if tag == 'fp32' else 'double'},5,2,1024,false,5>: the "
+                                       f"whole instance resident in one CTA, 2 nodes a thread (the automatic "
+                                       f"choice for a batch too small to give every SM a warp)")}
             rec["fp32_E_over_fp64_E"] = rec["fp32"]["E"] / rec["fp64"]["E"]
             if refs and name in refs:
                 rec["oracle_single_thread"] = refs[name]["oracle"]

@@ -376,8 +376,10 @@ int lbhpde_server_destroy(lbhpde_server_t s);
  *   cuda_stream     stream for the two kernels and the copy of the result (NULL = legacy)
  * The per-block partial sums live in a file-scope device array of about 1 MiB that every GPU
  * loading the library keeps until the process exits.  The first call on a device (with that
- * device current) looks up the array's device address; make that first call before any
- * stream capture.  Every call writes each record it reads, so nothing is carried over between
+ * device current) looks up the array's device address and keeps it for the life of the
+ * process; make that first call before any stream capture, and make no call on a device after
+ * cudaDeviceReset() on it in the same process (the kept address belonged to the context the
+ * reset destroyed).  Every call writes each record it reads, so nothing is carried over between
  * calls, but all calls share the one array: calls that overlap on the GPU (other streams,
  * other host threads) race and must be serialised by the caller.  The call synchronises
  * cuda_stream.  Returns LBHPDE_ERR_DIVERGED (after filling out) if phi has a non-finite

@@ -989,13 +989,36 @@ int choose_kernels(lbhpde_batch_s *bt) {
         // K_req = kRingK asks for the 16-node resident kernel, whose windows keep the default (or
         // tuned) K; automatic choice: that kernel wherever it applies
         const int dcg = g.has_nu ? -1 : lbh::onchip_dc(g.b, g.maxD);
+        // a group too small to give every SM a warp at 16 nodes a thread is latency-bound: it
+        // takes the fewest nodes a thread (the most threads) whose CTA still holds its largest
+        // member (GB300, 100 000 steps: KdV on 400 nodes 0.29 us a step at 2 nodes a thread
+        // against 0.43 at 8 and 0.71 at 16; FP64 3.9 against 4.6)
+        long long thr16 = 0, nmax = 0;
+        for (int i : g.members) {
+            thr16 += (bt->N[i] + lbh::kRingK - 1) / lbh::kRingK;
+            nmax = std::max<long long>(nmax, bt->N[i]);
+        }
+        int sms = 0, dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            (void)cudaGetLastError();
+            sms = 0;
+        }
+        const bool small = bt->K_req == 0 && bt->kernel != LBHPDE_KERNEL_HALO && thr16 < 32LL * sms;
+        int K_small = 0;
+        if (small)
+            for (int Kc : {2, 4, 8})
+                if (Kc >= lbk::wmax(g.b) && (!g.has_nu || Kc >= 4) && lbh::onchip_maxt(bt->esz, g.b, Kc) > 0 &&
+                    nmax <= (long long)lbh::onchip_maxt(bt->esz, g.b, Kc) * Kc) {
+                    K_small = Kc;
+                    break;
+                }
         const bool ring16 = bt->kernel != LBHPDE_KERNEL_HALO && lbh::ring_split_ok(bt->esz, g.b, dcg) &&
-                            (bt->K_req == 0 || bt->K_req == lbh::kRingK);
+                            (bt->K_req == 0 || bt->K_req == lbh::kRingK) && !small;
         if (bt->K_req == lbh::kRingK && !ring16) return LBHPDE_ERR_UNSUPPORTED;
-        int K = bt->K_req > 0 && bt->K_req != lbh::kRingK ? bt->K_req : lbh::default_K(bt->esz, g.b);
+        int K = bt->K_req > 0 && bt->K_req != lbh::kRingK ? bt->K_req : (K_small ? K_small : lbh::default_K(bt->esz, g.b));
         int tblk = bt->spl_req;
         int tk = 0, tt = 0;
-        if (tuned_choice(bt->esz, g.b, dcg, &tk, &tt)) {
+        if (!K_small && tuned_choice(bt->esz, g.b, dcg, &tk, &tt)) {
             if (bt->K_req == 0 || bt->K_req == lbh::kRingK) K = tk;
             if (bt->spl_req == 0) tblk = tt;
         }

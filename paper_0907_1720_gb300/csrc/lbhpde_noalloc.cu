@@ -5,7 +5,9 @@
 // Every GPU that loads the library holds these arrays (about 1 MiB) until the process exits.
 // Host code must not hand the array names to a kernel: on the host they name a stand-in, not
 // device memory.  Their device addresses are taken once per device with
-// cudaGetSymbolAddress, on the first call made while that device is current.
+// cudaGetSymbolAddress, on the first call made while that device is current, and kept for the
+// life of the process: a cudaDeviceReset() of that device would leave them pointing into the
+// destroyed context, so the header asks callers not to call the entry point after one.
 #include <cuda_runtime.h>
 
 #include <mutex>

@@ -312,8 +312,10 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
                     const int a = -e;
 #pragma unroll
                     for (int k = K - a; k < K; ++k) {
+                        // head slot q = k + a - rem in [0, a - 1] (clamped both ways, so the
+                        // address not taken stays in bounds too)
                         int q = k + a - rem;
-                        q = q < a - 1 ? q : a - 1;
+                        q = q < 0 ? 0 : (q < a - 1 ? q : a - 1);
                         const T *src = k + a >= rem ? Lhd + P * PS + (eslot(a) + q) * MAXT
                                                     : Lrt + P * PS + (eslot(a) + k + a - K) * MAXT;
                         const T nv = *src;
