@@ -116,8 +116,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def ensemble_problems(rank=0, members=4096, world=1):
-    """Members rank, rank + world, ... of the one seeded ensemble (a partition over the ranks)."""
+def ensemble_problems(rank=0, members=4096, world=1, nodes=0):
+    """Members rank, rank + world, ... of the one seeded ensemble (a partition over the ranks);
+    nodes > 0: every member that many nodes (profiling cases)."""
+    if nodes > 0:
+        return W.kdv_burgers_ensemble(count=members, n_lo=nodes, n_hi=nodes)[rank::world]
     return W.kdv_burgers_ensemble(count=members)[rank::world]
 
 
@@ -154,10 +157,13 @@ def workload_problems(args, rank=0, world=1):
     workload by this description.  The ensemble is one seeded batch whose members rank,
     rank + world, ... this rank takes; the description names the whole batch."""
     if args.workload == "ensemble":
-        probs = ensemble_problems(rank, args.members, world)
+        nodes = getattr(args, "member_nodes", 0)
+        probs = ensemble_problems(rank, args.members, world, nodes)
         nsteps = W.ENSEMBLE_STEPS
-        total_n = sum(p.N for p in ensemble_problems(0, args.members, 1)) if world > 1 else sum(p.N for p in probs)
-        desc = (f"kdv_burgers_ensemble_{args.members}: {args.members} x N~U{{256..8192}} "
+        total_n = (sum(p.N for p in ensemble_problems(0, args.members, 1, nodes)) if world > 1
+                   else sum(p.N for p in probs))
+        sizes = f"N={nodes}" if nodes > 0 else "N~U{256..8192}"
+        desc = (f"kdv_burgers_ensemble_{args.members}: {args.members} x {sizes} "
                 f"(sum N = {total_n}), "
                 f"D1Q5 scheme 1, dx={W.ENSEMBLE_DX}, dt={W.ENSEMBLE_DT}, tau={W.ENSEMBLE_TAU}, "
                 f"{nsteps} steps per benchmark step")
@@ -791,7 +797,7 @@ def cpu_oracle_rate(args, sample_s=15.0, keep=False):
 
     cores = os.cpu_count() or 1
     if args.workload == "ensemble":
-        probs = ensemble_problems(0, args.members)
+        probs = ensemble_problems(0, args.members, 1, getattr(args, "member_nodes", 0))
         idx = ensemble_sample(probs, 2 * cores)
         steps = W.ENSEMBLE_STEPS
         outs, el = oracle_members(oracle, probs, idx, steps, min(cores, len(idx)))
@@ -939,6 +945,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 plain comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--members", type=int, default=4096, help="ensemble members (profiling: smaller)")
+    ap.add_argument("--member-nodes", type=int, default=0,
+                    help="ensemble: every member this many nodes (profiling cases; 0 = the configuration's sizes)")
     ap.add_argument("--nodes", type=int, default=1 << 24, help="long-grid nodes (profiling: smaller)")
     ap.add_argument("--no-tune", action="store_true", help="skip the on-chip autotuner")
     ap.add_argument("--onchip", default=None, metavar="K,T",
