@@ -15,7 +15,8 @@ windows; with --kernel stream, on the one-step-per-launch streaming kernel (HBM 
 --workload bounded: a tau sweep of Example 4.1 on its bounded grid (non-equilibrium
 extrapolation boundary, A_40 left out as for Table I): --sweep-members instances of N = 601,
 dx = 0.1, dt = 1e-3, tau spread over [1.989, 2.6], 1000 steps, one shared boundary array;
-every instance resident in one CTA (k_bounded), 12160 instances by default (80 per SM).
+every instance resident (FP32: 16 nodes a thread, 13 instances a CTA; FP64: one CTA each), 11856
+instances by default (78 per SM).
 --workload nu_grid: a 2^24-node periodic grid of u_t + u^1.5 u_x + u_xxx = 0 (class (1) with a
 real exponent), 1000 steps in on-chip windows (the real-exponent variant evaluates phi^nu once
 per node; ALU roofline), or on the streaming kernel with --kernel stream (HBM roofline).
@@ -173,7 +174,7 @@ def workload_problems(args, rank=0, world=1):
         desc = (f"ks_shock_tau_sweep_{args.sweep_members}: {args.sweep_members} x N=601 (Example 4.1 on "
                 f"[-30, 30], bounded grid, non-equilibrium extrapolation depth 2), D1Q5 scheme 1 without "
                 f"A_40, dx=0.1, dt=1e-3, tau in [{BOUNDED_TAU[0]}, {BOUNDED_TAU[1]}], {nsteps} steps per "
-                f"benchmark step, one resident CTA per instance")
+                f"benchmark step, every instance resident")
     elif args.workload == "nu_grid":
         p = W.gkdv_grid_config(N=args.nodes, nsteps=1000)
         probs, nsteps = [p], p.nsteps
@@ -392,8 +393,9 @@ def run_ours(args, rank, world, cpu=None):
             achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                     "frac": achieved / peak_tf, "traffic": None,
-                    "kernel": f"k_bounded<{'float' if esz == 4 else 'double'},5,4,512,5> (one resident CTA per "
-                              f"instance)",
+                    "kernel": ("k_ring_nee<float,5,16,512,5> (13 instances a CTA, interior nodes in registers, "
+                               "outer nodes in shared memory)" if esz == 4 else
+                               "k_bounded<double,5,4,512,5> (one resident CTA per instance)"),
                     "flops_per_node_update": fl, "peak_source": src}
         elif args.workload == "nu_grid" and args.kernel != "stream":
             A, Dg = nu_shape(L, probs[0])
@@ -931,8 +933,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ensemble",
                     choices=["ensemble", "long_grid", "serving", "bounded", "nu_grid"])
-    ap.add_argument("--sweep-members", type=int, default=12160,
-                    help="bounded: tau-sweep instances (12160 = 80 per SM; the state exceeds L2)")
+    ap.add_argument("--sweep-members", type=int, default=11856,
+                    help="bounded: tau-sweep instances (11856 = 152 SMs x 6 waves x 13 instances of 38 "
+                         "threads a CTA on the 16-node kernel; the state exceeds L2)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serving: mean arrival rate (requests/s)")
     ap.add_argument("--window", type=float, default=1.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--requests", type=int, default=2000, help="serving: cap on requests per rate")

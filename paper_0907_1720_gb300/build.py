@@ -20,7 +20,7 @@ LIB = os.path.join(BUILD, "liblbhpde.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["lbhpde_model.cpp", "lbhpde_api.cu", "lbhpde_onchip_f32.cu", "lbhpde_onchip_f64.cu", "lbhpde_ring.cu",
            "lbhpde_bounded.cu", "lbhpde_noalloc.cu", "lbhpde_server.cu"]
-HEADERS = ["lbhpde_kernels.cuh", "lbhpde_bounded.cuh", "lbhpde_ring.cuh", "lbhpde_internal.h", "lbhpde_onchip_launch.cuh"]
+HEADERS = ["lbhpde_kernels.cuh", "lbhpde_bounded.cuh", "lbhpde_ring.cuh", "lbhpde_ring_nee.cuh", "lbhpde_internal.h", "lbhpde_onchip_launch.cuh"]
 
 
 def _nvcc():

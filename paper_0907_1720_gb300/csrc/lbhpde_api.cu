@@ -70,6 +70,10 @@ struct Group {
     std::vector<lbk::BoundedInst> bnd_h;
     lbk::BoundedInst *bnd = nullptr;
     int bnd_threads = 0, bnd_dc = 0, bnd_D = 0;
+    lbh::PackedNee rn_h;               // bounded members on the 16-node resident kernel
+    lbk::RingNeeInst *rn_insts = nullptr;
+    int *rn_first = nullptr;
+    int rn_dc = 0;
     std::vector<int> smembers_h;       // streaming members
     int *smembers = nullptr;
     std::vector<int2> sblocks_h;       // their node blocks (kChunk nodes each)
@@ -931,9 +935,18 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
     g.smembers_h.clear();
     g.sblocks_h.clear();
     const int K = lbh::kBoundedK;
-    int maxthr = 0, maxD = 0;
+    int maxthr = 0, maxD = 0, maxDn = 0;
+    // FP32 D1Q5 polynomial members take the 16-node resident kernel (unless a kernel or 4 nodes
+    // a thread was asked for), the others one CTA each or the streaming step
+    std::vector<lbh::NeeMember> nee;
+    const bool nee_auto = bt->kernel == LBHPDE_KERNEL_AUTO || (bt->kernel == LBHPDE_KERNEL_ONCHIP && bt->K_req != K);
     for (int i : g.members) {
         const Seg &sg = bt->segs_h[i];
+        if (nee_auto && lbh::ring_nee_ok(bt->esz, g.b, sg)) {
+            nee.push_back(lbh::NeeMember{sg, i, 1 << 30});
+            maxDn = std::max(maxDn, sg.D);
+            continue;
+        }
         const int shift = bt->N[i] <= (long long)K * lbh::kBoundedMaxT && sg.A == 0
                               ? lbh::bounded_shift(g.b, sg.N, sg.pad)
                               : -1;  // real-exponent members stream
@@ -962,9 +975,20 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
     bt->dev_free(g.bnd);
     bt->dev_free(g.smembers);
     bt->dev_free(g.sblocks);
+    bt->dev_free(g.rn_insts);
+    bt->dev_free(g.rn_first);
     g.bnd = nullptr;
     g.smembers = nullptr;
     g.sblocks = nullptr;
+    g.rn_insts = nullptr;
+    g.rn_first = nullptr;
+    g.rn_h = lbh::PackedNee{};
+    if (!nee.empty()) {
+        g.rn_dc = lbh::onchip_dc(g.b, maxDn);
+        RC(lbh::pack_ring_nee(g.b, g.rn_dc, nee, g.rn_h, 512));
+        RC(bt->upload(&g.rn_insts, g.rn_h.insts));
+        RC(bt->upload(&g.rn_first, g.rn_h.first));
+    }
     if (!g.bnd_h.empty()) RC(bt->upload(&g.bnd, g.bnd_h));
     if (!g.smembers_h.empty()) {
         RC(bt->upload(&g.smembers, g.smembers_h));
@@ -1202,7 +1226,7 @@ int step_bounded(lbhpde_batch_s *bt, long nsteps, const double *pbd, long long s
     bool any_stream = false, any_res = false;
     for (auto &g : bt->bgroups) {
         if (!g.smembers_h.empty()) any_stream = true;
-        if (!g.bnd_h.empty()) any_res = true;
+        if (!g.bnd_h.empty() || g.rn_h.ncta()) any_res = true;
     }
     int a = cur0;
     if (any_stream) {
@@ -1220,6 +1244,13 @@ int step_bounded(lbhpde_batch_s *bt, long nsteps, const double *pbd, long long s
     const int target = fixed ? bt->cur : (any_stream ? a : cur0);
     if (any_res) {
         for (auto &g : bt->bgroups) {
+            for (long done = 0; g.rn_h.ncta() && done < nsteps;) {
+                const int n = (int)std::min<long>(nsteps - done, 1L << 30);
+                RC(lbh::launch_ring_nee_f32(g.rn_dc, g.rn_h, g.rn_insts, g.rn_first, bt->st[done == 0 ? cur0 : target],
+                                            bt->st[target], bt->coefT, pbd, stride, done, n, bt->stream));
+                ++bt->launches;
+                done += n;
+            }
             if (g.bnd_h.empty()) continue;
             for (long done = 0; done < nsteps;) {
                 const int n = (int)std::min<long>(nsteps - done, lbh::bounded_launch_steps(g.b, bt->esz));

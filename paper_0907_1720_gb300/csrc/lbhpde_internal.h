@@ -10,6 +10,7 @@
 #include "lbhpde_bounded.cuh"
 #include "lbhpde_kernels.cuh"
 #include "lbhpde_ring.cuh"
+#include "lbhpde_ring_nee.cuh"
 
 namespace lbh {
 
@@ -115,5 +116,28 @@ int launch_bounded(int b, size_t esz, int dc, int ninst, int nthreads, size_t sm
                    long long step0, int nsteps, cudaStream_t st);
 int launch_nee_fix(int b, size_t esz, void *st, const lbk::Seg *segs, const int *members, int nmem,
                    const void *coefT, const double *phib, long long stride, long long step, cudaStream_t stream);
+
+// Bounded members on the 16-node resident kernel (k_ring_nee, FP32 D1Q5 polynomial models): the
+// interior nodes W..N-W-1 in thread-granular runs of ceil((N - 2W) / 16) threads, first fit,
+// largest first, at most 32 instances per CTA of `threads` threads.
+struct PackedNee {
+    std::vector<lbk::RingNeeInst> insts;
+    std::vector<int> first;
+    int nthreads = 32, stride = 0;
+    size_t smem = 0;
+    int ncta() const { return first.empty() ? 0 : (int)first.size() - 1; }
+};
+struct NeeMember {
+    lbk::Seg seg;
+    int mi;     // batch member index (its boundary rows)
+    int steps;  // steps in the launch
+};
+// Whether a bounded member can take k_ring_nee: FP32 D1Q5 polynomial, its interior within one
+// 512-thread CTA, depth within the first and last 16 interior nodes' reach.
+bool ring_nee_ok(size_t esz, int b, const lbk::Seg &s);
+int pack_ring_nee(int b, int dc, const std::vector<NeeMember> &m, PackedNee &out, int threads);
+int launch_ring_nee_f32(int dc, const PackedNee &p, const lbk::RingNeeInst *insts_d, const int *first_d,
+                        const void *in, void *out, const void *coefT, const double *phib, long long stride,
+                        long long step0, int nsteps, cudaStream_t st);
 
 }  // namespace lbh

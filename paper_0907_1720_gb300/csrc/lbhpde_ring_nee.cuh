@@ -1,0 +1,358 @@
+// Bounded instances (non-equilibrium extrapolation boundary) resident at 16 nodes a thread.
+//
+// The step of k_ring (Eq. (LBE) in pull form, flux-difference update of phi, relaxation with
+// P_j = omega f^eq_j of Eqs. (EDF5)/(EDF7)) on the interior nodes W..N-W-1, and the rebuild of
+// the W = max|e| outer nodes at each end that the paper applies to its bounded test problems
+// (Sec. IV, after Guo et al.; the rule and its depth are this library's reading):
+//   phi(x_b) = phi_b,   s_j(x_b) = f^eq_j(phi_b) + [s_j(x_f) - f^eq_j(phi(x_f))],
+// x_f = W - 1 + depth on the left and N - W - depth on the right.  Collision scales the
+// non-equilibrium part of every node by (1 - omega) and leaves f^eq unchanged, so rebuilding
+// from the post-collision state equals rebuilding before the collision (as in k_bounded).
+//
+// Layout: the interior nodes of an instance sit in registers, 16 a thread in a thread-granular
+// run (interior node W + 16 t + k at position k of thread t).  The 2W outer nodes live in shared
+// memory, one block per instance and step parity, since their own collision and streaming would
+// be overwritten by the rebuild anyway:
+//   * the first thread's right-moving inflow from nodes below W reads the left outer nodes
+//     (fixed addresses);
+//   * the last thread's left-moving inflow from nodes past N-W-1 reads the right outer nodes:
+//     the registers of its first positions past the last interior node take them by a jump on
+//     the remainder, and neighbour reads past it take their address (as the wrap-around of
+//     k_ring);
+//   * after the relaxation, the thread that holds x_f of an end copies x_f's phi and s_j to its
+//     column of shared memory (a jump on the position that only reads registers), and writes the
+//     end's rebuilt outer nodes into the block of the next step's parity.  The next step's
+//     barrier orders that write before every read of it.
+// The terms that do not depend on the state, phi_b and f^eq_j(phi_b), are ready before the
+// rebuild needs them: during step s - 1 one helper thread per (instance, outer node, j >= 1)
+// evaluates f^eq_j(phi_b) for the rebuild of step s into a block of parity s & 1 (the barrier of
+// step s orders it before the rebuild; the block is rewritten only after the next barrier), from
+// a boundary value that it copied into shared memory by cp.async a step before (row step0 + s of
+// the member's block, phib + mi * stride), so neither the global load nor these polynomials lie
+// on the rebuild's path.  After the last step the first thread of each instance writes the outer
+// nodes back.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "lbhpde_ring.cuh"
+
+namespace lbk {
+
+// One bounded instance of the 16-node resident kernel.
+struct RingNeeInst {
+    long long off, ld;  // state placement (as Seg) in st_in
+    long long off2;     // placement of the result in st_out
+    int N, D;
+    int gcoef;          // coefficient block in global memory (as Seg::coef)
+    int scoef;          // this instance's P_j rows, f^eq_j rows and 1 - omega in shared memory
+    int tbase, nthr;    // first CTA thread, threads: ceil((N - 2W) / 16)
+    int mi;             // batch member index: its boundary rows start at phib + mi * stride
+    int depth;          // extrapolation depth
+    int il;             // index among the CTA's instances (outer-node block)
+    int steps;          // steps this instance takes in the launch (<= nsteps)
+};
+
+// Shared coefficient block of one bounded instance: P_j rows, f^eq_j rows (stride crow(D)),
+// 1 - omega, padded to a multiple of 4.
+__host__ __device__ constexpr int nee_cblock(int B, int D) { return 2 * (B - 1) * crow(D) + 4; }
+// Helper threads of a CTA: one per (instance, outer node, population j >= 1).
+__host__ __device__ constexpr int nee_helpers(int B) { return kRingMaxInst * 2 * wmax(B) * (B - 1); }
+// Shared elements (4-byte) of a k_ring_nee CTA of MAXT threads, without the coefficient blocks:
+// the exchange rows, the x_f column, the outer-node blocks and the boundary terms
+// [2 parities][kRingMaxInst][2W][B] (phi_b, f^eq_j(phi_b)), and the helpers' copied boundary
+// values [2 parities][helpers] doubles.
+__host__ __device__ constexpr int nee_fixed_elems(int B, int MAXT) {
+    return 4 * nedge(B) * MAXT + B * MAXT + 2 * 2 * kRingMaxInst * 2 * wmax(B) * B + 2 * 2 * nee_helpers(B);
+}
+
+// Asynchronous 8-byte copy global -> shared (visible to this thread after cp_async_wait_all).
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Horner of one coefficient row (degree DC at compile time, else D).
+template <typename T, int DC>
+__device__ __forceinline__ T nee_row(const T *c, int D, T x) {
+    if constexpr (DC > 0) {
+        T acc = c[DC];
+#pragma unroll
+        for (int p = DC - 1; p >= 0; --p) acc = fma_t(acc, x, c[p]);
+        return acc;
+    } else {
+        T acc = c[D];
+        for (int p = D - 1; p >= 0; --p) acc = fma_t(acc, x, c[p]);
+        return acc;
+    }
+}
+
+template <typename T, int B, int K, int MAXT, int DC>
+__global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
+    k_ring_nee(const T *__restrict__ st_in, T *__restrict__ st_out, const RingNeeInst *__restrict__ insts,
+               const int *__restrict__ cta_first, const T *__restrict__ coefs, const double *__restrict__ phib,
+               long long stride, long long step0, int nsteps) {
+    constexpr int W = wmax(B);
+    constexpr int NE = nedge(B);
+    constexpr int PS = NE * MAXT;                 // one parity of R (or L)
+    constexpr int OS = kRingMaxInst * 2 * W * B;  // one parity of the outer-node blocks
+    constexpr int RCH = 8;                        // Horner chunk, as in k_ring
+    static_assert(K >= 2 * W + 1 && K <= 16, "nodes a thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *R = reinterpret_cast<T *>(smem_raw);  // [2][NE][MAXT]
+    T *L = R + 2 * PS;                        // [2][NE][MAXT]
+    T *X = L + 2 * PS;                        // [B][MAXT]: x_f values of the rebuilding threads
+    T *OB = X + B * MAXT;                     // [2][kRingMaxInst][2W][B] outer nodes
+    T *GB = OB + 2 * OS;                      // [2][kRingMaxInst][2W][B] phi_b, f^eq_j(phi_b)
+    constexpr int NH = nee_helpers(B);
+    double *PBs = reinterpret_cast<double *>(GB + 2 * OS);  // [2][NH] helpers' boundary values
+    T *scoef = reinterpret_cast<T *>(PBs + 2 * NH);
+
+    const int nt = blockDim.x;
+    const int first = cta_first[blockIdx.x], last = cta_first[blockIdx.x + 1];
+    const int tid = threadIdx.x;
+    for (int i = first; i < last; ++i) {
+        const RingNeeInst I = insts[i];
+        const int Dk = DC > 0 ? DC : I.D;
+        const int cs = crow(Dk), n = (B - 1) * (I.D + 1);
+        for (int q = tid; q < 2 * (B - 1) * cs; q += nt) {
+            const int h = q / ((B - 1) * cs), r = q % ((B - 1) * cs);  // h = 0: P_j, 1: f^eq_j
+            const int j = r / cs, pp = r % cs;
+            scoef[I.scoef + q] = pp <= I.D ? coefs[I.gcoef + h * n + j * (I.D + 1) + pp] : T(0);
+        }
+        if (tid == 0) scoef[I.scoef + 2 * (B - 1) * cs] = coefs[I.gcoef + 2 * n];
+        // the outer nodes' initial state (parity 0): row j of node o (o < W: node o; else node
+        // N - 2W + o)
+        for (int q = tid; q < 2 * W * B; q += nt) {
+            const int o = q / B, j = q % B;
+            const long long x = o < W ? o : I.N - 2 * W + o;
+            OB[(I.il * 2 * W + o) * B + j] = st_in[I.off + (long long)j * I.ld + x];
+        }
+    }
+    // helper role: instance hi of the CTA, outer node ho (ho < W: left end), population hj;
+    // it copies the boundary value of rebuild r (row step0 + r) two rebuilds ahead
+    const int h_n = (last - first) * 2 * W * (B - 1);
+    const bool helper = tid < h_n;
+    const int hi = tid / (2 * W * (B - 1)), ho = (tid / (B - 1)) % (2 * W), hj = 1 + tid % (B - 1);
+    const double *hsrc = phib;
+    int hsteps = 0, hq = 0, hD = 0;
+    if (helper) {
+        const RingNeeInst &H = insts[first + hi];
+        hsrc = phib + (long long)H.mi * stride + step0 * (2 * W) + ho;
+        hsteps = H.steps;
+        hD = DC > 0 ? DC : H.D;
+        hq = H.scoef + (B - 1) * crow(hD) + (hj - 1) * crow(hD);
+        if (hsteps > 0) cp_async8(PBs + tid, hsrc);
+        if (hsteps > 1) cp_async8(PBs + NH + tid, hsrc + 2 * W);
+    }
+    T *const hdst = GB + (hi * 2 * W + ho) * B;  // + parity * OS
+    // f^eq_j(phi_b) of rebuild r into its parity, and the copy of row r + 2 into the freed slot
+    auto help = [&](int r) {
+        if (!helper || r >= hsteps) return;
+        cp_async_wait_all();
+        const T pb = (T)PBs[(r & 1) * NH + tid];
+        T *dst = hdst + (r & 1) * OS;
+        dst[hj] = nee_row<T, DC>(scoef + hq, hD, pb);
+        if (hj == 1) dst[0] = pb;
+        if (r + 2 < hsteps) cp_async8(PBs + (r & 1) * NH + tid, hsrc + (long long)(r + 2) * (2 * W));
+    };
+    int me = -1;
+    for (int i = first; i < last; ++i) {
+        const int tb = insts[i].tbase;
+        if (tid >= tb && tid < tb + insts[i].nthr) me = i;
+    }
+    RingNeeInst I{};
+    if (me >= 0) I = insts[me];
+    const int t = tid - I.tbase;
+    const bool has = me >= 0;
+    const int N = I.N;
+    const int xb = W + t * K;    // node of this thread's first position
+    const int rem = N - W - xb;  // positions k >= rem lie past the last interior node
+    T phi[K], v[B][K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const bool ok = has && k < rem;
+        phi[k] = ok ? st_in[I.off + xb + k] : T(0);
+#pragma unroll
+        for (int j = 1; j < B; ++j) v[j][k] = ok ? st_in[I.off + (long long)j * I.ld + xb + k] : T(0);
+    }
+    __syncthreads();  // coefficients and outer nodes staged
+    help(0);          // ordered before the rebuild of step 0 by the barrier of step 0
+    const T *sc = scoef + I.scoef;
+    const int D = DC > 0 ? DC : I.D;
+    const int cs = crow(D);
+    const T *Q = sc + (B - 1) * cs;  // f^eq_j rows
+    const T omw = has ? sc[2 * (B - 1) * cs] : T(0);
+    const int steps = has ? I.steps : 0;
+    T *const Rme = R + tid;
+    T *const Lme = L + tid;
+    T *const Xme = X + tid;
+    const bool has_right = has && t + 1 < I.nthr;
+    const T *const Lrt = L + (has_right ? tid + 1 : tid);
+    T *const OBi = OB + (has ? I.il : 0) * 2 * W * B;  // this instance's outer block, parity 0
+    // x_f of each end, as interior indices: its thread rebuilds that end
+    const int fL = has ? I.depth - 1 : -K, fR = has ? N - 2 * W - I.depth : -K;
+    const int side_mask = (fL >= t * K && fL < t * K + K ? 1 : 0) | (fR >= t * K && fR < t * K + K ? 2 : 0);
+
+    auto step = [&](auto parc, int s) {
+        constexpr int P = decltype(parc)::value;
+        const bool live = s < steps;
+        if (live) {
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const int e = vel(j);
+                if (e > 0) {
+#pragma unroll
+                    for (int i = 0; i < e; ++i) Rme[P * PS + (eslot(e) + i) * MAXT] = v[j][K - e + i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < -e; ++i) Lme[P * PS + (eslot(-e) + i) * MAXT] = v[j][i];
+                }
+            }
+        }
+        __syncthreads();
+        help(s + 1);
+        if (!live) return;
+        const T *ob = OBi + P * OS;  // the outer nodes of this step
+        // the last thread: its first positions past the last interior node take the right outer
+        // nodes' left-moving populations (named registers, a jump on the remainder)
+        if (rem < K) {
+            auto put = [&](auto rc) {
+                constexpr int Rr = decltype(rc)::value;
+#pragma unroll
+                for (int j = 1; j < B; ++j) {
+                    const int a = -vel(j);
+#pragma unroll
+                    for (int i = 0; i < a; ++i)
+                        if (Rr + i < K) v[j][Rr + i] = ob[(W + i) * B + j];
+                }
+            };
+            switch (rem) {
+#define LBK_NEE_REM(Rv)                         \
+    case Rv:                                    \
+        put(std::integral_constant<int, Rv>{}); \
+        break;
+                LBK_NEE_REM(1) LBK_NEE_REM(2) LBK_NEE_REM(3) LBK_NEE_REM(4) LBK_NEE_REM(5)
+                LBK_NEE_REM(6) LBK_NEE_REM(7) LBK_NEE_REM(8) LBK_NEE_REM(9) LBK_NEE_REM(10)
+                LBK_NEE_REM(11) LBK_NEE_REM(12) LBK_NEE_REM(13) LBK_NEE_REM(14) LBK_NEE_REM(15)
+#undef LBK_NEE_REM
+                default:
+                    break;
+            }
+        }
+        T d[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) d[k] = T(-0.0);
+        // sources in this thread's registers first, then the neighbours' or the outer nodes'
+#pragma unroll
+        for (int j = 1; j < B; ++j) {
+            const int e = vel(j);
+            if (e > 0) {
+#pragma unroll
+                for (int k = K - 1; k >= e; --k) {
+                    const T nv = v[j][k - e];
+                    d[k] += nv - v[j][k];
+                    v[j][k] = nv;
+                }
+            } else {
+                const int a = -e;
+#pragma unroll
+                for (int k = 0; k + a < K; ++k) {
+                    const T nv = v[j][k + a];
+                    d[k] += nv - v[j][k];
+                    v[j][k] = nv;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 1; j < B; ++j) {
+            const int e = vel(j);
+            if (e > 0) {
+#pragma unroll
+                for (int k = 0; k < e; ++k) {
+                    const T nv = t > 0 ? Rme[P * PS + (eslot(e) + k) * MAXT - 1] : ob[(W + k - e) * B + j];
+                    d[k] += nv - v[j][k];
+                    v[j][k] = nv;
+                }
+            } else {
+                const int a = -e;
+#pragma unroll
+                for (int k = K - a; k < K; ++k) {
+                    // right outer node index, clamped so that the address not taken stays in bounds
+                    int q = k + a - rem;
+                    q = q < 0 ? 0 : (q < W - 1 ? q : W - 1);
+                    const T *src = k + a >= rem ? ob + (W + q) * B + j : Lrt + P * PS + (eslot(a) + k + a - K) * MAXT;
+                    const T nv = *src;
+                    d[k] += nv - v[j][k];
+                    v[j][k] = nv;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) phi[k] += d[k];
+        ring_relax<T, B, K, DC, RCH, 0, K>(sc, cs, D, omw, phi, v);
+        // the rebuild: x_f's phi and s_j through this thread's column of X, then the outer nodes
+        // of the next step
+        auto rebuild = [&](int pf, int side) {
+            auto get = [&](auto pc) {
+                constexpr int Pv = decltype(pc)::value;
+                Xme[0] = phi[Pv];
+#pragma unroll
+                for (int j = 1; j < B; ++j) Xme[j * MAXT] = v[j][Pv];
+            };
+            switch (pf) {
+#define LBK_NEE_XF(Pv)                          \
+    case Pv:                                    \
+        get(std::integral_constant<int, Pv>{}); \
+        break;
+                LBK_NEE_XF(0) LBK_NEE_XF(1) LBK_NEE_XF(2) LBK_NEE_XF(3) LBK_NEE_XF(4) LBK_NEE_XF(5)
+                LBK_NEE_XF(6) LBK_NEE_XF(7) LBK_NEE_XF(8) LBK_NEE_XF(9) LBK_NEE_XF(10) LBK_NEE_XF(11)
+                LBK_NEE_XF(12) LBK_NEE_XF(13) LBK_NEE_XF(14) LBK_NEE_XF(15)
+#undef LBK_NEE_XF
+                default:
+                    break;
+            }
+            const T phf = Xme[0];
+            const int blk = (OBi - OB) + side * W * B;  // this end's outer nodes in a block
+            T *const nob = OB + (P ^ 1) * OS + blk;
+            const T *const g = GB + P * OS + blk;  // phi_b, f^eq_j(phi_b) of this rebuild
+#pragma unroll
+            for (int j = 1; j < B; ++j) {
+                const T fn = Xme[j * MAXT] - nee_row<T, DC>(Q + (j - 1) * cs, D, phf);
+#pragma unroll
+                for (int x = 0; x < W; ++x) nob[x * B + j] = g[x * B + j] + fn;
+            }
+#pragma unroll
+            for (int x = 0; x < W; ++x) nob[x * B] = g[x * B];
+        };
+        if (side_mask & 1) rebuild(fL - t * K, 0);
+        if (side_mask & 2) rebuild(fR - t * K, 1);
+    };
+    for (int s = 0; s < nsteps; s += 2) {
+        step(std::integral_constant<int, 0>{}, s);
+        if (s + 1 < nsteps) step(std::integral_constant<int, 1>{}, s + 1);
+    }
+    __syncthreads();  // the last rebuild's outer nodes are in the block of parity nsteps & 1
+    if (has) I = insts[me];
+    if (has && t == 0) {
+        const T *ob = OBi + (nsteps & 1) * OS;
+        for (int o = 0; o < 2 * W; ++o) {
+            const long long x = o < W ? o : N - 2 * W + o;
+#pragma unroll
+            for (int j = 0; j < B; ++j) st_out[I.off2 + (long long)j * I.ld + x] = ob[o * B + j];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (has && k < rem) {
+            st_out[I.off2 + xb + k] = phi[k];
+#pragma unroll
+            for (int j = 1; j < B; ++j) st_out[I.off2 + (long long)j * I.ld + xb + k] = v[j][k];
+        }
+    }
+}
+
+}  // namespace lbk

@@ -234,3 +234,90 @@ def test_tau_sweep_helper(L):
     for t, e in zip(taus, E):
         q = bounded("4.1", 1e-3, float(t), 300, 1 | NOA)
         assert e == pytest.approx(oracle.error_E(oracle_run(q), q.exact(q.t_end)), rel=1e-9)
+
+
+# ---------------------------------------------------------------- FP32: the 16-node kernel
+EPS32 = 2.0 ** -24
+
+
+def _growth(p, rel=1e-6, seed=0):
+    """Growth of a relative perturbation of phi0 over p's steps, measured with the oracle: the
+    factor by which the scheme amplifies errors made along the way on this problem."""
+    rng = np.random.default_rng(seed)
+    a = oracle_run(p)
+    q = W.Problem(p.eq, p.N, p.dx, p.dt, p.tau, p.nsteps, p.phi0 * (1 + rel * rng.standard_normal(p.N)),
+                  xl=p.xl, scheme=p.scheme, boundary=p.boundary, exact=p.exact, exact_xt=p.exact_xt, meta=p.meta)
+    b = oracle_run(q)
+    return normwise(b, a) / rel
+
+
+def fp32_bound(p):
+    """The FP32 parity bound of the periodic tests, 16 eps32 sqrt(n) + 4 eps32 (one rounding of
+    phi and of the stored deviations a step, added like a random walk, plus the initial
+    rounding), times the perturbation growth G >= 1 the oracle measures on the problem."""
+    return (16 * EPS32 * np.sqrt(p.nsteps) + 4 * EPS32) * max(1.0, _growth(p))
+
+
+# (name, example, dt, tau, scheme, depth, steps, dx): D1Q5, depths 1-4 and 20 (x_f in the second
+# thread of 16 nodes), grids of 501, 601 and 1001 nodes, tau at the paper's tau_opt (growth ~30)
+# and above it (growth < 1)
+FP32_CASES = [
+    ("ks_4.1_tauopt", "4.1", 1e-3, 1.989, 1 | NOA, 2, 1100, 0.1),
+    ("ks2_4.2_tauopt", "4.2", 1e-2, 4.569, 1 | NOA, 2, 600, 0.1),
+    ("ks_4.1_d1", "4.1", 1e-3, 2.05, 1 | NOA, 1, 600, 0.1),
+    ("ks_4.1_d3", "4.1", 1e-3, 2.05, 1 | NOA, 3, 600, 0.1),
+    ("ks_4.1_d4", "4.1", 1e-3, 2.05, 1 | NOA, 4, 600, 0.1),
+    ("ks_4.1_d20", "4.1", 1e-3, 2.1, 1 | NOA, 20, 400, 0.1),
+    ("ks_4.1_N501", "4.1", 1.2e-3, 2.05, 1 | NOA, 2, 500, 0.12),
+]
+
+
+def _bounded_dx(ex, dt, tau, n, scheme, depth, dx):
+    p = W.bounded_config(ex, dt, tau, n * dt, scheme=scheme, dx=dx)
+    p.meta["depth"] = depth
+    return p
+
+
+@pytest.mark.parametrize("case", FP32_CASES, ids=[c[0] for c in FP32_CASES])
+@pytest.mark.parametrize("kernel", ["auto", "resident4", "stream"])
+def test_fp32_matches_oracle(L, case, kernel):
+    """FP32 deviation storage on bounded grids, each kernel: the 16-node resident kernel (the
+    automatic choice for FP32 D1Q5), the one-instance-per-CTA kernel at 4 nodes a thread, and the
+    streaming step with the rebuild; launches split in two to cover the step offset of the
+    boundary rows.  Bound: fp32_bound."""
+    name, ex, dt, tau, scheme, depth, n, dx = case
+    p = _bounded_dx(ex, dt, tau, n, scheme, depth, dx)
+    want = oracle_run(p)
+    s = L.Solver.for_problem(p, precision=L.FP32_DEV)
+    if kernel == "resident4":
+        s.set_kernel(L.KERNEL_ONCHIP, 4)
+    elif kernel == "stream":
+        s.set_kernel(L.KERNEL_STREAM)
+    s.set_phi(p.phi0)
+    done = 0
+    for m in (n // 3, n - n // 3):
+        s.step_nee(m, W.boundary_values(p, 2, done, m))
+        done += m
+    got = s.read_phi()
+    s.close()
+    assert normwise(got, want) <= fp32_bound(p), kernel
+
+
+def test_fp32_bounded_batch_matches_alone_bitwise(L):
+    """Bounded FP32 members of different grids and depths packed into shared CTAs of the 16-node
+    kernel give the same bits as each alone, and each matches its oracle run."""
+    cases = [c for c in FP32_CASES if c[0] != "ks2_4.2_tauopt"]
+    probs = [_bounded_dx(ex, dt, tau, 300, scheme, depth, dx) for _, ex, dt, tau, scheme, depth, _, dx in cases]
+    stride = 300 * 4
+    phib = np.concatenate([W.boundary_values(p, 2, 0, 300).ravel() for p in probs])
+    b = L.Batch(probs, precision=L.FP32_DEV)
+    b.set_phi(np.concatenate([p.phi0 for p in probs])).step_nee(300, phib, stride)
+    got = b.read_phi()
+    b.close()
+    for i, p in enumerate(probs):
+        s = L.Solver.for_problem(p, precision=L.FP32_DEV)
+        alone = s.set_phi(p.phi0).step_nee(300, W.boundary_values(p, 2, 0, 300)).read_phi()
+        s.close()
+        seg = got[b.offsets[i]: b.offsets[i + 1]]
+        assert np.array_equal(seg, alone), (i, p.N, p.meta["depth"])
+        assert normwise(seg, oracle_run(p)) <= fp32_bound(p)

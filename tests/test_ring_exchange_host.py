@@ -206,3 +206,97 @@ def test_step_protocol_random_interleavings():
         nwarps = rnd.choice([1, 2, 3, 4, 8, 16])
         wrap = [rnd.random() < 0.3 for _ in range(nwarps)]
         assert _protocol(nwarps, wrap, 9, rnd) == 3 * 9 * nwarps
+
+
+def emulate_bounded_pull(cases, rng):
+    """The bounded variant (k_ring_nee in paper_0907_1720_gb300/csrc/lbhpde_ring_nee.cuh): the
+    interior nodes W..N-W-1 of each instance in thread-granular runs, the 2W outer nodes in a
+    shared block [instance][2W][B]; the first thread's right-moving inflow below node W reads
+    the left outer nodes, the last thread's left-moving inflow past node N-W-1 reads the right
+    outer nodes (registers by the jump on the remainder, neighbour reads by address)."""
+    runs, tb = [], 0
+    for il, N in enumerate(cases):
+        nthr = -(-(N - 2 * W) // K)
+        runs.append((tb, nthr, il))
+        tb += nthr
+    nt = (tb + 31) // 32 * 32
+    assert nt <= MAXT and len(cases) <= MAXI
+    s_true = [rng.standard_normal((B, N)) for N in cases]
+    OB = np.full((MAXI, 2 * W, B), np.nan)
+    v = np.full((nt, B, K), np.nan)
+    owner = [-1] * nt
+    for i, (tb, nthr, il) in enumerate(runs):
+        N = cases[i]
+        for o in range(2 * W):
+            x = o if o < W else N - 2 * W + o
+            OB[il, o, :] = s_true[i][:, x]
+        for t in range(nthr):
+            owner[tb + t] = i
+            for k in range(K):
+                x = W + t * K + k
+                v[tb + t, :, k] = s_true[i][:, x] if x < N - W else 0.0  # padding starts at zero
+    R = np.full(NE * MAXT, np.nan)
+    L = np.full(NE * MAXT, np.nan)
+    for tid in range(nt):
+        if owner[tid] < 0:
+            continue
+        for j in range(1, B):
+            e = VEL[j]
+            if e > 0:
+                for q in range(e):
+                    R[(eslot(e) + q) * MAXT + tid] = v[tid, j, K - e + q]
+            else:
+                for q in range(-e):
+                    L[(eslot(-e) + q) * MAXT + tid] = v[tid, j, q]
+    for tid in range(nt):
+        if owner[tid] < 0:
+            continue
+        i = owner[tid]
+        tb, nthr, il = runs[i]
+        t, N = tid - tb, cases[i]
+        xb = W + t * K
+        rem = N - W - xb
+        rt = tid + 1 if t + 1 < nthr else tid
+        w = v[tid].copy()
+        if rem < K:
+            for j in range(1, B):
+                a = -VEL[j]
+                for q in range(max(a, 0)):
+                    if rem + q < K:
+                        w[j, rem + q] = OB[il, W + q, j]
+        for j in range(1, B):
+            e = VEL[j]
+            for k in range(K):
+                if xb + k >= N - W:
+                    continue  # padding: not checked
+                if e > 0:
+                    if k >= e:
+                        nv = w[j, k - e]
+                    elif t > 0:
+                        nv = R[(eslot(e) + k) * MAXT + tid - 1]
+                    else:
+                        nv = OB[il, W + k - e, j]
+                else:
+                    a = -e
+                    if k + a < K:
+                        nv = w[j, k + a]
+                    elif k + a >= rem:
+                        q = min(max(k + a - rem, 0), W - 1)
+                        nv = OB[il, W + q, j]
+                    else:
+                        nv = L[(eslot(a) + k + a - K) * MAXT + rt]
+                x = xb + k
+                assert nv == s_true[i][j, x - e], (cases, i, x, j)
+
+
+def test_bounded_pull_matches_exact_shift():
+    rng = np.random.default_rng(601)
+    cases = [[2 * (W + 1)], [2 * (W + 4)], [601], [601] * 13, [20, 21, 22, 36, 37, 38, 100], [8196], [8195]]
+    cases += [[2 * W + 16 * r + q for q in range(1, 17)] for r in (0, 1)]
+    for _ in range(20):
+        sizes = [int(rng.integers(6, 1500)) for _ in range(int(rng.integers(1, 10)))]
+        while sum(-(-(n - 2 * W) // K) for n in sizes) > 512:
+            sizes.pop()
+        cases.append(sizes)
+    for c in cases:
+        emulate_bounded_pull(c, rng)
