@@ -85,7 +85,7 @@ int pack_ring_nee(int b, int dc, const std::vector<NeeMember> &m, PackedNee &out
     out = PackedNee{};
     const int W = lbk::wmax(b), K = kRingK;
     // one helper thread per (instance, outer node, population j >= 1) must exist in the CTA
-    const int hper = 2 * W * (b - 1);
+    const int hper = 2 * lbk::nedge(b);
     const int max_inst = std::min(lbk::kRingMaxInst, threads / hper);
     auto thr = [&](const NeeMember &x) { return (x.seg.N - 2 * W + K - 1) / K; };
     std::vector<int> order(m.size());
@@ -151,7 +151,7 @@ int launch_ring_nee_f32(int dc, const PackedNee &p, const lbk::RingNeeInst *inst
     if (p.ncta() == 0 || nsteps <= 0) return LBHPDE_OK;
     if (p.nthreads > p.stride || p.nthreads % 32 != 0) return LBHPDE_ERR_ARG;
     for (int c = 0; c < p.ncta(); ++c)  // every helper role has its thread
-        if ((p.first[c + 1] - p.first[c]) * 2 * lbk::wmax(5) * 4 > p.nthreads) return LBHPDE_ERR_ARG;
+        if ((p.first[c + 1] - p.first[c]) * lbk::nee_roles(5) > p.nthreads) return LBHPDE_ERR_ARG;
     if (p.stride == 128)
         return launch_ring_nee_d<128>(dc, p, insts_d, first_d, in, out, coefT, phib, stride, step0, nsteps, st);
     if (p.stride == 512)

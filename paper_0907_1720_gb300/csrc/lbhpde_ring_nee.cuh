@@ -23,14 +23,17 @@
 //     column of shared memory (a jump on the position that only reads registers), and writes the
 //     end's rebuilt outer nodes into the block of the next step's parity.  The next step's
 //     barrier orders that write before every read of it.
-// The terms that do not depend on the state, phi_b and f^eq_j(phi_b), are ready before the
-// rebuild needs them: during step s - 1 one helper thread per (instance, outer node, j >= 1)
-// evaluates f^eq_j(phi_b) for the rebuild of step s into a block of parity s & 1 (the barrier of
-// step s orders it before the rebuild; the block is rewritten only after the next barrier), from
-// a boundary value that it copied into shared memory by cp.async a step before (row step0 + s of
-// the member's block, phib + mi * stride), so neither the global load nor these polynomials lie
-// on the rebuild's path.  After the last step the first thread of each instance writes the outer
-// nodes back.
+// The interior reads only the inflow populations of the outer nodes (at the left end those with
+// e_j > 0 at nodes W - e_j .. W - 1, at the right end those with e_j < 0 at nodes N - W ..
+// N - W - 1 - e_j: 2 nedge(B) values an instance), so every step but the last rebuilds only those;
+// the last rebuilds every population and phi_b, the state written back.  The state-free term of
+// an inflow value, f^eq_j(phi_b), is ready before the rebuild needs it: during step s - 1 one
+// helper thread per (instance, inflow value) evaluates it for the rebuild of step s into a block
+// of parity s & 1 (the barrier of step s orders it before the rebuild; the block is rewritten only
+// after the next barrier), from a boundary value that it copied into shared memory by cp.async
+// a step before (row step0 + s of the member's block, phib + mi * stride), so neither the global
+// load nor that polynomial lies on the rebuild's path.  After the last step the first thread of
+// each instance writes the outer nodes back.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -52,18 +55,20 @@ struct RingNeeInst {
     int mi;             // batch member index: its boundary rows start at phib + mi * stride
     int depth;          // extrapolation depth
     int il;             // index among the CTA's instances (outer-node block)
-    int steps;          // steps this instance takes in the launch (<= nsteps)
+    int steps;          // steps this instance takes in the launch (capped at nsteps)
 };
 
 // Shared coefficient block of one bounded instance: P_j rows, f^eq_j rows (stride crow(D)),
 // 1 - omega, padded to a multiple of 4.
 __host__ __device__ constexpr int nee_cblock(int B, int D) { return 2 * (B - 1) * crow(D) + 4; }
-// Helper threads of a CTA: one per (instance, outer node, population j >= 1).
-__host__ __device__ constexpr int nee_helpers(int B) { return kRingMaxInst * 2 * wmax(B) * (B - 1); }
+// Helper threads of an instance: one per inflow value of its outer nodes (nedge(B) an end).
+__host__ __device__ constexpr int nee_roles(int B) { return 2 * nedge(B); }
+// Helper threads of a CTA at most.
+__host__ __device__ constexpr int nee_helpers(int B) { return kRingMaxInst * nee_roles(B); }
 // Shared elements (4-byte) of a k_ring_nee CTA of MAXT threads, without the coefficient blocks:
 // the exchange rows, the x_f column, the outer-node blocks and the boundary terms
-// [2 parities][kRingMaxInst][2W][B] (phi_b, f^eq_j(phi_b)), and the helpers' copied boundary
-// values [2 parities][helpers] doubles.
+// [2 parities][kRingMaxInst][2W][B] (f^eq_j(phi_b) of the inflow values), and the helpers' copied
+// boundary values [2 parities][helpers] doubles.
 __host__ __device__ constexpr int nee_fixed_elems(int B, int MAXT) {
     return 4 * nedge(B) * MAXT + B * MAXT + 2 * 2 * kRingMaxInst * 2 * wmax(B) * B + 2 * 2 * nee_helpers(B);
 }
@@ -106,7 +111,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     T *L = R + 2 * PS;                        // [2][NE][MAXT]
     T *X = L + 2 * PS;                        // [B][MAXT]: x_f values of the rebuilding threads
     T *OB = X + B * MAXT;                     // [2][kRingMaxInst][2W][B] outer nodes
-    T *GB = OB + 2 * OS;                      // [2][kRingMaxInst][2W][B] phi_b, f^eq_j(phi_b)
+    T *GB = OB + 2 * OS;                      // [2][kRingMaxInst][2W][B] f^eq_j(phi_b), inflow
     constexpr int NH = nee_helpers(B);
     double *PBs = reinterpret_cast<double *>(GB + 2 * OS);  // [2][NH] helpers' boundary values
     T *scoef = reinterpret_cast<T *>(PBs + 2 * NH);
@@ -132,17 +137,24 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
             OB[(I.il * 2 * W + o) * B + j] = st_in[I.off + (long long)j * I.ld + x];
         }
     }
-    // helper role: instance hi of the CTA, outer node ho (ho < W: left end), population hj;
-    // it copies the boundary value of rebuild r (row step0 + r) two rebuilds ahead
-    const int h_n = (last - first) * 2 * W * (B - 1);
+    // helper role: instance hi of the CTA, inflow value of outer node ho (ho < W: left end) and
+    // population hj (|e| = ha, the ha - 1 - hk-th node from the interior at the left end, the
+    // hk-th at the right); it copies the boundary value of rebuild r (row step0 + r) two
+    // rebuilds ahead
+    constexpr int HP = nee_roles(B);
+    const int h_n = (last - first) * HP;
     const bool helper = tid < h_n;
-    const int hi = tid / (2 * W * (B - 1)), ho = (tid / (B - 1)) % (2 * W), hj = 1 + tid % (B - 1);
+    const int hi = tid / HP, hr = tid % HP, hside = hr / NE, hrr = hr % NE;
+    int ha = 1;
+    while (ha < W && hrr >= eslot(ha + 1)) ++ha;
+    const int hk = hrr - eslot(ha);
+    const int ho = hside == 0 ? W - ha + hk : W + hk, hj = hside == 0 ? 2 * ha - 1 : 2 * ha;
     const double *hsrc = phib;
     int hsteps = 0, hq = 0, hD = 0;
     if (helper) {
         const RingNeeInst &H = insts[first + hi];
         hsrc = phib + (long long)H.mi * stride + step0 * (2 * W) + ho;
-        hsteps = H.steps;
+        hsteps = H.steps < nsteps ? H.steps : nsteps;
         hD = DC > 0 ? DC : H.D;
         hq = H.scoef + (B - 1) * crow(hD) + (hj - 1) * crow(hD);
         if (hsteps > 0) cp_async8(PBs + tid, hsrc);
@@ -156,7 +168,6 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
         const T pb = (T)PBs[(r & 1) * NH + tid];
         T *dst = hdst + (r & 1) * OS;
         dst[hj] = nee_row<T, DC>(scoef + hq, hD, pb);
-        if (hj == 1) dst[0] = pb;
         if (r + 2 < hsteps) cp_async8(PBs + (r & 1) * NH + tid, hsrc + (long long)(r + 2) * (2 * W));
     };
     int me = -1;
@@ -186,7 +197,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     const int cs = crow(D);
     const T *Q = sc + (B - 1) * cs;  // f^eq_j rows
     const T omw = has ? sc[2 * (B - 1) * cs] : T(0);
-    const int steps = has ? I.steps : 0;
+    const int steps = has ? (I.steps < nsteps ? I.steps : nsteps) : 0;
     T *const Rme = R + tid;
     T *const Lme = L + tid;
     T *const Xme = X + tid;
@@ -197,6 +208,62 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     const int fL = has ? I.depth - 1 : -K, fR = has ? N - 2 * W - I.depth : -K;
     const int side_mask = (fL >= t * K && fL < t * K + K ? 1 : 0) | (fR >= t * K && fR < t * K + K ? 2 : 0);
 
+    // x_f's phi and s_j into this thread's column of X (a jump on its position pf)
+    auto extract = [&](int pf) {
+        auto get = [&](auto pc) {
+            constexpr int Pv = decltype(pc)::value;
+            Xme[0] = phi[Pv];
+#pragma unroll
+            for (int j = 1; j < B; ++j) Xme[j * MAXT] = v[j][Pv];
+        };
+        switch (pf) {
+#define LBK_NEE_XF(Pv)                          \
+    case Pv:                                    \
+        get(std::integral_constant<int, Pv>{}); \
+        break;
+            LBK_NEE_XF(0) LBK_NEE_XF(1) LBK_NEE_XF(2) LBK_NEE_XF(3) LBK_NEE_XF(4) LBK_NEE_XF(5)
+            LBK_NEE_XF(6) LBK_NEE_XF(7) LBK_NEE_XF(8) LBK_NEE_XF(9) LBK_NEE_XF(10) LBK_NEE_XF(11)
+            LBK_NEE_XF(12) LBK_NEE_XF(13) LBK_NEE_XF(14) LBK_NEE_XF(15)
+#undef LBK_NEE_XF
+            default:
+                break;
+        }
+    };
+    // the inflow values of one end after step s (of parity P) into the block of parity P ^ 1
+    auto rebuild_inflow = [&](int P, int pf, auto sidec) {
+        constexpr int side = decltype(sidec)::value;
+        extract(pf);
+        const T phf = Xme[0];
+        const int blk = (OBi - OB) + side * W * B;  // this end's outer nodes in a block
+        T *const nob = OB + (P ^ 1) * OS + blk;
+        const T *const g = GB + P * OS + blk;  // f^eq_j(phi_b), from the helpers
+#pragma unroll
+        for (int a = 1; a <= W; ++a) {
+            const int j = side == 0 ? 2 * a - 1 : 2 * a;
+            const T fn = Xme[j * MAXT] - nee_row<T, DC>(Q + (j - 1) * cs, D, phf);
+#pragma unroll
+            for (int k = 0; k < a; ++k) {
+                const int o = side == 0 ? W - a + k : k;
+                nob[o * B + j] = g[o * B + j] + fn;
+            }
+        }
+    };
+    // every population and phi_b of one end after the last step (the state written back), into
+    // the block of parity steps & 1
+    auto rebuild_all = [&](int pf, int side) {
+        extract(pf);
+        const T phf = Xme[0];
+        T *const nob = OB + (steps & 1) * OS + (OBi - OB) + side * W * B;
+        const double *row = phib + (long long)I.mi * stride + (step0 + steps - 1) * (2 * W) + side * W;
+        for (int x = 0; x < W; ++x) {
+            const T pb = (T)row[x];
+            for (int j = 1; j < B; ++j) {
+                const T *q = Q + (j - 1) * cs;
+                nob[x * B + j] = nee_row<T, DC>(q, D, pb) + (Xme[j * MAXT] - nee_row<T, DC>(q, D, phf));
+            }
+            nob[x * B] = pb;
+        }
+    };
     auto step = [&](auto parc, int s) {
         constexpr int P = decltype(parc)::value;
         const bool live = s < steps;
@@ -294,51 +361,24 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
 #pragma unroll
         for (int k = 0; k < K; ++k) phi[k] += d[k];
         ring_relax<T, B, K, DC, RCH, 0, K>(sc, cs, D, omw, phi, v);
-        // the rebuild: x_f's phi and s_j through this thread's column of X, then the outer nodes
-        // of the next step
-        auto rebuild = [&](int pf, int side) {
-            auto get = [&](auto pc) {
-                constexpr int Pv = decltype(pc)::value;
-                Xme[0] = phi[Pv];
-#pragma unroll
-                for (int j = 1; j < B; ++j) Xme[j * MAXT] = v[j][Pv];
-            };
-            switch (pf) {
-#define LBK_NEE_XF(Pv)                          \
-    case Pv:                                    \
-        get(std::integral_constant<int, Pv>{}); \
-        break;
-                LBK_NEE_XF(0) LBK_NEE_XF(1) LBK_NEE_XF(2) LBK_NEE_XF(3) LBK_NEE_XF(4) LBK_NEE_XF(5)
-                LBK_NEE_XF(6) LBK_NEE_XF(7) LBK_NEE_XF(8) LBK_NEE_XF(9) LBK_NEE_XF(10) LBK_NEE_XF(11)
-                LBK_NEE_XF(12) LBK_NEE_XF(13) LBK_NEE_XF(14) LBK_NEE_XF(15)
-#undef LBK_NEE_XF
-                default:
-                    break;
-            }
-            const T phf = Xme[0];
-            const int blk = (OBi - OB) + side * W * B;  // this end's outer nodes in a block
-            T *const nob = OB + (P ^ 1) * OS + blk;
-            const T *const g = GB + P * OS + blk;  // phi_b, f^eq_j(phi_b) of this rebuild
-#pragma unroll
-            for (int j = 1; j < B; ++j) {
-                const T fn = Xme[j * MAXT] - nee_row<T, DC>(Q + (j - 1) * cs, D, phf);
-#pragma unroll
-                for (int x = 0; x < W; ++x) nob[x * B + j] = g[x * B + j] + fn;
-            }
-#pragma unroll
-            for (int x = 0; x < W; ++x) nob[x * B] = g[x * B];
-        };
-        if (side_mask & 1) rebuild(fL - t * K, 0);
-        if (side_mask & 2) rebuild(fR - t * K, 1);
+        // the rebuild of the inflow values (population j with |e_j| = a at its a nodes next to
+        // the interior) from x_f's phi and s_j, which pass through this thread's column of X
+        if (s + 1 < steps) {
+            if (side_mask & 1) rebuild_inflow(P, fL - t * K, std::integral_constant<int, 0>{});
+            if (side_mask & 2) rebuild_inflow(P, fR - t * K, std::integral_constant<int, 1>{});
+        }
     };
     for (int s = 0; s < nsteps; s += 2) {
         step(std::integral_constant<int, 0>{}, s);
         if (s + 1 < nsteps) step(std::integral_constant<int, 1>{}, s + 1);
     }
-    __syncthreads();  // the last rebuild's outer nodes are in the block of parity nsteps & 1
+    // (parity steps & 1 was last read in step steps - 2, before the barrier of step steps - 1)
+    if (steps > 0 && (side_mask & 1)) rebuild_all(fL - t * K, 0);
+    if (steps > 0 && (side_mask & 2)) rebuild_all(fR - t * K, 1);
+    __syncthreads();  // the outer nodes after the last step are in the block of parity steps & 1
     if (has) I = insts[me];
     if (has && t == 0) {
-        const T *ob = OBi + (nsteps & 1) * OS;
+        const T *ob = OBi + (steps & 1) * OS;
         for (int o = 0; o < 2 * W; ++o) {
             const long long x = o < W ? o : N - 2 * W + o;
 #pragma unroll

@@ -213,7 +213,9 @@ def emulate_bounded_pull(cases, rng):
     interior nodes W..N-W-1 of each instance in thread-granular runs, the 2W outer nodes in a
     shared block [instance][2W][B]; the first thread's right-moving inflow below node W reads
     the left outer nodes, the last thread's left-moving inflow past node N-W-1 reads the right
-    outer nodes (registers by the jump on the remainder, neighbour reads by address)."""
+    outer nodes (registers by the jump on the remainder, neighbour reads by address).  Only the
+    inflow values of the outer nodes (e_j > 0 at the left end, e_j < 0 at the right, within |e_j|
+    of the interior) hold data; the others are NaN and must never reach a real node."""
     runs, tb = [], 0
     for il, N in enumerate(cases):
         nthr = -(-(N - 2 * W) // K)
@@ -230,6 +232,12 @@ def emulate_bounded_pull(cases, rng):
         for o in range(2 * W):
             x = o if o < W else N - 2 * W + o
             OB[il, o, :] = s_true[i][:, x]
+            # only the inflow values are rebuilt between steps: the rest must never be read
+            for j in range(1, B):
+                e = VEL[j]
+                inflow = (e > 0 and o >= W - e) if o < W else (e < 0 and o - W < -e)
+                if not inflow:
+                    OB[il, o, j] = np.nan
         for t in range(nthr):
             owner[tb + t] = i
             for k in range(K):
