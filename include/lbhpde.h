@@ -348,6 +348,18 @@ int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t device_byte
  * (invalid request), LBHPDE_ERR_OOM (larger than the whole arena), LBHPDE_ERR_CUDA (the server
  * has failed). */
 int lbhpde_submit(lbhpde_server_t s, const lbhpde_request *req, uint64_t *id);
+/* As lbhpde_submit for a bounded request (the non-equilibrium extrapolation boundary of Sec. IV,
+ * as for lbhpde_create).  boundary: LBHPDE_NEE or LBHPDE_NEE_DEPTH(d), N >= 2 (W + depth).
+ * phib: [nsteps][2W] host doubles, W = max|e_j|, row n holding phi_b at time (n + 1) dt at nodes
+ * 0..W-1 followed by nodes N-W..N-1 (the layout of lbhpde_step_nee); copied by the call (may
+ * be NULL when nsteps = 0).  The request stays resident in one CTA of the bounded kernel, whose
+ * arithmetic is that of lbhpde_step_nee on a single instance with LBHPDE_KERNEL_ONCHIP at 4 nodes
+ * a thread, so its result is the same alone and in the mix.
+ * Errors: LBHPDE_ERR_ARG (boundary LBHPDE_PERIODIC or malformed, N too small, phib NULL with
+ * nsteps > 0); LBHPDE_ERR_UNSUPPORTED for real-exponent models and for grids the bounded kernel
+ * does not hold (N > 2048, or no placement of both ends' extrapolation nodes in one warp). */
+int lbhpde_submit_nee(lbhpde_server_t s, const lbhpde_request *req, int boundary, const double *phib,
+                      uint64_t *id);
 /* Non-blocking.  LBHPDE_PENDING while the request is queued or running (info is filled);
  * otherwise its final status, phi copied to phi_out ([N] host doubles, may be NULL), and the
  * request released (a later poll returns LBHPDE_ERR_NOT_FOUND). */

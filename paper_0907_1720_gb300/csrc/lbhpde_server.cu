@@ -8,6 +8,10 @@
 // the next block boundary; each finished request is read back and released, freeing memory
 // for the queue.  Work per request is identical to a single-instance solve, so each result is
 // the same alone and in the mix.
+//
+// Bounded requests (the non-equilibrium extrapolation boundary of Sec. IV, submitted with their
+// boundary values for every step) stay resident one CTA each on the bounded kernel; a step
+// block gathers the boundary rows its requests need into one table per lattice and class.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -102,6 +106,8 @@ struct Req {
     long long ld = 0, off[2] = {0, 0};  // element offsets of the two state buffers
     int cur = 0;                     // buffer holding the state
     int slot = -1;                   // coefficient slot
+    int depth = 0;                   // bounded: extrapolation depth (0: periodic)
+    std::vector<double> phib;        // bounded: [nsteps][2W] boundary values
     Seg seg() const {
         Seg s{};
         s.off = off[cur];
@@ -112,6 +118,7 @@ struct Req {
         s.Dg = mi.nu_deg;
         s.nu = mi.nu;
         s.coef = slot * kCoefStride;
+        s.pad = depth;
         return s;
     }
 };
@@ -155,7 +162,8 @@ struct lbhpde_server_s {
     // per CTA size class, and the window launches, which follow each other) run on lanes of
     // their own, after the table uploads on `stream`, and join it before the block's one
     // synchronisation.
-    static constexpr int kLanes = 4 * 6;  // 4 per (lattice, class)
+    // (and one lane per lattice and polynomial class for the bounded requests)
+    static constexpr int kLanes = 4 * 6 + 4;  // 4 per (lattice, class), then the bounded lanes
     cudaStream_t lane[kLanes] = {};
     cudaEvent_t ev_up = nullptr, ev_done[kLanes] = {};
     cudaEvent_t ev_t0[2] = {}, ev_t1[2] = {};  // timing of the step blocks (by block parity)
@@ -169,6 +177,8 @@ struct lbhpde_server_s {
     double *coefD_d = nullptr;
     std::vector<int> free_slots;
     DevBuf<lbk::OnchipInst> insts_d;
+    DevBuf<lbk::BoundedInst> binsts_d;
+    DevBuf<double> phibt_d;
     DevBuf<int> first_d;
     DevBuf<Seg> segs_d;
     DevBuf<int2> blocks_d;
@@ -290,12 +300,78 @@ struct Planned {
     size_t ioff = 0, foff = 0;  // offsets of its tables in the block's device arrays
 };
 
+// One bounded launch of a step block: instances of one lattice and class for steps
+// [step0, step0 + nsteps) of the block, reading their boundary rows from the block's table of
+// that lattice and class (rows of instance mi at table + mi * stride).
+struct PlannedBnd {
+    int b, dc, lane, nthreads, nsteps;
+    long long step0, stride;
+    size_t smem;
+    std::vector<lbk::BoundedInst> insts;
+    size_t ioff = 0, toff = 0;  // offsets of its instances and of its table in the block's arrays
+};
+
 // A planned step block: its launches and, per request, the steps it advances.
 struct Block {
     long long id = -1;
     std::vector<Planned> plan;
+    std::vector<PlannedBnd> bplan;
+    std::vector<double> phibt;  // the bounded requests' boundary rows, one table per lattice and class
     std::vector<std::pair<Req *, int>> members;
 };
+
+// The bounded requests of one lattice and polynomial class in a step block: each advances by
+// up to S->block steps on the bounded kernel (one CTA an instance, in place).  Their boundary
+// rows for the block go into a table of their own; the launches cover the block in spans that
+// end where a request's steps end or the kernel's staged-row limit falls, so that every launch
+// has one step count.
+int plan_bounded(lbhpde_server_s *S, Block &blk, int b, int kind, int maxD, std::vector<Req *> &bnd) {
+    const int W = (b - 1) / 2, K = lbh::kBoundedK;
+    const long long stride = (long long)S->block * 2 * W;
+    const size_t toff = blk.phibt.size();
+    blk.phibt.resize(toff + bnd.size() * (size_t)stride, 0.0);
+    std::vector<int> st(bnd.size());
+    for (size_t q = 0; q < bnd.size(); ++q) {
+        Req *r = bnd[q];
+        st[q] = (int)std::min<long>(S->block, r->nsteps - r->done);
+        std::memcpy(blk.phibt.data() + toff + q * stride, r->phib.data() + (size_t)r->done * 2 * W,
+                    sizeof(double) * (size_t)st[q] * 2 * W);
+        blk.members.emplace_back(r, st[q]);
+    }
+    const int dc = kind == 1 ? 0 : lbh::onchip_dc(b, maxD);
+    const int D = dc > 0 ? dc : maxD;
+    const int span = lbh::bounded_launch_steps(b, S->esz);
+    for (int c0 = 0;;) {
+        int c1 = c0 + span;
+        PlannedBnd pl{b, dc, 4 * kClasses + 2 * (b == 7) + kind, 32, 0, c0, stride, 0, {}};
+        for (size_t q = 0; q < bnd.size(); ++q)
+            if (st[q] > c0) c1 = std::min(c1, st[q]);
+        for (size_t q = 0; q < bnd.size(); ++q) {
+            if (st[q] <= c0) continue;
+            const Seg sg = bnd[q]->seg();
+            lbk::BoundedInst I{};
+            I.off = sg.off;
+            I.ld = sg.ld;
+            I.mi = (int)q;
+            I.N = sg.N;
+            I.D = sg.D;
+            I.gcoef = sg.coef;
+            I.depth = sg.pad;
+            I.shift = lbh::bounded_shift(b, sg.N, sg.pad);
+            I.nthr = (sg.N + I.shift + K - 1) / K;
+            pl.nthreads = std::max(pl.nthreads, (I.nthr + 31) / 32 * 32);
+            pl.insts.push_back(I);
+        }
+        if (pl.insts.empty()) break;
+        pl.nsteps = c1 - c0;
+        pl.smem = lbh::bounded_smem(b, S->esz, pl.nthreads, D, pl.nsteps);
+        pl.toff = toff;
+        blk.bplan.push_back(std::move(pl));
+        c0 = c1;
+    }
+    for (Req *r : bnd) r->done += std::min<long>(S->block, r->nsteps - r->done);
+    return LBHPDE_OK;
+}
 
 // Plan the next step block on the host: every active request advances by up to S->block steps
 // (resident instances once per lattice and class, windows in chunks of tblk steps).  Requests'
@@ -323,14 +399,20 @@ int plan_block(lbhpde_server_s *S, Block &blk) {
         // 0.20 s p99 latency at 500/s)
         const int Kr = K;
         const int capr = lbh::onchip_maxt(S->esz, b, Kr) * Kr;
-        std::vector<Req *> ring, halo;
-        int maxD = 0;
+        std::vector<Req *> ring, halo, bnd;
+        int maxD = 0, maxDb = 0;
         for (Req *r : S->active)
             if (r->mi.b == b && r->done < r->nsteps &&
                 (r->mi.nu_rows > 1 ? 2 : (r->mi.D > dcmax ? 1 : 0)) == kind) {
+                if (r->depth > 0) {
+                    bnd.push_back(r);
+                    maxDb = std::max(maxDb, r->mi.D);
+                    continue;
+                }
                 (r->N <= capr ? ring : halo).push_back(r);
                 maxD = std::max(maxD, r->mi.D);
             }
+        if (!bnd.empty()) SRC(plan_bounded(S, blk, b, kind, maxDb, bnd));
         if (ring.empty() && halo.empty()) continue;
         const int dc = kind == 2 ? -1 : lbh::onchip_dc(b, maxD);
         if (!ring.empty()) {
@@ -377,7 +459,7 @@ int plan_block(lbhpde_server_s *S, Block &blk) {
             }
         }
     }
-    if (plan.empty()) {
+    if (plan.empty() && blk.bplan.empty()) {
         blk.id = -1;
         return LBHPDE_OK;
     }
@@ -404,12 +486,28 @@ int launch_block(lbhpde_server_s *S, Block &blk) {
         insts.insert(insts.end(), pl.p.insts.begin(), pl.p.insts.end());
         first.insert(first.end(), pl.p.first.begin(), pl.p.first.end());
     }
+    std::vector<lbk::BoundedInst> binsts;
+    for (PlannedBnd &pl : blk.bplan) {
+        pl.ioff = binsts.size();
+        binsts.insert(binsts.end(), pl.insts.begin(), pl.insts.end());
+    }
     SRC(S->insts_d.ensure(insts.size()));
     SRC(S->first_d.ensure(first.size()));
+    SRC(S->binsts_d.ensure(binsts.size()));
+    SRC(S->phibt_d.ensure(blk.phibt.size()));
     SCK(cudaEventRecord(S->ev_t0[par], S->stream));
-    SCK(cudaMemcpyAsync(S->insts_d.p, insts.data(), sizeof(lbk::OnchipInst) * insts.size(), cudaMemcpyHostToDevice,
-                        S->stream));
-    SCK(cudaMemcpyAsync(S->first_d.p, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice, S->stream));
+    if (!insts.empty()) {
+        SCK(cudaMemcpyAsync(S->insts_d.p, insts.data(), sizeof(lbk::OnchipInst) * insts.size(),
+                            cudaMemcpyHostToDevice, S->stream));
+        SCK(cudaMemcpyAsync(S->first_d.p, first.data(), sizeof(int) * first.size(), cudaMemcpyHostToDevice,
+                            S->stream));
+    }
+    if (!binsts.empty()) {
+        SCK(cudaMemcpyAsync(S->binsts_d.p, binsts.data(), sizeof(lbk::BoundedInst) * binsts.size(),
+                            cudaMemcpyHostToDevice, S->stream));
+        SCK(cudaMemcpyAsync(S->phibt_d.p, blk.phibt.data(), sizeof(double) * blk.phibt.size(),
+                            cudaMemcpyHostToDevice, S->stream));
+    }
     // the lanes start after the uploads; different lanes touch disjoint requests
     SCK(cudaEventRecord(S->ev_up, S->stream));
     bool used[lbhpde_server_s::kLanes] = {};
@@ -419,6 +517,15 @@ int launch_block(lbhpde_server_s *S, Block &blk) {
         SRC(lbh::launch_onchip(pl.b, S->esz, pl.K, pl.dc, pl.halo, pl.p, S->insts_d.p + pl.ioff,
                                S->first_d.p + pl.foff, S->arena_d, S->arena_d, S->coefT_d, pl.nsteps,
                                S->lane[pl.lane]));
+        ++S->launches;
+    }
+    // bounded launches of one lattice and class follow each other on their lane (in place)
+    for (const PlannedBnd &pl : blk.bplan) {
+        if (!used[pl.lane]) SCK(cudaStreamWaitEvent(S->lane[pl.lane], S->ev_up, 0));
+        used[pl.lane] = true;
+        SRC(lbh::launch_bounded(pl.b, S->esz, pl.dc, (int)pl.insts.size(), pl.nthreads, pl.smem,
+                                S->binsts_d.p + pl.ioff, S->arena_d, S->arena_d, S->coefT_d, S->phibt_d.p + pl.toff,
+                                pl.stride, pl.step0, pl.nsteps, S->lane[pl.lane]));
         ++S->launches;
     }
     for (int i = 0; i < lbhpde_server_s::kLanes; ++i)
@@ -655,7 +762,8 @@ extern "C" int lbhpde_server_create(lbhpde_server_t *out, int precision, size_t 
     return LBHPDE_OK;
 }
 
-extern "C" int lbhpde_submit(lbhpde_server_t S, const lbhpde_request *q, uint64_t *id) {
+static int submit_common(lbhpde_server_t S, const lbhpde_request *q, int boundary, const double *phib,
+                         uint64_t *id) {
     if (!S || !q || !id || !q->phi0 || q->nsteps < 0) return LBHPDE_ERR_ARG;
     auto *r = new (std::nothrow) Req();
     if (!r) return LBHPDE_ERR_OOM;
@@ -664,10 +772,23 @@ extern "C" int lbhpde_submit(lbhpde_server_t S, const lbhpde_request *q, uint64_
     if (rc == LBHPDE_OK && (q->N < 2 * W || q->N > (1L << 26))) rc = LBHPDE_ERR_ARG;
     // real-exponent models take the on-chip variant that evaluates four or more nodes a thread
     if (rc == LBHPDE_OK && r->mi.nu_rows > 1 && lbh::default_K(S->esz, r->mi.b) < 4) rc = LBHPDE_ERR_UNSUPPORTED;
+    if (rc == LBHPDE_OK && boundary != LBHPDE_PERIODIC) {
+        // LBHPDE_NEE with the depth in the bits above the kind (0: depth 2)
+        const int kind = boundary & 0xff, dcode = boundary >> 8;
+        r->depth = dcode == 0 ? 2 : dcode;
+        if (boundary < 0 || kind != LBHPDE_NEE || r->depth > 4096 || q->N < 2L * (W + r->depth) ||
+            (q->nsteps > 0 && !phib))
+            rc = LBHPDE_ERR_ARG;
+        // the bounded kernel: polynomial models of up to kBoundedK * kBoundedMaxT nodes
+        else if (r->mi.nu_rows > 1 || q->N > (long)lbh::kBoundedK * lbh::kBoundedMaxT ||
+                 lbh::bounded_shift(r->mi.b, (int)q->N, r->depth) < 0)
+            rc = LBHPDE_ERR_UNSUPPORTED;
+    }
     if (rc != LBHPDE_OK) {
         delete r;
         return rc;
     }
+    if (r->depth > 0) r->phib.assign(phib, phib + (size_t)q->nsteps * 2 * W);
     r->N = q->N;
     r->ld = (q->N + 31) / 32 * 32;
     r->nsteps = q->nsteps;
@@ -689,6 +810,16 @@ extern "C" int lbhpde_submit(lbhpde_server_t S, const lbhpde_request *q, uint64_
     *id = r->id;
     S->cv_work.notify_one();
     return LBHPDE_OK;
+}
+
+extern "C" int lbhpde_submit(lbhpde_server_t S, const lbhpde_request *q, uint64_t *id) {
+    return submit_common(S, q, LBHPDE_PERIODIC, nullptr, id);
+}
+
+extern "C" int lbhpde_submit_nee(lbhpde_server_t S, const lbhpde_request *q, int boundary, const double *phib,
+                                 uint64_t *id) {
+    if (boundary == LBHPDE_PERIODIC) return LBHPDE_ERR_ARG;
+    return submit_common(S, q, boundary, phib, id);
 }
 
 static int take_result(lbhpde_server_t S, std::unordered_map<uint64_t, Req *>::iterator it, double *phi_out,
@@ -761,6 +892,8 @@ extern "C" int lbhpde_server_destroy(lbhpde_server_t S) {
     for (auto &kv : S->reqs) delete kv.second;
     S->reqs.clear();
     S->insts_d.release();
+    S->binsts_d.release();
+    S->phibt_d.release();
     S->first_d.release();
     S->segs_d.release();
     S->blocks_d.release();

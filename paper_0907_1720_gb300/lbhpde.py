@@ -144,6 +144,7 @@ _SIGS = {
     "lbhpde_phi_diagnostics_noalloc": (_I, [_V, _L, _V, _P(lbhpde_diag), _V]),
     "lbhpde_server_create": (_I, [_P(_V), _I, _S, _I, _I, _I]),
     "lbhpde_submit": (_I, [_V, _P(lbhpde_request), _P(ctypes.c_uint64)]),
+    "lbhpde_submit_nee": (_I, [_V, _P(lbhpde_request), _I, _V, _P(ctypes.c_uint64)]),
     "lbhpde_poll": (_I, [_V, ctypes.c_uint64, _V, _P(lbhpde_result)]),
     "lbhpde_wait": (_I, [_V, ctypes.c_uint64, _D, _V, _P(lbhpde_result)]),
     "lbhpde_server_stats": (_I, [_V, _P(lbhpde_server_info)]),
@@ -545,7 +546,9 @@ class Server:
         self.h = h
         self.sizes = {}
 
-    def submit(self, eq, N, dx, dt, tau, nsteps, phi0, scheme=1) -> int:
+    def submit(self, eq, N, dx, dt, tau, nsteps, phi0, scheme=1, boundary=PERIODIC, phib=None) -> int:
+        """A request; a bounded one (boundary NEE or nee_depth(d)) with its [nsteps][2W] boundary
+        values phib (host, copied)."""
         q = lbhpde_request()
         q.m = eq.m
         pis = _pis(eq.pi, getattr(eq, "nu", 0.0), getattr(eq, "pi_nu", None))
@@ -558,12 +561,20 @@ class Server:
             int(eq.lattice), int(scheme), int(nsteps)
         q.phi0 = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         rid = ctypes.c_uint64()
-        _check(lib().lbhpde_submit(self.h, ctypes.byref(q), ctypes.byref(rid)), "lbhpde_submit")
+        if boundary == PERIODIC:
+            _check(lib().lbhpde_submit(self.h, ctypes.byref(q), ctypes.byref(rid)), "lbhpde_submit")
+        else:
+            pb = None if phib is None else np.ascontiguousarray(np.asarray(phib, dtype=np.float64))
+            ptr = None if pb is None else pb.ctypes.data_as(ctypes.c_void_p)
+            _check(lib().lbhpde_submit_nee(self.h, ctypes.byref(q), int(boundary), ptr, ctypes.byref(rid)),
+                   "lbhpde_submit_nee")
         self.sizes[rid.value] = int(N)
         return rid.value
 
-    def submit_problem(self, p, nsteps=None) -> int:
-        return self.submit(p.eq, p.N, p.dx, p.dt, p.tau, p.nsteps if nsteps is None else nsteps, p.phi0, p.scheme)
+    def submit_problem(self, p, nsteps=None, phib=None) -> int:
+        """p's request; a bounded p needs its [nsteps][2W] boundary values phib."""
+        return self.submit(p.eq, p.N, p.dx, p.dt, p.tau, p.nsteps if nsteps is None else nsteps, p.phi0, p.scheme,
+                           boundary=_boundary_code(p), phib=phib)
 
     def poll(self, rid):
         """(status, phi or None, info dict); phi only once finished."""

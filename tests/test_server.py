@@ -5,6 +5,7 @@ blocked windows) are submitted while others are running; every result must be id
 bit for bit, to the same request solved alone with the single-instance API, and agree with
 the oracle.  Also: bounded waits, unknown ids, requests larger than the arena, bad arguments.
 """
+import copy
 import time
 
 import numpy as np
@@ -99,6 +100,112 @@ def test_results_identical_alone_and_in_the_mix(L, precision):
         want = oracle.run_problem(p)
         got = results[rid][1]
         assert np.abs(got - want).max() <= tol * np.abs(want).max()
+
+
+def _bounded_requests(n, seed):
+    """Bounded requests (Sec. IV examples on D1Q5 and D1Q7, depths 1-3, grids of 601-2001
+    nodes) with random step counts, each with its boundary values from the exact solution."""
+    menu = [("4.1", 1e-3, 1.989, 1 | oracle.NO_AUX_CORRECTION, 2), ("4.2", 1e-2, 4.569, 1 | oracle.NO_AUX_CORRECTION, 2),
+            ("4.5", 1e-4, 2.02, 1, 1), ("4.6", 1e-2, 4.04, 2, 3), ("4.7", 1e-3, 3.31, 1, 2)]
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        ex, dt, tau, scheme, depth = menu[i % len(menu)]
+        steps = int(rng.integers(0, 400))
+        p = W.bounded_config(ex, dt, tau, steps * dt, scheme=scheme)
+        p.meta["depth"] = depth
+        out.append(p)
+    return out
+
+
+def _bounded_alone(L, p, precision, phib):
+    """The same bounded request solved alone on the one-instance-per-CTA bounded kernel."""
+    s = L.Solver.for_problem(p, precision=precision)
+    s.set_kernel(L.KERNEL_ONCHIP, 4)
+    s.set_phi(p.phi0)
+    if p.nsteps:
+        s.step_nee(p.nsteps, phib)
+    out = s.read_phi(check=False)
+    s.close()
+    return out
+
+
+def _wd(p):
+    """max|e_j| of p's lattice (the columns of its boundary rows are 2 max|e_j|)."""
+    M = oracle.Model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, lattice=p.eq.lattice, scheme=p.scheme)
+    return (M.b - 1) // 2
+
+
+def _oracle_nee(p):
+    M = oracle.Model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, lattice=p.eq.lattice, scheme=p.scheme)
+    f = M.init(p.phi0)
+    if p.nsteps:
+        M.step_nee(f, W.boundary_values(p, (M.b - 1) // 2, 0, p.nsteps), p.meta["depth"])
+    return M.phi(f)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_bounded_requests_in_the_mix(L, precision):
+    """Bounded requests among periodic ones, over several step blocks whose launches end where a
+    request's steps end: each result equals, bit for bit, the request solved alone on the bounded
+    kernel, and agrees with the oracle's bounded step."""
+    P = L.FP32_DEV if precision == "fp32" else L.FP64
+    srv = L.Server(precision=P, device_bytes=64 << 20, max_active=64, steps_per_block=128)
+    bnd = _bounded_requests(10, seed=3)
+    per = mixed_requests(10, seed=4)
+    ids = []
+    for i in range(10):
+        p = bnd[i]
+        Wd = _wd(p)
+        ids.append((srv.submit_problem(p, phib=W.boundary_values(p, Wd, 0, p.nsteps)), p, True))
+        ids.append((srv.submit_problem(per[i]), per[i], False))
+    results = {rid: srv.wait(rid, timeout=120) for rid, _, _ in ids}
+    st = srv.stats()
+    srv.close()
+    assert st["error"] == 0 and st["completed"] == len(ids)
+    for rid, p, is_bnd in ids:
+        rc, phi, info = results[rid]
+        assert rc == L.OK and info["steps_done"] == p.nsteps, (p.N, rc)
+        if is_bnd:
+            Wd = _wd(p)
+            want = _bounded_alone(L, p, P, W.boundary_values(p, Wd, 0, p.nsteps))
+        else:
+            want = alone(L, p, P)
+        assert np.array_equal(phi, want), (p.eq.name, p.N, p.nsteps, is_bnd)
+    for rid, p, is_bnd in ids[::3]:
+        if not is_bnd or p.nsteps == 0:
+            continue
+        want = _oracle_nee(p)
+        got = results[rid][1]
+        if P == L.FP64:
+            tol = 1e-12
+        else:
+            # one FP32 rounding of phi and of the stored deviations a step, added like a random
+            # walk, times the growth of a perturbation of phi0 that the oracle measures on p
+            q = copy.copy(p)
+            q.phi0 = p.phi0 * (1 + 1e-6 * np.random.default_rng(0).standard_normal(p.N))
+            growth = np.abs(_oracle_nee(q) - want).max() / np.abs(want).max() / 1e-6
+            tol = (16 * 2.0 ** -24 * np.sqrt(p.nsteps) + 4 * 2.0 ** -24) * max(1.0, growth)
+        assert np.abs(got - want).max() <= tol * np.abs(want).max(), (p.meta, p.nsteps)
+
+
+def test_bounded_request_arguments(L):
+    srv = L.Server(precision=L.FP32_DEV, device_bytes=8 << 20, max_active=4)
+    p = W.bounded_config("4.1", 1e-3, 1.989, 0.01, scheme=1 | oracle.NO_AUX_CORRECTION)
+    with pytest.raises(L.LbhpdeError) as ei:  # boundary values missing
+        srv.submit(p.eq, p.N, p.dx, p.dt, p.tau, p.nsteps, p.phi0, p.scheme, boundary=L.NEE, phib=None)
+    assert ei.value.code == L.ERR_ARG
+    with pytest.raises(L.LbhpdeError) as ei:  # N < 2 (W + depth)
+        srv.submit(p.eq, 7, p.dx, p.dt, p.tau, 1, p.phi0[:7], p.scheme, boundary=L.NEE, phib=np.zeros((1, 4)))
+    assert ei.value.code == L.ERR_ARG
+    big = W.bounded_config("4.1", 1e-3, 1.989, 0.001, scheme=1, dx=0.02)  # 3001 nodes: over one CTA
+    with pytest.raises(L.LbhpdeError) as ei:
+        srv.submit_problem(big, phib=W.boundary_values(big, 2, 0, big.nsteps))
+    assert ei.value.code == L.ERR_UNSUPPORTED
+    rid = srv.submit_problem(p, phib=W.boundary_values(p, 2, 0, p.nsteps))
+    rc, phi, info = srv.wait(rid, timeout=60)
+    assert rc == L.OK and info["steps_done"] == p.nsteps
+    srv.close()
 
 
 def test_admission_is_bounded_by_memory(L):
