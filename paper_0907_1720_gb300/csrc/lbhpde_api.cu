@@ -936,8 +936,10 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
     g.sblocks_h.clear();
     const int K = lbh::kBoundedK;
     int maxthr = 0, maxD = 0, maxDn = 0;
+    bool real = false;
     // FP32 D1Q5 polynomial members take the 16-node resident kernel (unless a kernel or 4 nodes
-    // a thread was asked for), the others one CTA each or the streaming step
+    // a thread was asked for), the others one CTA each (real-exponent members on its variant
+    // with the generalised f^eq) or the streaming step
     std::vector<lbh::NeeMember> nee;
     const bool nee_auto = bt->kernel == LBHPDE_KERNEL_AUTO || (bt->kernel == LBHPDE_KERNEL_ONCHIP && bt->K_req != K);
     for (int i : g.members) {
@@ -947,9 +949,8 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
             maxDn = std::max(maxDn, sg.D);
             continue;
         }
-        const int shift = bt->N[i] <= (long long)K * lbh::kBoundedMaxT && sg.A == 0
-                              ? lbh::bounded_shift(g.b, sg.N, sg.pad)
-                              : -1;  // real-exponent members stream
+        const int shift =
+            bt->N[i] <= (long long)K * lbh::kBoundedMaxT ? lbh::bounded_shift(g.b, sg.N, sg.pad) : -1;
         if (bt->kernel != LBHPDE_KERNEL_STREAM && shift >= 0) {
             lbk::BoundedInst I{};
             I.off = sg.off;
@@ -961,6 +962,10 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
             I.depth = sg.pad;
             I.shift = shift;
             I.nthr = (sg.N + shift + K - 1) / K;
+            I.A = sg.A;
+            I.Dg = sg.Dg;
+            I.nu = sg.nu;
+            real = real || sg.A > 0;
             g.bnd_h.push_back(I);
             maxthr = std::max(maxthr, I.nthr);
             maxD = std::max(maxD, sg.D);
@@ -970,7 +975,7 @@ int plan_bounded(lbhpde_batch_s *bt, Group &g) {
         }
     }
     g.bnd_threads = (maxthr + 31) / 32 * 32;
-    g.bnd_dc = lbh::onchip_dc(g.b, maxD);
+    g.bnd_dc = real ? -1 : lbh::onchip_dc(g.b, maxD);
     g.bnd_D = g.bnd_dc > 0 ? g.bnd_dc : maxD;
     bt->dev_free(g.bnd);
     bt->dev_free(g.smembers);

@@ -45,6 +45,7 @@ template <typename T, int B>
 int launch_bounded_d(int dc, const BoundedArgs &a) {
     constexpr int DC = B == 5 ? 5 : 7;
     if (dc == DC) return launch_bounded_t<T, B, DC>(a);
+    if (dc < 0) return launch_bounded_t<T, B, -1>(a);  // real-exponent members
     return launch_bounded_t<T, B, 0>(a);
 }
 

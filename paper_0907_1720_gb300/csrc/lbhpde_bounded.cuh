@@ -26,6 +26,8 @@ struct BoundedInst {
     int shift;          // node x sits at position x + shift
     int nthr;           // threads that own positions: ceil((N + shift) / K)
     int pad;
+    int A, Dg;          // real-exponent models (variant DC < 0 only): f^eq_j and P_j =
+    double nu;          //   sum_{a<=A} (phi^nu)^a sum_{i<=Dg} c[a(Dg+1)+i] phi^i; A = 0: polynomial
 };
 
 // Horner evaluation of one 16-byte aligned coefficient row of degree DC (DC > 0) or D (DC == 0).
@@ -43,6 +45,16 @@ __device__ __forceinline__ T row_eval(const T *c, int D, T x) {
         for (int p = D - 1; p >= 0; --p) acc = fma_t(acc, x, c[p]);
         return acc;
     }
+}
+
+// f^eq_j or P_j at x: the row of degree DC or D, or (variant DC < 0, instances with A > 0) the
+// real-exponent form in x and w = x^nu.
+template <typename T, int DC>
+__device__ __forceinline__ T feq_eval(const T *c, int D, const BoundedInst &I, T x) {
+    if constexpr (DC < 0) {
+        if (I.A > 0) return gen_eval<T>(c, I.A, I.Dg, x, nu_pow<T>(x, I.nu));
+    }
+    return row_eval<T, DC>(c, D, x);
 }
 
 // nsteps steps of every bounded instance, one instance per CTA, the state in registers for the
@@ -94,7 +106,7 @@ __global__ void __launch_bounds__(MAXT, 1)
         const T pbv = (T)pb[q];
         PB[q * B] = pbv;
 #pragma unroll
-        for (int j = 1; j < B; ++j) PB[q * B + j] = row_eval<T, DC>(Q + (j - 1) * cs, D, pbv);
+        for (int j = 1; j < B; ++j) PB[q * B + j] = feq_eval<T, DC>(Q + (j - 1) * cs, D, I, pbv);
     }
 
     const bool has = tid < I.nthr;
@@ -164,12 +176,35 @@ __global__ void __launch_bounds__(MAXT, 1)
             }
 #pragma unroll
             for (int k = 0; k < K; ++k) phi[k] += d[k];
-            // relax: s'_j = (1 - omega) f_j + P_j(phi')
+            // relax: s'_j = (1 - omega) f_j + P_j(phi') (real exponents: w = phi^nu once per
+            // node, then the rows in phi and w)
+            T w[K];
+            bool relaxed = false;
+            if constexpr (DC < 0) {
+                if (I.A > 0) {
 #pragma unroll
-            for (int j = 1; j < B; ++j) {
+                    for (int k = 0; k < K; ++k) w[k] = nu_pow<T>(phi[k], I.nu);
+                    if constexpr (sizeof(T) == 4) relaxed = relax_rows_fixed<T, B, K>(I.A, I.Dg, P, cs, phi, w, v, omw);
+                }
+            }
+#pragma unroll
+            for (int j = 1; j < B && !relaxed; ++j) {
                 const T *c = P + (j - 1) * cs;
                 T acc[K];
-                if constexpr (DC > 0) {
+                if constexpr (DC < 0) {
+                    if (I.A > 0) {
+                        gen_evalK<T, K>(c, I.A, I.Dg, phi, w, acc);
+                    } else {
+                        const T cD = c[D];
+#pragma unroll
+                        for (int k = 0; k < K; ++k) acc[k] = cD;
+                        for (int p = D - 1; p >= 0; --p) {
+                            const T cp = c[p];
+#pragma unroll
+                            for (int k = 0; k < K; ++k) acc[k] = fma_t(acc[k], phi[k], cp);
+                        }
+                    }
+                } else if constexpr (DC > 0) {
                     T cr[crow(DC)];
                     load_row<T, crow(DC)>(c, cr);
 #pragma unroll
@@ -213,7 +248,7 @@ __global__ void __launch_bounds__(MAXT, 1)
             for (int k = 0; k < K; ++k)
                 if (has && x0 + k == kf) {
 #pragma unroll
-                    for (int j = 1; j < B; ++j) fneq[j] = v[j][k] - row_eval<T, DC>(Q + (j - 1) * cs, D, phi[k]);
+                    for (int j = 1; j < B; ++j) fneq[j] = v[j][k] - feq_eval<T, DC>(Q + (j - 1) * cs, D, I, phi[k]);
                 }
 #pragma unroll
             for (int j = 1; j < B; ++j) fneq[j] = __shfl_sync(0xffffffffu, fneq[j], side == 0 ? srcL : srcR);

@@ -111,6 +111,8 @@ int bounded_launch_steps(int b, size_t esz);
 // Smallest position shift that puts each end's outer nodes and extrapolation node in one warp of
 // the resident kernel (and keeps the instance within one CTA); -1 if there is none.
 int bounded_shift(int b, int N, int depth);
+// dc: the compiled degree (5 on D1Q5, 7 on D1Q7), 0 for a run-time degree, -1 for the variant
+// that also evaluates real-exponent instances (A > 0).
 int launch_bounded(int b, size_t esz, int dc, int ninst, int nthreads, size_t smem, const lbk::BoundedInst *insts_d,
                    const void *in, void *out, const void *coefT, const double *phib, long long stride,
                    long long step0, int nsteps, cudaStream_t st);

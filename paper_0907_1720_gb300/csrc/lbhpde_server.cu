@@ -162,8 +162,8 @@ struct lbhpde_server_s {
     // per CTA size class, and the window launches, which follow each other) run on lanes of
     // their own, after the table uploads on `stream`, and join it before the block's one
     // synchronisation.
-    // (and one lane per lattice and polynomial class for the bounded requests)
-    static constexpr int kLanes = 4 * 6 + 4;  // 4 per (lattice, class), then the bounded lanes
+    // (and one lane per lattice and class for the bounded requests)
+    static constexpr int kLanes = 4 * 6 + 6;  // 4 per (lattice, class), then the bounded lanes
     cudaStream_t lane[kLanes] = {};
     cudaEvent_t ev_up = nullptr, ev_done[kLanes] = {};
     cudaEvent_t ev_t0[2] = {}, ev_t1[2] = {};  // timing of the step blocks (by block parity)
@@ -338,12 +338,12 @@ int plan_bounded(lbhpde_server_s *S, Block &blk, int b, int kind, int maxD, std:
                     sizeof(double) * (size_t)st[q] * 2 * W);
         blk.members.emplace_back(r, st[q]);
     }
-    const int dc = kind == 1 ? 0 : lbh::onchip_dc(b, maxD);
+    const int dc = kind == 2 ? -1 : (kind == 1 ? 0 : lbh::onchip_dc(b, maxD));
     const int D = dc > 0 ? dc : maxD;
     const int span = lbh::bounded_launch_steps(b, S->esz);
     for (int c0 = 0;;) {
         int c1 = c0 + span;
-        PlannedBnd pl{b, dc, 4 * kClasses + 2 * (b == 7) + kind, 32, 0, c0, stride, 0, {}};
+        PlannedBnd pl{b, dc, 4 * kClasses + 3 * (b == 7) + kind, 32, 0, c0, stride, 0, {}};
         for (size_t q = 0; q < bnd.size(); ++q)
             if (st[q] > c0) c1 = std::min(c1, st[q]);
         for (size_t q = 0; q < bnd.size(); ++q) {
@@ -359,6 +359,9 @@ int plan_bounded(lbhpde_server_s *S, Block &blk, int b, int kind, int maxD, std:
             I.depth = sg.pad;
             I.shift = lbh::bounded_shift(b, sg.N, sg.pad);
             I.nthr = (sg.N + I.shift + K - 1) / K;
+            I.A = sg.A;
+            I.Dg = sg.Dg;
+            I.nu = sg.nu;
             pl.nthreads = std::max(pl.nthreads, (I.nthr + 31) / 32 * 32);
             pl.insts.push_back(I);
         }
@@ -779,8 +782,8 @@ static int submit_common(lbhpde_server_t S, const lbhpde_request *q, int boundar
         if (boundary < 0 || kind != LBHPDE_NEE || r->depth > 4096 || q->N < 2L * (W + r->depth) ||
             (q->nsteps > 0 && !phib))
             rc = LBHPDE_ERR_ARG;
-        // the bounded kernel: polynomial models of up to kBoundedK * kBoundedMaxT nodes
-        else if (r->mi.nu_rows > 1 || q->N > (long)lbh::kBoundedK * lbh::kBoundedMaxT ||
+        // the bounded kernel: instances of up to kBoundedK * kBoundedMaxT nodes
+        else if (q->N > (long)lbh::kBoundedK * lbh::kBoundedMaxT ||
                  lbh::bounded_shift(r->mi.b, (int)q->N, r->depth) < 0)
             rc = LBHPDE_ERR_UNSUPPORTED;
     }

@@ -111,22 +111,67 @@ def test_batch_with_real_exponent_and_polynomial_members(L):
         assert normwise(g, want) <= FP64_TOL, p.eq.name
 
 
-def test_bounded_real_exponent(L):
-    """The gKdV soliton (n = 1.5) on a bounded grid with exact boundary values: the streaming
-    step and the outer-node rebuild with the generalised f^eq."""
-    n, dt, tau, steps = 1.5, 1e-4, 1.3, 1500
+def _bounded_real_problems():
+    """Real-exponent models on bounded grids with boundary values from a known profile: the gKdV
+    soliton (n = 1.5, D1Q5) with its exact solution, and a D1Q7 class (1) model whose boundary
+    holds its initial values (a slowly varying profile whose ends stay at the background)."""
+    n, dt, tau = 1.5, 1e-4, 1.3
     ex = lambda x, t: W.gkdv_soliton(x, t, n, x0=-5.0)  # noqa: E731
     x = W.grid(-30.0, 601, DX)
-    p = W.Problem(W.gkdv(n), 601, DX, dt, tau, steps, ex(x, 0.0), xl=-30.0, exact=lambda t: ex(x, t),
-                  boundary="nee", exact_xt=ex, meta={"depth": 2})
-    M = oracle.Model(p.eq.alpha, p.eq.pi, DX, dt, tau, nu=n, pi_nu=p.eq.pi_nu)
-    pb = W.boundary_values(p, 2, 0, steps)
-    f = M.init(p.phi0)
-    want = M.phi(M.step_nee(f, pb, 2))
-    s = L.Solver.for_problem(p, precision=L.FP64)
-    got = s.set_phi(p.phi0).step_nee(steps, pb).read_phi()
+    gk = W.Problem(W.gkdv(n), 601, DX, dt, tau, 1500, ex(x, 0.0), xl=-30.0, exact=lambda t: ex(x, t),
+                   boundary="nee", exact_xt=ex, meta={"depth": 2})
+    prof = lambda x, t: 0.5 + 0.3 * W.sech(x / 3.0) ** 2 + 0.0 * t  # noqa: E731
+    kw = W.Problem(W.class1_real(1.0, -0.4, 1.7, (0.0, 1.0, 0.0, -1.0)), 601, DX, 1e-4, 2.02, 600, prof(x, 0.0),
+                   xl=-30.0, exact=lambda t: prof(x, t), boundary="nee", exact_xt=prof, meta={"depth": 2})
+    return {"gkdv_1.5_soliton_q5": gk, "kawahara_real_q7": kw}
+
+
+def _oracle_bounded(p, phi0=None):
+    M = oracle.Model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, lattice=p.eq.lattice, scheme=p.scheme, nu=p.eq.nu,
+                     pi_nu=p.eq.pi_nu)
+    f = M.init(p.phi0 if phi0 is None else phi0)
+    return M.phi(M.step_nee(f, W.boundary_values(p, (M.b - 1) // 2, 0, p.nsteps), p.meta["depth"]))
+
+
+def _gpu_bounded(L, p, precision, kernel):
+    s = L.Solver.for_problem(p, precision=precision)
+    s.set_kernel(kernel)
+    Wd = (s.model().b - 1) // 2
+    s.set_phi(p.phi0)
+    done = 0
+    for m in (p.nsteps // 3, p.nsteps - p.nsteps // 3):  # two launches: the boundary rows' offset
+        s.step_nee(m, W.boundary_values(p, Wd, done, m))
+        done += m
+    got = s.read_phi()
     s.close()
+    return got
+
+
+@pytest.mark.parametrize("name", list(_bounded_real_problems()))
+@pytest.mark.parametrize("kernel", ["resident", "stream"])
+def test_bounded_real_exponent(L, name, kernel):
+    """Real exponents on bounded grids: the resident bounded kernel's variant with the
+    generalised f^eq (in the relaxation, at x_f and at the boundary values), and the streaming
+    step with the outer-node rebuild, against the oracle's bounded step."""
+    p = _bounded_real_problems()[name]
+    want = _oracle_bounded(p)
+    got = _gpu_bounded(L, p, L.FP64, L.KERNEL_STREAM if kernel == "stream" else L.KERNEL_AUTO)
     assert normwise(got, want) <= FP64_TOL
+
+
+@pytest.mark.parametrize("name", list(_bounded_real_problems()))
+def test_fp32_bounded_real_exponent(L, name):
+    """FP32 on the resident bounded kernel with real exponents: within one FP32 rounding of phi
+    and of the stored deviations a step, added like a random walk, times the growth of a
+    perturbation of phi0 that the oracle measures on the problem."""
+    p = _bounded_real_problems()[name]
+    want = _oracle_bounded(p)
+    rng = np.random.default_rng(0)
+    pert = _oracle_bounded(p, p.phi0 * (1 + 1e-6 * rng.standard_normal(p.N)))
+    growth = max(1.0, normwise(pert, want) / 1e-6)
+    eps = 2.0 ** -24
+    got = _gpu_bounded(L, p, L.FP32_DEV, L.KERNEL_AUTO)
+    assert normwise(got, want) <= (16 * eps * np.sqrt(p.nsteps) + 4 * eps) * growth
 
 
 def test_fp32_accuracy(L):

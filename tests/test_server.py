@@ -104,7 +104,8 @@ def test_results_identical_alone_and_in_the_mix(L, precision):
 
 def _bounded_requests(n, seed):
     """Bounded requests (Sec. IV examples on D1Q5 and D1Q7, depths 1-3, grids of 601-2001
-    nodes) with random step counts, each with its boundary values from the exact solution."""
+    nodes, and the gKdV soliton with the real exponent 1.5) with random step counts, each with
+    its boundary values from the exact solution."""
     menu = [("4.1", 1e-3, 1.989, 1 | oracle.NO_AUX_CORRECTION, 2), ("4.2", 1e-2, 4.569, 1 | oracle.NO_AUX_CORRECTION, 2),
             ("4.5", 1e-4, 2.02, 1, 1), ("4.6", 1e-2, 4.04, 2, 3), ("4.7", 1e-3, 3.31, 1, 2)]
     rng = np.random.default_rng(seed)
@@ -112,8 +113,14 @@ def _bounded_requests(n, seed):
     for i in range(n):
         ex, dt, tau, scheme, depth = menu[i % len(menu)]
         steps = int(rng.integers(0, 400))
-        p = W.bounded_config(ex, dt, tau, steps * dt, scheme=scheme)
-        p.meta["depth"] = depth
+        if i % 6 == 5:
+            ex_ = lambda x, t: W.gkdv_soliton(x, t, 1.5, x0=-5.0)  # noqa: E731
+            x = W.grid(-30.0, 601, 0.1)
+            p = W.Problem(W.gkdv(1.5), 601, 0.1, 1e-4, 1.3, steps, ex_(x, 0.0), xl=-30.0,
+                          exact=lambda t, x=x: ex_(x, t), boundary="nee", exact_xt=ex_, meta={"depth": 2})
+        else:
+            p = W.bounded_config(ex, dt, tau, steps * dt, scheme=scheme)
+            p.meta["depth"] = depth
         out.append(p)
     return out
 
@@ -132,12 +139,14 @@ def _bounded_alone(L, p, precision, phib):
 
 def _wd(p):
     """max|e_j| of p's lattice (the columns of its boundary rows are 2 max|e_j|)."""
-    M = oracle.Model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, lattice=p.eq.lattice, scheme=p.scheme)
+    M = oracle.Model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, lattice=p.eq.lattice, scheme=p.scheme, nu=p.eq.nu,
+                     pi_nu=p.eq.pi_nu)
     return (M.b - 1) // 2
 
 
 def _oracle_nee(p):
-    M = oracle.Model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, lattice=p.eq.lattice, scheme=p.scheme)
+    M = oracle.Model(p.eq.alpha, p.eq.pi, p.dx, p.dt, p.tau, lattice=p.eq.lattice, scheme=p.scheme, nu=p.eq.nu,
+                     pi_nu=p.eq.pi_nu)
     f = M.init(p.phi0)
     if p.nsteps:
         M.step_nee(f, W.boundary_values(p, (M.b - 1) // 2, 0, p.nsteps), p.meta["depth"])
