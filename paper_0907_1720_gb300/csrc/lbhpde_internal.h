@@ -126,6 +126,7 @@ struct PackedNee {
     std::vector<lbk::RingNeeInst> insts;
     std::vector<int> first;
     int nthreads = 32, stride = 0;
+    bool d2 = false;  // every member of depth 2 with at least 2 interior nodes in its last thread
     size_t smem = 0;
     int ncta() const { return first.empty() ? 0 : (int)first.size() - 1; }
 };

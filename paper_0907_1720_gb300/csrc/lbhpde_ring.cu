@@ -50,11 +50,11 @@ int launch_ring_f32(int dc, const Packed &p, const lbk::OnchipInst *insts_d, con
 
 namespace {
 
-template <int MAXT, int DC>
+template <int MAXT, int DC, bool D2>
 int launch_ring_nee_t(const PackedNee &p, const lbk::RingNeeInst *insts, const int *first, const void *in, void *out,
                       const void *coefT, const double *phib, long long stride, long long step0, int nsteps,
                       cudaStream_t st) {
-    auto fn = lbk::k_ring_nee<float, 5, kRingK, MAXT, DC>;
+    auto fn = lbk::k_ring_nee<float, 5, kRingK, MAXT, DC, D2>;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) != cudaSuccess) {
         (void)cudaGetLastError();
         return LBHPDE_ERR_CUDA;
@@ -69,8 +69,12 @@ template <int MAXT>
 int launch_ring_nee_d(int dc, const PackedNee &p, const lbk::RingNeeInst *insts, const int *first, const void *in,
                       void *out, const void *coefT, const double *phib, long long stride, long long step0, int nsteps,
                       cudaStream_t st) {
-    if (dc == 5) return launch_ring_nee_t<MAXT, 5>(p, insts, first, in, out, coefT, phib, stride, step0, nsteps, st);
-    if (dc == 0) return launch_ring_nee_t<MAXT, 0>(p, insts, first, in, out, coefT, phib, stride, step0, nsteps, st);
+    if (dc == 5 && p.d2)
+        return launch_ring_nee_t<MAXT, 5, true>(p, insts, first, in, out, coefT, phib, stride, step0, nsteps, st);
+    if (dc == 5) return launch_ring_nee_t<MAXT, 5, false>(p, insts, first, in, out, coefT, phib, stride, step0, nsteps, st);
+    if (dc == 0 && p.d2)
+        return launch_ring_nee_t<MAXT, 0, true>(p, insts, first, in, out, coefT, phib, stride, step0, nsteps, st);
+    if (dc == 0) return launch_ring_nee_t<MAXT, 0, false>(p, insts, first, in, out, coefT, phib, stride, step0, nsteps, st);
     return LBHPDE_ERR_UNSUPPORTED;
 }
 
@@ -99,6 +103,13 @@ int pack_ring_nee(int b, int dc, const std::vector<NeeMember> &m, PackedNee &out
         std::vector<int> inst;
     };
     std::vector<Cta> ctas;
+    // depth 2 with x_f of the right end in the last thread (at least 2 nodes there) in every
+    // member: the variant that rebuilds the inflow at fixed register positions
+    out.d2 = true;
+    for (const NeeMember &x : m) {
+        const int last_nodes = x.seg.N - 2 * W - K * (thr(x) - 1);
+        if (x.seg.pad != 2 || last_nodes < 2) out.d2 = false;
+    }
     for (int i : order) {
         bool placed = false;
         for (auto &c : ctas)
@@ -152,8 +163,6 @@ int launch_ring_nee_f32(int dc, const PackedNee &p, const lbk::RingNeeInst *inst
     if (p.nthreads > p.stride || p.nthreads % 32 != 0) return LBHPDE_ERR_ARG;
     for (int c = 0; c < p.ncta(); ++c)  // every helper role has its thread
         if ((p.first[c + 1] - p.first[c]) * lbk::nee_roles(5) > p.nthreads) return LBHPDE_ERR_ARG;
-    if (p.stride == 128)
-        return launch_ring_nee_d<128>(dc, p, insts_d, first_d, in, out, coefT, phib, stride, step0, nsteps, st);
     if (p.stride == 512)
         return launch_ring_nee_d<512>(dc, p, insts_d, first_d, in, out, coefT, phib, stride, step0, nsteps, st);
     return LBHPDE_ERR_UNSUPPORTED;

@@ -67,10 +67,12 @@ __host__ __device__ constexpr int nee_roles(int B) { return 2 * nedge(B); }
 __host__ __device__ constexpr int nee_helpers(int B) { return kRingMaxInst * nee_roles(B); }
 // Shared elements (4-byte) of a k_ring_nee CTA of MAXT threads, without the coefficient blocks:
 // the exchange rows, the x_f column, the outer-node blocks and the boundary terms
-// [2 parities][kRingMaxInst][2W][B] (f^eq_j(phi_b) of the inflow values), and the helpers' copied
-// boundary values [2 parities][helpers] doubles.
+// [2 parities][kRingMaxInst][2W][B] (f^eq_j(phi_b) of the inflow values), the helpers' copied
+// boundary values [2 parities][helpers] doubles, and each helper's source address (8 bytes) and
+// its int4 (coefficient row, steps, destination, -) in shared memory rather than in registers.
 __host__ __device__ constexpr int nee_fixed_elems(int B, int MAXT) {
-    return 4 * nedge(B) * MAXT + B * MAXT + 2 * 2 * kRingMaxInst * 2 * wmax(B) * B + 2 * 2 * nee_helpers(B);
+    return 4 * nedge(B) * MAXT + B * MAXT + 2 * 2 * kRingMaxInst * 2 * wmax(B) * B + 2 * 2 * nee_helpers(B) +
+           2 * nee_helpers(B) + 4 * nee_helpers(B);
 }
 
 // Asynchronous 8-byte copy global -> shared (visible to this thread after cp_async_wait_all).
@@ -95,7 +97,7 @@ __device__ __forceinline__ T nee_row(const T *c, int D, T x) {
     }
 }
 
-template <typename T, int B, int K, int MAXT, int DC>
+template <typename T, int B, int K, int MAXT, int DC, bool D2>
 __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     k_ring_nee(const T *__restrict__ st_in, T *__restrict__ st_out, const RingNeeInst *__restrict__ insts,
                const int *__restrict__ cta_first, const T *__restrict__ coefs, const double *__restrict__ phib,
@@ -114,7 +116,9 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     T *GB = OB + 2 * OS;                      // [2][kRingMaxInst][2W][B] f^eq_j(phi_b), inflow
     constexpr int NH = nee_helpers(B);
     double *PBs = reinterpret_cast<double *>(GB + 2 * OS);  // [2][NH] helpers' boundary values
-    T *scoef = reinterpret_cast<T *>(PBs + 2 * NH);
+    const double **HSrc = reinterpret_cast<const double **>(PBs + 2 * NH);  // [NH] helper's next row
+    int4 *HMeta = reinterpret_cast<int4 *>(HSrc + NH);  // [NH] row of f^eq_j, steps, destination
+    T *scoef = reinterpret_cast<T *>(HMeta + NH);
 
     const int nt = blockDim.x;
     const int first = cta_first[blockIdx.x], last = cta_first[blockIdx.x + 1];
@@ -149,26 +153,31 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     while (ha < W && hrr >= eslot(ha + 1)) ++ha;
     const int hk = hrr - eslot(ha);
     const int ho = hside == 0 ? W - ha + hk : W + hk, hj = hside == 0 ? 2 * ha - 1 : 2 * ha;
-    const double *hsrc = phib;
-    int hsteps = 0, hq = 0, hD = 0;
     if (helper) {
         const RingNeeInst &H = insts[first + hi];
-        hsrc = phib + (long long)H.mi * stride + step0 * (2 * W) + ho;
-        hsteps = H.steps < nsteps ? H.steps : nsteps;
-        hD = DC > 0 ? DC : H.D;
-        hq = H.scoef + (B - 1) * crow(hD) + (hj - 1) * crow(hD);
+        const double *hsrc = phib + (long long)H.mi * stride + step0 * (2 * W) + ho;
+        const int hsteps = H.steps < nsteps ? H.steps : nsteps;
+        const int hD = DC > 0 ? DC : H.D;
+        HSrc[tid] = hsrc + 2 * (2 * W);
+        HMeta[tid] = make_int4(H.scoef + (B - 1) * crow(hD) + (hj - 1) * crow(hD), hsteps,
+                               (hi * 2 * W + ho) * B + hj, hD);
         if (hsteps > 0) cp_async8(PBs + tid, hsrc);
         if (hsteps > 1) cp_async8(PBs + NH + tid, hsrc + 2 * W);
     }
-    T *const hdst = GB + (hi * 2 * W + ho) * B;  // + parity * OS
     // f^eq_j(phi_b) of rebuild r into its parity, and the copy of row r + 2 into the freed slot
+    // (the helper's state comes from shared memory each step: no registers held across steps)
     auto help = [&](int r) {
-        if (!helper || r >= hsteps) return;
+        if (!helper) return;
+        const int4 m = HMeta[tid];
+        if (r >= m.y) return;
         cp_async_wait_all();
         const T pb = (T)PBs[(r & 1) * NH + tid];
-        T *dst = hdst + (r & 1) * OS;
-        dst[hj] = nee_row<T, DC>(scoef + hq, hD, pb);
-        if (r + 2 < hsteps) cp_async8(PBs + (r & 1) * NH + tid, hsrc + (long long)(r + 2) * (2 * W));
+        GB[(r & 1) * OS + m.z] = nee_row<T, DC>(scoef + m.x, m.w, pb);
+        if (r + 2 < m.y) {
+            const double *src = HSrc[tid];
+            cp_async8(PBs + (r & 1) * NH + tid, src);
+            HSrc[tid] = src + 2 * W;
+        }
     };
     int me = -1;
     for (int i = first; i < last; ++i) {
@@ -191,7 +200,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
         for (int j = 1; j < B; ++j) v[j][k] = ok ? st_in[I.off + (long long)j * I.ld + xb + k] : T(0);
     }
     __syncthreads();  // coefficients and outer nodes staged
-    help(0);          // ordered before the rebuild of step 0 by the barrier of step 0
+    if constexpr (!D2) help(0);  // ordered before the rebuild of step 0 by the barrier of step 0
     const T *sc = scoef + I.scoef;
     const int D = DC > 0 ? DC : I.D;
     const int cs = crow(D);
@@ -205,8 +214,13 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     const T *const Lrt = L + (has_right ? tid + 1 : tid);
     T *const OBi = OB + (has ? I.il : 0) * 2 * W * B;  // this instance's outer block, parity 0
     // x_f of each end, as interior indices: its thread rebuilds that end
-    const int fL = has ? I.depth - 1 : -K, fR = has ? N - 2 * W - I.depth : -K;
-    const int side_mask = (fL >= t * K && fL < t * K + K ? 1 : 0) | (fR >= t * K && fR < t * K + K ? 2 : 0);
+    // (packed: bit 0 left end, bit 1 right end, then x_f's position in this thread for each end)
+    int rbk = 0;
+    {
+        const int fL = has ? I.depth - 1 : -K, fR = has ? N - 2 * W - I.depth : -K;
+        if (fL >= t * K && fL < t * K + K) rbk |= 1 | (fL - t * K) << 2;
+        if (fR >= t * K && fR < t * K + K) rbk |= 2 | (fR - t * K) << 6;
+    }
 
     // x_f's phi and s_j into this thread's column of X (a jump on its position pf)
     auto extract = [&](int pf) {
@@ -281,22 +295,82 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
             }
         }
         __syncthreads();
-        help(s + 1);
+        if constexpr (D2)
+            help(s);  // read at the start of step s + 1
+        else
+            help(s + 1);
         if (!live) return;
         const T *ob = OBi + P * OS;  // the outer nodes of this step
+        // depth 2 (every instance of the launch, x_f of each end in its end thread): the inflow of
+        // step s is rebuilt at its start by the thread that reads it, from x_f's state after step
+        // s - 1 at a fixed register position (position 1 of the first thread; position rem - 2 of
+        // the last, in the jump on the remainder), with f^eq_j(phi_b) of rebuild s - 1 from the
+        // helpers (block of parity s - 1)
+        T inL[NE] = {};
+        if constexpr (D2) {
+            if (t == 0) {
+                if (s == 0) {
+#pragma unroll
+                    for (int e = 1; e <= W; ++e)
+#pragma unroll
+                        for (int k = 0; k < e; ++k) inL[eslot(e) + k] = ob[(W - e + k) * B + 2 * e - 1];
+                } else {
+                    const T *const g = GB + (P ^ 1) * OS + (OBi - OB);
+#pragma unroll
+                    for (int e = 1; e <= W; ++e) {
+                        const int j = 2 * e - 1;
+                        const T fn = v[j][1] - nee_row<T, DC>(Q + (j - 1) * cs, D, phi[1]);
+#pragma unroll
+                        for (int k = 0; k < e; ++k) inL[eslot(e) + k] = g[(W - e + k) * B + j] + fn;
+                    }
+                }
+            }
+        }
         // the last thread: its first positions past the last interior node take the right outer
         // nodes' left-moving populations (named registers, a jump on the remainder)
-        if (rem < K) {
-            auto put = [&](auto rc) {
-                constexpr int Rr = decltype(rc)::value;
+        auto put = [&](auto rc) {
+            constexpr int Rr = decltype(rc)::value;
 #pragma unroll
-                for (int j = 1; j < B; ++j) {
-                    const int a = -vel(j);
+            for (int j = 1; j < B; ++j) {
+                const int a = -vel(j);
 #pragma unroll
-                    for (int i = 0; i < a; ++i)
-                        if (Rr + i < K) v[j][Rr + i] = ob[(W + i) * B + j];
+                for (int i = 0; i < a; ++i)
+                    if (Rr + i < K) v[j][Rr + i] = ob[(W + i) * B + j];
+            }
+        };
+        if constexpr (D2) {
+            // the last thread (rem >= 2): the right end's inflow values into this step's block
+            // (read back by the jump below and by the neighbour reads past the last node)
+            auto fixput = [&](auto rc) {
+                constexpr int Rr = decltype(rc)::value, pf = Rr - 2;
+                if (s > 0) {
+                    T *const o = OBi + P * OS + W * B;
+                    const T *const g = GB + (P ^ 1) * OS + (OBi - OB) + W * B;
+#pragma unroll
+                    for (int a = 1; a <= W; ++a) {
+                        const int j = 2 * a;
+                        const T fn = v[j][pf] - nee_row<T, DC>(Q + (j - 1) * cs, D, phi[pf]);
+#pragma unroll
+                        for (int i = 0; i < a; ++i) o[i * B + j] = g[i * B + j] + fn;
+                    }
                 }
+                put(rc);
             };
+            if (has && !has_right) {
+                switch (rem < K ? rem : K) {
+#define LBK_NEE_FIX(Rv)                            \
+    case Rv:                                       \
+        fixput(std::integral_constant<int, Rv>{}); \
+        break;
+                    LBK_NEE_FIX(2) LBK_NEE_FIX(3) LBK_NEE_FIX(4) LBK_NEE_FIX(5) LBK_NEE_FIX(6) LBK_NEE_FIX(7)
+                    LBK_NEE_FIX(8) LBK_NEE_FIX(9) LBK_NEE_FIX(10) LBK_NEE_FIX(11) LBK_NEE_FIX(12) LBK_NEE_FIX(13)
+                    LBK_NEE_FIX(14) LBK_NEE_FIX(15) LBK_NEE_FIX(16)
+#undef LBK_NEE_FIX
+                    default:
+                        break;
+                }
+            }
+        } else if (rem < K) {
             switch (rem) {
 #define LBK_NEE_REM(Rv)                         \
     case Rv:                                    \
@@ -340,7 +414,8 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
             if (e > 0) {
 #pragma unroll
                 for (int k = 0; k < e; ++k) {
-                    const T nv = t > 0 ? Rme[P * PS + (eslot(e) + k) * MAXT - 1] : ob[(W + k - e) * B + j];
+                    const T nv = t > 0 ? Rme[P * PS + (eslot(e) + k) * MAXT - 1]
+                                       : (D2 ? inL[eslot(e) + k] : ob[(W + k - e) * B + j]);
                     d[k] += nv - v[j][k];
                     v[j][k] = nv;
                 }
@@ -363,9 +438,9 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
         ring_relax<T, B, K, DC, RCH, 0, K>(sc, cs, D, omw, phi, v);
         // the rebuild of the inflow values (population j with |e_j| = a at its a nodes next to
         // the interior) from x_f's phi and s_j, which pass through this thread's column of X
-        if (s + 1 < steps) {
-            if (side_mask & 1) rebuild_inflow(P, fL - t * K, std::integral_constant<int, 0>{});
-            if (side_mask & 2) rebuild_inflow(P, fR - t * K, std::integral_constant<int, 1>{});
+        if (!D2 && rbk && s + 1 < steps) {
+            if (rbk & 1) rebuild_inflow(P, (rbk >> 2) & 15, std::integral_constant<int, 0>{});
+            if (rbk & 2) rebuild_inflow(P, (rbk >> 6) & 15, std::integral_constant<int, 1>{});
         }
     };
     for (int s = 0; s < nsteps; s += 2) {
@@ -373,10 +448,10 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
         if (s + 1 < nsteps) step(std::integral_constant<int, 1>{}, s + 1);
     }
     // (parity steps & 1 was last read in step steps - 2, before the barrier of step steps - 1)
-    if (steps > 0 && (side_mask & 1)) rebuild_all(fL - t * K, 0);
-    if (steps > 0 && (side_mask & 2)) rebuild_all(fR - t * K, 1);
+    if (has) I = insts[me];  // reloaded: nothing of it stays in registers across the steps
+    if (steps > 0 && (rbk & 1)) rebuild_all((rbk >> 2) & 15, 0);
+    if (steps > 0 && (rbk & 2)) rebuild_all((rbk >> 6) & 15, 1);
     __syncthreads();  // the outer nodes after the last step are in the block of parity steps & 1
-    if (has) I = insts[me];
     if (has && t == 0) {
         const T *ob = OBi + (steps & 1) * OS;
         for (int o = 0; o < 2 * W; ++o) {

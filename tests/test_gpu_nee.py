@@ -259,7 +259,7 @@ def fp32_bound(p):
 
 
 # (name, example, dt, tau, scheme, depth, steps, dx): D1Q5, depths 1-4 and 20 (x_f in the second
-# thread of 16 nodes), grids of 501, 601 and 1001 nodes, tau at the paper's tau_opt (growth ~30)
+# thread of 16 nodes), grids of 484, 486, 501, 601 and 1001 nodes, tau at the paper's tau_opt (growth ~30)
 # and above it (growth < 1)
 FP32_CASES = [
     ("ks_4.1_tauopt", "4.1", 1e-3, 1.989, 1 | NOA, 2, 1100, 0.1),
@@ -269,6 +269,10 @@ FP32_CASES = [
     ("ks_4.1_d4", "4.1", 1e-3, 2.05, 1 | NOA, 4, 600, 0.1),
     ("ks_4.1_d20", "4.1", 1e-3, 2.1, 1 | NOA, 20, 400, 0.1),
     ("ks_4.1_N501", "4.1", 1.2e-3, 2.05, 1 | NOA, 2, 500, 0.12),
+    # 16 r + 2 and 16 r interior nodes: the right end's x_f at the first and the last position
+    # where the depth-2 variant of the 16-node kernel finds it in the last thread
+    ("ks_4.1_N486", "4.1", 1.2e-3, 2.05, 1 | NOA, 2, 500, 60.0 / 485),
+    ("ks_4.1_N484", "4.1", 1.2e-3, 2.05, 1 | NOA, 2, 500, 60.0 / 483),
 ]
 
 
