@@ -393,8 +393,8 @@ def run_ours(args, rank, world, cpu=None):
             achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                     "frac": achieved / peak_tf, "traffic": None,
-                    "kernel": ("k_ring_nee<float,5,16,512,5> (13 instances a CTA, interior nodes in registers, "
-                               "outer nodes in shared memory)" if esz == 4 else
+                    "kernel": ("k_ring_nee<float,5,16,512,5,D2> (13 instances a CTA, interior nodes in registers, "
+                               "depth-2 inflow rebuilt by its reader at fixed register positions)" if esz == 4 else
                                "k_bounded<double,5,4,512,5> (one resident CTA per instance)"),
                     "flops_per_node_update": fl, "peak_source": src}
         elif args.workload == "nu_grid" and args.kernel != "stream":
