@@ -831,9 +831,70 @@ struct DiagPart {
     long long pad;
 };
 
+// Error-free sum in float pairs (Knuth's TwoSum): hi + lo carries the running sum of float values
+// to about 2^-48 relative, with FP32 operations only (FP64 ones are scarce on this part).
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+    const float s = hi + x, bp = s - hi;
+    lo += (hi - (s - bp)) + (x - bp);
+    hi = s;
+}
+
+// Sum, max|phi| and non-finite count of FP32 phi without a reference solution: float-pair sums
+// per thread and across the warp, FP64 only for the warps' partial sums.
+static __device__ void diag_block_f32(const float *__restrict__ st, const Seg &s, int x0, int chunk,
+                               DiagPart *__restrict__ dst) {
+    float hi = 0.f, lo = 0.f, mx = 0.f;
+    int nf = 0;
+    const int xend = min(x0 + chunk, s.N);
+    for (int x = x0 + threadIdx.x; x < xend; x += blockDim.x) {
+        const float ph = st[s.off + x];
+        if (!isfinite(ph)) {
+            ++nf;
+            continue;
+        }
+        two_sum_acc(hi, lo, ph);
+        mx = fmaxf(mx, fabsf(ph));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(0xffffffffu, hi, o), l2 = __shfl_down_sync(0xffffffffu, lo, o);
+        two_sum_acc(hi, lo, h2);
+        lo += l2;
+        mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, o));
+        nf += __shfl_down_sync(0xffffffffu, nf, o);
+    }
+    __shared__ double rs[32];
+    __shared__ float rm[32];
+    __shared__ int rn[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        rs[w] = (double)hi + (double)lo;
+        rm[w] = mx;
+        rn[w] = nf;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        DiagPart r{};
+        float m = 0.f;
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 0; i < nw; ++i) {
+            r.sum += rs[i];
+            m = fmaxf(m, rm[i]);
+            r.nonfinite += rn[i];
+        }
+        r.maxabs = m;
+        *dst = r;
+    }
+}
+
 template <typename T>
 __device__ void diag_block(const T *__restrict__ st, const Seg &s, int x0, int chunk, const double *__restrict__ ps,
                            DiagPart *__restrict__ dst) {
+    if constexpr (sizeof(T) == 4) {
+        if (!ps) {
+            diag_block_f32(st, s, x0, chunk, dst);
+            return;
+        }
+    }
     double a[6] = {0, 0, 0, 0, 0, 0};
     long long nf = 0;
     const int xend = min(x0 + chunk, s.N);
