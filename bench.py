@@ -419,7 +419,8 @@ def run_ours(args, rank, world, cpu=None):
             achieved = fl * upd_step / (kern_ms / 1e3) / 1e12
             roof = {"bound": "alu", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                     "frac": achieved / peak_tf, "traffic": None,
-                    "kernel": (f"k_ring<float,5,16,MAXT,5> (every member resident, 16 nodes a thread)"
+                    "kernel": (f"k_ring<float,5,16,512,5> (every member resident: whole waves at 16 nodes a "
+                               f"thread, then the tail on k_onchip<float,5,8,512,0,5>)"
                                if args.workload == "ensemble" and esz == 4 else
                                f"k_onchip<{'float' if esz == 4 else 'double'},{b},K> "
                                f"({'resident instances + halo windows' if args.workload == 'ensemble' else 'halo windows'})"),

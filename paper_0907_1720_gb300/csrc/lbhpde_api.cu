@@ -62,6 +62,7 @@ struct Group {
     } ring[lbh::kRingClasses], halo;  // resident instances by CTA size class; windows
     int K = 0, maxt = 0, tblk = 0;
     int Kr = 0;  // nodes per thread of the resident plans (lbh::kRingK: k_ring)
+    int Kt = 0;  // nodes per thread of the tail of a plan in whole waves
     int dc = 0;  // compile-time degree of the on-chip kernel variant (0 = run time)
     bool uniform = false;  // every member has the same model (coefficients and omega)
     bool has_nu = false;   // a member has real-exponent terms: the real-exponent variants (on chip: degree code -1)
@@ -733,6 +734,9 @@ int upload_plan(lbhpde_batch_s *bt, Group::Plan &pl) {
 // force_halo) are cut into temporally blocked windows of tblk steps.
 // Kr: nodes per thread of the resident instances (K, or lbh::kRingK for the 16-node kernel, whose
 // instances hold up to 8192 nodes; the windows then keep K).
+// Nodes a thread of the tail of a plan in whole waves (members that fit it; the others keep 16)
+constexpr int kTailK = 8;
+
 int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int Kr, int tblk, bool force_halo) {
     g.onchip_ok = false;
     const int maxt = lbh::onchip_maxt(bt->esz, g.b, Kr);
@@ -758,6 +762,7 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int Kr, int tblk, bool forc
         CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     }
     g.waves = Kr == lbh::kRingK && lbh::split_ring_waves(g.b, Kr, sms, resident, full, tail);
+    g.Kt = 0;
     if (g.waves) {
         for (auto &v : ring) v.clear();
         ring[lbh::kRingClasses - 1] = full;
@@ -779,14 +784,19 @@ int plan_onchip(lbhpde_batch_s *bt, Group &g, int K, int Kr, int tblk, bool forc
     for (int c = 0; c < lbh::kRingClasses; ++c) {
         if (ring[c].empty()) continue;
         int threads = lbh::ring_class_threads(bt->esz, g.b, Kr, c);
-        if (g.waves && c == 0) {  // the tail: the smallest class that holds its largest member
+        int Kc = Kr;
+        if (g.waves && c == 0) {
+            // the tail runs after the waves with an SM to itself per CTA: fewer nodes a thread
+            // (more warps) when its members fit, in the smallest class that holds the largest
             long long nmax = 0;
             for (const auto &mb : ring[c]) nmax = std::max<long long>(nmax, mb.seg.N);
+            if (nmax <= (long long)lbh::onchip_maxt(bt->esz, g.b, kTailK) * kTailK) Kc = kTailK;
             int cl = 0;
-            while (cl < lbh::kRingClasses - 1 && nmax > (long long)lbh::ring_class_threads(bt->esz, g.b, Kr, cl) * Kr) ++cl;
-            threads = lbh::ring_class_threads(bt->esz, g.b, Kr, cl);
+            while (cl < lbh::kRingClasses - 1 && nmax > (long long)lbh::ring_class_threads(bt->esz, g.b, Kc, cl) * Kc) ++cl;
+            threads = lbh::ring_class_threads(bt->esz, g.b, Kc, cl);
+            g.Kt = Kc;
         }
-        RC(lbh::pack_ring(g.b, bt->esz, Kr, g.dc, ring[c], g.ring[c].host, threads));
+        RC(lbh::pack_ring(g.b, bt->esz, Kc, g.dc, ring[c], g.ring[c].host, threads));
         RC(upload_plan(bt, g.ring[c]));
     }
     if (!halo.empty()) RC(lbh::pack_halo(g.b, bt->esz, K, g.dc, H, halo, g.halo.host));
@@ -803,8 +813,9 @@ int launch_group(lbhpde_batch_s *bt, Group &g, bool halo, const void *in, void *
                  int cls = lbh::kRingClasses - 1) {
     Group::Plan &pl = halo ? g.halo : g.ring[cls];
     if (pl.ncta() > 0 && nsteps > 0) ++bt->launches;
-    return lbh::launch_onchip(g.b, bt->esz, halo ? g.K : g.Kr, g.dc, halo, pl.host, pl.insts, pl.cta_first, in, out,
-                              bt->coefT, nsteps, st);
+    const int Kx = halo ? g.K : (g.waves && cls == 0 && g.Kt ? g.Kt : g.Kr);
+    return lbh::launch_onchip(g.b, bt->esz, Kx, g.dc, halo, pl.host, pl.insts, pl.cta_first, in, out, bt->coefT,
+                              nsteps, st);
 }
 
 int batch_build(lbhpde_batch_s *bt, int count, const lbhpde_instance *m) {
