@@ -50,8 +50,12 @@ __device__ __forceinline__ void load_coefs(const T *c, T (&cr)[NC]) {
 
 // Relax the nodes [K0, K1) and [K2, K3) of a thread: s'_j = (1 - omega) f_j + P_j(phi'), Horner in
 // phi with the coefficient rows of P_j in shared memory (stride cs; DC > 0: degree DC at compile
-// time, each row loaded once per call by vector loads).  The nodes go through the recursion in
-// chunks of CH (fewer live registers than one chain per node at once).
+// time).  The nodes go through the recursion in chunks of CH (fewer live registers than one
+// chain per node at once).  In FP32 with a compile-time degree, two neighbouring nodes take one
+// packed multiply-add (__ffma2_rn: each half rounds as one fmaf, so the result is bit for bit
+// that of one node at a time), which halves the issue slots of the recursion.  (Measured on
+// GB300: 4% faster on the ensemble; pairing two populations of one node instead, or loading
+// duplicated coefficient pairs by 8-byte loads, was slower than the unpaired recursion.)
 template <typename T, int B, int K, int DC, int CH, int K0, int K1, int K2 = K1, int K3 = K1>
 __device__ __forceinline__ void ring_relax(const T *sc, int cs, int D, T omw, const T (&phi)[K], T (&v)[B][K]) {
     constexpr int NA = K1 - K0, NN = NA + (K3 - K2);
@@ -60,7 +64,29 @@ __device__ __forceinline__ void ring_relax(const T *sc, int cs, int D, T omw, co
 #pragma unroll
         for (int j = 1; j < B; ++j) {
             const T *c = sc + (j - 1) * cs;
-            if constexpr (DC > 0) {
+            if constexpr (DC > 0 && std::is_same<T, float>::value && CH % 2 == 0 && NN % CH == 0) {
+                // two nodes per packed FP32 multiply-add (the same roundings as one at a time)
+#pragma unroll
+                for (int i0 = 0; i0 < NN; i0 += CH) {
+                    float2 acc[CH / 2];
+                    const float cD = c[DC];
+#pragma unroll
+                    for (int i = 0; i < CH / 2; ++i) acc[i] = make_float2(cD, cD);
+#pragma unroll
+                    for (int p = DC - 1; p >= 0; --p) {
+                        const float cp = c[p];
+                        const float2 cp2 = make_float2(cp, cp);
+#pragma unroll
+                        for (int i = 0; i < CH / 2; ++i)
+                            acc[i] = __ffma2_rn(acc[i], make_float2(phi[node(i0 + 2 * i)], phi[node(i0 + 2 * i + 1)]), cp2);
+                    }
+#pragma unroll
+                    for (int i = 0; i < CH / 2; ++i) {
+                        v[j][node(i0 + 2 * i)] = fma_t(omw, v[j][node(i0 + 2 * i)], acc[i].x);
+                        v[j][node(i0 + 2 * i + 1)] = fma_t(omw, v[j][node(i0 + 2 * i + 1)], acc[i].y);
+                    }
+                }
+            } else if constexpr (DC > 0) {
 #pragma unroll
                 for (int i0 = 0; i0 < NN; i0 += CH) {
                     T acc[CH];
