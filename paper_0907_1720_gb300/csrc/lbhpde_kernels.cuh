@@ -739,7 +739,24 @@ __global__ void __launch_bounds__(MAXT, onchip_minb(sizeof(T), B, K, MAXT))
             for (int j = 1; j < B && !relaxed; ++j) {
                 const T *c = sc + (j - 1) * cs;
                 T acc[K];
-                if constexpr (DC > 0) {
+                if constexpr (DC > 0 && std::is_same<T, float>::value && K % 2 == 0) {
+                    // two nodes per packed multiply-add (each half rounds as one fmaf)
+                    T cr[crow(DC)];
+                    load_row<T, crow(DC)>(c, cr);
+                    float2 a2[K / 2];
+#pragma unroll
+                    for (int k = 0; k < K / 2; ++k) a2[k] = make_float2(cr[DC], cr[DC]);
+#pragma unroll
+                    for (int p = DC - 1; p >= 0; --p)
+#pragma unroll
+                        for (int k = 0; k < K / 2; ++k)
+                            a2[k] = __ffma2_rn(a2[k], make_float2(phi[2 * k], phi[2 * k + 1]), make_float2(cr[p], cr[p]));
+#pragma unroll
+                    for (int k = 0; k < K / 2; ++k) {
+                        acc[2 * k] = a2[k].x;
+                        acc[2 * k + 1] = a2[k].y;
+                    }
+                } else if constexpr (DC > 0) {
                     T cr[crow(DC)];
                     load_row<T, crow(DC)>(c, cr);
 #pragma unroll
