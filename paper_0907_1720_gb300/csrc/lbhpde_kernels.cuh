@@ -118,6 +118,37 @@ __device__ __forceinline__ void gen_evalN(const T *c, int A_, int Dg, const T (&
                                           T (&out)[NN]) {
     const int dg = DG >= 0 ? DG : Dg;
     const int A = AA >= 0 ? AA : A_;  // AA >= 0: the row count at compile time (the rows unroll)
+    if constexpr (std::is_same<T, float>::value && DG >= 0 && AA >= 0 && NN % 2 == 0) {
+        // pairs of nodes through packed multiply-adds (each half rounds as one fmaf)
+        float2 o2[NN / 2];
+        auto row2 = [&](int a, float2 (&h)[NN / 2]) {
+            const T *r = c + a * (DG + 1);
+            T cr[DG + 1];
+#pragma unroll
+            for (int p = 0; p <= DG; ++p) cr[p] = r[p];
+#pragma unroll
+            for (int n = 0; n < NN / 2; ++n) h[n] = make_float2(cr[DG], cr[DG]);
+#pragma unroll
+            for (int p = DG - 1; p >= 0; --p)
+#pragma unroll
+                for (int n = 0; n < NN / 2; ++n)
+                    h[n] = __ffma2_rn(h[n], make_float2(phi[2 * n], phi[2 * n + 1]), make_float2(cr[p], cr[p]));
+        };
+        row2(AA, o2);
+#pragma unroll
+        for (int a = AA - 1; a >= 0; --a) {
+            float2 h[NN / 2];
+            row2(a, h);
+#pragma unroll
+            for (int n = 0; n < NN / 2; ++n) o2[n] = __ffma2_rn(o2[n], make_float2(w[2 * n], w[2 * n + 1]), h[n]);
+        }
+#pragma unroll
+        for (int n = 0; n < NN / 2; ++n) {
+            out[2 * n] = o2[n].x;
+            out[2 * n + 1] = o2[n].y;
+        }
+        return;
+    }
     auto row = [&](int a, T (&h)[NN]) {  // Q_a(phi) for every node
         const T *r = c + a * (dg + 1);
         if constexpr (DG >= 0) {
