@@ -325,3 +325,31 @@ def test_fp32_bounded_batch_matches_alone_bitwise(L):
         seg = got[b.offsets[i]: b.offsets[i + 1]]
         assert np.array_equal(seg, alone), (i, p.N, p.meta["depth"])
         assert normwise(seg, oracle_run(p)) <= fp32_bound(p)
+
+
+@pytest.mark.parametrize("depths", [(2,), (1, 2, 3)], ids=["depth2", "mixed_depths"])
+def test_fp32_tiny_bounded_grids_share_ctas(L, depths):
+    """Bounded FP32 grids of 8 to 100 nodes (one or a few threads of the 16-node kernel, many
+    instances a CTA: more helper roles than interior threads), 100 steps: each member matches its
+    oracle run within fp32_bound and equals, bit for bit, the same member solved alone."""
+    sizes = (8, 9, 12, 20, 21, 37, 100)
+    probs = []
+    for i, n in enumerate(sizes * 3):
+        p = W.bounded_config("4.1", 1e-3, 2.05 + 0.01 * i, 0.1, scheme=1 | NOA, dx=60.0 / (n - 1))
+        p.meta["depth"] = depths[i % len(depths)]
+        if p.N < 2 * (2 + p.meta["depth"]):
+            p.meta["depth"] = 2
+        probs.append(p)
+    steps = probs[0].nsteps
+    phib = np.concatenate([W.boundary_values(p, 2, 0, steps).ravel() for p in probs])
+    b = L.Batch(probs, precision=L.FP32_DEV)
+    b.set_phi(np.concatenate([p.phi0 for p in probs])).step_nee(steps, phib, steps * 4)
+    got = b.read_phi()
+    b.close()
+    for i, p in enumerate(probs):
+        seg = got[b.offsets[i]: b.offsets[i + 1]]
+        s = L.Solver.for_problem(p, precision=L.FP32_DEV)
+        alone = s.set_phi(p.phi0).step_nee(steps, W.boundary_values(p, 2, 0, steps)).read_phi()
+        s.close()
+        assert np.array_equal(seg, alone), (i, p.N, p.meta["depth"])
+        assert normwise(seg, oracle_run(p)) <= fp32_bound(p), (i, p.N, p.meta["depth"])
