@@ -292,6 +292,25 @@ int lbhpde_batch_set_kernel(lbhpde_batch_t b, int kernel, int nodes_per_thread, 
 int lbhpde_batch_size(lbhpde_batch_t b, long *total_nodes, size_t *device_bytes);
 int lbhpde_batch_destroy(lbhpde_batch_t b);
 
+/* ------------------------------------------------------------ checkpoint / resume */
+
+/* The paper has no checkpoint; these keep a long solve restartable.  A checkpoint holds the
+ * batch's full state (every member's phi and stored populations, in the batch's precision, as
+ * on the device), the steps taken, and a fingerprint of the layout (member count, sizes,
+ * lattices, depths, precision).  Loading it into a batch created with the same members
+ * continues bit for bit as the saved batch would have; the members' models are the loading
+ * batch's own.  Both calls copy through host memory and synchronise the batch's stream.
+ *   bytes: the size of buf; checkpoint_size gives the size needed.
+ * Errors: LBHPDE_ERR_ARG for a NULL argument, a buffer that is too small, saving a batch whose
+ * phi was never set, or loading a checkpoint of another layout or precision (nothing changes). */
+int lbhpde_batch_checkpoint_size(lbhpde_batch_t b, size_t *bytes);
+int lbhpde_batch_save(lbhpde_batch_t b, void *buf, size_t bytes);
+int lbhpde_batch_load(lbhpde_batch_t b, const void *buf, size_t bytes);
+/* The same for a single instance. */
+int lbhpde_checkpoint_size(lbhpde_t h, size_t *bytes);
+int lbhpde_save(lbhpde_t h, void *buf, size_t bytes);
+int lbhpde_load(lbhpde_t h, const void *buf, size_t bytes);
+
 /* ------------------------------------------------------------------ serving */
 
 /* A request server: continuous batching of independent solves on one GPU (the paper has no

@@ -1485,6 +1485,74 @@ extern "C" int lbhpde_batch_size(lbhpde_batch_t b, long *total_nodes, size_t *de
     }
     return LBHPDE_OK;
 }
+// ------------------------------------------------------------------ checkpoint / resume
+// A checkpoint is a header (format, layout fingerprint, state bytes, steps taken, precision,
+// member count) followed by the batch's state arena as it is on the device (every member's phi
+// row and stored populations, in the state's type).  Loading it into a batch of the same layout
+// continues bit for bit where the saved batch stood.
+namespace {
+constexpr uint64_t kCkptMagic = 0x314b43504448424cull;  // "LBHDPCK1" read as little-endian bytes
+struct CkptHeader {
+    uint64_t magic, layout, state_bytes;
+    int64_t steps;
+    int32_t precision, count;
+};
+uint64_t layout_fingerprint(const lbhpde_batch_s *bt) {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the layout of every member
+    auto mix = [&](long long v) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (uint64_t)((v >> (8 * i)) & 0xff);
+            h *= 1099511628211ull;
+        }
+    };
+    mix(bt->count);
+    mix((long long)bt->esz);
+    for (int i = 0; i < bt->count; ++i) {
+        mix(bt->N[i]);
+        mix(bt->mi[i].b);
+        mix(bt->segs_h[i].off);
+        mix(bt->segs_h[i].ld);
+        mix(bt->depth[i]);
+    }
+    return h;
+}
+}  // namespace
+
+extern "C" int lbhpde_batch_checkpoint_size(lbhpde_batch_t b, size_t *bytes) {
+    if (!b || !bytes) return LBHPDE_ERR_ARG;
+    *bytes = sizeof(CkptHeader) + b->st_bytes;
+    return LBHPDE_OK;
+}
+extern "C" int lbhpde_batch_save(lbhpde_batch_t b, void *buf, size_t bytes) {
+    if (!b || !buf || !b->initialised || bytes < sizeof(CkptHeader) + b->st_bytes) return LBHPDE_ERR_ARG;
+    CkptHeader h{kCkptMagic, layout_fingerprint(b), b->st_bytes, b->steps, b->precision, b->count};
+    std::memcpy(buf, &h, sizeof h);
+    CK(cudaMemcpyAsync((char *)buf + sizeof h, b->st[b->cur], b->st_bytes, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return LBHPDE_OK;
+}
+extern "C" int lbhpde_batch_load(lbhpde_batch_t b, const void *buf, size_t bytes) {
+    if (!b || !buf || bytes < sizeof(CkptHeader)) return LBHPDE_ERR_ARG;
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (h.magic != kCkptMagic || h.layout != layout_fingerprint(b) || h.state_bytes != b->st_bytes ||
+        h.precision != b->precision || h.count != b->count || h.steps < 0 || bytes < sizeof h + b->st_bytes)
+        return LBHPDE_ERR_ARG;
+    CK(cudaMemcpyAsync(b->st[0], (const char *)buf + sizeof h, b->st_bytes, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));  // the caller may free buf once the call returns
+    b->cur = 0;
+    b->steps = (long)h.steps;
+    b->initialised = true;
+    return LBHPDE_OK;
+}
+extern "C" int lbhpde_checkpoint_size(lbhpde_t h, size_t *bytes) {
+    return h ? lbhpde_batch_checkpoint_size(h->b, bytes) : LBHPDE_ERR_ARG;
+}
+extern "C" int lbhpde_save(lbhpde_t h, void *buf, size_t bytes) { return h ? lbhpde_batch_save(h->b, buf, bytes) : LBHPDE_ERR_ARG; }
+extern "C" int lbhpde_load(lbhpde_t h, const void *buf, size_t bytes) {
+    return h ? lbhpde_batch_load(h->b, buf, bytes) : LBHPDE_ERR_ARG;
+}
+
 extern "C" int lbhpde_batch_destroy(lbhpde_batch_t b) {
     if (!b) return LBHPDE_ERR_ARG;
     b->free_all();

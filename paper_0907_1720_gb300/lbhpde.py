@@ -141,6 +141,12 @@ _SIGS = {
     "lbhpde_batch_set_kernel": (_I, [_V, _I, _I, _I]),
     "lbhpde_batch_size": (_I, [_V, _P(_L), _P(_S)]),
     "lbhpde_batch_destroy": (_I, [_V]),
+    "lbhpde_batch_checkpoint_size": (_I, [_V, _P(_S)]),
+    "lbhpde_batch_save": (_I, [_V, _V, _S]),
+    "lbhpde_batch_load": (_I, [_V, _V, _S]),
+    "lbhpde_checkpoint_size": (_I, [_V, _P(_S)]),
+    "lbhpde_save": (_I, [_V, _V, _S]),
+    "lbhpde_load": (_I, [_V, _V, _S]),
     "lbhpde_phi_diagnostics_noalloc": (_I, [_V, _L, _V, _P(lbhpde_diag), _V]),
     "lbhpde_server_create": (_I, [_P(_V), _I, _S, _I, _I, _I]),
     "lbhpde_submit": (_I, [_V, _P(lbhpde_request), _P(ctypes.c_uint64)]),
@@ -361,6 +367,20 @@ def _current_stream():
 
 # ----------------------------------------------------------------- handles
 
+def _save(h, size_fn, save_fn, where):
+    n = ctypes.c_size_t()
+    _check(size_fn(h, ctypes.byref(n)), where)
+    buf = np.empty(n.value, dtype=np.uint8)
+    _check(save_fn(h, buf.ctypes.data_as(ctypes.c_void_p), buf.size), where)
+    return buf
+
+
+def _load(h, buf, load_fn, where):
+    a = np.ascontiguousarray(np.frombuffer(buf, dtype=np.uint8) if isinstance(buf, (bytes, bytearray)) else buf,
+                             dtype=np.uint8)
+    _check(load_fn(h, a.ctypes.data_as(ctypes.c_void_p), a.size), where)
+
+
 class Solver:
     """One instance (lbhpde_create ... lbhpde_destroy), periodic or bounded (boundary=NEE)."""
 
@@ -431,6 +451,15 @@ class Solver:
         out = lbhpde_model_info()
         _check(lib().lbhpde_get_model(self.h, ctypes.byref(out)), "lbhpde_get_model")
         return out
+
+    def save(self) -> np.ndarray:
+        """lbhpde_save: the instance's checkpoint as a byte array."""
+        return _save(self.h, lib().lbhpde_checkpoint_size, lib().lbhpde_save, "lbhpde_save")
+
+    def load(self, buf):
+        """lbhpde_load: restore a checkpoint made by save() on an instance of the same layout."""
+        _load(self.h, buf, lib().lbhpde_load, "lbhpde_load")
+        return self
 
     def close(self):
         if self.h:
@@ -520,6 +549,15 @@ class Batch:
         n, b = ctypes.c_long(), ctypes.c_size_t()
         _check(lib().lbhpde_batch_size(self.h, ctypes.byref(n), ctypes.byref(b)), "lbhpde_batch_size")
         return n.value, b.value
+
+    def save(self) -> np.ndarray:
+        """lbhpde_batch_save: the batch's checkpoint as a byte array."""
+        return _save(self.h, lib().lbhpde_batch_checkpoint_size, lib().lbhpde_batch_save, "lbhpde_batch_save")
+
+    def load(self, buf):
+        """lbhpde_batch_load: restore a checkpoint made by save() on a batch of the same layout."""
+        _load(self.h, buf, lib().lbhpde_batch_load, "lbhpde_batch_load")
+        return self
 
     def close(self):
         if self.h:
