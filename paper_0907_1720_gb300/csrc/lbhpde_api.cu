@@ -1294,6 +1294,7 @@ int step_bounded(lbhpde_batch_s *bt, long nsteps, const double *pbd, long long s
 
 int batch_step(lbhpde_batch_s *bt, long nsteps, const double *phib = nullptr, long long stride = 0,
                int on_device = 0) {
+    lbh::TraceRange trace("lbhpde.step");
     if (nsteps < 0) return LBHPDE_ERR_ARG;
     if (!bt->initialised) return LBHPDE_ERR_ARG;
     if (bt->nbounded && !phib) return LBHPDE_ERR_ARG;
@@ -1311,6 +1312,7 @@ int batch_step(lbhpde_batch_s *bt, long nsteps, const double *phib = nullptr, lo
 }
 
 int batch_set_phi(lbhpde_batch_s *bt, const double *phi0, int on_device) {
+    lbh::TraceRange trace("lbhpde.set_phi");
     if (!phi0) return LBHPDE_ERR_ARG;
     const double *src = phi0;
     if (!on_device) {
@@ -1331,6 +1333,7 @@ int batch_set_phi(lbhpde_batch_s *bt, const double *phi0, int on_device) {
 }
 
 int batch_read_phi(lbhpde_batch_s *bt, double *out, int on_device) {
+    lbh::TraceRange trace("lbhpde.read_phi");
     if (!out) return LBHPDE_ERR_ARG;
     if (!bt->initialised) return LBHPDE_ERR_ARG;
     double *dst = on_device ? out : bt->phi_buf;
@@ -1356,6 +1359,7 @@ int batch_read_phi(lbhpde_batch_s *bt, double *out, int on_device) {
 }
 
 int batch_diag(lbhpde_batch_s *bt, const double *phistar, lbhpde_diag *out) {
+    lbh::TraceRange trace("lbhpde.diagnostics");
     if (!out) return LBHPDE_ERR_ARG;
     if (!bt->initialised) return LBHPDE_ERR_ARG;
     const int nb = (int)bt->all_blocks_h.size();

@@ -3,6 +3,7 @@
 // kernel launchers.  Implemented in lbhpde_api.cu, so each kernel is compiled once.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -13,6 +14,15 @@
 #include "lbhpde_ring_nee.cuh"
 
 namespace lbh {
+
+// A named NVTX range for the scope (tracing: host phases of the API and of the server show in
+// Nsight timelines and can filter ncu captures; without a tool attached it costs a branch).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 constexpr int kChunk = 1024;          // nodes per block of the node-parallel kernels
 constexpr int kGenericThreads = 256;  // init / readout / diagnostics threads per block

@@ -633,14 +633,24 @@ void worker_main(lbhpde_server_s *S) {
         }
         // admission, set-up and the plan of the next block run while the block in flight runs
         const auto ts = Clock::now();
-        int rc = setup_admitted(S, adm);
+        int rc;
+        {
+            lbh::TraceRange trace("lbhpde.server.setup");
+            rc = setup_admitted(S, adm);
+        }
         for (Req *r : adm) S->active.push_back(r);
         const auto tv = Clock::now();
         Block next;
-        if (rc == LBHPDE_OK) rc = plan_block(S, next);
+        if (rc == LBHPDE_OK) {
+            lbh::TraceRange trace("lbhpde.server.plan");
+            rc = plan_block(S, next);
+        }
         // wait for the block in flight and the set-up of the admitted requests
         const auto tw = Clock::now();
-        if (rc == LBHPDE_OK) rc = cudaStreamSynchronize(S->stream) == cudaSuccess ? LBHPDE_OK : LBHPDE_ERR_CUDA;
+        if (rc == LBHPDE_OK) {
+            lbh::TraceRange trace("lbhpde.server.wait");
+            rc = cudaStreamSynchronize(S->stream) == cudaSuccess ? LBHPDE_OK : LBHPDE_ERR_CUDA;
+        }
         const auto tr = Clock::now();
         if (rc == LBHPDE_OK) rc = complete_block(S, inflight);
         const long long done_id = inflight.id;
@@ -668,6 +678,7 @@ void worker_main(lbhpde_server_s *S) {
             S->t_retire += std::chrono::duration<double>(Clock::now() - tr).count();
         }
         if (rc == LBHPDE_OK && next.id >= 0) {
+            lbh::TraceRange trace("lbhpde.server.launch");
             rc = launch_block(S, next);
             if (rc == LBHPDE_OK) inflight = std::move(next);
         }
