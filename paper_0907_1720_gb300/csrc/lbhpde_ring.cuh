@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     constexpr int TS = NE * kRingMaxInst;  // one parity of the tails
     constexpr int RCH = 8;                 // Horner chunk (12 and 16 were slower on GB300; no spills)
     static_assert(K >= 2 * W + 1, "a thread must own interior nodes");
+    static_assert(std::is_same<T, float>::value, "the 16-node kernel is FP32 (packed pairs)");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *R = reinterpret_cast<T *>(smem_raw);                   // [2][NE][MAXT]
     T *L = R + 2 * PS;                                        // [2][NE][MAXT]
@@ -306,7 +307,32 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
 #pragma unroll
             for (int j = 1; j < B; ++j) {
                 const int e = vel(j);
-                if (e > 0) {
+                if (e == 2 && K % 2 == 0) {
+                    // |e| = 2: a pair of nodes (k, k + 1) pulls from the pair (k - 2, k - 1), so
+                    // the difference and its sum into d take one packed operation each (a
+                    // multiply-add by -1 rounds as the subtraction; each half as one operation)
+#pragma unroll
+                    for (int k = K - 2; k >= 2; k -= 2) {
+                        const float2 nv = make_float2(v[j][k - 2], v[j][k - 1]);
+                        const float2 df = __ffma2_rn(make_float2(v[j][k], v[j][k + 1]), make_float2(-1.f, -1.f), nv);
+                        const float2 dd = __fadd2_rn(make_float2(d[k], d[k + 1]), df);
+                        d[k] = dd.x;
+                        d[k + 1] = dd.y;
+                        v[j][k] = nv.x;
+                        v[j][k + 1] = nv.y;
+                    }
+                } else if (e == -2 && K % 2 == 0) {
+#pragma unroll
+                    for (int k = 0; k + 2 < K; k += 2) {
+                        const float2 nv = make_float2(v[j][k + 2], v[j][k + 3]);
+                        const float2 df = __ffma2_rn(make_float2(v[j][k], v[j][k + 1]), make_float2(-1.f, -1.f), nv);
+                        const float2 dd = __fadd2_rn(make_float2(d[k], d[k + 1]), df);
+                        d[k] = dd.x;
+                        d[k + 1] = dd.y;
+                        v[j][k] = nv.x;
+                        v[j][k + 1] = nv.y;
+                    }
+                } else if (e > 0) {
 #pragma unroll
                     for (int k = K - 1; k >= e; --k) {
                         const T nv = v[j][k - e];
@@ -351,7 +377,11 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
                 }
             }
 #pragma unroll
-            for (int k = 0; k < K; ++k) phi[k] += d[k];
+            for (int k = 0; k < K; k += 2) {  // phi takes the sums once, two nodes per packed add
+                const float2 p2 = __fadd2_rn(make_float2(phi[k], phi[k + 1]), make_float2(d[k], d[k + 1]));
+                phi[k] = p2.x;
+                phi[k + 1] = p2.y;
+            }
             ring_relax<T, B, K, DC, RCH, 0, K>(sc, cs, D, omw, phi, v);
         }
     };
