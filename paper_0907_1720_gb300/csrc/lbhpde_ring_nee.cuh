@@ -108,6 +108,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     constexpr int OS = kRingMaxInst * 2 * W * B;  // one parity of the outer-node blocks
     constexpr int RCH = 8;                        // Horner chunk, as in k_ring
     static_assert(K >= 2 * W + 1 && K <= 16, "nodes a thread");
+    static_assert(std::is_same<T, float>::value, "the bounded 16-node kernel is FP32 (packed pairs)");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *R = reinterpret_cast<T *>(smem_raw);  // [2][NE][MAXT]
     T *L = R + 2 * PS;                        // [2][NE][MAXT]
@@ -391,7 +392,30 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
 #pragma unroll
         for (int j = 1; j < B; ++j) {
             const int e = vel(j);
-            if (e > 0) {
+            if (e == 2 && K % 2 == 0) {
+                // |e| = 2: pairs of nodes in one packed operation each (as in k_ring)
+#pragma unroll
+                for (int k = K - 2; k >= 2; k -= 2) {
+                    const float2 nv = make_float2(v[j][k - 2], v[j][k - 1]);
+                    const float2 df = __ffma2_rn(make_float2(v[j][k], v[j][k + 1]), make_float2(-1.f, -1.f), nv);
+                    const float2 dd = __fadd2_rn(make_float2(d[k], d[k + 1]), df);
+                    d[k] = dd.x;
+                    d[k + 1] = dd.y;
+                    v[j][k] = nv.x;
+                    v[j][k + 1] = nv.y;
+                }
+            } else if (e == -2 && K % 2 == 0) {
+#pragma unroll
+                for (int k = 0; k + 2 < K; k += 2) {
+                    const float2 nv = make_float2(v[j][k + 2], v[j][k + 3]);
+                    const float2 df = __ffma2_rn(make_float2(v[j][k], v[j][k + 1]), make_float2(-1.f, -1.f), nv);
+                    const float2 dd = __fadd2_rn(make_float2(d[k], d[k + 1]), df);
+                    d[k] = dd.x;
+                    d[k + 1] = dd.y;
+                    v[j][k] = nv.x;
+                    v[j][k + 1] = nv.y;
+                }
+            } else if (e > 0) {
 #pragma unroll
                 for (int k = K - 1; k >= e; --k) {
                     const T nv = v[j][k - e];
@@ -434,7 +458,11 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
             }
         }
 #pragma unroll
-        for (int k = 0; k < K; ++k) phi[k] += d[k];
+        for (int k = 0; k < K; k += 2) {  // two nodes per packed add
+            const float2 p2 = __fadd2_rn(make_float2(phi[k], phi[k + 1]), make_float2(d[k], d[k + 1]));
+            phi[k] = p2.x;
+            phi[k + 1] = p2.y;
+        }
         ring_relax<T, B, K, DC, RCH, 0, K>(sc, cs, D, omw, phi, v);
         // the rebuild of the inflow values (population j with |e_j| = a at its a nodes next to
         // the interior) from x_f's phi and s_j, which pass through this thread's column of X
