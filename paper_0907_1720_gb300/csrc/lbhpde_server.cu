@@ -554,19 +554,20 @@ int complete_block(lbhpde_server_s *S, Block &blk) {
     return LBHPDE_OK;
 }
 
-// Copy a finished request's phi to the host and release its device resources.
+// Copy a finished request's phi to the host and release its device resources.  The copy runs on
+// the set-up stream, beside the block in flight (which does not touch the request).
 int retire(lbhpde_server_s *S, Req *r) {
     r->phi.resize(r->N);
     if (S->esz == 4) {
         std::vector<float> tmp(r->N);
         SCK(cudaMemcpyAsync(tmp.data(), (float *)S->arena_d + r->off[r->cur], sizeof(float) * r->N,
-                            cudaMemcpyDeviceToHost, S->stream));
-        SCK(cudaStreamSynchronize(S->stream));
+                            cudaMemcpyDeviceToHost, S->up));
+        SCK(cudaStreamSynchronize(S->up));
         for (long long i = 0; i < r->N; ++i) r->phi[i] = tmp[i];
     } else {
         SCK(cudaMemcpyAsync(r->phi.data(), (double *)S->arena_d + r->off[r->cur], sizeof(double) * r->N,
-                            cudaMemcpyDeviceToHost, S->stream));
-        SCK(cudaStreamSynchronize(S->stream));
+                            cudaMemcpyDeviceToHost, S->up));
+        SCK(cudaStreamSynchronize(S->up));
     }
     double sum = 0.0;
     long nf = 0;
@@ -661,8 +662,17 @@ void worker_main(lbhpde_server_s *S) {
             S->t_setup += std::chrono::duration<double>(tv - ts).count();
             S->t_wait += std::chrono::duration<double>(tr - tw).count();
         }
-        // retire the requests whose last block has completed (and those that take no steps);
-        // the ones that finish in the planned block stay until it has run
+        // the next block goes to the GPU first; the requests whose last block has completed (and
+        // those that take no steps) are retired while it runs (their copies on the set-up stream;
+        // the block touches none of them).  The ones that finish in the next block stay until it
+        // has run.
+        const auto tl = Clock::now();
+        if (rc == LBHPDE_OK && next.id >= 0) {
+            lbh::TraceRange trace("lbhpde.server.launch");
+            rc = launch_block(S, next);
+            if (rc == LBHPDE_OK) inflight = std::move(next);
+        }
+        const auto tt = Clock::now();
         std::vector<Req *> still;
         for (Req *r : S->active) {
             if (rc == LBHPDE_OK && r->done >= r->nsteps && r->final_block <= done_id) {
@@ -675,12 +685,8 @@ void worker_main(lbhpde_server_s *S) {
         S->active.swap(still);
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            S->t_retire += std::chrono::duration<double>(Clock::now() - tr).count();
-        }
-        if (rc == LBHPDE_OK && next.id >= 0) {
-            lbh::TraceRange trace("lbhpde.server.launch");
-            rc = launch_block(S, next);
-            if (rc == LBHPDE_OK) inflight = std::move(next);
+            S->t_retire += std::chrono::duration<double>(Clock::now() - tt).count() +
+                           std::chrono::duration<double>(tl - tr).count();
         }
         if (rc != LBHPDE_OK) {
             std::lock_guard<std::mutex> lk(S->mu);
