@@ -646,32 +646,33 @@ void worker_main(lbhpde_server_s *S) {
             lbh::TraceRange trace("lbhpde.server.plan");
             rc = plan_block(S, next);
         }
-        // wait for the block in flight and the set-up of the admitted requests
+        // the next block is queued behind the one in flight, so the GPU goes from one to the other
+        // without waiting for the host; then the host waits for the block in flight only (the
+        // next one touches no request that the block in flight finishes)
+        Block launched;
+        if (rc == LBHPDE_OK && next.id >= 0) {
+            lbh::TraceRange trace("lbhpde.server.launch");
+            rc = launch_block(S, next);
+            if (rc == LBHPDE_OK) launched = std::move(next);
+        }
         const auto tw = Clock::now();
-        if (rc == LBHPDE_OK) {
+        if (rc == LBHPDE_OK && inflight.id >= 0) {
             lbh::TraceRange trace("lbhpde.server.wait");
-            rc = cudaStreamSynchronize(S->stream) == cudaSuccess ? LBHPDE_OK : LBHPDE_ERR_CUDA;
+            rc = cudaEventSynchronize(S->ev_t1[inflight.id & 1]) == cudaSuccess ? LBHPDE_OK : LBHPDE_ERR_CUDA;
         }
         const auto tr = Clock::now();
         if (rc == LBHPDE_OK) rc = complete_block(S, inflight);
         const long long done_id = inflight.id;
-        inflight = Block{};
+        inflight = std::move(launched);
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->t_admit += std::chrono::duration<double>(ts - ta).count();
             S->t_setup += std::chrono::duration<double>(tv - ts).count();
             S->t_wait += std::chrono::duration<double>(tr - tw).count();
         }
-        // the next block goes to the GPU first; the requests whose last block has completed (and
-        // those that take no steps) are retired while it runs (their copies on the set-up stream;
-        // the block touches none of them).  The ones that finish in the next block stay until it
-        // has run.
-        const auto tl = Clock::now();
-        if (rc == LBHPDE_OK && next.id >= 0) {
-            lbh::TraceRange trace("lbhpde.server.launch");
-            rc = launch_block(S, next);
-            if (rc == LBHPDE_OK) inflight = std::move(next);
-        }
+        // the requests whose last block has completed (and those that take no steps) are retired
+        // while the next block runs (their copies on the set-up stream); the ones that finish in
+        // a block still queued or running stay until it has run
         const auto tt = Clock::now();
         std::vector<Req *> still;
         for (Req *r : S->active) {
@@ -685,8 +686,7 @@ void worker_main(lbhpde_server_s *S) {
         S->active.swap(still);
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            S->t_retire += std::chrono::duration<double>(Clock::now() - tt).count() +
-                           std::chrono::duration<double>(tl - tr).count();
+            S->t_retire += std::chrono::duration<double>(Clock::now() - tt).count();
         }
         if (rc != LBHPDE_OK) {
             std::lock_guard<std::mutex> lk(S->mu);
