@@ -271,14 +271,46 @@ def _boundary_code(p):
     return PERIODIC
 
 
-def _phib_arg(phib):
-    """(pointer, on_device, keep-alive) for boundary values given as a torch tensor or array."""
-    if phib is None:
+def _on_device(x):
+    return hasattr(x, "data_ptr") and bool(getattr(x, "is_cuda", False))
+
+
+def _host_array(x):
+    """A C-contiguous float64 view of host data (a CPU tensor's own memory, so page-locked memory
+    stays page-locked), copied only when its layout or type requires it."""
+    if hasattr(x, "data_ptr"):
+        x = x.detach().numpy()
+    return np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+
+
+def _in_arg(x, n=None):
+    """(pointer, on_device, keep-alive) for a double input: a CUDA tensor is passed as device
+    memory, anything else as host memory."""
+    if x is None:
         return None, 0, None
-    if hasattr(phib, "data_ptr"):
-        return ctypes.c_void_p(phib.data_ptr()), 1, phib
-    a = np.ascontiguousarray(np.asarray(phib, dtype=np.float64))
+    if _on_device(x):
+        return ctypes.c_void_p(x.data_ptr()), 1, x
+    a = _host_array(x)
+    assert n is None or a.size == n
     return a.ctypes.data_as(ctypes.c_void_p), 0, a
+
+
+def _out_arg(out, n):
+    """(pointer, on_device, result, host array) for a [n] double output: a CUDA tensor (device),
+    a float64 host array or CPU tensor written in place, or a new array."""
+    if out is None:
+        a = np.empty(n)
+        return a.ctypes.data_as(ctypes.c_void_p), 0, a, a
+    if _on_device(out):
+        return ctypes.c_void_p(out.data_ptr()), 1, out, None
+    a = out.detach().numpy() if hasattr(out, "data_ptr") else out
+    assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == n, "output: [n] contiguous float64"
+    return a.ctypes.data_as(ctypes.c_void_p), 0, out, a
+
+
+def _phib_arg(phib):
+    """(pointer, on_device, keep-alive) for boundary values given as a tensor or array."""
+    return _in_arg(phib)
 
 
 def autotune(precision, lattice, degree):
@@ -405,12 +437,9 @@ class Solver:
         return self
 
     def set_phi(self, phi0):
-        if hasattr(phi0, "data_ptr"):
-            _check(lib().lbhpde_set_phi(self.h, ctypes.c_void_p(phi0.data_ptr()), 1), "lbhpde_set_phi")
-        else:
-            a = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64))
-            assert a.size == self.N
-            _check(lib().lbhpde_set_phi(self.h, a.ctypes.data_as(ctypes.c_void_p), 0), "lbhpde_set_phi")
+        """phi0: [N] doubles, a CUDA tensor (device) or host memory (array or CPU tensor)."""
+        ptr, dev, keep = _in_arg(phi0, self.N)
+        _check(lib().lbhpde_set_phi(self.h, ptr, dev), "lbhpde_set_phi")
         return self
 
     def step(self, nsteps):
@@ -424,14 +453,12 @@ class Solver:
         return self
 
     def read_phi(self, out=None, check=True):
-        if out is not None and hasattr(out, "data_ptr"):
-            rc = lib().lbhpde_read_phi(self.h, ctypes.c_void_p(out.data_ptr()), 1)
-        else:
-            out = np.empty(self.N)
-            rc = lib().lbhpde_read_phi(self.h, out.ctypes.data_as(ctypes.c_void_p), 0)
+        """phi into out ([N] doubles: a CUDA tensor, a host array or CPU tensor; None: a new array)."""
+        ptr, dev, res, keep = _out_arg(out, self.N)
+        rc = lib().lbhpde_read_phi(self.h, ptr, dev)
         if check or rc != ERR_DIVERGED:
             _check(rc, "lbhpde_read_phi")
-        return out
+        return res
 
     def diagnostics(self, phistar_device=None) -> dict:
         d = lbhpde_diag()
@@ -496,12 +523,9 @@ class Batch:
         return self
 
     def set_phi(self, phi0):
-        if hasattr(phi0, "data_ptr"):
-            _check(lib().lbhpde_batch_set_phi(self.h, ctypes.c_void_p(phi0.data_ptr()), 1), "lbhpde_batch_set_phi")
-        else:
-            a = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64))
-            assert a.size == self.total
-            _check(lib().lbhpde_batch_set_phi(self.h, a.ctypes.data_as(ctypes.c_void_p), 0), "lbhpde_batch_set_phi")
+        """phi0: [sum N] doubles, a CUDA tensor (device) or host memory (array or CPU tensor)."""
+        ptr, dev, keep = _in_arg(phi0, self.total)
+        _check(lib().lbhpde_batch_set_phi(self.h, ptr, dev), "lbhpde_batch_set_phi")
         return self
 
     def step(self, nsteps):
@@ -517,14 +541,13 @@ class Batch:
         return self
 
     def read_phi(self, out=None, check=True):
-        if out is not None and hasattr(out, "data_ptr"):
-            rc = lib().lbhpde_batch_read_phi(self.h, ctypes.c_void_p(out.data_ptr()), 1)
-        else:
-            out = np.empty(self.total)
-            rc = lib().lbhpde_batch_read_phi(self.h, out.ctypes.data_as(ctypes.c_void_p), 0)
+        """phi into out ([sum N] doubles: a CUDA tensor, a host array or CPU tensor; None: a new
+        array)."""
+        ptr, dev, res, keep = _out_arg(out, self.total)
+        rc = lib().lbhpde_batch_read_phi(self.h, ptr, dev)
         if check or rc != ERR_DIVERGED:
             _check(rc, "lbhpde_batch_read_phi")
-        return out
+        return res
 
     def split(self, flat):
         return [flat[self.offsets[i]:self.offsets[i + 1]] for i in range(len(self.sizes))]
