@@ -291,7 +291,8 @@ def _in_arg(x, n=None):
     if _on_device(x):
         return ctypes.c_void_p(x.data_ptr()), 1, x
     a = _host_array(x)
-    assert n is None or a.size == n
+    if n is not None and a.size != n:
+        raise ValueError(f"input of {a.size} values, {n} expected")
     return a.ctypes.data_as(ctypes.c_void_p), 0, a
 
 
@@ -304,7 +305,8 @@ def _out_arg(out, n):
     if _on_device(out):
         return ctypes.c_void_p(out.data_ptr()), 1, out, None
     a = out.detach().numpy() if hasattr(out, "data_ptr") else out
-    assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == n, "output: [n] contiguous float64"
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.size == n):
+        raise ValueError(f"output: a contiguous float64 buffer of {n} values expected")
     return a.ctypes.data_as(ctypes.c_void_p), 0, out, a
 
 
@@ -616,8 +618,9 @@ class Server:
         for k in range(eq.m):
             q.alpha[k] = float(eq.alpha[k])
             q.pi[k] = pis[k]
-        a = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64))
-        assert a.size == N
+        a = _host_array(phi0)
+        if a.size != N:
+            raise ValueError(f"phi0 of {a.size} values, N = {N}")
         q.N, q.dx, q.dt, q.tau, q.lattice, q.scheme, q.nsteps = int(N), float(dx), float(dt), float(tau), \
             int(eq.lattice), int(scheme), int(nsteps)
         q.phi0 = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))

@@ -39,7 +39,7 @@ def test_inputs():
     ptr, dev, keep = L._in_arg([1, 2, 3], 3)  # other types: converted to a float64 array
     assert dev == 0 and keep.dtype == np.float64 and list(keep) == [1.0, 2.0, 3.0]
     assert L._in_arg(None) == (None, 0, None)
-    with pytest.raises(AssertionError):
+    with pytest.raises(ValueError):
         L._in_arg(a, 9)
 
 
@@ -55,7 +55,7 @@ def test_outputs_in_place():
     f = FakeCuda()
     ptr, dev, res, host = L._out_arg(f, 8)
     assert dev == 1 and res is f
-    with pytest.raises(AssertionError):
+    with pytest.raises(ValueError):
         L._out_arg(np.empty(8, dtype=np.float32), 8)
-    with pytest.raises(AssertionError):
+    with pytest.raises(ValueError):
         L._out_arg(np.empty(16)[::2], 8)
