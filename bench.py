@@ -365,6 +365,10 @@ def run_ours(args, rank, world, cpu=None):
 
         # end to end through the public API, host buffers
         e2e_steps = 0 if args.quick else max(3, args.steps)  # as many steps as the timed region
+        if e2e_steps:  # one untimed step through the same calls (first-touch of the host buffers)
+            solver.set_phi(pinned_in)
+            advance(phib_h)
+            solver.read_phi(pinned_out.numpy())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
