@@ -1,6 +1,7 @@
 // Host-side check of the on-chip planning (no GPU): size classes, resident packing and window
-// cutting on random member sets, and the position shift of bounded resident instances, called
-// through the library's exported functions.  Prints
+// cutting on random member sets, the position shift of bounded resident instances, and the
+// packing of bounded members on the 16-node kernel, called through the library's exported
+// functions.  Prints
 // "ok" and exits 0 when every invariant holds; otherwise prints the first violation and exits 1.
 #include <cstdio>
 #include <cstdlib>
@@ -199,6 +200,65 @@ int main() {
             }
     }
     CHECK(shifted > 10000, "only %lld bounded cases placed", shifted);
+
+    // bounded members on the 16-node kernel (pack_ring_nee, FP32 D1Q5): every member once, thread
+    // runs of ceil((N - 2W) / 16) threads one after the other, at most 32 instances a CTA and at
+    // least one thread per helper role (2 nedge(B) an instance) in the launch, coefficient blocks
+    // of nee_cblock at 16-byte aligned offsets, shared memory within 227 KB, and the depth-2
+    // variant chosen exactly when every member has depth 2 and 2 or more nodes in its last thread
+    for (int trial = 0; trial < 60; ++trial) {
+        const int b = 5, W = 2, K = lbh::kRingK, dc = trial % 3 ? 5 : 0;
+        std::uniform_int_distribution<int> dcount(1, 400), ddepth(1, 4);
+        const bool only2 = trial % 2 == 0;
+        const long long nmax = trial % 5 == 0 ? 40 : 512LL * K + 2 * W;
+        std::vector<lbh::NeeMember> m;
+        const int count = dcount(g);
+        long long off = 0;
+        bool d2 = true;
+        for (int i = 0; i < count; ++i) {
+            lbh::NeeMember x{};
+            x.seg.pad = only2 ? 2 : ddepth(g);
+            std::uniform_int_distribution<long long> dn(2 * (W + x.seg.pad), nmax);
+            x.seg.N = (int)dn(g);
+            x.seg.ld = (x.seg.N + 31) / 32 * 32;
+            x.seg.off = off;
+            x.seg.D = 5;
+            x.mi = i;
+            x.steps = 1 << 30;
+            off += x.seg.ld * b;
+            const int thr = (x.seg.N - 2 * W + K - 1) / K;
+            if (x.seg.pad != 2 || x.seg.N - 2 * W - K * (thr - 1) < 2) d2 = false;
+            CHECK(lbh::ring_nee_ok(4, b, x.seg), "ring_nee_ok refused N = %d depth %d", x.seg.N, x.seg.pad);
+            m.push_back(x);
+        }
+        lbh::PackedNee p;
+        CHECK(lbh::pack_ring_nee(b, dc, m, p, 512) == LBHPDE_OK, "pack_ring_nee failed (trial %d)", trial);
+        CHECK(p.d2 == d2, "depth-2 variant %d, expected %d (trial %d)", (int)p.d2, (int)d2, trial);
+        CHECK(p.nthreads % 32 == 0 && p.nthreads <= 512 && p.stride == 512, "launch of %d threads", p.nthreads);
+        CHECK(p.smem <= 227 * 1024, "shared memory %zu", p.smem);
+        std::set<int> seen;
+        for (int c = 0; c < p.ncta(); ++c) {
+            const int i0 = p.first[c], i1 = p.first[c + 1];
+            CHECK(i1 > i0 && i1 - i0 <= lbk::kRingMaxInst, "cta %d holds %d instances", c, i1 - i0);
+            CHECK((i1 - i0) * lbk::nee_roles(b) <= p.nthreads, "cta %d: %d helper roles, %d threads", c,
+                  (i1 - i0) * lbk::nee_roles(b), p.nthreads);
+            int tb = 0, sco = 0;
+            for (int i = i0; i < i1; ++i) {
+                const lbk::RingNeeInst &I = p.insts[i];
+                CHECK(I.tbase == tb, "instance %d: thread base %d, expected %d", i, I.tbase, tb);
+                CHECK(I.nthr == (I.N - 2 * W + K - 1) / K, "instance %d: %d threads for N = %d", i, I.nthr, I.N);
+                CHECK(I.il == i - i0, "instance %d: block %d", i, I.il);
+                CHECK(I.scoef == sco && I.scoef % 4 == 0, "instance %d: coefficient offset %d", i, I.scoef);
+                CHECK(I.depth == m[I.mi].seg.pad && I.N == m[I.mi].seg.N && I.off == m[I.mi].seg.off,
+                      "instance %d: member %d", i, I.mi);
+                sco += lbk::nee_cblock(b, dc > 0 ? dc : I.D);
+                tb += I.nthr;
+                CHECK(seen.insert(I.mi).second, "member %d placed twice", I.mi);
+            }
+            CHECK(tb <= p.nthreads, "cta %d: %d threads of runs, launch of %d", c, tb, p.nthreads);
+        }
+        CHECK((int)seen.size() == count, "%zu of %d members placed", seen.size(), count);
+    }
     if (fails) {
         std::printf("%d failures\n", fails);
         return 1;

@@ -7,7 +7,10 @@ the CTA size; at most 32 instances per CTA; 16-byte aligned coefficient offsets;
 move up a size class; the valid nodes of a member's windows cover each of its nodes exactly
 once; window depths leave the stated share of a window valid; for bounded resident instances,
 the position shift puts each end's outer nodes and extrapolation node in one warp inside the CTA
-(every depth 1-4 and grid size up to the CTA's 2048 nodes).
+(every depth 1-4 and grid size up to the CTA's 2048 nodes); for bounded members on the 16-node
+kernel, contiguous thread runs, at most 32 instances and enough threads for the helper roles in
+every CTA, aligned coefficient blocks, shared memory within 227 KB, and the depth-2 variant chosen
+exactly when every member allows it.
 """
 import os
 import shutil
