@@ -251,16 +251,34 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
                 }
             }
             if (near_end) {
+                // tail slot i of a right-moving population holds node N - e + i, at the position
+                // k = rem - e + i of this thread: one compile-time case of rem (1 .. K + W - 1)
+                auto tput = [&](auto rc) {
+                    constexpr int R = decltype(rc)::value;
 #pragma unroll
-                for (int j = 1; j < B; ++j) {
-                    const int e = vel(j);
-                    if (e > 0) {
+                    for (int j = 1; j < B; ++j) {
+                        const int e = vel(j);
+                        if (e > 0) {
 #pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            const int x = xb + k;
-                            if (x >= N - e && x < N) Tme[P * TS + (eslot(e) + x - (N - e)) * kRingMaxInst] = v[j][k];
+                            for (int i = 0; i < e; ++i)
+                                if (R - e + i >= 0 && R - e + i < K)
+                                    Tme[P * TS + (eslot(e) + i) * kRingMaxInst] = v[j][R - e + i];
                         }
                     }
+                };
+                static_assert(K + W - 1 <= 18, "tail cases");
+                switch (rem) {
+#define LBK_RING_TAIL(R)                        \
+    case R:                                     \
+        tput(std::integral_constant<int, R>{}); \
+        break;
+                    LBK_RING_TAIL(1) LBK_RING_TAIL(2) LBK_RING_TAIL(3) LBK_RING_TAIL(4) LBK_RING_TAIL(5)
+                    LBK_RING_TAIL(6) LBK_RING_TAIL(7) LBK_RING_TAIL(8) LBK_RING_TAIL(9) LBK_RING_TAIL(10)
+                    LBK_RING_TAIL(11) LBK_RING_TAIL(12) LBK_RING_TAIL(13) LBK_RING_TAIL(14) LBK_RING_TAIL(15)
+                    LBK_RING_TAIL(16) LBK_RING_TAIL(17) LBK_RING_TAIL(18)
+#undef LBK_RING_TAIL
+                    default:
+                        break;
                 }
             }
         }
@@ -360,7 +378,8 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
                         d[k] += nv - v[j][k];
                         v[j][k] = nv;
                     }
-                } else {
+                } else if (near_end) {
+                    // near-end threads only (a branch, not a select in every thread)
                     const int a = -e;
 #pragma unroll
                     for (int k = K - a; k < K; ++k) {
@@ -371,6 +390,15 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
                         const T *src = k + a >= rem ? Lhd + P * PS + (eslot(a) + q) * MAXT
                                                     : Lrt + P * PS + (eslot(a) + k + a - K) * MAXT;
                         const T nv = *src;
+                        d[k] += nv - v[j][k];
+                        v[j][k] = nv;
+                    }
+                } else {
+                    // the other threads (rem >= K + W): every source is the next thread's
+                    const int a = -e;
+#pragma unroll
+                    for (int k = K - a; k < K; ++k) {
+                        const T nv = Lrt[P * PS + (eslot(a) + k + a - K) * MAXT];
                         d[k] += nv - v[j][k];
                         v[j][k] = nv;
                     }
