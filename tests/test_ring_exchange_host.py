@@ -3,8 +3,10 @@ paper_0907_1720_gb300/csrc/lbhpde_ring.cuh), no GPU.
 
 The emulation restates the kernel's index arithmetic for one CTA holding several periodic
 instances in thread-granular runs of 16 nodes a thread (instances may share a warp):
-publication of the edge populations (R, L) and of the wrap-around tail, the pull from own
-registers, from the neighbours' slots and, past an instance's last node, from its head slots.  Checked against the exact periodic shift f_j(x) = s_j((x - e_j) mod N) of Eq. (LBE) for
+publication of the edge populations (R, L) and of the wrap-around tail (one case of the
+remainder N - xb in the last threads), the pull from own registers, from the neighbours' slots
+and, past an instance's last node, from its head slots (a branch taken by the last two threads
+of an instance only).  Checked against the exact periodic shift f_j(x) = s_j((x - e_j) mod N) of Eq. (LBE) for
 every node, D1Q5, many instance sizes, including N = 4 (the minimum, 2 max|e|), N = 16 r + 1 and
 every remainder mod 16.  Every shared-memory index is checked to stay inside its buffer.
 
@@ -88,15 +90,19 @@ def emulate_pull(sizes, rng):
                 for q in range(-e):
                     L[(eslot(-e) + q) * MAXT + tid] = v[tid, j, q]
         if near_end:
+            # one case of the remainder R = N - xb (1 .. K + W - 1): tail slot q of a right-moving
+            # population takes position R - e + q, node N - e + q, where this thread holds it
+            R_ = N - t * K
+            assert 1 <= R_ <= K + W - 1
             for j in range(1, B):
                 e = VEL[j]
                 if e > 0:
-                    for k in range(K):
-                        x = t * K + k
-                        if N - e <= x < N:
-                            slot = eslot(e) + x - (N - e)
-                            assert 0 <= slot < NE and 0 <= il < MAXI
-                            T[slot * MAXI + il] = v[tid, j, k]
+                    for q in range(e):
+                        k = R_ - e + q
+                        if 0 <= k < K:
+                            assert t * K + k == N - e + q
+                            assert 0 <= eslot(e) + q < NE and 0 <= il < MAXI
+                            T[(eslot(e) + q) * MAXI + il] = v[tid, j, k]
     new = np.full((nt, B, K), np.nan)
     for tid in range(nt):
         if owner[tid] < 0:
@@ -129,6 +135,10 @@ def emulate_pull(sizes, rng):
                     a = -e
                     if k + a < K:
                         nv = w[j, k + a]
+                    elif not near_end:
+                        # the branch of the other threads: never a source past node N - 1
+                        assert k + a < rem and rt == tid + 1
+                        nv = L[(eslot(a) + k + a - K) * MAXT + rt]
                     elif k + a >= rem:
                         nv = L[(eslot(a) + min(k + a - rem, a - 1)) * MAXT + tb]
                     else:
