@@ -132,12 +132,12 @@ __device__ __forceinline__ void ring_relax(const T *sc, int cs, int D, T omw, co
 // registers); a smaller CTA asks for the registers of 512 / MAXT CTAs per SM.
 __host__ __device__ constexpr int ring_minb(int MAXT) { return 512 / MAXT > 1 ? 512 / MAXT : 1; }
 
-// Shared memory of a k_ring launch: the exchange buffers R and L (two step parities each, row
-// stride MAXT, the CTA size of the plan's class), the wrap-around tails (row stride
-// kRingMaxInst) and the coefficient rows.  Compile-time strides keep every exchange address an
-// immediate offset from one per-thread base.
+// Shared memory of a k_ring launch: the exchange buffers R and L and the wrap-around tails (two
+// step parities each, row stride MAXT, the CTA size of the plan's class; an instance's tail sits
+// in the column of its first thread) and the coefficient rows.  Compile-time strides keep every
+// exchange address an immediate offset from one per-thread base.
 constexpr int kRingMaxInst = 32;  // instances per CTA (the packer's limit)
-__host__ __device__ constexpr int ring_xchg_elems(int B, int MAXT) { return 4 * nedge(B) * MAXT + 2 * nedge(B) * kRingMaxInst; }
+__host__ __device__ constexpr int ring_xchg_elems(int B, int MAXT) { return 6 * nedge(B) * MAXT; }
 
 template <typename T, int B, int K, int MAXT, int DC>
 __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
@@ -145,16 +145,15 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
            const int *__restrict__ cta_first, const T *__restrict__ coefs, int nsteps) {
     constexpr int W = wmax(B);
     constexpr int NE = nedge(B);
-    constexpr int PS = NE * MAXT;          // one parity of R (or L)
-    constexpr int TS = NE * kRingMaxInst;  // one parity of the tails
+    constexpr int PS = NE * MAXT;          // one parity of R, L or the tails
     constexpr int RCH = 8;                 // Horner chunk (12 and 16 were slower on GB300; no spills)
     static_assert(K >= 2 * W + 1, "a thread must own interior nodes");
     static_assert(std::is_same<T, float>::value, "the 16-node kernel is FP32 (packed pairs)");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *R = reinterpret_cast<T *>(smem_raw);                   // [2][NE][MAXT]
     T *L = R + 2 * PS;                                        // [2][NE][MAXT]
-    T *tail = L + 2 * PS;                                     // [2][NE][kRingMaxInst]
-    T *scoef = tail + 2 * TS;
+    T *tail = L + 2 * PS;                                     // [2][NE][MAXT]
+    T *scoef = tail + 2 * PS;
 
     const int nt = blockDim.x;  // <= MAXT
     const int first = cta_first[blockIdx.x], last = cta_first[blockIdx.x + 1];
@@ -231,7 +230,9 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
     T *const Lme = L + tid;
     const T *const Lrt = L + ((t + 1 >= I.nthr) ? tid : tid + 1);
     const T *const Lhd = L + I.tbase;
-    T *const Tme = tail + I.il;
+    T *const Thd = tail + I.tbase;  // the instance's tail column
+    // right-moving pulls: the previous thread's slots, or the tail for the instance's first thread
+    const T *const Rsrc = t > 0 ? Rme - 1 : tail + tid;
     const int rem = N - xb;  // positions k >= rem lie past node N-1 (near-end threads only)
 
     // one step with the parity of its exchange buffers known at compile time
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
 #pragma unroll
                             for (int i = 0; i < e; ++i)
                                 if (R - e + i >= 0 && R - e + i < K)
-                                    Tme[P * TS + (eslot(e) + i) * kRingMaxInst] = v[j][R - e + i];
+                                    Thd[P * PS + (eslot(e) + i) * MAXT] = v[j][R - e + i];
                         }
                     }
                 };
@@ -373,8 +374,7 @@ __global__ void __launch_bounds__(MAXT, ring_minb(MAXT))
                 if (e > 0) {
 #pragma unroll
                     for (int k = 0; k < e; ++k) {
-                        const T nv = t > 0 ? Rme[P * PS + (eslot(e) + k) * MAXT - 1]
-                                           : Tme[P * TS + (eslot(e) + k) * kRingMaxInst];
+                        const T nv = Rsrc[P * PS + (eslot(e) + k) * MAXT];
                         d[k] += nv - v[j][k];
                         v[j][k] = nv;
                     }

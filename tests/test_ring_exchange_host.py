@@ -11,7 +11,7 @@ every node, D1Q5, many instance sizes, including N = 4 (the minimum, 2 max|e|), 
 every remainder mod 16.  Every shared-memory index is checked to stay inside its buffer.
 
 The buffers are laid out as in the kernel: rows of stride MAXT (the CTA size class, 512 here)
-for the R and L slots and kRingMaxInst = 32 for the tails.
+for the R and L slots and for the tails, an instance's tail in the column of its first thread.
 
 A second check replays the step protocol under random warp interleavings: publish into the
 buffers of the step's parity, one CTA barrier, then the reads.  Every read must see the value
@@ -35,7 +35,7 @@ def eslot(a):
 
 NE = W * (W + 1) // 2
 MAXT = 512
-MAXI = 32  # kRingMaxInst
+MAXI = 32  # kRingMaxInst (instances a CTA)
 
 
 def plan(sizes):
@@ -66,7 +66,7 @@ def emulate_pull(sizes, rng):
                     v[tb + t, :, k] = 1e300  # padding: must never reach a real node
     R = np.full(NE * MAXT, np.nan)  # one parity: slot row q at q * MAXT
     L = np.full(NE * MAXT, np.nan)
-    T = np.full(NE * MAXI, np.nan)
+    T = np.full(NE * MAXT, np.nan)
 
     def info(tid):
         i = owner[tid]
@@ -101,8 +101,8 @@ def emulate_pull(sizes, rng):
                         k = R_ - e + q
                         if 0 <= k < K:
                             assert t * K + k == N - e + q
-                            assert 0 <= eslot(e) + q < NE and 0 <= il < MAXI
-                            T[(eslot(e) + q) * MAXI + il] = v[tid, j, k]
+                            assert 0 <= eslot(e) + q < NE and 0 <= tb < MAXT
+                            T[(eslot(e) + q) * MAXT + tb] = v[tid, j, k]
     new = np.full((nt, B, K), np.nan)
     for tid in range(nt):
         if owner[tid] < 0:
@@ -130,7 +130,8 @@ def emulate_pull(sizes, rng):
                         assert 0 <= tid - 1 < nt
                         nv = R[(eslot(e) + k) * MAXT + tid - 1]
                     else:
-                        nv = T[(eslot(e) + k) * MAXI + il]
+                        assert tid == tb
+                        nv = T[(eslot(e) + k) * MAXT + tid]
                 else:
                     a = -e
                     if k + a < K:
