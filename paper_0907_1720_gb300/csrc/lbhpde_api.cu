@@ -440,7 +440,7 @@ int pack_ring(int b, size_t esz, int K, int dc, const std::vector<Member> &m, Pa
     out.nthreads = (out.nthreads + 31) & ~31;
     out.max_inst = (out.max_inst + 3) & ~3;  // keeps the shared-memory coefficient rows 16-byte aligned
     const int ne = lbk::nedge(b);
-    if (K == kRingK) {  // exchange rows at the class's CTA size, tails for kRingMaxInst instances
+    if (K == kRingK) {  // exchange rows and tails at the class's CTA size
         out.stride = maxt;
         out.smem = (size_t(lbk::ring_xchg_elems(b, maxt)) + coef_max) * esz;
     } else {

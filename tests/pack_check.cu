@@ -63,7 +63,7 @@ static void check_ring(const lbh::Packed &p, const std::vector<lbh::Member> &m, 
         CHECK(tb <= threads && tb <= p.nthreads, "cta %d uses %d threads of %d (plan %d)", c, tb, threads, p.nthreads);
     }
     CHECK(p.nthreads <= threads && p.nthreads % 32 == 0, "plan threads %d, CTA size %d", p.nthreads, threads);
-    if (K == lbh::kRingK) {  // exchange rows at the class stride, tails for kRingMaxInst instances
+    if (K == lbh::kRingK) {  // exchange rows and tails at the class stride
         const size_t xchg = size_t(4) * lbk::ring_xchg_elems(b, threads);
         CHECK(p.stride == threads && p.max_inst <= lbk::kRingMaxInst && p.smem > xchg && p.smem <= 227 * 1024,
               "k_ring plan: stride %d (class %d), %d instances, shared memory %zu (exchange %zu)", p.stride, threads,
